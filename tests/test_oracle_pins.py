@@ -1,0 +1,340 @@
+"""Pins of the FP64 oracle against facts fixed by the mathematics and the
+paper, independent of the oracle's own formulas (CPU only)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import erfc
+from scipy.stats import beta as beta_dist
+
+import rxsim
+from oracle import rx_oracle as O
+
+
+def Q(x):
+    return 0.5 * erfc(x / math.sqrt(2.0))
+
+
+def clopper_pearson(k, n, alpha=0.01):
+    lo = beta_dist.ppf(alpha / 2, k, n - k + 1) if k > 0 else 0.0
+    hi = beta_dist.ppf(1 - alpha / 2, k + 1, n - k) if k < n else 1.0
+    return lo, hi
+
+
+def quiet_link(**kw):
+    base = dict(n_sym=1 << 14, snr_db=None, fo_hz=0.0, linewidth_hz=0.0, rotate=False,
+                delay_frac=0.0, phase0=0.0, seed=11, prbs_seed=3)
+    base.update(kw)
+    return rxsim.LinkConfig(**base)
+
+
+# ---------------------------------------------------------------- a1 CD ---
+
+@pytest.mark.parametrize("L", [1000e3, 10000e3])
+def test_cd_round_trip_1e12(L):
+    """Fibre CD (simulator) then receiver CD compensation (oracle, full
+    length, matched filter off) returns the dispersion-free signal."""
+    ref = rxsim.simulate(quiet_link(fiber_len_m=0.0))["rx"]
+    rx = rxsim.simulate(quiet_link(fiber_len_m=L))["rx"]
+    cfg = O.RxConfig(fiber_len_m=L, rrc_rolloff=-1.0)
+    back = O.full_length_cd(rx, cfg)
+    err = np.linalg.norm(back - ref) / np.linalg.norm(ref)
+    assert err < 1e-12
+
+
+def test_matched_filter_gives_isi_free_symbols():
+    """Tx RRC (simulator) * Rx RRC (oracle) is a raised cosine: Nyquist, so
+    the even samples are the transmitted symbols (noiseless, CD compensated)."""
+    sim = rxsim.simulate(quiet_link(fiber_len_m=2000e3))
+    cfg = O.RxConfig(fiber_len_m=2000e3)
+    z = O.full_length_cd(sim["rx"], cfg)[:, ::2]
+    tx = sim["tx_syms"]
+    a = np.vdot(tx[0], z[0]) / np.vdot(tx[0], tx[0])
+    assert abs(abs(a) - 1.0) < 1e-9
+    assert np.linalg.norm(z - a * tx) / np.linalg.norm(a * tx) < 1e-10
+
+
+def test_ols_exact_for_filters_inside_the_halo():
+    """Overlap-save with a filter whose impulse response lies inside [-h, h]
+    equals direct linear convolution (numpy.convolve) everywhere, including
+    the zero-padded stream edges and a ragged last block."""
+    rng = np.random.default_rng(5)
+    N, halo = 256, 40
+    h = halo // 2
+    taps = rng.standard_normal(halo + 1) + 1j * rng.standard_normal(halo + 1)  # lags -h..h
+    circ = np.zeros(N, complex)
+    for i, lag in enumerate(range(-h, h + 1)):
+        circ[lag % N] = taps[i]
+    H = np.fft.fft(circ)
+    x = rng.standard_normal(3001) + 1j * rng.standard_normal(3001)
+    out = O.ols_cd(x, 0, x.size, H, h, N, N - halo, x.size)
+    ref = np.convolve(x, taps)[h:h + x.size]
+    assert np.max(np.abs(out - ref)) < 1e-12
+    # an output range starting before the stream (negative index) and a
+    # block grid offset by an odd number of samples
+    out2 = O.ols_cd(x, -7, 1995, H, h, N, N - halo, x.size)
+    xp = np.concatenate([np.zeros(7 + h, complex), x])
+    ref2 = np.convolve(xp, taps)[2 * h:2 * h + 2002]
+    assert np.max(np.abs(out2 - ref2)) < 1e-12
+
+
+def test_paper_ols_geometry_golden():
+    """Sec. II: a 2^22-sample buffer, 1024-point FFTs, 100 % overlap (512 new
+    per block) gives 8192 blocks."""
+    vals = {}
+    with open(__file__.replace("test_oracle_pins.py", "golden/paper_ols_geometry.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = int(v)
+    g = O.geometry(O.RxConfig(fft_n=vals["fft_n"], cd_halo=vals["overlap_per_block"]))
+    assert g.L == vals["new_per_block"]
+    assert -(-vals["buffer_samples"] // g.L) == vals["blocks"]
+
+
+@pytest.mark.parametrize("L", [1000e3, 10000e3])
+def test_ols_cd_matches_full_length_in_the_interior(L):
+    """With the halo rule (1.1 x CD memory), the OLS output differs from the
+    full-length filter only by the truncated response tails (< 1e-3 rms)."""
+    sim = rxsim.simulate(quiet_link(fiber_len_m=L, n_sym=1 << 15))
+    cfg = O.RxConfig(fiber_len_m=L)
+    g = O.geometry(cfg)
+    x = sim["rx"][0]
+    full = O.full_length_cd(x, cfg)
+    ols = O.ols_cd(x, 0, x.size, O.cd_frequency_response(cfg, g.N), g.h, g.N, g.L, x.size)
+    a, b = 4 * g.halo, x.size - 4 * g.halo
+    assert np.linalg.norm(ols[a:b] - full[a:b]) / np.linalg.norm(full[a:b]) < 1e-3
+
+
+# --------------------------------------------------- a3 timing, a2 FOE ---
+
+@pytest.mark.parametrize("delay", [0.1, 0.3, 0.45, 0.62, 0.9])
+def test_godard_recovers_injected_delay(delay):
+    sim = rxsim.simulate(quiet_link(fiber_len_m=500e3, delay_frac=delay))
+    cfg = O.RxConfig(fiber_len_m=500e3)
+    Y = np.fft.fft(O.full_length_cd(sim["rx"], cfg), axis=-1)
+    tau = O.timing_residual(O.godard_sum(Y[0]) + O.godard_sum(Y[1]), cfg.baud_hz)
+    est = tau * cfg.baud_hz
+    err = (est - delay + 0.5) % 1.0 - 0.5  # modulo one symbol
+    assert abs(err) < 0.01
+
+
+def test_godard_block_sign_for_odd_window_start():
+    """Shifting the FFT window by one sample leaves the estimate unchanged
+    once the (-1)^n0 factor is applied."""
+    sim = rxsim.simulate(quiet_link(fiber_len_m=0.0, delay_frac=0.27))
+    x = sim["rx"][0]
+    N = 4096
+    ests = []
+    for n0 in (1000, 1001):
+        Y = np.fft.fft(x[n0:n0 + N])
+        ests.append(O.timing_residual(O.godard_sum(Y, n0), 28e9) * 28e9)
+    assert abs(ests[0] - ests[1]) < 0.02 and abs(ests[0] - 0.27) < 0.03
+
+
+@pytest.mark.parametrize("fo", [100e6, -250e6, 1.234e9])
+def test_foe_recovers_injected_offset(fo):
+    L = 1000e3
+    sim = rxsim.simulate(quiet_link(fiber_len_m=L, fo_hz=fo, rotate=True, n_sym=1 << 15))
+    cfg = O.RxConfig(fiber_len_m=L, frame_syms=1 << 15)
+    rx = O.Receiver(cfg)
+    n = sim["rx"].shape[1]
+    _, acc = rx._cd_frame(sim["rx"], n, 0, n, 0.0, 0, n, True)
+    est = O.foe_from_periodogram(acc["S"], cfg.baud_hz)
+    bin_hz = cfg.baud_hz / (rx.g.N // 2) / 4.0
+    # Gaussian interpolation of a barely zero-padded Dirichlet peak with
+    # data self-noise: within a fifth of a bin (1.4 MHz at N = 2048)
+    assert abs(est - fo) < bin_hz / 5
+
+
+# ------------------------------------------------------- a4/a5 MIMO ---
+
+def test_mimo_fir_single_tap_is_a_shift():
+    rng = np.random.default_rng(2)
+    T = 7
+    r = rng.standard_normal((2, 300)) + 1j * rng.standard_normal((2, 300))
+    for t0 in range(T):
+        w = np.zeros((2, 2, T), complex)
+        w[0, 1, t0] = 2.0 - 1j
+        w[1, 0, t0] = 0.5j
+        y, _ = O.mimo_fir(w, r, 3, 100)
+        k = np.arange(3, 100)
+        assert np.allclose(y[0], (2.0 - 1j) * r[1, 2 * k + t0], atol=1e-14)
+        assert np.allclose(y[1], 0.5j * r[0, 2 * k + t0], atol=1e-14)
+
+
+def test_mimo_fir_inverse_of_known_unitary():
+    rng = np.random.default_rng(4)
+    U = rxsim.channel.haar_unitary(rng)
+    s = rng.standard_normal((2, 400)) + 1j * rng.standard_normal((2, 400))
+    r = U @ s
+    T = 15
+    w = np.zeros((2, 2, T), complex)
+    w[:, :, 7] = U.conj().T
+    y, _ = O.mimo_fir(w, r, 0, 190)
+    assert np.max(np.abs(y - s[:, 7:2 * 190 + 7:2])) < 1e-13
+
+
+def test_cma_converges_to_inverse_rotation():
+    """Noiseless, no CD, no offsets: after acquisition the FIR's DC response
+    times U is diagonal or anti-diagonal (cross terms below -30 dB)."""
+    for seed in (11, 12, 13):
+        sim = rxsim.simulate(quiet_link(fiber_len_m=0.0, rotate=True, seed=seed, n_sym=1 << 14))
+        cfg = O.RxConfig(fiber_len_m=0.0, frame_syms=1 << 14)
+        res = O.Receiver(cfg).run(sim["rx"])
+        M = res["w_acq"].sum(axis=2) @ sim["U"]
+        p = np.abs(M) ** 2
+        ratio = min((p[0, 1] + p[1, 0]) / (p[0, 0] + p[1, 1]), (p[0, 0] + p[1, 1]) / (p[0, 1] + p[1, 0]))
+        assert 10 * math.log10(ratio) < -30
+
+
+# ------------------------------------------------------- a6 BPS, a7 ---
+
+@pytest.mark.parametrize("bps_", [2, 4])
+def test_bps_recovers_constant_phase_mod_half_pi(bps_):
+    rng = np.random.default_rng(9)
+    B, W = 64, 16
+    bits = rng.integers(0, 2, 4000 * bps_).astype(np.uint8)
+    s = rxsim.gray_map(bits, bps_)
+    noise = 0.02 * (rng.standard_normal(s.size) + 1j * rng.standard_normal(s.size))
+    for theta in (0.3, -1.2, 2.9, 0.7853):
+        y = (s + noise) * np.exp(1j * theta)
+        bh = O.bps(y, B, W, bps_)
+        m = O.unwrap_increments(bh, B)
+        ph = O.bps_angles(B)[bh] + m * math.pi / 2
+        err = (ph - theta + math.pi / 4) % (math.pi / 2) - math.pi / 4
+        # nearest or next grid angle (noise can tip a near-tie), never further
+        assert np.max(np.abs(err)) <= math.pi / 2 / B + 1e-3
+        assert np.median(np.abs(err)) <= math.pi / 2 / B / 2 + 1e-3
+        # no slips: the unwrapped phase stays on one branch theta + k pi/2
+        branch = np.round((ph - theta) / (math.pi / 2))
+        assert np.all(branch == branch[0])
+
+
+def test_unwrap_follows_a_ramp_across_quadrants():
+    rng = np.random.default_rng(10)
+    n, B = 20000, 64
+    bits = rng.integers(0, 2, 2 * n).astype(np.uint8)
+    s = rxsim.gray_map(bits, 2)
+    theta = np.linspace(0.0, 3.0 * math.pi, n)
+    y = s * np.exp(1j * theta)
+    bh = O.bps(y, B, 16, 2)
+    ph = O.bps_angles(B)[bh] + O.unwrap_increments(bh, B) * math.pi / 2
+    off = ph - theta
+    k0 = np.round(off[100] / (math.pi / 2))
+    assert np.max(np.abs(off[100:-100] - k0 * math.pi / 2)) < math.pi / 2 / B
+
+
+@pytest.mark.parametrize("bps_", [2, 4])
+def test_demap_exhaustive_and_gray(bps_):
+    n = 1 << bps_
+    bits = np.array([[(v >> (bps_ - 1 - i)) & 1 for i in range(bps_)] for v in range(n)],
+                    dtype=np.uint8).ravel()
+    pts = O.const_map(bits, bps_)
+    # the oracle's constellation is the simulator's independent mapper
+    assert np.allclose(pts, rxsim.gray_map(bits, bps_), atol=1e-15)
+    assert np.array_equal(O.demap(pts, bps_).ravel(), bits)
+    assert abs(np.mean(np.abs(pts) ** 2) - 1.0) < 1e-12
+    dmin = np.min([abs(a - b) for i, a in enumerate(pts) for b in pts[i + 1:]])
+    lab = bits.reshape(n, bps_)
+    for i in range(n):
+        for j in range(n):
+            if i != j and abs(abs(pts[i] - pts[j]) - dmin) < 1e-9:
+                assert np.sum(lab[i] != lab[j]) == 1
+
+
+def test_decision_ties_take_larger_level():
+    assert O.decide(np.array([0.0 + 0.0j]), 2)[0] == (1 + 1j) / math.sqrt(2)
+    assert O.decide(np.array([2 / math.sqrt(10) + 0j]), 4)[0].real == pytest.approx(3 / math.sqrt(10))
+
+
+# ---------------------------------------------------------------- a8 ---
+
+def _polymod_pow_x(e, poly, deg):
+    """x^e mod poly over GF(2) (ints as bit vectors)."""
+    result, base = 1, 2
+
+    def mulmod(a, b):
+        r = 0
+        while b:
+            if b & 1:
+                r ^= a
+            b >>= 1
+            a <<= 1
+            if a >> deg & 1:
+                a ^= poly
+        return r
+
+    while e:
+        if e & 1:
+            result = mulmod(result, base)
+        base = mulmod(base, base)
+        e >>= 1
+    return result
+
+
+def test_prbs_recurrence_is_maximal_length():
+    """b[n] = b[n-28] ^ b[n-31] has characteristic polynomial x^31 + x^3 + 1;
+    2^31 - 1 is prime, so x^(2^31-1) = 1 mod p proves the period is maximal."""
+    poly = (1 << 31) | (1 << 3) | 1
+    assert _polymod_pow_x((1 << 31) - 1, poly, 31) == 1
+    assert _polymod_pow_x(1, poly, 31) != 1
+
+
+def test_prbs_independent_generators_agree():
+    for seed in (1, 7, 123456789, (1 << 40) + 3):
+        for p in (0, 1):
+            st = O.prbs_state(seed, p)
+            assert st == rxsim.pol_seed_state(seed, p)
+            a = O.prbs31_bits(st, 5000)
+            b = rxsim.prbs31(st, 5000)
+            assert np.array_equal(a, b)
+    big = O.prbs31_bits(O.prbs_state(7, 0), 1 << 20)
+    assert abs(big.mean() - 0.5) < 0.003
+    n = np.arange(31, big.size)
+    assert np.array_equal(big[n], big[n - 28] ^ big[n - 31])
+
+
+@pytest.mark.parametrize("bps_,snr_db", [(2, 7.0), (4, 14.0)])
+def test_awgn_ber_matches_closed_form(bps_, snr_db):
+    """Ideal symbols + AWGN at Es/N0 = SNR, oracle decisions: measured BER
+    inside the 99 % Clopper-Pearson interval of the Gray-code closed form."""
+    rng = np.random.default_rng(17)
+    n = 1 << 17
+    bits = rng.integers(0, 2, n * bps_).astype(np.uint8)
+    s = rxsim.gray_map(bits, bps_)
+    snr = 10 ** (snr_db / 10)
+    y = s + math.sqrt(1 / (2 * snr)) * (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+    errs = int(np.sum(O.demap(y, bps_).ravel() != bits))
+    if bps_ == 2:
+        pb = Q(math.sqrt(snr))
+    else:
+        d = math.sqrt(snr / 5)
+        pb = (3 * Q(d) + 2 * Q(3 * d) - Q(5 * d)) / 4
+    assert pb * bits.size > 100
+    lo, hi = clopper_pearson(errs, bits.size)
+    assert lo <= pb <= hi
+
+
+# ----------------------------------------------------------- chain ---
+
+def test_chain_noiseless_all_impairments_is_error_free():
+    sim = rxsim.simulate(rxsim.LinkConfig(n_sym=1 << 15, snr_db=None, fiber_len_m=1000e3,
+                                          prbs_seed=5, seed=21))
+    cfg = O.RxConfig(fiber_len_m=1000e3, prbs_seed=5, frame_syms=1 << 14)
+    b = O.Receiver(cfg).run(sim["rx"])["ber"]
+    assert b["errors"] == 0 and b["slips"] == 0 and b["bits"] > 100000
+
+
+@pytest.mark.slow
+def test_chain_ber_within_half_db_of_theory():
+    """All impairments of the 1,000 km QPSK workload at 10 dB: the BER is
+    at most the closed form at 0.5 dB lower SNR (upper 99 % CP bound)."""
+    snr_db = 10.0
+    sim = rxsim.simulate(rxsim.LinkConfig(n_sym=1 << 17, snr_db=snr_db, fiber_len_m=1000e3,
+                                          prbs_seed=7, seed=1001))
+    cfg = O.RxConfig(fiber_len_m=1000e3, prbs_seed=7)
+    b = O.Receiver(cfg).run(sim["rx"])["ber"]
+    lo, _ = clopper_pearson(b["errors"], b["bits"])
+    assert lo <= Q(math.sqrt(10 ** ((snr_db - 0.5) / 10)))
+    assert b["slips"] == 0
