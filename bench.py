@@ -1,0 +1,331 @@
+"""Throughput benchmark of the receiver hot path on one GB300.
+
+Workload (one step): a continuous DP-QPSK 28 GBd stream of 2^24 symbols per
+polarisation (2^25 complex64 samples per polarisation, 10,000 km of
+D = 17 ps/(nm km), SNR 10 dB, 100 MHz frequency offset, 100 kHz Wiener
+phase noise, random polarisation rotation), pushed in 2^16-symbol blocks
+with all receiver state carried across blocks, through the whole chain
+(CD/OLS, timing, FO, MIMO + adaptation, BPS, decisions, demap, BER).
+Every step starts a fresh stream on the same handle (rx_reset), so the
+acquisition of the first frame is inside every step.  Inputs are resident
+in HBM and larger than L2 (512 MiB).
+
+Prints one JSON line.  --impl reference times the FP64 oracle on the host
+cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r for r in self.rows if len(r) >= 7]
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload():
+    from paper_2108_07001_gb300 import workloads
+    return workloads.DP_QPSK_10000KM_STREAM
+
+
+def stage_work(wl, n_sym):
+    """Algorithmic work per step of each stage (flops or bytes).  One step
+    processes n_sym symbols per polarisation = 4 n_sym complex samples."""
+    rx = wl["rx"]
+    B, T = rx["bps_angles"], rx["mimo_taps"]
+    samples = 4 * n_sym
+    return {
+        # CD: each complex64 sample read once from the ring, written once
+        "cd": ("hbm", samples * 16.0),
+        # FIR (2 outputs x 2 inputs x T complex MACs) + gradient (same), 8 flops per CMAC
+        "mimo": ("alu", n_sym * 2 * (4 * T) * 8.0),
+        # per symbol, polarisation and angle: rotation 6, |Re|+|Im| 1, window add/sub 2
+        "bps": ("alu", n_sym * 2 * B * 9.0),
+    }
+
+
+def run_ours(args):
+    import torch
+    from paper_2108_07001_gb300 import rx
+
+    wl = workload()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    import rxsim
+    t0 = time.time()
+    sim = rxsim.simulate(rxsim.LinkConfig(**wl["link"]))
+    x = sim["rx"]  # [2, 2^25] complex64
+    del sim
+    gen_s = time.time() - t0
+    n_samp = x.shape[1]
+    n_sym = n_samp // 2
+    m = 2 * wl["push_syms"]
+    nb = n_samp // m
+    blocks = np.ascontiguousarray(x.reshape(2, nb, m).transpose(1, 0, 2))  # [nb][2][m]
+    del x
+    dx = torch.from_numpy(blocks).to(dev)  # resident in HBM
+    stream = torch.cuda.current_stream().cuda_stream
+    cfg = rx.default_config(**wl["rx"], profile=1)
+    r = rx.Receiver(cfg)
+    lib = r.lib
+    base = dx.data_ptr()
+    bbytes = 2 * m * 8
+    out_bytes = n_sym * 2 * cfg.modulation // 8
+    outbuf = np.empty(out_bytes + 16, dtype=np.uint8)
+
+    def step():
+        r.reset()
+        for b in range(nb):
+            rc = lib.rx_push_block(r.h, ctypes.c_void_p(base + b * bbytes), m, rx.RX_C64, 1, ctypes.c_void_p(stream))
+            if rc:
+                raise rx.RxError(rc, lib.rx_last_error().decode())
+        r.end()
+        r.join(stream)
+
+    for _ in range(args.warmup):
+        step()
+        r.pull_bytes(outbuf)
+    torch.cuda.synchronize()
+    before = r.stage_times()
+    clk = ClockSampler()
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    host0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    host1 = time.perf_counter()
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    after = r.stage_times()
+    stage_tot = {k: [after[k][0] - before[k][0], after[k][1] - before[k][1]] for k in rx.STAGES}
+    stats = r.stats()
+    total_ms = ev0.elapsed_time(ev1)
+    ms_step = total_ms / args.steps
+    samples_step = 2 * n_samp
+    bits_step = n_sym * 2 * cfg.modulation
+    value = samples_step / (ms_step * 1e-3) / 1e9
+    gbps = bits_step / (ms_step * 1e-3) / 1e9
+
+    # roofline of the dominant stage (live stage timings of the timed steps)
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    work = stage_work(wl, n_sym)
+    stages = {}
+    for k in ("cd", "mimo", "bps"):
+        ms, n = stage_tot[k]
+        bound, w = work[k]
+        sec = ms * 1e-3 / args.steps
+        if bound == "hbm":
+            ach = w / sec / 1e9
+            peak = hbm_peak or 6800.0
+            unit = "GB/s"
+        else:
+            ach = w / sec / 1e12
+            peak = FP32_PEAK_TFLOPS
+            unit = "TFLOP/s"
+        stages[k] = {"bound": bound, "achieved": round(ach, 2), "peak": round(peak, 1), "unit": unit,
+                     "frac": round(ach / peak, 4), "ms_per_step": round(ms / args.steps, 3),
+                     "launches_per_step": n / args.steps}
+    other_ms = {k: round(v[0] / args.steps, 3) for k, v in stage_tot.items() if k not in stages}
+    dom = max(stages, key=lambda k: stages[k]["ms_per_step"])
+    roof = dict(stages[dom])
+    roof["kernel"] = dom
+    roof["traffic"] = None
+    roof.pop("launches_per_step", None)
+    roof["peak_source"] = ("measured MEASURED_PEAKS.json hbm_gbs" if roof["bound"] == "hbm" and hbm_peak
+                           else "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz")
+    gpu_launches = int(sum(v[1] for v in stage_tot.values()))
+
+    # e2e: the same stream from pinned host memory, bits read back to the host
+    hx = torch.from_numpy(blocks).pin_memory()
+    hbase = hx.data_ptr()
+
+    def step_host():
+        r.reset()
+        for b in range(nb):
+            rc = lib.rx_push_block(r.h, ctypes.c_void_p(hbase + b * bbytes), m, rx.RX_C64, 0, ctypes.c_void_p(stream))
+            if rc:
+                raise rx.RxError(rc, lib.rx_last_error().decode())
+        r.end()
+        r.pull_bytes(outbuf, timeout_ms=-1)
+        r.stats()
+
+    step_host()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    ke = max(1, min(args.steps, 3))
+    for _ in range(ke):
+        step_host()
+    torch.cuda.synchronize()
+    e_s = (time.perf_counter() - e0) / ke
+    e2e = {"value": round(samples_step / e_s / 1e9, 3), "unit": "Gsamples/s",
+           "h2d_bytes_per_step": int(blocks.nbytes), "d2h_bytes_per_step": int(out_bytes),
+           "ms_per_step": round(e_s * 1e3, 2)}
+
+    cpu = cpu_baseline(wl) if args.cpu_baseline else None
+    line = {
+        "metric": "gsamples_per_s", "value": round(value, 3), "unit": "Gsamples/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded link simulator)",
+        "config": {"workload": wl["name"], "symbols_per_pol": n_sym, "push_syms": wl["push_syms"],
+                   "frame_syms": cfg.frame_syms, "fft_n_auto": True, "mimo_taps": cfg.mimo_taps,
+                   "bps_angles": cfg.bps_angles, "storage": "c64", "input": "resident in HBM, 512 MiB > L2",
+                   "l2": "inputs larger than L2"},
+        "decoded_gbps": round(gbps, 3),
+        "ber": stats["ber"], "bits": stats["bits"], "bit_errors": stats["bit_errors"],
+        "cycle_slips": stats["cycle_slips"], "latency_p50_ms": round(stats["latency_p50_ms"], 3),
+        "latency_p99_ms": round(stats["latency_p99_ms"], 3),
+        "roofline": roof, "stages": stages, "other_stage_ms": other_ms,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
+        "host_launch_s_per_step": round((host1 - host0) / args.steps, 4), "sim_seconds": round(gen_s, 1),
+    }
+    r.close()
+    return line
+
+
+def oracle_sample(wl, n_sym):
+    """Run the oracle on the first n_sym symbols of the workload's link."""
+    import rxsim
+    from oracle import rx_oracle as O
+    from paper_2108_07001_gb300.workloads import oracle_kwargs
+    lk = dict(wl["link"])
+    lk["n_sym"] = n_sym
+    sim = rxsim.simulate(rxsim.LinkConfig(**lk))
+    x = sim["rx"].astype(np.complex128)
+    kw = oracle_kwargs(wl["rx"])
+    t0 = time.perf_counter()
+    O.Receiver(O.RxConfig(**kw)).run(x)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(wl, n_sym=1 << 16):
+    t = oracle_sample(wl, n_sym)
+    v = 4 * n_sym / t / 1e9
+    return {"value": round(v, 6), "unit": "Gsamples/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n_sym} symbols/pol of the workload (one partial frame incl. acquisition), "
+                      f"FP64 numpy, {t:.1f} s"}
+
+
+def run_reference(args):
+    wl = workload()
+    n_sym = 1 << 15
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = oracle_sample(wl, n_sym)
+        if i >= args.warmup:
+            times.append(t)
+    t = sum(times) / len(times)
+    v = 4 * n_sym / t / 1e9
+    return {"impl": "reference", "metric": "gsamples_per_s", "value": round(v, 6), "unit": "Gsamples/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded link simulator)",
+            "config": {"workload": wl["name"], "sample_symbols_per_pol": n_sym},
+            "cpu_baseline": {"value": round(v, 6), "unit": "Gsamples/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {n_sym} symbols/pol per step"},
+            "e2e": {"value": round(v, 6), "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        # replicas only: every rank runs its own stream on its own GPU
+        import torch
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        dist.barrier()
+        line = run_ours(args)
+        t = torch.tensor([line["ms_per_step"]], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        if rank == 0:
+            line["n_gpus"] = world
+            line["ms_per_step"] = float(t.item())
+            line["value"] = round(world * 2 * (1 << 25) / (line["ms_per_step"] * 1e-3) / 1e9, 3)
+            line["config"]["parallelism"] = f"replicas x{world}"
+            print(json.dumps(line), flush=True)
+        dist.destroy_process_group()
+        return
+    print(json.dumps(run_ours(args)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * rx.h -- C ABI of the GB300 dual-polarisation coherent receiver.
+ *
+ * One handle = one receiver stream.  The handle owns device memory on one
+ * CUDA device and two CUDA streams of its own; every step of the chain runs
+ * in hand-written CUDA kernels (sm_103a) behind these calls.
+ *
+ * The chain (per stream, both polarisations jointly), with the passage of
+ * arXiv 2108.07001 each step follows where the paper has one:
+ *   ingest    pushed samples are appended to a device ring so that the stream
+ *             stays contiguous across pushes (Sec. II: a kernel handles the
+ *             overlap with the last block of the previous buffer);
+ *   CD        overlap-save FFT -> x H -> IFFT with
+ *             H = exp(+j beta2 L w^2/2) * RRC matched filter * exp(+j w tau)
+ *             (Sec. II: 100 % overlap-save frequency-domain processing and
+ *             frequency-domain static equalisation that compensates CD);
+ *   timing    Godard band-edge spectral correlation, fed back per frame;
+ *   FO        4th-power periodogram peak per frame, phase-continuous removal;
+ *   MIMO      2x2 butterfly FIR, T taps at T/2 spacing, block-LMS adaptation
+ *             (CMA acquisition, then decision-directed LMS: Sec. II uses a
+ *             DD-LMS time-domain equaliser);
+ *   BPS       blind phase search over B test angles, pi/2 unwrap;
+ *   decide    hard decisions and Gray demapping (Sec. II);
+ *   BER       against the known PRBS-31 payload, Q from BER (Sec. III).
+ * The paper describes a single-polarisation Kramers-Kronig receiver; the
+ * polarisation demultiplexing, CMA, FO/timing recovery and blind phase
+ * search follow their textbook definitions.
+ *
+ * Error behaviour: every call returns RX_OK (0) or a negative RX_E* code;
+ * rx_last_error() gives a message for the last failing call of the calling
+ * thread.  No call aborts the process.
+ */
+#ifndef GB300_RX_H
+#define GB300_RX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  RX_OK = 0,
+  RX_EINVAL = -1,     /* bad argument or configuration */
+  RX_ENOMEM = -2,     /* device or host allocation failed */
+  RX_EAGAIN = -3,     /* no room: pull bits first (backpressure, not a failure) */
+  RX_ETIMEDOUT = -4,  /* a wait ran out */
+  RX_EDEVICE = -5,    /* CUDA error; see rx_last_error() */
+  RX_ESTATE = -6      /* call not valid in this state (e.g. push after end of stream) */
+};
+
+enum { RX_QPSK = 2, RX_QAM16 = 4 };          /* bits per symbol per polarisation */
+enum { RX_C128 = 0, RX_C64 = 1, RX_C16 = 2 }; /* complex double / float / half */
+
+/* Receiver configuration.  Fill with rx_config_default() and override.
+ * Sizes are in symbols per polarisation unless stated; sps is fixed at 2. */
+typedef struct rx_config {
+  double baud_hz;          /* symbol rate Rs; sample rate is 2 Rs */
+  int modulation;          /* RX_QPSK or RX_QAM16 */
+  double fiber_len_m;      /* fibre length L */
+  double D_ps_nm_km;       /* dispersion parameter D */
+  double lambda_m;         /* carrier wavelength (1550e-9) */
+  double rrc_rolloff;      /* RRC matched filter roll-off folded into H; < 0: none */
+  int fft_n;               /* OLS FFT size (power of two, 1024..16384); 0: auto */
+  int cd_halo;             /* OLS overlap M-1 in samples (even); 0: 1.1 x CD memory */
+  int mimo_taps;           /* T, odd, 3..31 */
+  int bps_angles;          /* B: 32 or 64 */
+  int bps_half_window;     /* W: window is 2W+1 symbols, 1..32 */
+  int sub_block_syms;      /* K: symbols per tap update (64) */
+  int seg_syms;            /* S: symbols per adaptive segment (multiple of K) */
+  int frame_syms;          /* F: symbols per processing frame (multiple of S) */
+  int cma_syms;            /* CMA portion of the acquisition */
+  int acq_syms;            /* acquisition length (<= frame_syms) */
+  float mu_cma, mu_dd;     /* LMS step sizes */
+  float timing_gain;       /* feedback gain of the per-frame timing update */
+  int storage_dtype;       /* device ring storage: RX_C64 or RX_C16 */
+  uint64_t prbs_seed;      /* payload PRBS seed for BER counting; 0: no BER */
+  int ber_skip_syms;       /* first symbol of the BER sync window */
+  int sync_syms;           /* sync window length */
+  int sync_max_delay;      /* delay search range +- */
+  int slip_window;         /* cycle-slip window (symbols) */
+  size_t max_block_samples;/* largest n_per_pol accepted by one push */
+  int64_t history_syms;    /* keep equalised symbols, BPS angles and unwrap
+                              counters of the first history_syms symbols on
+                              the device for inspection; 0: off */
+  int profile;             /* 1: time every stage with CUDA events */
+  int device;              /* CUDA device ordinal */
+} rx_config;
+
+/* Stages reported by rx_stage_times, in this order. */
+enum { RX_STAGE_INGEST = 0, RX_STAGE_CD, RX_STAGE_EST, RX_STAGE_ACQUIRE, RX_STAGE_MIMO,
+       RX_STAGE_BPS, RX_STAGE_DEMAP, RX_STAGE_BER, RX_NSTAGES };
+
+/* Counters and the latest estimates.  All counts cover symbols processed
+ * by completed frames. */
+typedef struct rx_stats_t {
+  uint64_t samples_in;     /* samples per polarisation pushed */
+  uint64_t symbols_out;    /* symbols per polarisation decided */
+  uint64_t frames;         /* frames completed */
+  uint64_t bits;           /* payload bits compared (both polarisations) */
+  uint64_t bit_errors;
+  double ber;
+  double q_db;             /* 20 log10(sqrt(2) erfcinv(2 BER)); 0 if no BER */
+  double evm;              /* error power / reference power over counted symbols */
+  uint64_t cycle_slips;
+  int synced;              /* BER sync done */
+  int sync_delay, sync_perm, sync_quadrant_x, sync_quadrant_y;
+  int cma_reinit;          /* singularity re-initialisation happened */
+  double fo_hz;            /* last frame's frequency offset estimate */
+  double tau_s;            /* timing correction applied to the last frame */
+  double latency_p50_ms, latency_p99_ms; /* push-to-decided latency of frames */
+  double gpu_ms_total;     /* device time of completed frames */
+} rx_stats_t;
+
+typedef struct rx_handle rx_handle;
+
+/* Defaults: QPSK at 28 GBd over 1,000 km of D = 17 ps/(nm km) at 1550 nm,
+ * RRC 0.1, T = 15, B = 64, W = 16, K = 64, S = 512, F = 65536,
+ * CMA 8192 of 12288 acquisition symbols, mu_cma 3e-2, mu_dd 5e-3, timing
+ * gain 0.5, complex64 storage, no BER, 2^17-sample pushes, no history,
+ * device 0. */
+void rx_config_default(rx_config* cfg);
+
+/* Validates cfg, computes the CD filter in FP64 on the host and allocates
+ * all device state on cfg->device.  *out receives the handle (caller frees
+ * it with rx_destroy).  Returns RX_EINVAL (message says which field),
+ * RX_ENOMEM or RX_EDEVICE. */
+int rx_create(const rx_config* cfg, rx_handle** out);
+
+/* Appends n_per_pol samples of both polarisations.  Layout: planar
+ * [pol][n_per_pol], each sample re/im interleaved, element type dtype
+ * (RX_C128 / RX_C64 / RX_C16).  samples is a device pointer if on_device,
+ * else a host pointer.  The call is asynchronous: the copy into the
+ * library's ring is a kernel launched on cuda_stream (a cudaStream_t, NULL =
+ * legacy default stream), so it follows the work already queued there and
+ * later work on cuda_stream follows it; the caller may reuse a device
+ * buffer in stream order.  A host buffer is copied before the call returns.
+ * When the ring is full, cuda_stream is made to wait for the frames that
+ * still read the overwritten slots.
+ * Complete frames are processed on the library's own stream.
+ * samples == NULL with n_per_pol == 0 marks the end of the stream: the
+ * remaining samples are processed with zeros beyond the end.
+ * Returns RX_EINVAL (size > max_block_samples, bad dtype), RX_ESTATE (after
+ * end of stream), RX_EAGAIN (decided bits not pulled and the output ring
+ * is full) or RX_EDEVICE. */
+int rx_push_block(rx_handle* h, const void* samples, size_t n_per_pol, int dtype,
+                  int on_device, void* cuda_stream);
+
+/* Copies up to cap_bytes*8 decided bits to the host buffer out (caller
+ * owned) and removes them from the library.  Bit order: symbol-major,
+ * polarisation x then y, per symbol the I bits then the Q bits, MSB first;
+ * bit i of the stream is bit (7 - i%8) of out[i/8].  Only whole bytes are
+ * returned; *n_bits receives the count.  Waits up to timeout_ms for queued
+ * frames to finish (0: no wait, < 0: wait for all queued work).  Returns
+ * RX_ETIMEDOUT if the wait ran out (bits decided so far are still
+ * returned), RX_EDEVICE on a CUDA error. */
+int rx_pull_bits(rx_handle* h, uint8_t* out, size_t cap_bytes, size_t* n_bits, int timeout_ms);
+
+/* Waits for all queued work, then fills *out.  RX_EDEVICE on CUDA error. */
+int rx_stats(rx_handle* h, rx_stats_t* out);
+
+/* Waits for queued work and frees everything the handle owns. */
+int rx_destroy(rx_handle* h);
+
+/* Starts a new stream on the handle: the device state is re-initialised
+ * in stream order after all queued work (no host wait), the host counters
+ * restart, allocations and the CD filter are kept.  Bits of the previous
+ * stream that were not pulled are dropped.  Stage timings are kept. */
+int rx_reset(rx_handle* h);
+
+/* Makes later work queued on cuda_stream (a cudaStream_t) wait for all
+ * work the library has queued so far (stream-ordered completion; no host
+ * wait).  Returns RX_EDEVICE on a CUDA error. */
+int rx_join(rx_handle* h, void* cuda_stream);
+
+/* Per-stage kernel launch counts since rx_create and, with
+ * cfg.profile = 1, per-stage device time in ms (event pairs around each
+ * stage on the library's streams); arrays of RX_NSTAGES entries indexed by
+ * RX_STAGE_*.  Waits for queued work. */
+int rx_stage_times(rx_handle* h, double* ms, int64_t* launches);
+
+/* Message of the last failing call in this thread ("" if none). */
+const char* rx_last_error(void);
+
+/* ---- inspection (tests and tools) -------------------------------------
+ * Per-frame estimates of the last completed frames, oldest first:
+ * out[4*i + 0] = tau (s) applied, out[4*i+1] = FO estimate (Hz),
+ * out[4*i+2] = AGC gain, out[4*i+3] = FO phase at the frame start (rad).
+ * Returns the number of frames written (<= cap_frames) or a negative code.
+ * The first 4096 frames of the stream are kept. */
+int rx_frame_trace(rx_handle* h, double* out, int cap_frames);
+
+/* Copies the 2x2xT complex taps [p][q][t] of the acquisition result
+ * (which = -1) or of adaptive chain `which` (0 <= which < F/S) as float
+ * re/im pairs into out (capacity 8*T floats).  Waits for queued work. */
+int rx_get_taps(rx_handle* h, int which, float* out);
+
+/* Copies equalised symbols y (MIMO output before carrier recovery) of
+ * symbols [first, first + n) from the inspection history into host out as
+ * complex float [pol][n] (re/im interleaved).  Waits for queued work.
+ * RX_EINVAL if the range is outside [0, history_syms). */
+int rx_get_equalised(rx_handle* h, int64_t first, int64_t n, float* out);
+
+/* Copies the BPS angle index b (uint8, [pol][n]) and the unwrap counter m
+ * (int32, [pol][n]) of symbols [first, first + n) from the inspection
+ * history.  Waits for queued work.  RX_EINVAL outside the history. */
+int rx_get_phase(rx_handle* h, int64_t first, int64_t n, uint8_t* bhat, int32_t* m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_RX_H */

@@ -1,0 +1,270 @@
+// a8 BER counting against the known payload (paper Sec. III: the Q-factor
+// is estimated from the BER) and the ingest conversion kernel.
+//
+// Reference bits: PRBS-31, b[i] = (state >> i) & 1 for i < 31, then
+// b[n] = b[n-28] ^ b[n-31].  The 31-bit window s_p = b[p..p+30] advances
+// as s_{p+1} = A s_p over GF(2); A^(2^i) (columns, host-computed) give
+// s_P for any P in O(log P) matrix-vector products, after which the
+// sequence is produced 28 bits per step: b[p..p+27] = s & (2^28 - 1),
+// s <- (s >> 28) | (((s ^ (s >> 3)) & (2^28 - 1)) << 3).
+//
+// Sync (once): every delay d in [-Dmax, Dmax] and polarisation order is
+// tried on the sync window, each polarisation keeping its best quadrant;
+// the smallest total wins (first in (d, order) order on ties).  Counting:
+// per slip window, errors under all four quadrants are accumulated; a
+// sequential pass then keeps the current quadrant unless its errors exceed
+// a quarter of the window's bits, in which case the window's best quadrant
+// is taken and a slip is counted.
+#include "rx_internal.cuh"
+
+namespace rx {
+
+__device__ __forceinline__ uint32_t gf2_apply(const uint32_t* __restrict__ M, uint32_t s) {
+  uint32_t r = 0;
+#pragma unroll
+  for (int j = 0; j < 31; ++j) r ^= M[j] & (0u - ((s >> j) & 1u));
+  return r;
+}
+
+__device__ uint32_t prbs_window_at(const RxDev& d, int pol, long long P) {
+  uint32_t s = d.prbs_state0[pol];
+  for (int i = 0; P > 0; ++i, P >>= 1)
+    if (P & 1) s = gf2_apply(d.prbs_jump + i * 31, s);
+  return s;
+}
+
+// Bits [B0, B0 + nbits) of each polarisation's PRBS into d.ref (LSB first).
+// B0 = (sym0 - delay) * bps, delay read from the device state if use_delay.
+__global__ void ref_gen_kernel(RxDev d, long long sym0, int nbits, int use_delay) {
+  const int pol = blockIdx.y;
+  const int chunk = blockIdx.x * blockDim.x + threadIdx.x;
+  const int start = chunk * 1024;
+  if (start >= nbits) return;
+  const long long delay = use_delay ? d.st->sync_delay : 0;
+  const long long B0 = (sym0 - delay) * d.bps;
+  uint32_t s = prbs_window_at(d, pol, B0 + start);
+  uint32_t* out = d.ref + (long long)pol * d.ref_words + start / 32;
+  const int nw = min(32, (nbits - start + 31) / 32);
+  unsigned long long acc = 0;
+  int nacc = 0, wc = 0;
+  while (wc < nw) {
+    acc |= (unsigned long long)(s & 0x0FFFFFFFu) << nacc;
+    nacc += 28;
+    const uint32_t nx = (s ^ (s >> 3)) & 0x0FFFFFFFu;
+    s = (s >> 28) | (nx << 3);
+    while (nacc >= 32 && wc < nw) {
+      out[wc++] = (uint32_t)acc;
+      acc >>= 32;
+      nacc -= 32;
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t ref_bits(const uint32_t* ref, long long off, int n) {
+  const long long w = off >> 5;
+  const int sh = (int)(off & 31);
+  const unsigned long long v = ((unsigned long long)ref[w + 1] << 32) | ref[w];
+  return (uint32_t)(v >> sh) & ((1u << n) - 1u);
+}
+
+// Received bits of levels (lI, lQ) rotated by q quarter turns (x j each),
+// in payload order: I bits MSB first then Q bits, bit j of the result is
+// the j-th bit of the symbol.
+__device__ __forceinline__ uint32_t rx_sym_bits(int lI, int lQ, int q, int nl) {
+  for (int i = 0; i < q; ++i) {
+    const int t = lI;
+    lI = nl - 1 - lQ;
+    lQ = t;
+  }
+  if (nl == 2) return (uint32_t)(1 - lI) | ((uint32_t)(1 - lQ) << 1);
+  const uint32_t gI = (uint32_t)(lI ^ (lI >> 1)), gQ = (uint32_t)(lQ ^ (lQ >> 1));
+  return ((gI >> 1) & 1u) | ((gI & 1u) << 1) | (((gQ >> 1) & 1u) << 2) | ((gQ & 1u) << 3);
+}
+
+// One block per (delay, order) candidate over the sync window; the
+// reference holds tx symbols [k_s - Dmax, k_s + n_sync + Dmax).
+__global__ void __launch_bounds__(256) sync_kernel(RxDev d) {
+  __shared__ unsigned red[8][8];
+  const int cand = blockIdx.x;
+  const int delay = cand / 2 - d.sync_dmax, perm = cand & 1;
+  const long long ks = d.ber_skip;
+  unsigned err[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  for (int i = threadIdx.x; i < d.sync_syms; i += 256) {
+    const long long k = ks + i;
+    const uint8_t v = d.dec[k % d.dec_cap];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int tx = p ^ perm;
+      const long long off = (long long)(i - delay + d.sync_dmax) * d.bps;
+      const uint32_t rb = ref_bits(d.ref + (long long)tx * d.ref_words, off, d.bps);
+      const int lv = (v >> (4 * p)) & 15;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) err[p][q] += __popc(rx_sym_bits(lv & 3, lv >> 2, q, d.nl) ^ rb);
+    }
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      unsigned v = err[p][q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (l == 0) red[w][p * 4 + q] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    unsigned s = 0;
+    for (int ww = 0; ww < 8; ++ww) s += red[ww][threadIdx.x];
+    d.sync_err[cand * 8 + threadIdx.x] = s;
+  }
+}
+
+__global__ void sync_select_kernel(RxDev d) {
+  const int ncand = (2 * d.sync_dmax + 1) * 2;
+  unsigned best = 0xffffffffu;
+  int bc = 0, bq[2] = {0, 0};
+  for (int c = 0; c < ncand; ++c) {
+    unsigned tot = 0;
+    int qs[2];
+    for (int p = 0; p < 2; ++p) {
+      unsigned m = 0xffffffffu;
+      int qb = 0;
+      for (int q = 0; q < 4; ++q) {
+        const unsigned e = d.sync_err[c * 8 + p * 4 + q];
+        if (e < m) { m = e; qb = q; }
+      }
+      tot += m;
+      qs[p] = qb;
+    }
+    if (tot < best) { best = tot; bc = c; bq[0] = qs[0]; bq[1] = qs[1]; }
+  }
+  StreamState* st = d.st;
+  st->sync_delay = bc / 2 - d.sync_dmax;
+  st->sync_perm = bc & 1;
+  st->sync_q[0] = st->q_cur[0] = bq[0];
+  st->sync_q[1] = st->q_cur[1] = bq[1];
+  st->synced = 1;
+}
+
+// Errors of symbols [ka, kb) under the four quadrants, per slip window.
+// Threads are aligned so that every warp lies inside one window; the
+// reference holds tx symbols [ka - delay, kb - delay).
+__global__ void __launch_bounds__(256) ber_count_kernel(RxDev d, long long ka, long long kb, int n_win_ring) {
+  const long long ks = d.ber_skip;
+  const long long kal = ks + ((ka - ks) / 32) * 32;
+  const long long k = kal + (long long)blockIdx.x * 256 + threadIdx.x;
+  const int perm = d.st->sync_perm;
+  unsigned err[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  if (k >= ka && k < kb) {
+    const uint8_t v = d.dec[k % d.dec_cap];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int tx = p ^ perm;
+      const uint32_t rb = ref_bits(d.ref + (long long)tx * d.ref_words, (k - ka) * d.bps, d.bps);
+      const int lv = (v >> (4 * p)) & 15;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) err[p][q] = __popc(rx_sym_bits(lv & 3, lv >> 2, q, d.nl) ^ rb);
+    }
+  }
+  const long long kw = kal + (long long)blockIdx.x * 256 + (threadIdx.x & ~31);
+  const long long win = (kw - ks) / d.slip_win;
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      unsigned s = err[p][q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if ((threadIdx.x & 31) == 0 && s) atomicAdd(&d.win_err[(win % n_win_ring) * 8 + p * 4 + q], s);
+    }
+}
+
+// Sequential slip pass over windows [w_from, w_to); window w covers
+// symbols [ks + w SW, ks + (w+1) SW) clipped to k_lim.  Slots are cleared.
+__global__ void ber_finalize_kernel(RxDev d, long long w_from, long long w_to, long long k_lim, int n_win_ring) {
+  const int p = threadIdx.x;
+  if (p >= 2) return;
+  StreamState* st = d.st;
+  int q = st->q_cur[p];
+  unsigned long long errors = 0, bits = 0, slips = 0;
+  const long long ks = d.ber_skip;
+  for (long long w = w_from; w < w_to; ++w) {
+    const long long a = ks + w * d.slip_win;
+    const long long b = min(a + d.slip_win, k_lim);
+    const long long nb = (b - a) * d.bps;
+    unsigned* e = d.win_err + (w % n_win_ring) * 8 + p * 4;
+    unsigned ev[4] = {e[0], e[1], e[2], e[3]};
+    if ((long long)ev[q] * 4 > nb) {
+      int qb = 0;
+      for (int qq = 1; qq < 4; ++qq)
+        if (ev[qq] < ev[qb]) qb = qq;
+      q = qb;
+      ++slips;
+    }
+    errors += ev[q];
+    bits += nb;
+    e[0] = e[1] = e[2] = e[3] = 0;
+  }
+  st->q_cur[p] = q;
+  atomicAdd(&st->errors, errors);
+  atomicAdd(&st->bits, bits);
+  atomicAdd(&st->slips, slips);
+}
+
+// Push conversion: src planar [2][n] of dtype (0 c128, 1 c64, 2 c16) into
+// the ring at absolute sample offset w0 (index mod cap), storage dtype.
+__global__ void ingest_kernel(RxDev d, const void* __restrict__ src, int dtype, long long n, long long w0) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * n) return;
+  const int pol = i >= n;
+  const long long j = i - pol * n;
+  float2 v;
+  if (dtype == 0) {
+    const double2 a = reinterpret_cast<const double2*>(src)[i];
+    v = make_float2((float)a.x, (float)a.y);
+  } else if (dtype == 1) {
+    v = reinterpret_cast<const float2*>(src)[i];
+  } else {
+    v = __half22float2(reinterpret_cast<const __half2*>(src)[i]);
+  }
+  const long long dst = (long long)pol * d.ring_cap + (w0 + j) % d.ring_cap;
+  if (d.storage == 2) reinterpret_cast<__half2*>(d.ring)[dst] = __float22half2_rn(v);
+  else reinterpret_cast<float2*>(d.ring)[dst] = v;
+}
+
+// ---- launchers ------------------------------------------------------------
+
+cudaError_t launch_ref_gen(const RxDev& d, long long sym0, int nbits, int use_delay, cudaStream_t s) {
+  const int chunks = (nbits + 1023) / 1024;
+  dim3 grid((chunks + 127) / 128, 2);
+  ref_gen_kernel<<<grid, 128, 0, s>>>(d, sym0, nbits, use_delay);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sync(const RxDev& d, cudaStream_t s) {
+  sync_kernel<<<(2 * d.sync_dmax + 1) * 2, 256, 0, s>>>(d);
+  sync_select_kernel<<<1, 1, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ber(const RxDev& d, long long ka, long long kb, long long w_from, long long w_to,
+                       long long k_lim, int n_win_ring, cudaStream_t s) {
+  if (kb > ka) {
+    const long long ks = d.ber_skip;
+    const long long kal = ks + ((ka - ks) / 32) * 32;
+    const long long n = kb - kal;
+    ber_count_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d, ka, kb, n_win_ring);
+  }
+  if (w_to > w_from) ber_finalize_kernel<<<1, 32, 0, s>>>(d, w_from, w_to, k_lim, n_win_ring);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ingest(const RxDev& d, const void* src, int dtype, long long n, long long w0, cudaStream_t s) {
+  const long long tot = 2 * n;
+  if (tot == 0) return cudaSuccess;
+  ingest_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d, src, dtype, n, w0);
+  return cudaGetLastError();
+}
+
+}  // namespace rx

@@ -1,0 +1,152 @@
+// Internal definitions shared by the receiver's kernels and its host runtime.
+// Device state of one receiver stream lives in HBM; RxDev is passed by value
+// to every kernel.  Layouts (per stream):
+//   ring   [2][ring_cap]       pushed samples, storage dtype, index n mod cap
+//   z      [2][zlen]           CD output of the frame, complex float; index
+//                              i <-> absolute sample 2fF - c + i
+//   y      [2 buf][2][F]       equaliser output, frame f in buffer f % 2
+//   bl     [2][F + 2W]         per decided symbol: BPS angle | levels << 8
+//   taps   [G][2][2][T]        adaptive chains, complex float
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace rx {
+
+constexpr int kMaxTaps = 31;
+constexpr int kRotLo = 1024;          // FO rotation table split: n = hi*1024 + lo
+constexpr int kRun = 256;             // BPS run / demap tile length (symbols)
+constexpr int kMaxTrace = 4096;       // per-frame estimate records kept
+constexpr int kWinRing = 64;          // BER slip windows in flight
+
+// Per-frame estimates written by the estimator kernel (also the trace).
+struct FrameRec {
+  double tau;      // timing advance applied to the frame (s)
+  double dfo;      // FO estimate (Hz)
+  double gain;     // AGC gain
+  double theta;    // FO phase at the frame start (rad)
+};
+
+// Accumulators filled by the CD kernel, consumed and cleared by the
+// estimator kernel.
+struct FrameAcc {
+  float C[2];      // Godard sum (re, im), both polarisations
+  float P;         // sum |z|^2 of in-frame samples, both polarisations
+  float pad;
+};
+
+// Scalars carried from frame to frame (device resident).
+struct StreamState {
+  double tau;          // timing advance for the next CD pass (s)
+  double theta;        // FO phase at the next frame start
+  int bhat_last[2];    // BPS angle of the last decided symbol (-1: none)
+  int m_last[2];       // unwrap counter of the last decided symbol
+  int synced;
+  int sync_delay, sync_perm, sync_q[2];
+  int q_cur[2];        // BER quadrant in use per polarisation
+  int reinit;          // CMA singularity re-initialisation happened
+  int pad;
+  unsigned long long bits, errors, slips;
+  double evm_num, evm_den;
+};
+
+struct RxDev {
+  // geometry
+  int N, halo, h, L, c, T, K, S, F, G, B, W, bps;
+  int nl;                      // levels per dimension (2 or 4)
+  int zlen;                    // 2F + 2c
+  int storage;                 // RX_C64 / RX_C16
+  long long ring_cap;          // samples per polarisation
+  double Rs, fs;
+  float mu_cma, mu_dd, R2;
+  float timing_gain;
+  int cma_syms, acq_syms;
+  int ber_on, ber_skip, sync_syms, sync_dmax, slip_win;
+  long long out_cap_bytes;
+  long long dec_cap;           // decision ring capacity (symbols)
+  long long hist_syms;         // inspection history length (0: off)
+  // buffers
+  void* ring;
+  float2* Hs;                  // static CD x RRC response, 1/N folded in
+  float2* Hf;                  // Hs x timing phase of the coming pass
+  float2* tw;                  // tw[k] = exp(-2 pi i k / N)
+  float2* z;
+  float2* rot_hi;              // [ceil(zlen/1024)]  gain * exp(-j(theta + w (hi*1024 - c)))
+  float2* rot_lo;              // [1024]             exp(-j w lo)
+  FrameAcc* acc;
+  float* psd;                  // [N/2] FOE periodogram
+  FrameRec* rec;               // [kMaxTrace]
+  StreamState* st;
+  float2* w_acq;               // [2][2][T]
+  float2* chains;              // [G][2][2][T]
+  float2* y;                   // [2][2][F]
+  uint16_t* bl;                // [2][F + 2W]
+  int* run_int;                // [2][nruns] internal unwrap increment sums
+  int* run_m0;                 // [2][nruns] unwrap counter at each run's first symbol
+  uint8_t* dec;                // decision ring [dec_cap]: x levels | y levels << 4
+  uint8_t* out;                // output bit ring (bytes)
+  uint32_t* prbs_jump;         // [64][31] columns of A^(2^i)
+  uint32_t* ref;               // [2][ref_words] reference bits of the frame range
+  int ref_words;
+  unsigned* sync_err;          // [(2 dmax + 1) * 2][2][4]
+  unsigned* win_err;           // [kWinRing][2][4]
+  uint32_t prbs_state0[2];     // PRBS start state per polarisation
+  // inspection history (optional)
+  float2* hist_y;              // [2][hist_syms]
+  uint8_t* hist_bhat;          // [2][hist_syms]
+  int* hist_m;                 // [2][hist_syms]
+};
+
+// Arguments of one frame.
+struct FrameArgs {
+  long long f;         // frame index
+  int Ff;              // symbols in this frame
+  long long s0;        // first CD output sample (absolute) = 2fF - c
+  long long f0, f1;    // in-frame samples [f0, f1)
+  long long n_valid;   // samples per pol that exist (beyond: zero)
+  long long k_a, k_b;  // decided symbol range of this frame
+  long long k_end;     // BER count limit (exclusive); LLONG_MAX before end of stream
+  long long n_sym;     // symbols in the stream if known (final), else LLONG_MAX
+  int est_only;        // CD pass that only accumulates the Godard sum
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Nearest level index per dimension for unit-energy square QAM; values on
+// a threshold take the larger level.  nl = 2: levels -1,+1 (/sqrt2);
+// nl = 4: -3,-1,1,3 (/sqrt10).
+__device__ __forceinline__ int level_of(float x, int nl) {
+  if (nl == 2) return x >= 0.f ? 1 : 0;
+  const float t = 0.63245553203367588f;  // 2/sqrt(10)
+  return (x >= t) ? 3 : (x >= 0.f ? 2 : (x >= -t ? 1 : 0));
+}
+__device__ __forceinline__ float level_val(int l, int nl) {
+  if (nl == 2) return l ? 0.70710678118654752f : -0.70710678118654752f;
+  return (2 * l - 3) * 0.31622776601683794f;
+}
+
+// Loads one stored sample as complex float.
+__device__ __forceinline__ float2 load_sample(const void* ring, int storage, long long idx) {
+  if (storage == 2) {  // RX_C16
+    __half2 hv = reinterpret_cast<const __half2*>(ring)[idx];
+    return __half22float2(hv);
+  }
+  return reinterpret_cast<const float2*>(ring)[idx];
+}
+
+}  // namespace rx

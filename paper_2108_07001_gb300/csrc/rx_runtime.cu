@@ -1,0 +1,896 @@
+// Host runtime behind the C ABI in include/rx.h: configuration checks,
+// FP64 set-up of the CD filter and FFT twiddles, device allocation, the
+// push ring, frame scheduling on the library's compute stream, bit pulls
+// and statistics.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/rx.h"
+#include "rx_internal.cuh"
+
+namespace rx {
+cudaError_t launch_cd(const RxDev& d, const FrameArgs& fa, cudaStream_t s);
+cudaError_t launch_est(const RxDev& d, const FrameArgs& fa, int mode, cudaStream_t s);
+cudaError_t launch_acquire(const RxDev& d, const FrameArgs& fa, cudaStream_t s);
+cudaError_t launch_mimo(const RxDev& d, const FrameArgs& fa, cudaStream_t s);
+cudaError_t launch_bps(const RxDev& d, const FrameArgs& fa, cudaStream_t s);
+cudaError_t launch_unwrap_demap(const RxDev& d, const FrameArgs& fa, cudaStream_t s);
+cudaError_t launch_ref_gen(const RxDev& d, long long sym0, int nbits, int use_delay, cudaStream_t s);
+cudaError_t launch_sync(const RxDev& d, cudaStream_t s);
+cudaError_t launch_ber(const RxDev& d, long long ka, long long kb, long long w_from, long long w_to,
+                       long long k_lim, int n_win_ring, cudaStream_t s);
+cudaError_t launch_ingest(const RxDev& d, const void* src, int dtype, long long n, long long w0, cudaStream_t s);
+}  // namespace rx
+
+using namespace rx;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return RX_EDEVICE;
+}
+
+#define RX_CK(call)                                    \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+constexpr double kC = 299792458.0;
+
+struct StageEv {
+  int stage;
+  cudaEvent_t a, b;
+};
+
+struct PendingFrame {
+  long long f;
+  long long gen;         // stream generation (rx_reset increments it)
+  long long bits_after;  // bits produced once this frame completes
+  long long dec_after;
+  cudaEvent_t ev_in, ev_start, ev_done;
+  std::vector<StageEv> sev;
+};
+
+}  // namespace
+
+struct rx_handle {
+  rx_config cfg;
+  RxDev d;
+  cudaStream_t s_copy = nullptr, s_comp = nullptr;
+  cudaEvent_t ev_copy = nullptr;   // last ingest (recorded on the pushing stream)
+  cudaEvent_t ev_reset = nullptr;  // last rx_reset (recorded on the compute stream)
+  bool reset_pending = false;
+  cudaStream_t last_cs = nullptr;  // stream of the last push (input arrival events)
+  long long pushed = 0;       // samples per pol written to the ring
+  long long n_total = -1;     // samples per pol in the stream (after end)
+  bool ended = false;
+  long long f_next = 0;       // next frame to launch
+  long long f_waited = 0;     // frames whose CD pass the copy stream has waited for
+  long long decided = 0;      // symbols decided by launched work
+  long long bits_done = 0;    // bits of completed frames
+  long long bits_pulled = 0;
+  long long dec_done = 0;
+  bool synced = false;
+  bool tail_launched = false;
+  long long w_next = 0;       // next BER slip window to finalise
+  int n_win_ring = 0;
+  int la = 0;                 // lookahead samples beyond a frame
+  int tail = 0;               // symbols excluded from BER at the stream end
+  std::vector<cudaEvent_t> cd_done;   // per frame slot (ring of 64)
+  std::deque<PendingFrame> pend;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<double> lat_ms;
+  double gpu_ms = 0.0;
+  long long frames_done = 0;
+  void* stage = nullptr;      // device staging for host pushes
+  size_t stage_bytes = 0;
+  std::deque<StageEv> ingest_ev;
+  long long gen = 0;
+  StreamState st_init{};             // initial device state (host copy for resets)
+  double stage_ms[RX_NSTAGES] = {0};
+  long long stage_n[RX_NSTAGES] = {0};   // kernel launches per stage
+};
+
+namespace {
+
+int log2i(long long v) {
+  int r = 0;
+  while ((1LL << r) < v) ++r;
+  return r;
+}
+
+cudaEvent_t get_event(rx_handle* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// GF(2) 31x31 matrices as 31 column words.
+void gf2_mul(const uint32_t* A, const uint32_t* B, uint32_t* C) {  // C = A B
+  for (int j = 0; j < 31; ++j) {
+    uint32_t col = 0;
+    for (int k = 0; k < 31; ++k)
+      if ((B[j] >> k) & 1u) col ^= A[k];
+    C[j] = col;
+  }
+}
+
+uint32_t prbs_state(uint64_t seed, int pol) {
+  const uint64_t p = (1ULL << 31) - 1;
+  const uint64_t off = pol == 0 ? 0 : 0x2545F491ULL;
+  const uint64_t v = (seed % p + off) % p;
+  return (uint32_t)((v * 1103515245ULL) % p + 1);
+}
+
+double rrc_amp(double f, double Rs, double rho) {
+  const double a = std::fabs(f) / Rs;
+  if (a <= (1 - rho) / 2) return 1.0;
+  if (rho <= 0 || a > (1 + rho) / 2) return 0.0;
+  return std::sqrt(0.5 * (1.0 + std::cos(M_PI / rho * (a - (1 - rho) / 2))));
+}
+
+double erfcinv_host(double y) {  // solve erfc(x) = y, 0 < y < 1, Newton from a rational start
+  double x = std::sqrt(-std::log(y / 2.0 + 1e-300));
+  for (int i = 0; i < 60; ++i) {
+    const double fx = std::erfc(x) - y;
+    const double dfx = -2.0 / std::sqrt(M_PI) * std::exp(-x * x);
+    const double nx = x - fx / dfx;
+    if (std::fabs(nx - x) < 1e-15 * std::max(1.0, std::fabs(x))) { x = nx; break; }
+    x = nx;
+  }
+  return x;
+}
+
+template <typename T>
+int dalloc(T** p, size_t n) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) return fail(RX_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  e = cudaMemset(*p, 0, n * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+  return RX_OK;
+}
+
+void free_all(rx_handle* h) {
+  RxDev& d = h->d;
+  void* ptrs[] = {d.ring, d.Hs, d.Hf, d.tw, d.z, d.rot_hi, d.rot_lo, d.acc, d.psd, d.rec, d.st, d.w_acq,
+                  d.chains, d.y, d.bl, d.run_int, d.run_m0, d.dec, d.out, d.prbs_jump, d.ref,
+                  d.sync_err, d.win_err, d.hist_y, d.hist_bhat, d.hist_m, h->stage};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : h->cd_done)
+    if (e) cudaEventDestroy(e);
+  for (auto& pf : h->pend) {
+    cudaEventDestroy(pf.ev_in);
+    cudaEventDestroy(pf.ev_start);
+    cudaEventDestroy(pf.ev_done);
+    for (auto& se : pf.sev) {
+      cudaEventDestroy(se.a);
+      cudaEventDestroy(se.b);
+    }
+  }
+  for (auto& se : h->ingest_ev) {
+    cudaEventDestroy(se.a);
+    cudaEventDestroy(se.b);
+  }
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->ev_copy) cudaEventDestroy(h->ev_copy);
+  if (h->ev_reset) cudaEventDestroy(h->ev_reset);
+  if (h->s_copy) cudaStreamDestroy(h->s_copy);
+  if (h->s_comp) cudaStreamDestroy(h->s_comp);
+}
+
+// Harvest completed frames (in order): latency, device time, bits.
+void harvest(rx_handle* h) {
+  while (!h->pend.empty()) {
+    PendingFrame& pf = h->pend.front();
+    if (cudaEventQuery(pf.ev_done) != cudaSuccess) break;
+    float a = 0.f, b = 0.f;
+    if (pf.gen == h->gen) {
+      if (cudaEventElapsedTime(&a, pf.ev_in, pf.ev_done) == cudaSuccess) h->lat_ms.push_back(a);
+      if (cudaEventElapsedTime(&b, pf.ev_start, pf.ev_done) == cudaSuccess) h->gpu_ms += b;
+      h->bits_done = pf.bits_after;
+      h->dec_done = pf.dec_after;
+      if (pf.f >= 0) h->frames_done++;
+    }
+    for (auto& se : pf.sev) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, se.a, se.b) == cudaSuccess) h->stage_ms[se.stage] += ms;
+      h->ev_pool.push_back(se.a);
+      h->ev_pool.push_back(se.b);
+    }
+    h->ev_pool.push_back(pf.ev_in);
+    h->ev_pool.push_back(pf.ev_start);
+    h->ev_pool.push_back(pf.ev_done);
+    h->pend.pop_front();
+  }
+  while (!h->ingest_ev.empty()) {
+    StageEv& se = h->ingest_ev.front();
+    if (cudaEventQuery(se.b) != cudaSuccess) break;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, se.a, se.b) == cudaSuccess) h->stage_ms[RX_STAGE_INGEST] += ms;
+    h->ev_pool.push_back(se.a);
+    h->ev_pool.push_back(se.b);
+    h->ingest_ev.pop_front();
+  }
+  cudaGetLastError();  // clear cudaErrorNotReady
+}
+
+// Runs fn (which enqueues work on the compute stream) between two timing
+// events when profiling is on.
+template <typename Fn>
+int staged(rx_handle* h, PendingFrame& pf, int stage, Fn&& fn) {
+  if (!h->cfg.profile) return fn();
+  StageEv se{stage, get_event(h), get_event(h)};
+  RX_CK(cudaEventRecord(se.a, h->s_comp));
+  int rc = fn();
+  RX_CK(cudaEventRecord(se.b, h->s_comp));
+  pf.sev.push_back(se);
+  return rc;
+}
+
+#define RX_STAGE(st, nk, call)                                                   \
+  do {                                                                           \
+    int rc_ = staged(h, pf, st, [&]() -> int {                                   \
+      cudaError_t e_ = (call);                                                   \
+      return e_ == cudaSuccess ? RX_OK : cuda_fail(e_, #call);                   \
+    });                                                                          \
+    if (rc_ != RX_OK) return rc_;                                                \
+    h->stage_n[st] += (nk);                                                      \
+  } while (0)
+
+// Launch the decision stages (BPS .. BER) for decided range [k_a, k_b).
+int launch_decide(rx_handle* h, PendingFrame& pf, const FrameArgs& fa, bool final_) {
+  const RxDev& d = h->d;
+  RX_STAGE(RX_STAGE_BPS, 1, launch_bps(d, fa, h->s_comp));
+  RX_STAGE(RX_STAGE_DEMAP, 2, launch_unwrap_demap(d, fa, h->s_comp));
+  if (d.ber_on) {
+    return staged(h, pf, RX_STAGE_BER, [&]() -> int {
+    const long long ks = d.ber_skip;
+    const long long need = ks + d.sync_syms;
+    if (!h->synced && fa.k_b >= need && need <= fa.k_end && ks > d.sync_dmax) {
+      const int nb = (d.sync_syms + 2 * d.sync_dmax) * d.bps;
+      RX_CK(launch_ref_gen(d, ks - d.sync_dmax, nb, 0, h->s_comp));
+      RX_CK(launch_sync(d, h->s_comp));
+      h->stage_n[RX_STAGE_BER] += 3;
+      h->synced = true;
+      h->w_next = 0;
+    }
+    if (h->synced) {
+      // count everything decided since the sync window start that is not yet counted
+      // the sync window lies in the first frame, so counting starts there
+      const long long ka = std::max(fa.k_a, ks);
+      const long long hi = std::min(fa.k_b, fa.k_end);
+      if (hi > ka) {
+        const int nbits = (int)((hi - ka) * d.bps);
+        RX_CK(launch_ref_gen(d, ka, nbits, 1, h->s_comp));
+        h->stage_n[RX_STAGE_BER] += 2;  // reference + count
+      }
+      const long long klim = final_ ? fa.k_end : fa.k_b;
+      long long w_to = klim > ks ? (final_ ? (klim - ks + d.slip_win - 1) / d.slip_win : (klim - ks) / d.slip_win) : 0;
+      if (w_to < h->w_next) w_to = h->w_next;
+      RX_CK(launch_ber(d, ka, std::max(hi, ka), h->w_next, w_to, klim, h->n_win_ring, h->s_comp));
+      if (w_to > h->w_next) h->stage_n[RX_STAGE_BER] += 1;  // slip pass
+      h->w_next = w_to;
+    }
+    return RX_OK;
+    });
+  }
+  return RX_OK;
+}
+
+int launch_frame(rx_handle* h, long long f, bool final_) {
+  RxDev& d = h->d;
+  const long long F = d.F;
+  const long long n_sym = h->ended ? h->n_total / 2 : LLONG_MAX;
+  FrameArgs fa{};
+  fa.f = f;
+  fa.Ff = (int)std::min(F, (h->ended ? n_sym : LLONG_MAX) - f * F);
+  fa.s0 = 2 * f * F - d.c;
+  fa.f0 = 2 * f * F;
+  fa.f1 = fa.f0 + 2LL * fa.Ff;
+  fa.n_valid = h->ended ? h->n_total : h->pushed;
+  fa.k_a = std::max(f * F - d.W, 0LL);
+  fa.k_b = final_ ? n_sym : (f + 1) * F - d.W;
+  fa.k_end = h->ended ? n_sym - h->tail : LLONG_MAX;
+  fa.n_sym = n_sym;
+  fa.est_only = 0;
+
+  PendingFrame pf;
+  pf.f = f;
+  pf.gen = h->gen;
+  pf.ev_in = get_event(h);
+  pf.ev_start = get_event(h);
+  pf.ev_done = get_event(h);
+  RX_CK(cudaEventRecord(pf.ev_in, h->last_cs));
+  RX_CK(cudaStreamWaitEvent(h->s_comp, h->ev_copy, 0));
+  RX_CK(cudaEventRecord(pf.ev_start, h->s_comp));
+  if (f == 0) {
+    FrameArgs fe = fa;
+    fe.est_only = 1;
+    RX_STAGE(RX_STAGE_CD, 1, launch_cd(d, fe, h->s_comp));
+    RX_STAGE(RX_STAGE_EST, 1, launch_est(d, fe, 0, h->s_comp));
+  }
+  RX_STAGE(RX_STAGE_CD, 1, launch_cd(d, fa, h->s_comp));
+  RX_CK(cudaEventRecord(h->cd_done[f % h->cd_done.size()], h->s_comp));
+  RX_STAGE(RX_STAGE_EST, 1, launch_est(d, fa, 1, h->s_comp));
+  if (f == 0) RX_STAGE(RX_STAGE_ACQUIRE, 1, launch_acquire(d, fa, h->s_comp));
+  RX_STAGE(RX_STAGE_MIMO, 1, launch_mimo(d, fa, h->s_comp));
+  int rc = launch_decide(h, pf, fa, final_);
+  if (rc != RX_OK) return rc;
+  RX_CK(cudaEventRecord(pf.ev_done, h->s_comp));
+  h->decided = fa.k_b;
+  pf.dec_after = fa.k_b;
+  pf.bits_after = 2LL * d.bps * fa.k_b;
+  h->pend.push_back(pf);
+  h->f_next = f + 1;
+  return RX_OK;
+}
+
+// Decide the last W symbols when the stream ended exactly at a frame end.
+int launch_tail(rx_handle* h) {
+  RxDev& d = h->d;
+  const long long n_sym = h->n_total / 2;
+  if (h->f_next == 0 || h->decided >= n_sym) return RX_OK;
+  FrameArgs fa{};
+  fa.f = h->f_next - 1;
+  fa.Ff = d.F;
+  fa.k_a = h->decided;
+  fa.k_b = n_sym;
+  fa.k_end = n_sym - h->tail;
+  fa.n_sym = n_sym;
+  PendingFrame pf;
+  pf.f = -1;
+  pf.gen = h->gen;
+  pf.ev_in = get_event(h);
+  pf.ev_start = get_event(h);
+  pf.ev_done = get_event(h);
+  RX_CK(cudaEventRecord(pf.ev_in, h->last_cs));
+  RX_CK(cudaStreamWaitEvent(h->s_comp, h->ev_copy, 0));
+  RX_CK(cudaEventRecord(pf.ev_start, h->s_comp));
+  int rc = launch_decide(h, pf, fa, true);
+  if (rc != RX_OK) return rc;
+  RX_CK(cudaEventRecord(pf.ev_done, h->s_comp));
+  h->decided = n_sym;
+  pf.dec_after = n_sym;
+  pf.bits_after = 2LL * d.bps * n_sym;
+  h->pend.push_back(pf);
+  return RX_OK;
+}
+
+int validate(const rx_config* c, std::string& why) {
+  if (!(c->baud_hz > 0)) return why = "baud_hz must be > 0", RX_EINVAL;
+  if (c->modulation != RX_QPSK && c->modulation != RX_QAM16) return why = "modulation must be RX_QPSK or RX_QAM16", RX_EINVAL;
+  if (c->fiber_len_m < 0 || !(c->lambda_m > 0)) return why = "fiber_len_m >= 0 and lambda_m > 0 required", RX_EINVAL;
+  if (c->mimo_taps < 3 || c->mimo_taps > kMaxTaps || (c->mimo_taps & 1) == 0) return why = "mimo_taps must be odd in [3, 31]", RX_EINVAL;
+  if (c->bps_angles != 32 && c->bps_angles != 64) return why = "bps_angles must be 32 or 64", RX_EINVAL;
+  const int W = c->bps_half_window;
+  if (W != 8 && W != 12 && W != 16 && W != 24 && W != 32) return why = "bps_half_window must be one of 8, 12, 16, 24, 32", RX_EINVAL;
+  if (c->sub_block_syms != 64) return why = "sub_block_syms must be 64", RX_EINVAL;
+  if (c->seg_syms < 64 || c->seg_syms % 64) return why = "seg_syms must be a positive multiple of 64", RX_EINVAL;
+  if (c->frame_syms < c->seg_syms || c->frame_syms % c->seg_syms || c->frame_syms % kRun)
+    return why = "frame_syms must be a multiple of seg_syms and of 256", RX_EINVAL;
+  if (c->frame_syms > (1 << 24)) return why = "frame_syms must be <= 2^24", RX_EINVAL;
+  if (c->acq_syms < 64 || c->acq_syms > c->frame_syms || c->cma_syms < 0) return why = "need 64 <= acq_syms <= frame_syms, cma_syms >= 0", RX_EINVAL;
+  if (c->storage_dtype != RX_C64 && c->storage_dtype != RX_C16) return why = "storage_dtype must be RX_C64 or RX_C16", RX_EINVAL;
+  if (c->max_block_samples < 1) return why = "max_block_samples must be >= 1", RX_EINVAL;
+  if (c->prbs_seed) {
+    if (c->slip_window < 32 || c->slip_window % 32) return why = "slip_window must be a positive multiple of 32", RX_EINVAL;
+    if (c->ber_skip_syms <= c->sync_max_delay || c->sync_max_delay < 0) return why = "ber_skip_syms must exceed sync_max_delay", RX_EINVAL;
+    if (c->sync_syms < 64) return why = "sync_syms must be >= 64", RX_EINVAL;
+    if ((long long)c->ber_skip_syms + c->sync_syms + c->bps_half_window > c->frame_syms)
+      return why = "frame_syms must cover ber_skip_syms + sync_syms + bps_half_window (sync in the first frame)", RX_EINVAL;
+  }
+  return RX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rx_last_error(void) { return g_err.c_str(); }
+
+void rx_config_default(rx_config* c) {
+  std::memset(c, 0, sizeof(*c));
+  c->baud_hz = 28e9;
+  c->modulation = RX_QPSK;
+  c->fiber_len_m = 1000e3;
+  c->D_ps_nm_km = 17.0;
+  c->lambda_m = 1550e-9;
+  c->rrc_rolloff = 0.1;
+  c->fft_n = 0;
+  c->cd_halo = 0;
+  c->mimo_taps = 15;
+  c->bps_angles = 64;
+  c->bps_half_window = 16;
+  c->sub_block_syms = 64;
+  c->seg_syms = 512;
+  c->frame_syms = 1 << 16;
+  c->cma_syms = 8192;
+  c->acq_syms = 12288;
+  c->mu_cma = 3e-2f;
+  c->mu_dd = 5e-3f;
+  c->timing_gain = 0.5f;
+  c->storage_dtype = RX_C64;
+  c->prbs_seed = 0;
+  c->ber_skip_syms = 4096;
+  c->sync_syms = 4096;
+  c->sync_max_delay = 32;
+  c->slip_window = 1024;
+  c->max_block_samples = 1 << 17;
+  c->history_syms = 0;
+  c->profile = 0;
+  c->device = 0;
+}
+
+int rx_create(const rx_config* cfg, rx_handle** out) {
+  if (!cfg || !out) return fail(RX_EINVAL, "null argument");
+  *out = nullptr;
+  std::string why;
+  if (validate(cfg, why) != RX_OK) return fail(RX_EINVAL, why);
+  rx_handle* h = new rx_handle();
+  h->cfg = *cfg;
+  RxDev& d = h->d;
+  std::memset(&d, 0, sizeof(d));
+  // geometry (FP64)
+  const double Rs = cfg->baud_hz, fs = 2.0 * Rs;
+  const double rho = std::max(cfg->rrc_rolloff, 0.0);
+  const double Dsm = std::fabs(cfg->D_ps_nm_km) * 1e-6;
+  const double dlam = cfg->lambda_m * cfg->lambda_m * Rs * (1.0 + rho) / kC;
+  const double mem = Dsm * cfg->fiber_len_m * dlam * fs;
+  int halo = cfg->cd_halo > 0 ? cfg->cd_halo : (int)std::ceil(1.1 * mem);
+  halo += halo & 1;
+  halo = std::max(halo, 2);
+  int N = cfg->fft_n;
+  if (N <= 0) {
+    N = 1024;
+    while (N < 4 * halo && N < 16384) N *= 2;
+  }
+  if (N < 1024 || N > 16384 || (N & (N - 1))) { delete h; return fail(RX_EINVAL, "fft_n must be a power of two in [1024, 16384]"); }
+  if (N - halo < 256) { delete h; return fail(RX_EINVAL, "CD halo too long for the FFT size (need N - halo >= 256)"); }
+  {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+      cudaGetLastError();
+      delete h;
+      return fail(RX_EDEVICE, "no such CUDA device");
+    }
+    cudaError_t e = cudaSetDevice(cfg->device);
+    if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaSetDevice"); }
+  }
+  d.N = N;
+  d.halo = halo;
+  d.h = halo / 2;
+  d.L = N - halo;
+  d.T = cfg->mimo_taps;
+  d.c = (d.T - 1) / 2;
+  d.K = 64;
+  d.S = cfg->seg_syms;
+  d.F = cfg->frame_syms;
+  d.G = d.F / d.S;
+  d.B = cfg->bps_angles;
+  d.W = cfg->bps_half_window;
+  d.bps = cfg->modulation;
+  d.nl = d.bps == 2 ? 2 : 4;
+  d.zlen = 2 * d.F + 2 * d.c;
+  d.storage = cfg->storage_dtype;
+  d.Rs = Rs;
+  d.fs = fs;
+  d.mu_cma = cfg->mu_cma;
+  d.mu_dd = cfg->mu_dd;
+  d.R2 = d.bps == 2 ? 1.0f : 1.32f;
+  d.timing_gain = cfg->timing_gain;
+  d.cma_syms = cfg->cma_syms;
+  d.acq_syms = cfg->acq_syms;
+  d.ber_on = cfg->prbs_seed != 0;
+  d.ber_skip = cfg->ber_skip_syms;
+  d.sync_syms = cfg->sync_syms;
+  d.sync_dmax = cfg->sync_max_delay;
+  d.slip_win = cfg->slip_window;
+  d.hist_syms = cfg->history_syms;
+
+  h->tail = (d.h + 1) / 2 + d.T + d.W;
+  h->la = std::max(d.c + d.h + 2, 2 * (h->tail + d.W + 2));
+  const long long mb = (long long)cfg->max_block_samples;
+  d.ring_cap = 2LL * d.F + 2LL * h->la + d.c + d.h + mb + 1024;
+  d.out_cap_bytes = std::max<long long>(1 << 20, 32LL * d.F * 2 * d.bps / 8);
+  d.dec_cap = 2LL * d.F + 8192;
+  h->n_win_ring = d.F / std::max(d.slip_win, 32) + 8;
+  const int nruns = d.F / kRun + 4;
+  d.ref_words = (int)(((long long)(d.F + 2 * d.W + 2 * d.sync_dmax + d.sync_syms + d.ber_skip) * d.bps) / 32 + 8);
+
+  int rc = RX_OK;
+  const size_t elt = d.storage == RX_C16 ? 4 : 8;
+  {
+    cudaError_t e = cudaMalloc(&d.ring, 2 * d.ring_cap * elt);
+    if (e != cudaSuccess) { free_all(h); delete h; return fail(RX_ENOMEM, "ring allocation failed"); }
+    cudaMemset(d.ring, 0, 2 * d.ring_cap * elt);
+  }
+#define RX_AL(p, n) if ((rc = dalloc(&p, n)) != RX_OK) { free_all(h); delete h; return rc; }
+  RX_AL(d.Hs, N);
+  RX_AL(d.Hf, N);
+  RX_AL(d.tw, N);
+  RX_AL(d.z, 2LL * d.zlen);
+  RX_AL(d.rot_hi, d.zlen / kRotLo + 2);
+  RX_AL(d.rot_lo, kRotLo);
+  RX_AL(d.acc, 1);
+  RX_AL(d.psd, N / 2);
+  RX_AL(d.rec, kMaxTrace);
+  RX_AL(d.st, 1);
+  RX_AL(d.w_acq, 4 * d.T);
+  RX_AL(d.chains, (size_t)d.G * 4 * d.T);
+  RX_AL(d.y, 4LL * d.F);
+  RX_AL(d.bl, 2LL * (d.F + 2 * d.W));
+  RX_AL(d.run_int, 2LL * nruns);
+  RX_AL(d.run_m0, 2LL * nruns);
+  RX_AL(d.dec, d.dec_cap);
+  RX_AL(d.out, d.out_cap_bytes);
+  RX_AL(d.prbs_jump, 64 * 31);
+  RX_AL(d.ref, 2LL * d.ref_words + 4);
+  RX_AL(d.sync_err, (size_t)(2 * d.sync_dmax + 1) * 2 * 8);
+  RX_AL(d.win_err, (size_t)h->n_win_ring * 8);
+  if (d.hist_syms > 0) {
+    RX_AL(d.hist_y, 2LL * d.hist_syms);
+    RX_AL(d.hist_bhat, 2LL * d.hist_syms);
+    RX_AL(d.hist_m, 2LL * d.hist_syms);
+  }
+#undef RX_AL
+
+  // CD x RRC response (FP64 phase reduced mod 2 pi), 1/N folded in; twiddles
+  {
+    const double L = cfg->fiber_len_m;
+    const double Dsi = cfg->D_ps_nm_km * 1e-6;
+    const double b2 = -Dsi * cfg->lambda_m * cfg->lambda_m / (2.0 * M_PI * kC);
+    std::vector<float2> Hs(N), tw(N);
+    for (int k = 0; k < N; ++k) {
+      const double fk = (k < N / 2 ? k : k - N) * (fs / N);
+      const double w = 2.0 * M_PI * fk;
+      const double ph = std::fmod(b2 * L * w * w / 2.0, 2.0 * M_PI);
+      double amp = 1.0 / N;
+      if (cfg->rrc_rolloff >= 0) amp *= rrc_amp(fk, Rs, cfg->rrc_rolloff);
+      Hs[k] = make_float2((float)(amp * std::cos(ph)), (float)(amp * std::sin(ph)));
+      const double a = -2.0 * M_PI * (double)k / N;
+      tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    cudaMemcpy(d.Hs, Hs.data(), N * sizeof(float2), cudaMemcpyHostToDevice);
+    cudaMemcpy(d.Hf, Hs.data(), N * sizeof(float2), cudaMemcpyHostToDevice);
+    cudaMemcpy(d.tw, tw.data(), N * sizeof(float2), cudaMemcpyHostToDevice);
+  }
+  // PRBS jump matrices A^(2^i): A shifts the window down one bit and sets
+  // bit 30 = bit 3 ^ bit 0.
+  {
+    std::vector<uint32_t> M(64 * 31);
+    uint32_t A[31];
+    for (int j = 0; j < 31; ++j) A[j] = (j >= 1 ? 1u << (j - 1) : 0u) | ((j == 0 || j == 3) ? 1u << 30 : 0u);
+    std::memcpy(&M[0], A, sizeof(A));
+    for (int i = 1; i < 64; ++i) gf2_mul(&M[(i - 1) * 31], &M[(i - 1) * 31], &M[i * 31]);
+    cudaMemcpy(d.prbs_jump, M.data(), M.size() * 4, cudaMemcpyHostToDevice);
+    d.prbs_state0[0] = prbs_state(cfg->prbs_seed, 0);
+    d.prbs_state0[1] = prbs_state(cfg->prbs_seed, 1);
+  }
+  h->st_init = StreamState{};
+  h->st_init.bhat_last[0] = h->st_init.bhat_last[1] = -1;
+  cudaMemcpy(d.st, &h->st_init, sizeof(StreamState), cudaMemcpyHostToDevice);
+  h->stage_bytes = (size_t)mb * 2 * 16;
+  if (cudaMalloc(&h->stage, h->stage_bytes) != cudaSuccess) { free_all(h); delete h; return fail(RX_ENOMEM, "staging allocation failed"); }
+  cudaError_t e = cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_comp, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_reset, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_copy, h->s_copy);
+  h->cd_done.assign(64, nullptr);
+  for (auto& ev : h->cd_done)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) { free_all(h); delete h; return cuda_fail(e, "rx_create"); }
+  *out = h;
+  return RX_OK;
+}
+
+int rx_push_block(rx_handle* h, const void* samples, size_t n_per_pol, int dtype, int on_device, void* cuda_stream) {
+  if (!h) return fail(RX_EINVAL, "null handle");
+  if (h->ended) return fail(RX_ESTATE, "push after end of stream");
+  RX_CK(cudaSetDevice(h->cfg.device));
+  RxDev& d = h->d;
+  const long long F = d.F;
+  if (samples == nullptr && n_per_pol == 0) {
+    h->ended = true;
+    h->n_total = h->pushed;
+    const long long n_sym = h->n_total / 2;
+    for (long long f = h->f_next; f * F < n_sym; ++f) {
+      const bool fin = (f + 1) * F >= n_sym;
+      int rc = launch_frame(h, f, fin);
+      if (rc != RX_OK) return rc;
+      if (fin) h->tail_launched = true;
+    }
+    if (!h->tail_launched) {
+      int rc = launch_tail(h);
+      if (rc != RX_OK) return rc;
+    }
+    return RX_OK;
+  }
+  if (samples == nullptr) return fail(RX_EINVAL, "samples is NULL");
+  if (dtype < RX_C128 || dtype > RX_C16) return fail(RX_EINVAL, "bad dtype");
+  if (n_per_pol > h->cfg.max_block_samples) return fail(RX_EINVAL, "n_per_pol exceeds max_block_samples");
+  if (n_per_pol == 0) return RX_OK;
+  const long long n = (long long)n_per_pol;
+  // output ring room for the frames this push completes
+  {
+    long long f = h->f_next, dec = h->decided;
+    while (h->pushed + n >= 2 * (f + 1) * F + h->la) {
+      dec = (f + 1) * F - d.W;
+      ++f;
+    }
+    harvest(h);
+    const long long bits_after = 2LL * d.bps * dec;
+    if (bits_after - h->bits_pulled + 64 > 8LL * d.out_cap_bytes)
+      return fail(RX_EAGAIN, "output ring full: pull bits first");
+  }
+  cudaStream_t cs = (cudaStream_t)cuda_stream;
+  // The copy runs on the caller's stream, so it is ordered after the
+  // caller's queued work and the caller's later work is ordered after it.
+  // Ring slots being overwritten must no longer be read by launched frames.
+  const long long w1 = h->pushed + n;
+  while (h->f_waited < h->f_next) {
+    const long long ws = 2 * h->f_waited * F - d.c - d.h;
+    if (ws >= w1 - d.ring_cap) break;
+    RX_CK(cudaStreamWaitEvent(cs, h->cd_done[h->f_waited % h->cd_done.size()], 0));
+    h->f_waited++;
+  }
+  if (h->reset_pending) {
+    RX_CK(cudaStreamWaitEvent(cs, h->ev_reset, 0));
+    h->reset_pending = false;
+  }
+  const size_t esz = dtype == RX_C128 ? 16 : (dtype == RX_C64 ? 8 : 4);
+  const void* src = samples;
+  if (!on_device) {
+    RX_CK(cudaMemcpyAsync(h->stage, samples, 2 * n * esz, cudaMemcpyHostToDevice, cs));
+    src = h->stage;
+  }
+  if (h->cfg.profile) {
+    StageEv se{RX_STAGE_INGEST, get_event(h), get_event(h)};
+    RX_CK(cudaEventRecord(se.a, cs));
+    RX_CK(launch_ingest(d, src, dtype, n, h->pushed, cs));
+    RX_CK(cudaEventRecord(se.b, cs));
+    h->ingest_ev.push_back(se);
+  } else {
+    RX_CK(launch_ingest(d, src, dtype, n, h->pushed, cs));
+  }
+  h->stage_n[RX_STAGE_INGEST] += 1;
+  RX_CK(cudaEventRecord(h->ev_copy, cs));
+  h->last_cs = cs;
+  if (!on_device) RX_CK(cudaEventSynchronize(h->ev_copy));  // host buffer and staging reusable
+  h->pushed += n;
+  while (h->pushed >= 2 * (h->f_next + 1) * F + h->la) {
+    int rc = launch_frame(h, h->f_next, false);
+    if (rc != RX_OK) return rc;
+  }
+  return RX_OK;
+}
+
+int rx_pull_bits(rx_handle* h, uint8_t* out, size_t cap_bytes, size_t* n_bits, int timeout_ms) {
+  if (!h || (!out && cap_bytes) || !n_bits) return fail(RX_EINVAL, "null argument");
+  RX_CK(cudaSetDevice(h->cfg.device));
+  *n_bits = 0;
+  int rc = RX_OK;
+  if (timeout_ms < 0) {
+    RX_CK(cudaStreamSynchronize(h->s_comp));
+  } else if (timeout_ms > 0) {
+    auto t0 = std::chrono::steady_clock::now();
+    while (true) {
+      harvest(h);
+      if (h->pend.empty()) break;
+      if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms)) { rc = RX_ETIMEDOUT; break; }
+      std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+  }
+  harvest(h);
+  cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess && le != cudaErrorNotReady) return cuda_fail(le, "device");
+  const bool all_done = h->ended && h->pend.empty() && h->decided >= h->n_total / 2;
+  long long avail = h->bits_done - h->bits_pulled;
+  long long nbytes = all_done ? (avail + 7) / 8 : avail / 8;
+  nbytes = std::min<long long>(nbytes, (long long)cap_bytes);
+  if (nbytes > 0) {
+    const long long b0 = h->bits_pulled / 8;
+    const long long cap = h->d.out_cap_bytes;
+    const long long o = b0 % cap;
+    const long long first = std::min(nbytes, cap - o);
+    RX_CK(cudaMemcpy(out, h->d.out + o, first, cudaMemcpyDeviceToHost));
+    if (nbytes > first) RX_CK(cudaMemcpy(out + first, h->d.out, nbytes - first, cudaMemcpyDeviceToHost));
+    const long long nb = std::min(nbytes * 8, avail);
+    h->bits_pulled += nb;
+    *n_bits = (size_t)nb;
+  }
+  if (rc != RX_OK) g_err = "pull wait timed out";
+  return rc;
+}
+
+int rx_stats(rx_handle* h, rx_stats_t* out) {
+  if (!h || !out) return fail(RX_EINVAL, "null argument");
+  RX_CK(cudaSetDevice(h->cfg.device));
+  RX_CK(cudaStreamSynchronize(h->s_comp));
+  harvest(h);
+  StreamState st;
+  RX_CK(cudaMemcpy(&st, h->d.st, sizeof(st), cudaMemcpyDeviceToHost));
+  std::memset(out, 0, sizeof(*out));
+  out->samples_in = (uint64_t)h->pushed;
+  out->symbols_out = (uint64_t)h->dec_done;
+  out->frames = (uint64_t)h->frames_done;
+  out->bits = st.bits;
+  out->bit_errors = st.errors;
+  out->ber = st.bits ? (double)st.errors / (double)st.bits : 0.0;
+  out->q_db = 0.0;
+  if (out->ber > 0 && out->ber < 0.5) out->q_db = 20.0 * std::log10(std::sqrt(2.0) * erfcinv_host(2.0 * out->ber));
+  out->evm = st.evm_den > 0 ? st.evm_num / st.evm_den : 0.0;
+  out->cycle_slips = st.slips;
+  out->synced = st.synced;
+  out->sync_delay = st.sync_delay;
+  out->sync_perm = st.sync_perm;
+  out->sync_quadrant_x = st.sync_q[0];
+  out->sync_quadrant_y = st.sync_q[1];
+  out->cma_reinit = st.reinit;
+  const long long last = std::min<long long>(h->f_next, kMaxTrace) - 1;
+  if (last >= 0) {
+    FrameRec r;
+    RX_CK(cudaMemcpy(&r, h->d.rec + last, sizeof(r), cudaMemcpyDeviceToHost));
+    out->fo_hz = r.dfo;
+    out->tau_s = r.tau;
+  }
+  if (!h->lat_ms.empty()) {
+    std::vector<double> v = h->lat_ms;
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double p) { return v[std::min(v.size() - 1, (size_t)std::floor(p * (v.size() - 1) + 0.5))]; };
+    out->latency_p50_ms = pct(0.5);
+    out->latency_p99_ms = pct(0.99);
+  }
+  out->gpu_ms_total = h->gpu_ms;
+  return RX_OK;
+}
+
+int rx_destroy(rx_handle* h) {
+  if (!h) return RX_OK;
+  cudaSetDevice(h->cfg.device);
+  if (h->s_comp) cudaStreamSynchronize(h->s_comp);
+  if (h->s_copy) cudaStreamSynchronize(h->s_copy);
+  free_all(h);
+  delete h;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RX_OK : cuda_fail(e, "rx_destroy");
+}
+
+int rx_reset(rx_handle* h) {
+  if (!h) return fail(RX_EINVAL, "null handle");
+  RX_CK(cudaSetDevice(h->cfg.device));
+  harvest(h);
+  RxDev& d = h->d;
+  cudaStream_t s = h->s_comp;
+  // stream-ordered: runs after all queued frames, before the next stream's work
+  RX_CK(cudaStreamWaitEvent(s, h->ev_copy, 0));
+  StreamState st{};
+  st.bhat_last[0] = st.bhat_last[1] = -1;
+  RX_CK(cudaMemcpyAsync(d.st, &h->st_init, sizeof(st), cudaMemcpyHostToDevice, s));
+  RX_CK(cudaMemcpyAsync(d.Hf, d.Hs, d.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  RX_CK(cudaMemsetAsync(d.acc, 0, sizeof(FrameAcc), s));
+  RX_CK(cudaMemsetAsync(d.psd, 0, (d.N / 2) * sizeof(float), s));
+  RX_CK(cudaMemsetAsync(d.win_err, 0, (size_t)h->n_win_ring * 8 * sizeof(unsigned), s));
+  RX_CK(cudaMemsetAsync(d.rec, 0, kMaxTrace * sizeof(FrameRec), s));
+  if (d.hist_syms > 0) {
+    RX_CK(cudaMemsetAsync(d.hist_y, 0, 2 * d.hist_syms * sizeof(float2), s));
+    RX_CK(cudaMemsetAsync(d.hist_bhat, 0, 2 * d.hist_syms, s));
+    RX_CK(cudaMemsetAsync(d.hist_m, 0, 2 * d.hist_syms * sizeof(int), s));
+  }
+  RX_CK(cudaEventRecord(h->ev_reset, s));
+  h->reset_pending = true;
+  h->gen++;
+  h->pushed = 0;
+  h->n_total = -1;
+  h->ended = false;
+  h->f_next = h->f_waited = 0;
+  h->decided = h->bits_done = h->bits_pulled = h->dec_done = 0;
+  h->synced = h->tail_launched = false;
+  h->w_next = 0;
+  h->lat_ms.clear();
+  h->gpu_ms = 0.0;
+  h->frames_done = 0;
+  return RX_OK;
+}
+
+int rx_join(rx_handle* h, void* cuda_stream) {
+  if (!h) return fail(RX_EINVAL, "null handle");
+  RX_CK(cudaSetDevice(h->cfg.device));
+  cudaEvent_t e = get_event(h);
+  RX_CK(cudaEventRecord(e, h->s_comp));
+  RX_CK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, e, 0));
+  h->ev_pool.push_back(e);
+  return RX_OK;
+}
+
+int rx_stage_times(rx_handle* h, double* ms, int64_t* launches) {
+  if (!h || !ms || !launches) return fail(RX_EINVAL, "null argument");
+  RX_CK(cudaSetDevice(h->cfg.device));
+  RX_CK(cudaStreamSynchronize(h->s_copy));
+  RX_CK(cudaStreamSynchronize(h->s_comp));
+  harvest(h);
+  for (int i = 0; i < RX_NSTAGES; ++i) {
+    ms[i] = h->stage_ms[i];
+    launches[i] = h->stage_n[i];
+  }
+  return RX_OK;
+}
+
+int rx_frame_trace(rx_handle* h, double* out, int cap_frames) {
+  if (!h || !out) return fail(RX_EINVAL, "null argument");
+  RX_CK(cudaSetDevice(h->cfg.device));
+  RX_CK(cudaStreamSynchronize(h->s_comp));
+  const int n = (int)std::min<long long>(std::min<long long>(h->f_next, kMaxTrace), cap_frames);
+  std::vector<FrameRec> r(n);
+  if (n > 0) RX_CK(cudaMemcpy(r.data(), h->d.rec, n * sizeof(FrameRec), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < n; ++i) {
+    out[4 * i + 0] = r[i].tau;
+    out[4 * i + 1] = r[i].dfo;
+    out[4 * i + 2] = r[i].gain;
+    out[4 * i + 3] = r[i].theta;
+  }
+  return n;
+}
+
+int rx_get_taps(rx_handle* h, int which, float* out) {
+  if (!h || !out) return fail(RX_EINVAL, "null argument");
+  if (which < -1 || which >= h->d.G) return fail(RX_EINVAL, "no such chain");
+  RX_CK(cudaSetDevice(h->cfg.device));
+  RX_CK(cudaStreamSynchronize(h->s_comp));
+  const float2* src = which < 0 ? h->d.w_acq : h->d.chains + (size_t)which * 4 * h->d.T;
+  RX_CK(cudaMemcpy(out, src, 4 * h->d.T * sizeof(float2), cudaMemcpyDeviceToHost));
+  return RX_OK;
+}
+
+int rx_get_equalised(rx_handle* h, int64_t first, int64_t n, float* out) {
+  if (!h || !out) return fail(RX_EINVAL, "null argument");
+  const long long H = h->d.hist_syms;
+  if (first < 0 || n < 0 || first + n > H) return fail(RX_EINVAL, "range outside the inspection history");
+  RX_CK(cudaSetDevice(h->cfg.device));
+  RX_CK(cudaStreamSynchronize(h->s_comp));
+  for (int p = 0; p < 2; ++p)
+    RX_CK(cudaMemcpy(out + 2 * p * n, h->d.hist_y + p * H + first, n * sizeof(float2), cudaMemcpyDeviceToHost));
+  return RX_OK;
+}
+
+int rx_get_phase(rx_handle* h, int64_t first, int64_t n, uint8_t* bhat, int32_t* m) {
+  if (!h || !bhat || !m) return fail(RX_EINVAL, "null argument");
+  const long long H = h->d.hist_syms;
+  if (first < 0 || n < 0 || first + n > H) return fail(RX_EINVAL, "range outside the inspection history");
+  RX_CK(cudaSetDevice(h->cfg.device));
+  RX_CK(cudaStreamSynchronize(h->s_comp));
+  for (int p = 0; p < 2; ++p) {
+    RX_CK(cudaMemcpy(bhat + p * n, h->d.hist_bhat + p * H + first, n, cudaMemcpyDeviceToHost));
+    RX_CK(cudaMemcpy(m + p * n, h->d.hist_m + p * H + first, n * 4, cudaMemcpyDeviceToHost));
+  }
+  return RX_OK;
+}
+
+}  // extern "C"

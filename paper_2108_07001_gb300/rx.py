@@ -1,0 +1,272 @@
+"""ctypes binding of the receiver's C ABI (include/rx.h).
+
+Argument marshalling only: every step of the chain runs in the CUDA
+kernels of librx.so.  Loading fails loudly when the library is missing;
+there is no fallback.  Device buffers come from PyTorch (``data_ptr()``)
+and streams from ``torch.cuda.current_stream().cuda_stream``; numpy arrays
+are pushed from host memory.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librx.so")
+
+RX_OK, RX_EINVAL, RX_ENOMEM, RX_EAGAIN, RX_ETIMEDOUT, RX_EDEVICE, RX_ESTATE = 0, -1, -2, -3, -4, -5, -6
+RX_QPSK, RX_QAM16 = 2, 4
+RX_C128, RX_C64, RX_C16 = 0, 1, 2
+STAGES = ["ingest", "cd", "est", "acquire", "mimo", "bps", "demap", "ber"]
+
+# every function declared in include/rx.h
+EXPORTS = ["rx_config_default", "rx_create", "rx_push_block", "rx_pull_bits", "rx_stats",
+           "rx_destroy", "rx_reset", "rx_join", "rx_stage_times", "rx_last_error",
+           "rx_frame_trace", "rx_get_taps", "rx_get_equalised", "rx_get_phase"]
+
+
+class RxConfig(ctypes.Structure):
+    _fields_ = [
+        ("baud_hz", ctypes.c_double),
+        ("modulation", ctypes.c_int),
+        ("fiber_len_m", ctypes.c_double),
+        ("D_ps_nm_km", ctypes.c_double),
+        ("lambda_m", ctypes.c_double),
+        ("rrc_rolloff", ctypes.c_double),
+        ("fft_n", ctypes.c_int),
+        ("cd_halo", ctypes.c_int),
+        ("mimo_taps", ctypes.c_int),
+        ("bps_angles", ctypes.c_int),
+        ("bps_half_window", ctypes.c_int),
+        ("sub_block_syms", ctypes.c_int),
+        ("seg_syms", ctypes.c_int),
+        ("frame_syms", ctypes.c_int),
+        ("cma_syms", ctypes.c_int),
+        ("acq_syms", ctypes.c_int),
+        ("mu_cma", ctypes.c_float),
+        ("mu_dd", ctypes.c_float),
+        ("timing_gain", ctypes.c_float),
+        ("storage_dtype", ctypes.c_int),
+        ("prbs_seed", ctypes.c_uint64),
+        ("ber_skip_syms", ctypes.c_int),
+        ("sync_syms", ctypes.c_int),
+        ("sync_max_delay", ctypes.c_int),
+        ("slip_window", ctypes.c_int),
+        ("max_block_samples", ctypes.c_size_t),
+        ("history_syms", ctypes.c_int64),
+        ("profile", ctypes.c_int),
+        ("device", ctypes.c_int),
+    ]
+
+
+class RxStats(ctypes.Structure):
+    _fields_ = [
+        ("samples_in", ctypes.c_uint64),
+        ("symbols_out", ctypes.c_uint64),
+        ("frames", ctypes.c_uint64),
+        ("bits", ctypes.c_uint64),
+        ("bit_errors", ctypes.c_uint64),
+        ("ber", ctypes.c_double),
+        ("q_db", ctypes.c_double),
+        ("evm", ctypes.c_double),
+        ("cycle_slips", ctypes.c_uint64),
+        ("synced", ctypes.c_int),
+        ("sync_delay", ctypes.c_int),
+        ("sync_perm", ctypes.c_int),
+        ("sync_quadrant_x", ctypes.c_int),
+        ("sync_quadrant_y", ctypes.c_int),
+        ("cma_reinit", ctypes.c_int),
+        ("fo_hz", ctypes.c_double),
+        ("tau_s", ctypes.c_double),
+        ("latency_p50_ms", ctypes.c_double),
+        ("latency_p99_ms", ctypes.c_double),
+        ("gpu_ms_total", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load librx.so and declare the signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"receiver library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    P, I, SZ, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_int64
+    lib.rx_config_default.argtypes = [ctypes.POINTER(RxConfig)]
+    lib.rx_config_default.restype = None
+    lib.rx_create.argtypes = [ctypes.POINTER(RxConfig), ctypes.POINTER(P)]
+    lib.rx_push_block.argtypes = [P, P, SZ, I, I, P]
+    lib.rx_pull_bits.argtypes = [P, P, SZ, ctypes.POINTER(SZ), I]
+    lib.rx_stats.argtypes = [P, ctypes.POINTER(RxStats)]
+    lib.rx_destroy.argtypes = [P]
+    lib.rx_reset.argtypes = [P]
+    lib.rx_join.argtypes = [P, P]
+    lib.rx_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)]
+    lib.rx_last_error.argtypes = []
+    lib.rx_last_error.restype = ctypes.c_char_p
+    lib.rx_frame_trace.argtypes = [P, ctypes.POINTER(ctypes.c_double), I]
+    lib.rx_get_taps.argtypes = [P, I, ctypes.POINTER(ctypes.c_float)]
+    lib.rx_get_equalised.argtypes = [P, I64, I64, ctypes.POINTER(ctypes.c_float)]
+    lib.rx_get_phase.argtypes = [P, I64, I64, ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_int32)]
+    for name in ["rx_create", "rx_push_block", "rx_pull_bits", "rx_stats", "rx_destroy", "rx_reset",
+                 "rx_join", "rx_stage_times", "rx_frame_trace", "rx_get_taps", "rx_get_equalised",
+                 "rx_get_phase"]:
+        getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+class RxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rx error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise RxError(rc, load().rx_last_error().decode())
+    return rc
+
+
+def default_config(**overrides) -> RxConfig:
+    cfg = RxConfig()
+    load().rx_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise KeyError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+_DT = {np.dtype(np.complex128): RX_C128, np.dtype(np.complex64): RX_C64}
+
+
+class Receiver:
+    """One receiver stream (rx_create ... rx_destroy)."""
+
+    def __init__(self, cfg: RxConfig | None = None, **overrides):
+        self.lib = load()
+        self.cfg = cfg if cfg is not None else default_config(**overrides)
+        h = ctypes.c_void_p()
+        _check(self.lib.rx_create(ctypes.byref(self.cfg), ctypes.byref(h)))
+        self.h = h
+
+    # -- pushing --
+    def push_device(self, ptr: int, n_per_pol: int, dtype: int, stream: int = 0) -> None:
+        """Push n_per_pol samples from device memory at ptr (planar [2][n])."""
+        _check(self.lib.rx_push_block(self.h, ctypes.c_void_p(ptr), n_per_pol, dtype, 1, ctypes.c_void_p(stream)))
+
+    def push_host(self, x: np.ndarray, stream: int = 0) -> None:
+        """Push a host array: complex [2, n] (c128/c64) or float16 [2, n, 2] (c16)."""
+        if x.dtype == np.float16:
+            dt = RX_C16
+            n = x.shape[1]
+        else:
+            dt = _DT[x.dtype]
+            n = x.shape[1]
+        x = np.ascontiguousarray(x)
+        _check(self.lib.rx_push_block(self.h, x.ctypes.data_as(ctypes.c_void_p), n, dt, 0, ctypes.c_void_p(stream)))
+
+    def push_tensor(self, t, stream: int | None = None) -> None:
+        """Push a CUDA tensor: complex [2, n] (complex128/complex64) or
+        float16 [2, n, 2]."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        if t.dtype == torch.float16:
+            dt, n = RX_C16, t.shape[1]
+        elif t.dtype == torch.complex128:
+            dt, n = RX_C128, t.shape[1]
+        elif t.dtype == torch.complex64:
+            dt, n = RX_C64, t.shape[1]
+        else:
+            raise TypeError(t.dtype)
+        assert t.is_cuda and t.is_contiguous()
+        self.push_device(t.data_ptr(), n, dt, stream)
+
+    def end(self) -> None:
+        _check(self.lib.rx_push_block(self.h, None, 0, RX_C64, 0, None))
+
+    # -- results --
+    def pull_bits(self, cap_bytes: int, timeout_ms: int = -1) -> np.ndarray:
+        """Returns the decided bits as a uint8 array of 0/1 values."""
+        buf = np.empty(max(cap_bytes, 1), dtype=np.uint8)
+        nb = ctypes.c_size_t(0)
+        rc = self.lib.rx_pull_bits(self.h, buf.ctypes.data_as(ctypes.c_void_p), cap_bytes, ctypes.byref(nb), timeout_ms)
+        if rc not in (RX_OK, RX_ETIMEDOUT):
+            _check(rc)
+        n = nb.value
+        return np.unpackbits(buf[:(n + 7) // 8])[:n]
+
+    def pull_bytes(self, out: np.ndarray, timeout_ms: int = -1) -> int:
+        nb = ctypes.c_size_t(0)
+        rc = self.lib.rx_pull_bits(self.h, out.ctypes.data_as(ctypes.c_void_p), out.nbytes, ctypes.byref(nb), timeout_ms)
+        if rc not in (RX_OK, RX_ETIMEDOUT):
+            _check(rc)
+        return nb.value
+
+    def stats(self) -> dict:
+        s = RxStats()
+        _check(self.lib.rx_stats(self.h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def stage_times(self) -> dict:
+        ms = (ctypes.c_double * len(STAGES))()
+        n = (ctypes.c_int64 * len(STAGES))()
+        _check(self.lib.rx_stage_times(self.h, ms, n))
+        return {STAGES[i]: (ms[i], n[i]) for i in range(len(STAGES))}
+
+    def frame_trace(self, cap: int = 4096) -> np.ndarray:
+        out = np.zeros(4 * cap, dtype=np.float64)
+        n = _check(self.lib.rx_frame_trace(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cap))
+        return out[:4 * n].reshape(n, 4)
+
+    def taps(self, which: int = -1) -> np.ndarray:
+        T = self.cfg.mimo_taps
+        out = np.zeros(8 * T, dtype=np.float32)
+        _check(self.lib.rx_get_taps(self.h, which, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out.view(np.complex64).reshape(2, 2, T)
+
+    def equalised(self, first: int, n: int) -> np.ndarray:
+        out = np.zeros(4 * n, dtype=np.float32)
+        _check(self.lib.rx_get_equalised(self.h, first, n, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out.view(np.complex64).reshape(2, n)
+
+    def phase(self, first: int, n: int):
+        b = np.zeros(2 * n, dtype=np.uint8)
+        m = np.zeros(2 * n, dtype=np.int32)
+        _check(self.lib.rx_get_phase(self.h, first, n, b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                     m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return b.reshape(2, n), m.reshape(2, n)
+
+    def reset(self) -> None:
+        _check(self.lib.rx_reset(self.h))
+
+    def join(self, stream: int) -> None:
+        _check(self.lib.rx_join(self.h, ctypes.c_void_p(stream)))
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.rx_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,139 @@
+"""Helpers shared by the GPU parity tests: run the CUDA receiver through the
+C ABI and the FP64 oracle on the same seeded samples, then compare.
+
+Tolerances (stated where used):
+  equalised symbols  rel RMS <= 1e-4 (FP32 path vs FP64 oracle);
+  BPS angle          the GPU's angle is the oracle's, or a near-tie of it:
+                     D_or[b_gpu] - min_b D_or <= 1e-4 * min_b D_or;
+  unwrapped phase    equal wherever the angles are equal;
+  bits               identical except for symbols whose oracle-corrected value
+                     lies within 1e-3 of a decision threshold or whose BPS
+                     angle is a near-tie.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import rxsim
+from oracle import rx_oracle as O
+
+Y_TOL = 1e-4
+BOUNDARY = 1e-3
+TIE = 1e-4
+
+
+def run_gpu(samples: np.ndarray, rx_kw: dict, pushes=None, dtype=None, history=True):
+    """Push samples (host array [2, n] complex or [2, n, 2] float16) in the given
+    block sizes from device memory; returns results and the receiver."""
+    import torch
+    from paper_2108_07001_gb300 import rx
+
+    n = samples.shape[1]
+    n_sym = n // 2
+    kw = dict(rx_kw)
+    if history:
+        kw["history_syms"] = n_sym
+    pushes = pushes or [n]
+    kw.setdefault("max_block_samples", max(max(pushes), 1))
+    r = rx.Receiver(**kw)
+    dev = torch.from_numpy(np.ascontiguousarray(samples)).to("cuda:0")
+    stream = torch.cuda.current_stream().cuda_stream
+    pos = 0
+    bits = []
+    for m in pushes:
+        blk = dev[:, pos:pos + m].contiguous()
+        r.push_tensor(blk, stream)
+        pos += m
+        bits.append(r.pull_bits(1 << 22, timeout_ms=0))
+    assert pos == n
+    r.end()
+    bits.append(r.pull_bits(1 << 24, timeout_ms=-1))
+    torch.cuda.synchronize()
+    out = {"bits": np.concatenate(bits), "stats": r.stats(), "trace": r.frame_trace()}
+    if history:
+        out["y"] = r.equalised(0, n_sym)
+        out["bhat"], out["m"] = r.phase(0, n_sym)
+    return out, r
+
+
+def run_oracle(samples: np.ndarray, rx_kw: dict):
+    from paper_2108_07001_gb300.workloads import oracle_kwargs
+    if samples.dtype == np.float16:
+        x = samples[..., 0].astype(np.float64) + 1j * samples[..., 1].astype(np.float64)
+    else:
+        x = samples.astype(np.complex128)
+    return O.Receiver(O.RxConfig(**oracle_kwargs(rx_kw))).run(x)
+
+
+def rel_rms(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def oracle_bps_metric(y: np.ndarray, k: np.ndarray, B: int, W: int, bits_per_sym: int) -> np.ndarray:
+    """D_{k,b} of the oracle's definition for the listed symbols k."""
+    n = y.size
+    phi = O.bps_angles(B)
+    out = np.zeros((k.size, B))
+    for i in range(-W, W + 1):
+        kk = k + i
+        ok = (kk >= 0) & (kk < n)
+        z = y[np.clip(kk, 0, n - 1)][:, None] * np.exp(-1j * phi)[None, :]
+        d = np.abs(z - O.decide(z, bits_per_sym)) ** 2
+        out += np.where(ok[:, None], d, 0.0)
+    return out
+
+
+def compare(gpu: dict, ref: dict, rx_kw: dict, check_bits=True) -> dict:
+    """All parity checks; returns a report (asserts on failure)."""
+    B = rx_kw.get("bps_angles", 64)
+    W = rx_kw.get("bps_half_window", 16)
+    bps = rx_kw.get("modulation", 2)
+    rep = {}
+    y_err = rel_rms(gpu["y"], ref["y"])
+    rep["y_rel_rms"] = y_err
+    assert y_err <= Y_TOL, f"equalised symbols: rel RMS {y_err:.3e} > {Y_TOL}"
+
+    # BPS angles: equal, or a near-tie under the oracle's own metric
+    bh_g = gpu["bhat"].astype(np.int64)
+    bh_o = ref["bhat"]
+    tie = np.zeros_like(bh_o, dtype=bool)
+    for p in range(2):
+        diff = np.nonzero(bh_g[p] != bh_o[p])[0]
+        if diff.size:
+            D = oracle_bps_metric(ref["y"][p], diff, B, W, bps)
+            dmin = D.min(axis=1)
+            dg = D[np.arange(diff.size), bh_g[p][diff]]
+            ok = dg - dmin <= TIE * dmin
+            assert ok.all(), f"pol {p}: {np.sum(~ok)} BPS angles are not near-ties"
+            tie[p, diff] = True
+    rep["bps_ties"] = int(tie.sum())
+    # unwrapped phase: angles equal -> phase equal (same unwrap counter modulo the
+    # branch shift a near-tie across the grid edge produces)
+    phi = O.bps_angles(B)
+    ph_g = phi[bh_g] + gpu["m"] * (math.pi / 2)
+    ph_o = phi[bh_o] + ref["m"] * (math.pi / 2)
+    dph = np.abs(ph_g - ph_o)
+    assert np.all(dph[~tie] < 1e-9), "unwrap counters differ where the BPS angles agree"
+    assert np.all(dph <= math.pi / 2 / B + 1e-9), "unwrapped phase differs by more than one grid step"
+
+    if check_bits:
+        # bits: symbol-major, pol x then y, I bits then Q bits
+        n_sym = ref["y"].shape[1]
+        sb = 2 * bps
+        gb = gpu["bits"][:n_sym * sb].reshape(n_sym, 2, bps)
+        ob = np.stack([ref["bits"][0], ref["bits"][1]], axis=1)  # [n, 2, bps]
+        assert gb.shape == ob.shape, (gb.shape, ob.shape)
+        mism = np.any(gb != ob, axis=2)  # [n, 2]
+        lv = O.levels(bps)
+        thr = 0.5 * (lv[1:] + lv[:-1])
+        zc = ref["zc"].T  # [n, 2]
+        near = np.zeros_like(mism)
+        for t in thr:
+            near |= (np.abs(zc.real - t) < BOUNDARY) | (np.abs(zc.imag - t) < BOUNDARY)
+        explained = near | tie.T
+        bad = mism & ~explained
+        rep["bit_mismatch_syms"] = int(mism.sum())
+        assert not bad.any(), f"{int(bad.sum())} decisions differ without a near-boundary or near-tie reason"
+    return rep

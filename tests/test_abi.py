@@ -1,0 +1,122 @@
+"""The C-ABI library: builds, loads, exports every declared entry point,
+struct layouts agree between C and the binding, and argument checks work
+without a GPU (no compute calls)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rx.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2108_07001_gb300 import build, rx
+    build.build()
+    return rx.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rx_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2108_07001_gb300 import rx
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(rx.EXPORTS) == names
+
+
+def test_struct_layout_matches_c(tmp_path, lib):
+    from paper_2108_07001_gb300 import rx
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "rx.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(rx_config), sizeof(rx_stats_t),"
+        " offsetof(rx_config, prbs_seed), offsetof(rx_config, device), offsetof(rx_stats_t, fo_hz),"
+        " offsetof(rx_config, history_syms)); return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals == [ctypes.sizeof(rx.RxConfig), ctypes.sizeof(rx.RxStats), rx.RxConfig.prbs_seed.offset,
+                    rx.RxConfig.device.offset, rx.RxStats.fo_hz.offset, rx.RxConfig.history_syms.offset]
+
+
+def test_defaults(lib):
+    from paper_2108_07001_gb300 import rx
+    c = rx.default_config()
+    assert c.baud_hz == 28e9 and c.modulation == rx.RX_QPSK and c.mimo_taps == 15
+    assert c.bps_angles == 64 and c.bps_half_window == 16 and c.sub_block_syms == 64
+    assert c.frame_syms == 65536 and c.seg_syms == 512 and c.storage_dtype == rx.RX_C64
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("mimo_taps", 16, "mimo_taps"),
+    ("mimo_taps", 33, "mimo_taps"),
+    ("bps_angles", 48, "bps_angles"),
+    ("bps_half_window", 5, "bps_half_window"),
+    ("sub_block_syms", 32, "sub_block_syms"),
+    ("seg_syms", 100, "seg_syms"),
+    ("frame_syms", 1000, "frame_syms"),
+    ("acq_syms", 1 << 20, "acq_syms"),
+    ("storage_dtype", 0, "storage_dtype"),
+    ("modulation", 3, "modulation"),
+    ("baud_hz", 0.0, "baud_hz"),
+    ("fft_n", 3000, "fft_n"),
+    ("fft_n", 1024, "halo"),
+])
+def test_invalid_config_is_rejected(lib, field, value, msg):
+    from paper_2108_07001_gb300 import rx
+    kw = {field: value}
+    if msg == "halo":
+        kw["fiber_len_m"] = 10000e3
+    c = rx.default_config(**kw)
+    h = ctypes.c_void_p()
+    rc = lib.rx_create(ctypes.byref(c), ctypes.byref(h))
+    assert rc == rx.RX_EINVAL
+    assert msg in lib.rx_last_error().decode()
+    assert not h.value
+
+
+def test_ber_frame_rule(lib):
+    from paper_2108_07001_gb300 import rx
+    c = rx.default_config(prbs_seed=5, frame_syms=4096, acq_syms=2048, cma_syms=1024)
+    h = ctypes.c_void_p()
+    assert lib.rx_create(ctypes.byref(c), ctypes.byref(h)) == rx.RX_EINVAL
+    assert "sync" in lib.rx_last_error().decode()
+
+
+def test_null_arguments(lib):
+    from paper_2108_07001_gb300 import rx
+    assert lib.rx_create(None, None) == rx.RX_EINVAL
+    assert lib.rx_push_block(None, None, 0, 1, 0, None) == rx.RX_EINVAL
+    assert lib.rx_stats(None, None) == rx.RX_EINVAL
+    assert lib.rx_destroy(None) == rx.RX_OK
+
+
+def test_valid_config_without_device(lib):
+    import torch
+    from paper_2108_07001_gb300 import rx
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    c = rx.default_config()
+    h = ctypes.c_void_p()
+    assert lib.rx_create(ctypes.byref(c), ctypes.byref(h)) == rx.RX_EDEVICE
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    from paper_2108_07001_gb300 import rx
+    old = rx._lib
+    rx._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="not built"):
+            rx.load(str(tmp_path / "missing.so"))
+    finally:
+        rx._lib = old

@@ -1,0 +1,198 @@
+"""GPU parity: the CUDA receiver (through the C ABI) against the FP64 oracle
+on the same seeded inputs.  Tolerances are in tests/parity_util.py."""
+import math
+
+import numpy as np
+import pytest
+
+import rxsim
+from paper_2108_07001_gb300 import workloads
+from parity_util import compare, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def link(**kw):
+    return rxsim.LinkConfig(**kw)
+
+
+def test_config0_parity():
+    """DP-QPSK 28 GBd, 2^16 symbols, complex128 input, 1,000 km, all
+    impairments at 12 dB: one frame, pushed whole."""
+    wl = workloads.DP_QPSK_1000KM
+    sim = rxsim.simulate(link(**wl["link"]))
+    gpu, r = run_gpu(sim["rx"], wl["rx"])
+    ref = run_oracle(sim["rx"], wl["rx"])
+    rep = compare(gpu, ref, wl["rx"])
+    st = gpu["stats"]
+    b = ref["ber"]
+    assert st["synced"] == 1
+    assert (st["sync_delay"], st["sync_perm"]) == (b["sync"]["delay"], b["sync"]["perm"])
+    assert st["bits"] == b["bits"]
+    assert abs(int(st["bit_errors"]) - b["errors"]) <= 2 * rep.get("bit_mismatch_syms", 0) * 2 + 2
+    assert st["cycle_slips"] == b["slips"]
+    assert abs(st["evm"] - b["evm"]) <= 1e-3 * b["evm"] + 1e-6
+    tr = gpu["trace"]
+    assert abs(tr[0, 0] - ref["trace"]["tau"][0]) * 28e9 < 1e-4
+    assert abs(tr[0, 1] - ref["trace"]["dfo"][0]) < 1e3
+    assert abs(tr[0, 2] - ref["trace"]["gain"][0]) < 1e-5
+    r.close()
+
+
+def test_multi_frame_ragged_pushes():
+    """Four frames plus a ragged tail, pushed in irregular blocks: state
+    (OLS overlap, FO phase, timing, adaptive chains, BPS window, unwrap)
+    carried across pushes and frames."""
+    F = 1 << 13
+    n_sym = 4 * F + 1234
+    sim = rxsim.simulate(link(n_sym=n_sym, snr_db=11.0, fiber_len_m=2000e3, prbs_seed=31, seed=1234,
+                              out_dtype="c64"))
+    rx_kw = dict(fiber_len_m=2000e3, frame_syms=F, acq_syms=F, cma_syms=4096, prbs_seed=31, seg_syms=512)
+    n = sim["rx"].shape[1]
+    pushes = []
+    rng = np.random.default_rng(3)
+    left = n
+    while left:
+        m = int(min(left, rng.integers(1, 9000)))
+        pushes.append(m)
+        left -= m
+    gpu, r = run_gpu(sim["rx"], rx_kw, pushes=pushes)
+    ref = run_oracle(sim["rx"], rx_kw)
+    compare(gpu, ref, rx_kw)
+    tr = gpu["trace"]
+    assert tr.shape[0] == len(ref["trace"]["tau"]) == 5
+    assert np.allclose(tr[:, 0], ref["trace"]["tau"], atol=1e-4 / 28e9)
+    assert np.allclose(tr[:, 1], ref["trace"]["dfo"], atol=2e3)
+    assert np.allclose(tr[:, 2], ref["trace"]["gain"], rtol=1e-5)
+    assert np.allclose(np.unwrap(tr[:, 3]), np.unwrap(ref["trace"]["theta"]), atol=1e-4)
+    st = gpu["stats"]
+    assert st["bits"] == ref["ber"]["bits"]
+    r.close()
+
+
+def test_qam16_parity():
+    """DP-16QAM 32 GBd, T = 25, B = 32, W = 32 over 5,000 km at 18 dB."""
+    sim = rxsim.simulate(link(baud_hz=32e9, bits_per_sym=4, n_sym=1 << 15, fiber_len_m=5000e3, snr_db=18.0,
+                              prbs_seed=17, seed=1002, out_dtype="c64"))
+    rx_kw = dict(baud_hz=32e9, modulation=4, fiber_len_m=5000e3, mimo_taps=25, bps_angles=32,
+                 bps_half_window=32, frame_syms=1 << 15, prbs_seed=17, mu_dd=2e-3)
+    gpu, r = run_gpu(sim["rx"], rx_kw)
+    ref = run_oracle(sim["rx"], rx_kw)
+    compare(gpu, ref, rx_kw)
+    assert gpu["stats"]["bits"] == ref["ber"]["bits"]
+    r.close()
+
+
+def test_fp16_storage_parity():
+    """Complex-half storage: the oracle runs on the same half-precision
+    samples, so only the arithmetic differs."""
+    sim = rxsim.simulate(link(n_sym=1 << 15, snr_db=12.0, fiber_len_m=1000e3, prbs_seed=5, seed=55,
+                              out_dtype="c16"))
+    rx_kw = dict(fiber_len_m=1000e3, frame_syms=1 << 15, prbs_seed=5, storage_dtype=2)
+    gpu, r = run_gpu(sim["rx"], rx_kw)
+    ref = run_oracle(sim["rx"], rx_kw)
+    compare(gpu, ref, rx_kw)
+    r.close()
+
+
+def test_c128_input_equals_c64_input_rounded():
+    sim = rxsim.simulate(link(n_sym=1 << 14, snr_db=12.0, fiber_len_m=800e3, seed=66))
+    rx_kw = dict(fiber_len_m=800e3, frame_syms=1 << 14, acq_syms=8192)
+    g1, r1 = run_gpu(sim["rx"], rx_kw)
+    g2, r2 = run_gpu(sim["rx"].astype(np.complex64), rx_kw)
+    assert np.array_equal(g1["y"], g2["y"])
+    r1.close()
+    r2.close()
+
+
+def test_noiseless_stream_is_error_free():
+    sim = rxsim.simulate(link(n_sym=1 << 16, snr_db=None, fiber_len_m=3000e3, prbs_seed=8, seed=8,
+                              out_dtype="c64"))
+    rx_kw = dict(fiber_len_m=3000e3, frame_syms=1 << 14, acq_syms=8192, prbs_seed=8)
+    gpu, r = run_gpu(sim["rx"], rx_kw, pushes=[1 << 15] * 4, history=False)
+    st = gpu["stats"]
+    assert st["synced"] and st["bit_errors"] == 0 and st["cycle_slips"] == 0 and st["bits"] > 400000
+    r.close()
+
+
+# ------------------------------------------------------------ edge cases ---
+
+def test_empty_stream_and_state_errors():
+    from paper_2108_07001_gb300 import rx
+    r = rx.Receiver(frame_syms=4096, acq_syms=2048, cma_syms=1024)
+    r.end()
+    assert r.pull_bits(16).size == 0
+    with pytest.raises(rx.RxError) as e:
+        r.push_host(np.zeros((2, 8), np.complex64))
+    assert e.value.code == rx.RX_ESTATE
+    r.close()
+
+
+def test_push_too_large_and_bad_dtype():
+    import ctypes
+    from paper_2108_07001_gb300 import rx
+    r = rx.Receiver(frame_syms=4096, acq_syms=2048, cma_syms=1024, max_block_samples=1000)
+    with pytest.raises(rx.RxError) as e:
+        r.push_host(np.zeros((2, 1001), np.complex64))
+    assert e.value.code == rx.RX_EINVAL
+    x = np.zeros((2, 10), np.complex64)
+    assert r.lib.rx_push_block(r.h, x.ctypes.data_as(ctypes.c_void_p), 10, 7, 0, None) == rx.RX_EINVAL
+    r.close()
+
+
+def test_stream_shorter_than_acquisition():
+    sim = rxsim.simulate(link(n_sym=3000, snr_db=15.0, fiber_len_m=300e3, seed=3))
+    rx_kw = dict(fiber_len_m=300e3, frame_syms=4096, acq_syms=4096, cma_syms=2048)
+    gpu, r = run_gpu(sim["rx"], rx_kw)
+    ref = run_oracle(sim["rx"], rx_kw)
+    compare(gpu, ref, rx_kw, check_bits=True)
+    assert gpu["bits"].size == 3000 * 4
+    r.close()
+
+
+def test_backpressure_when_bits_are_not_pulled():
+    import torch
+    from paper_2108_07001_gb300 import rx
+    r = rx.Receiver(frame_syms=1 << 16, max_block_samples=1 << 17)
+    x = torch.zeros((2, 1 << 17), dtype=torch.complex64, device="cuda:0")
+    codes = []
+    for _ in range(64):
+        try:
+            r.push_tensor(x)
+        except rx.RxError as e:
+            codes.append(e.code)
+            break
+    assert codes == [rx.RX_EAGAIN]
+    got = r.pull_bits(1 << 22)
+    assert got.size > 0
+    r.push_tensor(x)  # room again
+    r.close()
+
+
+def test_reset_reproduces_the_stream():
+    sim = rxsim.simulate(link(n_sym=1 << 14, snr_db=12.0, fiber_len_m=600e3, prbs_seed=4, seed=4,
+                              out_dtype="c64"))
+    rx_kw = dict(fiber_len_m=600e3, frame_syms=1 << 14, acq_syms=8192, prbs_seed=4)
+    g1, r = run_gpu(sim["rx"], rx_kw)
+    r.reset()
+    import torch
+    r.push_tensor(torch.from_numpy(sim["rx"]).to("cuda:0"))
+    r.end()
+    bits = r.pull_bits(1 << 20)
+    assert np.array_equal(bits, g1["bits"])
+    assert r.stats()["bit_errors"] == g1["stats"]["bit_errors"]
+    r.close()
+
+
+def test_host_push_equals_device_push():
+    sim = rxsim.simulate(link(n_sym=1 << 14, snr_db=12.0, fiber_len_m=600e3, seed=9, out_dtype="c64"))
+    rx_kw = dict(fiber_len_m=600e3, frame_syms=1 << 14, acq_syms=8192)
+    g1, r1 = run_gpu(sim["rx"], rx_kw)
+    from paper_2108_07001_gb300 import rx
+    r2 = rx.Receiver(**rx_kw, max_block_samples=1 << 15)
+    r2.push_host(sim["rx"])
+    r2.end()
+    bits = r2.pull_bits(1 << 20)
+    assert np.array_equal(bits, g1["bits"])
+    r1.close()
+    r2.close()
