@@ -114,7 +114,10 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     import rxsim
     t0 = time.time()
-    sim = rxsim.simulate(rxsim.LinkConfig(**wl["link"]))
+    lk = dict(wl["link"])
+    if args.symbols:
+        lk["n_sym"] = args.symbols
+    sim = rxsim.simulate(rxsim.LinkConfig(**lk))
     x = sim["rx"]  # [2, 2^25] complex64
     del sim
     gen_s = time.time() - t0
@@ -126,44 +129,51 @@ def run_ours(args):
     del x
     dx = torch.from_numpy(blocks).to(dev)  # resident in HBM
     stream = torch.cuda.current_stream().cuda_stream
-    cfg = rx.default_config(**wl["rx"], profile=1)
-    r = rx.Receiver(cfg)
+    cfg = rx.default_config(**wl["rx"])
+    r = rx.Receiver(cfg)                                 # timed for the value
+    rp = rx.Receiver(rx.default_config(**wl["rx"], profile=1))  # per-stage CUDA-event timings
     lib = r.lib
     base = dx.data_ptr()
     bbytes = 2 * m * 8
     out_bytes = n_sym * 2 * cfg.modulation // 8
     outbuf = np.empty(out_bytes + 16, dtype=np.uint8)
 
-    def step():
-        r.reset()
+    def step(rr):
+        rr.reset()
         for b in range(nb):
-            rc = lib.rx_push_block(r.h, ctypes.c_void_p(base + b * bbytes), m, rx.RX_C64, 1, ctypes.c_void_p(stream))
+            rc = lib.rx_push_block(rr.h, ctypes.c_void_p(base + b * bbytes), m, rx.RX_C64, 1, ctypes.c_void_p(stream))
             if rc:
                 raise rx.RxError(rc, lib.rx_last_error().decode())
-        r.end()
-        r.join(stream)
+        rr.end()
+        rr.join(stream)
 
-    for _ in range(args.warmup):
-        step()
-        r.pull_bytes(outbuf)
+    def timed(rr, steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        h0 = time.perf_counter()
+        for _ in range(steps):
+            step(rr)
+        h1 = time.perf_counter()
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1), h0, h1
+
+    for rr in (r, rp):
+        for _ in range(args.warmup):
+            step(rr)
+            rr.pull_bytes(outbuf)
     torch.cuda.synchronize()
-    before = r.stage_times()
     clk = ClockSampler()
     clk.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record()
-    host0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    host1 = time.perf_counter()
-    ev1.record()
-    torch.cuda.synchronize()
+    total_ms, host0, host1 = timed(r, args.steps)
     clocks = clk.stop()
-    after = r.stage_times()
-    stage_tot = {k: [after[k][0] - before[k][0], after[k][1] - before[k][1]] for k in rx.STAGES}
     stats = r.stats()
-    total_ms = ev0.elapsed_time(ev1)
+    before = rp.stage_times()
+    prof_ms, _, _ = timed(rp, args.steps)
+    after = rp.stage_times()
+    stage_tot = {k: [after[k][0] - before[k][0], after[k][1] - before[k][1]] for k in rx.STAGES}
+    rp.close()
     ms_step = total_ms / args.steps
     samples_step = 2 * n_samp
     bits_step = n_sym * 2 * cfg.modulation
@@ -201,6 +211,9 @@ def run_ours(args):
     gpu_launches = int(sum(v[1] for v in stage_tot.values()))
 
     # e2e: the same stream from pinned host memory, bits read back to the host
+    if not args.e2e:
+        return finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, other_ms,
+                      gpu_launches, clocks, host0, host1, gen_s, None)
     hx = torch.from_numpy(blocks).pin_memory()
     hbase = hx.data_ptr()
 
@@ -226,6 +239,12 @@ def run_ours(args):
            "h2d_bytes_per_step": int(blocks.nbytes), "d2h_bytes_per_step": int(out_bytes),
            "ms_per_step": round(e_s * 1e3, 2)}
 
+    return finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, other_ms,
+                  gpu_launches, clocks, host0, host1, gen_s, e2e)
+
+
+def finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, other_ms,
+           gpu_launches, clocks, host0, host1, gen_s, e2e):
     cpu = cpu_baseline(wl) if args.cpu_baseline else None
     line = {
         "metric": "gsamples_per_s", "value": round(value, 3), "unit": "Gsamples/s",
@@ -241,6 +260,7 @@ def run_ours(args):
         "cycle_slips": stats["cycle_slips"], "latency_p50_ms": round(stats["latency_p50_ms"], 3),
         "latency_p99_ms": round(stats["latency_p99_ms"], 3),
         "roofline": roof, "stages": stages, "other_stage_ms": other_ms,
+        "stage_timing": "per-stage CUDA events on a second, profiled handle over the same timed protocol",
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
         "host_launch_s_per_step": round((host1 - host0) / args.steps, 4), "sim_seconds": round(gen_s, 1),
     }
@@ -298,6 +318,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--symbols", type=int, default=0, help="stream length per pol (default: the workload's 2^24)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

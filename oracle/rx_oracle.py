@@ -14,7 +14,8 @@ The chain (per stream, both polarisations processed jointly):
       spectrum, tau_{f+1} = tau_f + gain * residual; frame 0 is first
       estimated with tau = 0 (acquisition pass).
   a2  frequency offset: Welch-averaged periodogram of the 4th power of the
-      symbol-spaced compensated samples, argmax + 3-point parabolic refine;
+      symbol-spaced compensated samples, argmax + 3-point refine on the log
+      (a frame shorter than 4096 symbols keeps the previous estimate);
       removed with a phase-continuous rotation together with the frame AGC.
   a4  2x2 butterfly FIR, T taps at T/2 spacing, one output per symbol.
   a5  block-LMS adaptation, one tap update per sub-block of K symbols with
@@ -41,6 +42,7 @@ import math
 import numpy as np
 
 C_LIGHT = 299792458.0
+FOE_MIN_SYMS = 4096  # a frame shorter than this keeps the previous FO estimate
 
 # Which functions are pinned by independent checks (tests/test_oracle_*.py).
 PIN_STATUS = {
@@ -609,6 +611,8 @@ class Receiver:
                 tau = timing_residual(acc0["C"], Rs)
             z, acc = self._cd_frame(x, n_samp, s0, s1, tau, f0, f1, True)
             dfo = foe_from_periodogram(acc["S"], Rs)
+            if f > 0 and Ff < FOE_MIN_SYMS:  # too short for its own estimate
+                dfo = trace["dfo"][-1]
             P = acc["P"] / (2.0 * (f1 - f0))
             gain = 1.0 / math.sqrt(P) if P > 0 else 1.0
             om = 2.0 * math.pi * dfo / g.fs

@@ -14,6 +14,8 @@
 
 namespace rx {
 
+constexpr int kTwSplit = 128;  // two-level twiddle split (N <= 128 * 128)
+
 __device__ __forceinline__ int swz(int i) { return i ^ ((i >> 4) & 15); }
 
 // exp(-2 pi i m / 16) for forward (INV = false), conjugate for inverse.
@@ -111,8 +113,14 @@ __device__ __forceinline__ void dft<16, false>(float2 (&v)[16]) { dft16_impl<fal
 template <>
 __device__ __forceinline__ void dft<16, true>(float2 (&v)[16]) { dft16_impl<true>(v); }
 
-// One Stockham pass.  tw[k * tws] = exp(-2 pi i k / (N * tws)) for the
-// table's full size; inverse passes conjugate it.
+// Twiddle exp(-2 pi i m / Nt) from the two-level shared table of the
+// transform size Nt = N * tws: tw_s[hi] = exp(-2 pi i (hi kTwSplit)/Nt),
+// tw_s[kTwSplit + lo] = exp(-2 pi i lo / Nt), m = hi kTwSplit + lo.
+__device__ __forceinline__ float2 twiddle(const float2* tw_s, int m) {
+  return cmul(tw_s[m / kTwSplit], tw_s[kTwSplit + (m % kTwSplit)]);
+}
+
+// One Stockham pass.  Inverse passes conjugate the twiddles.
 template <int N, int NT, int R, int NS, bool INV>
 __device__ __forceinline__ void fft_pass(float2* buf, const float2* __restrict__ tw, int tws) {
   constexpr int NB = N / R;
@@ -136,7 +144,7 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* __restrict__
         constexpr int STEP = N / (NS * R);
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          float2 w = __ldg(&tw[(r * k * STEP) * tws]);
+          float2 w = twiddle(tw, (r * k * STEP) * tws);
           if (INV) w.y = -w.y;
           v[u][r] = cmul(v[u][r], w);
         }

@@ -26,23 +26,26 @@ __device__ __forceinline__ uint32_t gf2_apply(const uint32_t* __restrict__ M, ui
   return r;
 }
 
-__device__ uint32_t prbs_window_at(const RxDev& d, int pol, long long P) {
-  uint32_t s = d.prbs_state0[pol];
+__device__ uint32_t prbs_window_at(const uint32_t* jump, uint32_t s, long long P) {
   for (int i = 0; P > 0; ++i, P >>= 1)
-    if (P & 1) s = gf2_apply(d.prbs_jump + i * 31, s);
+    if (P & 1) s = gf2_apply(jump + i * 31, s);
   return s;
 }
 
 // Bits [B0, B0 + nbits) of each polarisation's PRBS into d.ref (LSB first).
 // B0 = (sym0 - delay) * bps, delay read from the device state if use_delay.
-__global__ void ref_gen_kernel(RxDev d, long long sym0, int nbits, int use_delay) {
+// The jump matrices are staged in shared memory.
+__global__ void __launch_bounds__(128) ref_gen_kernel(RxDev d, long long sym0, int nbits, int use_delay) {
+  __shared__ uint32_t jump_s[48 * 31];
+  for (int i = threadIdx.x; i < 48 * 31; i += blockDim.x) jump_s[i] = d.prbs_jump[i];
+  __syncthreads();
   const int pol = blockIdx.y;
   const int chunk = blockIdx.x * blockDim.x + threadIdx.x;
   const int start = chunk * 1024;
   if (start >= nbits) return;
   const long long delay = use_delay ? d.st->sync_delay : 0;
   const long long B0 = (sym0 - delay) * d.bps;
-  uint32_t s = prbs_window_at(d, pol, B0 + start);
+  uint32_t s = prbs_window_at(jump_s, d.prbs_state0[pol], B0 + start);
   uint32_t* out = d.ref + (long long)pol * d.ref_words + start / 32;
   const int nw = min(32, (nbits - start + 31) / 32);
   unsigned long long acc = 0;
@@ -118,43 +121,69 @@ __global__ void __launch_bounds__(256) sync_kernel(RxDev d) {
     for (int ww = 0; ww < 8; ++ww) s += red[ww][threadIdx.x];
     d.sync_err[cand * 8 + threadIdx.x] = s;
   }
-}
-
-__global__ void sync_select_kernel(RxDev d) {
+  // the last block to finish selects the candidate (atomic counter; no waits)
+  __shared__ int am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = atomicAdd(&d.ber_done[0], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!am_last || threadIdx.x >= 32) return;
+  __threadfence();
   const int ncand = (2 * d.sync_dmax + 1) * 2;
   unsigned best = 0xffffffffu;
-  int bc = 0, bq[2] = {0, 0};
-  for (int c = 0; c < ncand; ++c) {
+  int bc = 0x7fffffff, bq0 = 0, bq1 = 0;
+  for (int c = threadIdx.x; c < ncand; c += 32) {
     unsigned tot = 0;
     int qs[2];
     for (int p = 0; p < 2; ++p) {
       unsigned m = 0xffffffffu;
       int qb = 0;
       for (int q = 0; q < 4; ++q) {
-        const unsigned e = d.sync_err[c * 8 + p * 4 + q];
+        const unsigned e = __ldcg(&d.sync_err[c * 8 + p * 4 + q]);
         if (e < m) { m = e; qb = q; }
       }
       tot += m;
       qs[p] = qb;
     }
-    if (tot < best) { best = tot; bc = c; bq[0] = qs[0]; bq[1] = qs[1]; }
+    if (tot < best) { best = tot; bc = c; bq0 = qs[0]; bq1 = qs[1]; }
   }
-  StreamState* st = d.st;
-  st->sync_delay = bc / 2 - d.sync_dmax;
-  st->sync_perm = bc & 1;
-  st->sync_q[0] = st->q_cur[0] = bq[0];
-  st->sync_q[1] = st->q_cur[1] = bq[1];
-  st->synced = 1;
+  // smallest total, first candidate on ties
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+    const int o0 = __shfl_xor_sync(0xffffffffu, bq0, o), o1 = __shfl_xor_sync(0xffffffffu, bq1, o);
+    if (ob < best || (ob == best && oc < bc)) { best = ob; bc = oc; bq0 = o0; bq1 = o1; }
+  }
+  if (threadIdx.x == 0) {
+    StreamState* st = d.st;
+    st->sync_delay = bc / 2 - d.sync_dmax;
+    st->sync_perm = bc & 1;
+    st->sync_q[0] = st->q_cur[0] = bq0;
+    st->sync_q[1] = st->q_cur[1] = bq1;
+    st->synced = 1;
+    d.ber_done[0] = 0;
+  }
 }
 
 // Errors of symbols [ka, kb) under the four quadrants, per slip window.
-// Threads are aligned so that every warp lies inside one window; the
-// reference holds tx symbols [ka - delay, kb - delay).
-__global__ void __launch_bounds__(256) ber_count_kernel(RxDev d, long long ka, long long kb, int n_win_ring) {
+// Blocks of 256 symbols are aligned to ks, so each lies inside one window
+// (slip_window is a multiple of 256 or 256 a multiple of it is not needed:
+// windows are multiples of 32 and warps reduce separately when a block
+// straddles windows).  The reference holds tx symbols [ka - delay, kb - delay).
+// The last block to finish runs the slip pass over windows [w_from, w_to).
+__device__ void slip_pass(const RxDev& d, long long w_from, long long w_to, long long k_lim, int n_win_ring,
+                          unsigned* win_s);
+
+__global__ void __launch_bounds__(256) ber_count_kernel(RxDev d, long long ka, long long kb, long long w_from,
+                                                        long long w_to, long long k_lim, int n_win_ring) {
+  __shared__ unsigned red[8][9];
+  __shared__ int am_last;
   const long long ks = d.ber_skip;
   const long long kal = ks + ((ka - ks) / 32) * 32;
   const long long k = kal + (long long)blockIdx.x * 256 + threadIdx.x;
   const int perm = d.st->sync_perm;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   unsigned err[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
   if (k >= ka && k < kb) {
     const uint8_t v = d.dec[k % d.dec_cap];
@@ -176,45 +205,116 @@ __global__ void __launch_bounds__(256) ber_count_kernel(RxDev d, long long ka, l
       unsigned s = err[p][q];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if ((threadIdx.x & 31) == 0 && s) atomicAdd(&d.win_err[(win % n_win_ring) * 8 + p * 4 + q], s);
+      if (l == 0) red[w][p * 4 + q] = s;
     }
+  if (l == 0) red[w][8] = (unsigned)win;  // windows differ by block only when SW < 256
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    const int j = threadIdx.x;
+    unsigned acc = 0;
+    unsigned cur = red[0][8];
+    for (int ww = 0; ww < 8; ++ww) {
+      if (red[ww][8] != cur) {
+        if (acc) atomicAdd(&d.win_err[(cur % n_win_ring) * 8 + j], acc);
+        acc = 0;
+        cur = red[ww][8];
+      }
+      acc += red[ww][j];
+    }
+    if (acc) atomicAdd(&d.win_err[(cur % n_win_ring) * 8 + j], acc);
+  }
+  if (w_to <= w_from) return;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = atomicAdd(&d.ber_done[1], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  extern __shared__ unsigned win_s[];
+  slip_pass(d, w_from, w_to, k_lim, n_win_ring, win_s);
+  if (threadIdx.x == 0) d.ber_done[1] = 0;
 }
 
-// Sequential slip pass over windows [w_from, w_to); window w covers
-// symbols [ks + w SW, ks + (w+1) SW) clipped to k_lim.  Slots are cleared.
-__global__ void ber_finalize_kernel(RxDev d, long long w_from, long long w_to, long long k_lim, int n_win_ring) {
-  const int p = threadIdx.x;
-  if (p >= 2) return;
+// Slip pass over windows [w_from, w_to); window w covers symbols
+// [ks + w SW, ks + (w+1) SW) clipped to k_lim.  A 4-state automaton (state =
+// quadrant in use) per polarisation: windows are staged in shared memory in
+// chunks of kSlipChunk, each lane of warp p runs its 32 windows of a chunk
+// from all four start states at once, and the lanes are chained in order,
+// which gives exactly the sequential result.  Window slots are cleared.
+constexpr int kSlipChunk = 1024;
+
+__device__ void slip_pass(const RxDev& d, long long w_from, long long w_to, long long k_lim, int n_win_ring,
+                          unsigned* win_s) {
+  const int p = threadIdx.x >> 5, lane = threadIdx.x & 31;
   StreamState* st = d.st;
-  int q = st->q_cur[p];
-  unsigned long long errors = 0, bits = 0, slips = 0;
   const long long ks = d.ber_skip;
-  for (long long w = w_from; w < w_to; ++w) {
-    const long long a = ks + w * d.slip_win;
-    const long long b = min(a + d.slip_win, k_lim);
-    const long long nb = (b - a) * d.bps;
-    unsigned* e = d.win_err + (w % n_win_ring) * 8 + p * 4;
-    unsigned ev[4] = {e[0], e[1], e[2], e[3]};
-    if ((long long)ev[q] * 4 > nb) {
-      int qb = 0;
-      for (int qq = 1; qq < 4; ++qq)
-        if (ev[qq] < ev[qb]) qb = qq;
-      q = qb;
-      ++slips;
+  int qc = p < 2 ? st->q_cur[p] : 0;
+  unsigned long long E = 0, SL = 0;
+  for (long long c0 = w_from; c0 < w_to; c0 += kSlipChunk) {
+    const int nw = (int)min((long long)kSlipChunk, w_to - c0);
+    for (int i = threadIdx.x; i < nw * 8; i += blockDim.x) {
+      const long long w = c0 + i / 8;
+      unsigned* e = d.win_err + (w % n_win_ring) * 8 + (i % 8);
+      win_s[i] = __ldcg(e);
+      *e = 0;
     }
-    errors += ev[q];
-    bits += nb;
-    e[0] = e[1] = e[2] = e[3] = 0;
+    __syncthreads();
+    if (p < 2) {
+      const int per = (nw + 31) / 32;
+      const int a0 = lane * per, a1 = min(a0 + per, nw);
+      int q[4] = {0, 1, 2, 3};
+      unsigned long long err[4] = {0, 0, 0, 0}, slp[4] = {0, 0, 0, 0};
+      for (int i = a0; i < a1; ++i) {
+        const long long a = ks + (c0 + i) * d.slip_win;
+        const long long nb = (min(a + d.slip_win, k_lim) - a) * d.bps;
+        const unsigned* ev = win_s + i * 8 + p * 4;
+        int qb = 0;
+#pragma unroll
+        for (int qq = 1; qq < 4; ++qq)
+          if (ev[qq] < ev[qb]) qb = qq;
+#pragma unroll
+        for (int s0 = 0; s0 < 4; ++s0) {
+          if ((long long)ev[q[s0]] * 4 > nb) {
+            q[s0] = qb;
+            ++slp[s0];
+          }
+          err[s0] += ev[q[s0]];
+        }
+      }
+      for (int ln = 0; ln < 32; ++ln) {
+        int nq[4];
+        unsigned long long re[4], rs[4];
+#pragma unroll
+        for (int s0 = 0; s0 < 4; ++s0) {
+          nq[s0] = __shfl_sync(0xffffffffu, q[s0], ln);
+          re[s0] = __shfl_sync(0xffffffffu, err[s0], ln);
+          rs[s0] = __shfl_sync(0xffffffffu, slp[s0], ln);
+        }
+        int nqc = nq[0];
+        unsigned long long ee = re[0], ss = rs[0];
+#pragma unroll
+        for (int s0 = 1; s0 < 4; ++s0)
+          if (qc == s0) { nqc = nq[s0]; ee = re[s0]; ss = rs[s0]; }
+        E += ee;
+        SL += ss;
+        qc = nqc;
+      }
+    }
+    __syncthreads();
   }
-  st->q_cur[p] = q;
-  atomicAdd(&st->errors, errors);
-  atomicAdd(&st->bits, bits);
-  atomicAdd(&st->slips, slips);
+  if (p < 2 && lane == 0) {
+    const long long a = ks + w_from * d.slip_win;
+    const long long b = min(ks + w_to * (long long)d.slip_win, k_lim);
+    st->q_cur[p] = qc;
+    atomicAdd(&st->errors, E);
+    atomicAdd(&st->bits, (unsigned long long)(max(b - a, 0LL) * d.bps));
+    atomicAdd(&st->slips, SL);
+  }
 }
 
 // Push conversion: src planar [2][n] of dtype (0 c128, 1 c64, 2 c16) into
 // the ring at absolute sample offset w0 (index mod cap), storage dtype.
-__global__ void ingest_kernel(RxDev d, const void* __restrict__ src, int dtype, long long n, long long w0) {
+__global__ void ingest_kernel(RxDev d, const void* __restrict__ src, int dtype, long long n, long long j0) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * n) return;
   const int pol = i >= n;
@@ -228,7 +328,9 @@ __global__ void ingest_kernel(RxDev d, const void* __restrict__ src, int dtype, 
   } else {
     v = __half22float2(reinterpret_cast<const __half2*>(src)[i]);
   }
-  const long long dst = (long long)pol * d.ring_cap + (w0 + j) % d.ring_cap;
+  long long slot = j0 + j;  // j0 = w0 mod cap, n <= cap
+  if (slot >= d.ring_cap) slot -= d.ring_cap;
+  const long long dst = (long long)pol * d.ring_cap + slot;
   if (d.storage == 2) reinterpret_cast<__half2*>(d.ring)[dst] = __float22half2_rn(v);
   else reinterpret_cast<float2*>(d.ring)[dst] = v;
 }
@@ -244,26 +346,29 @@ cudaError_t launch_ref_gen(const RxDev& d, long long sym0, int nbits, int use_de
 
 cudaError_t launch_sync(const RxDev& d, cudaStream_t s) {
   sync_kernel<<<(2 * d.sync_dmax + 1) * 2, 256, 0, s>>>(d);
-  sync_select_kernel<<<1, 1, 0, s>>>(d);
   return cudaGetLastError();
+}
+
+cudaError_t ber_set_attributes() {
+  return cudaFuncSetAttribute(ber_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(kSlipChunk * 8 * sizeof(unsigned)));
 }
 
 cudaError_t launch_ber(const RxDev& d, long long ka, long long kb, long long w_from, long long w_to,
                        long long k_lim, int n_win_ring, cudaStream_t s) {
-  if (kb > ka) {
-    const long long ks = d.ber_skip;
-    const long long kal = ks + ((ka - ks) / 32) * 32;
-    const long long n = kb - kal;
-    ber_count_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d, ka, kb, n_win_ring);
-  }
-  if (w_to > w_from) ber_finalize_kernel<<<1, 32, 0, s>>>(d, w_from, w_to, k_lim, n_win_ring);
+  if (kb <= ka && w_to <= w_from) return cudaSuccess;
+  const long long ks = d.ber_skip;
+  const long long kal = ks + ((max(ka, ks) - ks) / 32) * 32;
+  const long long n = max(kb - kal, 1LL);
+  ber_count_kernel<<<(unsigned)((n + 255) / 256), 256, kSlipChunk * 8 * sizeof(unsigned), s>>>(
+      d, ka, kb, w_from, w_to, k_lim, n_win_ring);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ingest(const RxDev& d, const void* src, int dtype, long long n, long long w0, cudaStream_t s) {
   const long long tot = 2 * n;
   if (tot == 0) return cudaSuccess;
-  ingest_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d, src, dtype, n, w0);
+  ingest_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d, src, dtype, n, w0 % d.ring_cap);
   return cudaGetLastError();
 }
 

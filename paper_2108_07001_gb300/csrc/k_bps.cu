@@ -11,14 +11,18 @@
 // Kernel layout: lane = test angle, a group of B/32 warps slides a
 // (2W+1)-symbol window along a run of kRun symbols of one polarisation,
 // keeping the last 2W+1 metrics in registers (the loop is unrolled by 2W+1
-// so the ring index is static).  Every 32 outputs the group writes its
-// window sums to shared memory as order-preserving keys
-// (float bits with the low 6 bits replaced by the angle code) and reduces
-// each symbol's B keys with integer min/max.  For QPSK the metric is the
-// equivalent |Re z| + |Im z| (maximised): |z - dec z|^2 = |z|^2 + 1 -
-// sqrt2 (|Re z| + |Im z|) and |z|^2 does not depend on b.  For 16QAM,
-// in sqrt10-scaled units, the per-dimension distance to the nearest of
-// {-3,-1,1,3} is ||u| - 2| - 1.
+// so the ring index is static).  After every 2W+1 steps the group has
+// written the window sums of those steps to shared memory as
+// order-preserving keys (float bits with the low 6 bits replaced by the
+// angle) and reduces each symbol's B keys with an integer min.  Runs that
+// touch no stream edge take an unpredicated path.  The last block of each
+// polarisation (found with an atomic counter after a fence; nothing waits)
+// turns the runs' unwrap sums into each run's starting counter.  The metric is the squared
+// distance in scaled units where the levels are odd integers: QPSK
+// (x sqrt2, levels +-1): per dimension |u| - 1; 16QAM (x sqrt10, levels
+// +-1, +-3): ||u| - 2| - 1.  Keeping the (small) distance itself, rather
+// than an equivalent large correlation, keeps the key's 17-bit resolution
+// relative to the quantity being minimised.
 #include "rx_internal.cuh"
 
 namespace rx {
@@ -37,35 +41,75 @@ __device__ __forceinline__ int unwrap_inc(int a, int b, int B) {  // floor((2(a-
   return (x >= 2 * B) - (x < 0);
 }
 
+template <int B, int W, bool QAM16, bool EDGE>
+__device__ __forceinline__ void bps_window_step(const float2* __restrict__ yb, int u, int s, int sv_lo, int sv_hi,
+                                                float c_s, float s_s, float& D, float& ring_u) {
+  float m = 0.f;
+  if (!EDGE || (s >= sv_lo && s < sv_hi)) {
+    const float2 yv = yb[u];
+    const float zx = fmaf(yv.x, c_s, yv.y * s_s);
+    const float zy = fmaf(yv.y, c_s, -yv.x * s_s);
+    float ex, ey;
+    if (QAM16) {
+      ex = fabsf(fabsf(zx) - 2.f) - 1.f;
+      ey = fabsf(fabsf(zy) - 2.f) - 1.f;
+    } else {
+      ex = fabsf(zx) - 1.f;
+      ey = fabsf(zy) - 1.f;
+    }
+    m = fmaf(ex, ex, ey * ey);
+  }
+  D += m;
+  D -= ring_u;
+  ring_u = m;
+}
+
+// One block = 8 warps = 256/B runs of kRun symbols of one polarisation.
 template <int B, int W, bool QAM16>
 __global__ void __launch_bounds__(256) bps_kernel(RxDev d, FrameArgs fa) {
   constexpr int HALVES = B / 32;         // warps per group
   constexpr int GROUPS = 8 / HALVES;     // runs per block
-  constexpr int NCH = B / 4;             // 16-byte chunks per key row
   constexpr int WIN = 2 * W + 1;
-  __shared__ __align__(16) uint32_t keys[GROUPS][32][B];
-  __shared__ int bh_s[GROUPS][33];
+  constexpr int ROW = B + 4;             // padded key row (words)
+  extern __shared__ __align__(16) uint32_t keys_smem[];  // [GROUPS][WIN][ROW]
+  __shared__ int bh_s[GROUPS][WIN];
+  __shared__ float2 cs_s[B];
   __shared__ float red_s[8][3];
+  __shared__ int part[256];
+  __shared__ int am_last;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = warp / HALVES, wg = warp % HALVES;
+  const int tg = wg * 32 + lane;  // thread index within the group
   const int pol = blockIdx.y;
   const long long n_dec = fa.k_b - fa.k_a;
+  const int nruns = (int)((n_dec + kRun - 1) / kRun);
   const int run = blockIdx.x * GROUPS + g;
   const long long kr = fa.k_a + (long long)run * kRun;
-  const bool active = kr < fa.k_b;
-  const int ract = active ? (int)min((long long)kRun, fa.k_b - kr) : 0;
+  const int ract = run < nruns ? (int)min((long long)kRun, fa.k_b - kr) : 0;
 
-  const int b = wg * 32 + lane;
+  if (threadIdx.x < B) {
+    float sb, cb;
+    sincospif(((float)threadIdx.x / (float)B - 0.5f) * 0.5f, &sb, &cb);
+    cs_s[threadIdx.x] = make_float2(cb, sb);
+  }
+  const int b = tg;  // this lane's test angle
   float cs, sn;
   sincospif(((float)b / (float)B - 0.5f) * 0.5f, &sn, &cs);
-  const float sc = QAM16 ? 3.16227766016837933f : 1.0f;
+  const float sc = QAM16 ? 3.16227766016837933f : 1.41421356237309505f;
   const float c_s = cs * sc, s_s = sn * sc;
 
-  const float2* ycur = d.y + (long long)(fa.f & 1) * 2 * d.F + (long long)pol * d.F;
-  const float2* yprev = d.y + (long long)((fa.f + 1) & 1) * 2 * d.F + (long long)pol * d.F;
+  // y of the frame with its history: symbol i is yf[i - fbase] for i >= fbase - kYHist
   const long long fbase = fa.f * (long long)d.F;
+  const float2* yf = d.y + ((long long)(fa.f & 1) * 2 + pol) * (kYHist + d.F) + kYHist;
   const long long ylim = min(fa.n_sym, fbase + fa.Ff);  // symbols beyond do not exist (yet)
+  // window step s reads symbol kr - W + s; valid steps [sv_lo, sv_hi)
+  const int total = ract + 2 * W;
+  const float2* yrun = yf + (kr - W - fbase);
+  const int sv_lo = (int)max(0LL, (long long)W - kr);
+  const int sv_hi = (int)min((long long)total, ylim - (kr - W));
+  const bool edge = sv_lo > 0 || sv_hi < total;
+  __syncthreads();  // cs_s
 
   float ring[WIN];
 #pragma unroll
@@ -73,91 +117,72 @@ __global__ void __launch_bounds__(256) bps_kernel(RxDev d, FrameArgs fa) {
   float D = 0.f;
   float evn = 0.f, evd = 0.f;
   int inc_sum = 0;
-  int bh_prev = -1;
-  const int total = ract + 2 * W;
+  int bh_prev = -1, bh_first = -1;
   uint16_t* blp = d.bl + (long long)pol * (d.F + 2 * d.W);
+  uint32_t* krow = keys_smem + (g * WIN) * ROW + b;
   for (int base = 0; base < total; base += WIN) {
+    const float2* yb = yrun + base;
+    if (!edge && base + WIN <= total) {
 #pragma unroll
-    for (int u = 0; u < WIN; ++u) {
-      const int s = base + u;
-      if (s < total) {
-        const long long i = kr - W + s;  // symbol entering the window
-        float m = 0.f;
-        if (i >= 0 && i < ylim) {
-          const float2 yv = (i >= fbase) ? ycur[i - fbase] : yprev[i - fbase + d.F];
-          const float zx = fmaf(yv.x, c_s, yv.y * s_s);
-          const float zy = fmaf(yv.y, c_s, -yv.x * s_s);
-          if (QAM16) {
-            const float ex = fabsf(fabsf(zx) - 2.f) - 1.f, ey = fabsf(fabsf(zy) - 2.f) - 1.f;
-            m = fmaf(ex, ex, ey * ey);
-          } else {
-            m = fabsf(zx) + fabsf(zy);
-          }
-        }
-        D += m - ring[u];
-        ring[u] = m;
-        const int o = s - 2 * W;
-        if (o >= 0) {
-          const int ol = o & 31;
-          const uint32_t code = QAM16 ? (uint32_t)b : (uint32_t)(63 - b);
-          const uint32_t key = (__float_as_uint(fmaxf(D, 0.f)) & ~63u) | code;
-          const int ch = (b >> 2) ^ (ol & (NCH - 1));
-          keys[g][ol][ch * 4 + (b & 3)] = key;
-          if (ol == 31 || o == ract - 1) {
-            group_sync<B>(g);
-            // reduce the chunk's outputs: thread t of the group -> output t / HALVES
-            const int tg = wg * 32 + lane;
-            const int oc = tg / HALVES, half = tg % HALVES;
-            const int nout = ol + 1;
-            uint32_t best = QAM16 ? 0xffffffffu : 0u;
-            if (oc < nout) {
+      for (int u = 0; u < WIN; ++u) {
+        bps_window_step<B, W, QAM16, false>(yb, u, base + u, sv_lo, sv_hi, c_s, s_s, D, ring[u]);
+        krow[u * ROW] = (__float_as_uint(fmaxf(D, 0.f)) & ~63u) | (uint32_t)b;
+      }
+    } else {
 #pragma unroll
-              for (int c4 = 0; c4 < 8; ++c4) {
-                const int chk = (half * 8 + c4) ^ (oc & (NCH - 1));
-                const uint4 v = *reinterpret_cast<const uint4*>(&keys[g][oc][chk * 4]);
-                if (QAM16) {
-                  best = min(best, min(min(v.x, v.y), min(v.z, v.w)));
-                } else {
-                  best = max(best, max(max(v.x, v.y), max(v.z, v.w)));
-                }
-              }
-            }
-            if (HALVES == 2) {
-              const uint32_t ob = __shfl_xor_sync(0xffffffffu, best, 1);
-              best = QAM16 ? min(best, ob) : max(best, ob);
-            }
-            const int bh = QAM16 ? (int)(best & 63u) : 63 - (int)(best & 63u);
-            if (half == 0 && oc < nout) bh_s[g][oc + 1] = bh;
-            if (tg == 0) bh_s[g][0] = bh_prev;
-            group_sync<B>(g);
-            if (half == 0 && oc < nout) {
-              const long long k = kr + (o - ol) + oc;
-              const int bprev = bh_s[g][oc];
-              if (bprev >= 0 && k > kr) inc_sum += unwrap_inc(bprev, bh, B);
-              // decision at the chosen angle
-              const float2 yv = (k >= fbase) ? ycur[k - fbase] : yprev[k - fbase + d.F];
-              float sb, cb;
-              sincospif(((float)bh / (float)B - 0.5f) * 0.5f, &sb, &cb);
-              const float zx = fmaf(yv.x, cb, yv.y * sb), zy = fmaf(yv.y, cb, -yv.x * sb);
-              const int lI = level_of(zx, d.nl), lQ = level_of(zy, d.nl);
-              blp[k - fa.k_a] = (uint16_t)(bh | (lI << 8) | (lQ << 12));
-              if (k >= d.ber_skip && k < fa.k_end) {
-                const float dx = level_val(lI, d.nl), dy = level_val(lQ, d.nl);
-                evn += (zx - dx) * (zx - dx) + (zy - dy) * (zy - dy);
-                evd += dx * dx + dy * dy;
-              }
-            }
-            // carry for the next chunk (read before the next chunk's first
-            // barrier, after which bh_s is rewritten)
-            bh_prev = bh_s[g][nout];
-          }
+      for (int u = 0; u < WIN; ++u) {
+        if (base + u < total) {
+          bps_window_step<B, W, QAM16, true>(yb, u, base + u, sv_lo, sv_hi, c_s, s_s, D, ring[u]);
+          krow[u * ROW] = (__float_as_uint(fmaxf(D, 0.f)) & ~63u) | (uint32_t)b;
         }
       }
     }
+    // outputs of this super-step: steps s in [max(base, 2W), min(base + WIN, total))
+    const int s_lo = max(base, 2 * W), s_hi = min(base + WIN, total);
+    if (s_hi > s_lo) {
+      group_sync<B>(g);
+      const int half = tg % HALVES;
+      for (int s = s_lo + tg / HALVES; s < s_lo + 32 * ((s_hi - s_lo + 31) / 32); s += 32) {
+        const int u = s - base;
+        const bool act = s < s_hi;
+        uint32_t best = 0xffffffffu;
+        if (act) {
+          const uint4* row = reinterpret_cast<const uint4*>(keys_smem + (g * WIN + u) * ROW + half * 32);
+#pragma unroll
+          for (int c4 = 0; c4 < 8; ++c4) {
+            const uint4 v = row[c4];
+            best = min(best, min(min(v.x, v.y), min(v.z, v.w)));
+          }
+        }
+        if (HALVES == 2) best = min(best, __shfl_xor_sync(0xffffffffu, best, 1));
+        if (act && half == 0) bh_s[g][u] = (int)(best & 63u);
+      }
+      group_sync<B>(g);
+      // decisions, unwrap increments and EVM of the super-step's outputs
+      for (int s = s_lo + tg; s < s_hi; s += B) {
+        const int u = s - base;
+        const int ko = s - 2 * W;  // output index in the run
+        const long long k = kr + ko;
+        const int bh = bh_s[g][u];
+        const int bprev = (s == s_lo) ? (s == 2 * W ? -1 : bh_prev) : bh_s[g][u - 1];
+        if (bprev >= 0) inc_sum += unwrap_inc(bprev, bh, B);
+        const float2 yv = yrun[W + ko];
+        const float2 csb = cs_s[bh];
+        const float zx = fmaf(yv.x, csb.x, yv.y * csb.y), zy = fmaf(yv.y, csb.x, -yv.x * csb.y);
+        const int lI = level_of(zx, d.nl), lQ = level_of(zy, d.nl);
+        blp[k - fa.k_a] = (uint16_t)(bh | (lI << 8) | (lQ << 12));
+        if (k >= d.ber_skip && k < fa.k_end) {
+          const float dx = level_val(lI, d.nl), dy = level_val(lQ, d.nl);
+          evn += (zx - dx) * (zx - dx) + (zy - dy) * (zy - dy);
+          evd += dx * dx + dy * dy;
+        }
+      }
+      if (s_lo == 2 * W) bh_first = bh_s[g][s_lo - base];
+      bh_prev = bh_s[g][s_hi - 1 - base];
+    }
   }
-  // block reduction of the run's unwrap increments and EVM sums
-  float incf = (float)inc_sum;
-  incf = warp_sum(incf);
+  // run results: internal unwrap sum, first and last angle
+  const float incf = warp_sum((float)inc_sum);
   evn = warp_sum(evn);
   evd = warp_sum(evd);
   if (lane == 0) {
@@ -166,14 +191,19 @@ __global__ void __launch_bounds__(256) bps_kernel(RxDev d, FrameArgs fa) {
     red_s[warp][2] = evd;
   }
   __syncthreads();
+  const int stride = d.F / kRun + 4;
   if (threadIdx.x < GROUPS) {
     const int gg = threadIdx.x;
-    float si = 0.f;
-    for (int w = 0; w < HALVES; ++w) si += red_s[gg * HALVES + w][0];
     const int rr = blockIdx.x * GROUPS + gg;
-    const long long krr = fa.k_a + (long long)rr * kRun;
-    const int nruns = (int)((n_dec + kRun - 1) / kRun);
-    if (krr < fa.k_b && rr < nruns) d.run_int[pol * (d.F / kRun + 4) + rr] = (int)lrintf(si);
+    if (rr < nruns) {
+      float si = 0.f;
+      for (int w = 0; w < HALVES; ++w) si += red_s[gg * HALVES + w][0];
+      d.run_int[pol * stride + rr] = (int)lrintf(si);
+    }
+  }
+  if (tg == 0 && run < nruns) {
+    d.run_edge[(pol * stride + run) * 2 + 0] = bh_first;
+    d.run_edge[(pol * stride + run) * 2 + 1] = bh_prev;
   }
   if (threadIdx.x == 0) {
     float a = 0.f, c = 0.f;
@@ -183,50 +213,44 @@ __global__ void __launch_bounds__(256) bps_kernel(RxDev d, FrameArgs fa) {
       atomicAdd(&d.st->evm_den, (double)c);
     }
   }
-}
-
-// Unwrap counter at the first symbol of every run (one block, per pol):
-// m(k_r) = m_last + sum over earlier runs of (boundary inc + internal incs)
-// + the run's own boundary increment.
-__global__ void __launch_bounds__(1024) unwrap_scan_kernel(RxDev d, FrameArgs fa) {
-  __shared__ int part[1024];
-  const long long n_dec = fa.k_b - fa.k_a;
-  const int nruns = (int)((n_dec + kRun - 1) / kRun);
-  const int stride = d.F / kRun + 4;
-  const int B = d.B;
-  for (int pol = 0; pol < 2; ++pol) {
-    const uint16_t* blp = d.bl + (long long)pol * (d.F + 2 * d.W);
-    const int per = (nruns + 1023) / 1024;
-    const int r0 = threadIdx.x * per;
-    int loc = 0;
-    for (int r = r0; r < min(r0 + per, nruns); ++r) {
-      const int bfirst = blp[(long long)r * kRun] & 63;
-      const int bprev = r == 0 ? d.st->bhat_last[pol] : (blp[(long long)r * kRun - 1] & 63);
-      const int binc = bprev >= 0 ? unwrap_inc(bprev, bfirst, B) : 0;
-      loc += binc + d.run_int[pol * stride + r];
-    }
-    part[threadIdx.x] = loc;
+  // the last block of this polarisation turns run sums into run start counters
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = atomicAdd(&d.bps_done[pol], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  const int per = (nruns + 255) / 256;
+  const int r0 = threadIdx.x * per, r1 = min(r0 + per, nruns);
+  const int b_last_prev = d.st->bhat_last[pol];
+  int loc = 0;
+  for (int r = r0; r < r1; ++r) {
+    const int bf = __ldcg(&d.run_edge[(pol * stride + r) * 2 + 0]);
+    const int bp = r == 0 ? b_last_prev : __ldcg(&d.run_edge[(pol * stride + r - 1) * 2 + 1]);
+    loc += (bp >= 0 ? unwrap_inc(bp, bf, B) : 0) + __ldcg(&d.run_int[pol * stride + r]);
+  }
+  part[threadIdx.x] = loc;
+  __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {
+    const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-      const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-      __syncthreads();
-      part[threadIdx.x] += v;
-      __syncthreads();
-    }
-    int acc = d.st->m_last[pol] + (threadIdx.x > 0 ? part[threadIdx.x - 1] : 0);
-    for (int r = r0; r < min(r0 + per, nruns); ++r) {
-      const int bfirst = blp[(long long)r * kRun] & 63;
-      const int bprev = r == 0 ? d.st->bhat_last[pol] : (blp[(long long)r * kRun - 1] & 63);
-      const int binc = bprev >= 0 ? unwrap_inc(bprev, bfirst, B) : 0;
-      d.run_m0[pol * stride + r] = acc + binc;
-      acc += binc + d.run_int[pol * stride + r];
-    }
+    part[threadIdx.x] += v;
     __syncthreads();
-    if (threadIdx.x == 1023) {
-      d.st->m_last[pol] = d.st->m_last[pol] + part[1023];
-      d.st->bhat_last[pol] = blp[n_dec - 1] & 63;
-    }
-    __syncthreads();
+  }
+  const int m_last = d.st->m_last[pol];
+  int acc = m_last + (threadIdx.x > 0 ? part[threadIdx.x - 1] : 0);
+  for (int r = r0; r < r1; ++r) {
+    const int bf = __ldcg(&d.run_edge[(pol * stride + r) * 2 + 0]);
+    const int bp = r == 0 ? b_last_prev : __ldcg(&d.run_edge[(pol * stride + r - 1) * 2 + 1]);
+    const int binc = bp >= 0 ? unwrap_inc(bp, bf, B) : 0;
+    d.run_m0[pol * stride + r] = acc + binc;
+    acc += binc + __ldcg(&d.run_int[pol * stride + r]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    d.st->m_last[pol] = m_last + part[255];
+    d.st->bhat_last[pol] = __ldcg(&d.run_edge[(pol * stride + nruns - 1) * 2 + 1]);
+    d.bps_done[pol] = 0;
   }
 }
 
@@ -332,7 +356,28 @@ static void launch_bps_t(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
   const long long n_dec = fa.k_b - fa.k_a;
   const int nruns = (int)((n_dec + kRun - 1) / kRun);
   dim3 grid((nruns + GROUPS - 1) / GROUPS, 2);
-  bps_kernel<B, W, Q><<<grid, 256, 0, s>>>(d, fa);
+  const size_t smem = sizeof(uint32_t) * GROUPS * (2 * W + 1) * (B + 4);
+  bps_kernel<B, W, Q><<<grid, 256, smem, s>>>(d, fa);
+}
+
+template <int B, int W>
+static cudaError_t bps_attr_t() {
+  constexpr int GROUPS = 8 / (B / 32);
+  const int smem = (int)(sizeof(uint32_t) * GROUPS * (2 * W + 1) * (B + 4));
+  cudaError_t e = cudaFuncSetAttribute(bps_kernel<B, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(bps_kernel<B, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
+
+// Opt-in to the dynamic shared memory of every instantiation (once per process).
+cudaError_t bps_set_attributes() {
+  cudaError_t e = cudaSuccess;
+#define RX_BA(b, w) if (e == cudaSuccess) e = bps_attr_t<b, w>();
+  RX_BA(64, 16) RX_BA(32, 16) RX_BA(64, 32) RX_BA(32, 32) RX_BA(64, 8) RX_BA(32, 8)
+  RX_BA(64, 12) RX_BA(32, 12) RX_BA(64, 24) RX_BA(32, 24)
+#undef RX_BA
+  return e;
 }
 
 cudaError_t launch_bps(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
@@ -352,9 +397,6 @@ cudaError_t launch_bps(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
 
 cudaError_t launch_unwrap_demap(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
   if (fa.k_b <= fa.k_a) return cudaSuccess;
-  unwrap_scan_kernel<<<1, 1024, 0, s>>>(d, fa);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   const long long n_dec = fa.k_b - fa.k_a;
   const int nruns = (int)((n_dec + kRun - 1) / kRun);
   demap_kernel<<<nruns, 128, 0, s>>>(d, fa);

@@ -41,6 +41,8 @@ template <int N, int NT, int STOR>
 __global__ void __launch_bounds__(NT) cd_ols_kernel(RxDev d, FrameArgs fa) {
   extern __shared__ float2 buf[];
   __shared__ float scratch[NT / 32];
+  __shared__ float2 tw_s[2 * kTwSplit];  // [hi | lo] two-level twiddle table
+  for (int i = threadIdx.x; i < 2 * kTwSplit; i += NT) tw_s[i] = d.tw2[i];
   const int pol = blockIdx.y;
   const long long a = fa.s0 + (long long)blockIdx.x * d.L;
   const long long zlen_f = 2LL * fa.Ff + 2 * d.c;
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(NT) cd_ols_kernel(RxDev d, FrameArgs fa) {
     buf[swz(i)] = v;
   }
   __syncthreads();
-  fft_smem<N, NT, false>(buf, d.tw, 1);
+  fft_smem<N, NT, false>(buf, tw_s, 1);
 
   // filter; Godard sum over bin pairs Rs apart
   float gr = 0.f, gi = 0.f;
@@ -73,12 +75,12 @@ __global__ void __launch_bounds__(NT) cd_ols_kernel(RxDev d, FrameArgs fa) {
   gi = block_sum<NT>(gi, scratch);
   if (threadIdx.x == 0) {
     const float sg = (lo & 1) ? -1.f : 1.f;
-    atomicAdd(&d.acc->C[0], sg * gr);
-    atomicAdd(&d.acc->C[1], sg * gi);
+    atomicAdd(&d.acc->C[0], (double)(sg * gr));
+    atomicAdd(&d.acc->C[1], (double)(sg * gi));
   }
   if (fa.est_only) return;
   __syncthreads();
-  fft_smem<N, NT, true>(buf, d.tw, 1);
+  fft_smem<N, NT, true>(buf, tw_s, 1);
 
   // kept samples -> z; in-frame power
   float2* zp = d.z + (long long)pol * d.zlen + (a - fa.s0);
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(NT) cd_ols_kernel(RxDev d, FrameArgs fa) {
     if (n >= fa.f0 && n < fa.f1) pw += v.x * v.x + v.y * v.y;
   }
   pw = block_sum<NT>(pw, scratch);
-  if (threadIdx.x == 0) atomicAdd(&d.acc->P, pw);
+  if (threadIdx.x == 0) atomicAdd(&d.acc->P, (double)pw);
 
   // 4th power of the even in-frame samples, zero padded to N/2
   const long long lo_n = max(a, fa.f0), hi_n = min(a + keep, fa.f1);
@@ -118,11 +120,17 @@ __global__ void __launch_bounds__(NT) cd_ols_kernel(RxDev d, FrameArgs fa) {
     if (idx < N / 2) buf[swz(idx)] = u[q];
   }
   __syncthreads();
-  fft_smem<N / 2, NT, false>(buf, d.tw, 2);
+  fft_smem<N / 2, NT, false>(buf, tw_s, 2);
   for (int k = threadIdx.x; k < N / 2; k += NT) {
     const float2 v = buf[swz(k)];
-    atomicAdd(&d.psd[k], v.x * v.x + v.y * v.y);
+    atomicAdd(&d.psd[k], (double)(v.x * v.x + v.y * v.y));
   }
+}
+
+// x reduced to [-pi, pi] in FP64 (x - 2 pi rint(x / 2 pi)).
+__device__ __forceinline__ double wrap_pi(double x) {
+  constexpr double kTwoPi = 6.283185307179586477, kInvTwoPi = 0.15915494309189533577;
+  return fma(-kTwoPi, rint(x * kInvTwoPi), x);
 }
 
 // Per-frame estimator (one block of 1024 threads).
@@ -135,7 +143,7 @@ __global__ void __launch_bounds__(NT) cd_ols_kernel(RxDev d, FrameArgs fa) {
 // pass and clear the accumulators.  Phases are formed in FP64 and reduced
 // before the single-precision sine/cosine.
 __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mode) {
-  __shared__ float sv[32];
+  __shared__ double sv[32];
   __shared__ int si[32];
   __shared__ double sh[4];
   const int tid = threadIdx.x;
@@ -144,15 +152,15 @@ __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mo
   const double resid = (C_re == 0.0 && C_im == 0.0) ? 0.0 : -atan2(C_im, C_re) / (2.0 * M_PI * d.Rs);
   if (mode == 1) {
     const int n2 = d.N / 2;
-    float best = -1.f;
+    double best = -1.0;
     int bi = 0;
     for (int k = tid; k < n2; k += 1024) {
-      const float v = d.psd[k];
+      const double v = d.psd[k];
       if (v > best) { best = v; bi = k; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
     }
@@ -163,7 +171,7 @@ __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mo
       bi = si[tid];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
       }
@@ -177,8 +185,11 @@ __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mo
         if (den < 0.0) dl = 0.5 * (lm - lp) / den;
       }
       const int ks = bi < n2 / 2 ? bi : bi - n2;
-      const double dfo = (ks + dl) * (d.Rs / n2) / 4.0;
-      const double P = (double)d.acc->P / (2.0 * (double)(fa.f1 - fa.f0));
+      double dfo = (ks + dl) * (d.Rs / n2) / 4.0;
+      // a frame shorter than kFoeMinSyms keeps the previous frame's estimate
+      if (fa.f > 0 && fa.Ff < kFoeMinSyms) dfo = st->dfo_prev;
+      st->dfo_prev = dfo;
+      const double P = d.acc->P / (2.0 * (double)(fa.f1 - fa.f0));
       const double gain = P > 0.0 ? 1.0 / sqrt(P) : 1.0;
       const double om = 2.0 * M_PI * dfo / d.fs;
       const double theta = st->theta;
@@ -193,20 +204,20 @@ __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mo
       sh[0] = om;
       sh[1] = theta;
       sh[2] = gain;
-      st->theta = fmod(theta + om * (double)(fa.f1 - fa.f0), 2.0 * M_PI);
+      st->theta = wrap_pi(theta + om * (double)(fa.f1 - fa.f0));
       st->tau = st->tau + (double)d.timing_gain * resid;
     }
     __syncthreads();
     const double om = sh[0], theta = sh[1], gain = sh[2];
+    const float omf = (float)om;  // |w l| < 1024 |w|: FP32 phase is exact to ~1e-6 rad
     for (int l = tid; l < kRotLo; l += 1024) {
-      const double ph = remainder(om * (double)l, 2.0 * M_PI);
       float s, c;
-      sincosf((float)ph, &s, &c);
+      sincosf(omf * (float)l, &s, &c);
       d.rot_lo[l] = make_float2(c, -s);
     }
     const int nhi = (d.zlen + kRotLo - 1) / kRotLo;
     for (int hh = tid; hh < nhi; hh += 1024) {
-      const double ph = remainder(theta + om * (double)(hh * kRotLo - d.c), 2.0 * M_PI);
+      const double ph = wrap_pi(theta + om * (double)(hh * kRotLo - d.c));
       float s, c;
       sincosf((float)ph, &s, &c);
       d.rot_hi[hh] = make_float2((float)gain * c, -(float)gain * s);
@@ -215,20 +226,20 @@ __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mo
     if (tid == 0) st->tau = resid;
   }
   __syncthreads();
-  const double tau = st->tau;
+  // exp(+j 2 pi f_k tau) = sincospi(2 (k'/N) fs tau), k' = k or k - N: the
+  // scalar fs tau is formed in FP64, the per-bin product (k'/N exact) in FP32
+  const float u2 = (float)(2.0 * d.fs * st->tau) / (float)d.N;
   for (int k = tid; k < d.N; k += 1024) {
-    const double fk = (k < d.N / 2 ? k : k - d.N) * (d.fs / d.N);
-    double x = 2.0 * fk * tau;           // phase / pi
-    x -= 2.0 * rint(0.5 * x);
+    const int kk = k < d.N / 2 ? k : k - d.N;
     float s, c;
-    sincospif((float)x, &s, &c);
+    sincospif((float)kk * u2, &s, &c);
     d.Hf[k] = cmul(d.Hs[k], make_float2(c, s));
   }
-  for (int k = tid; k < d.N / 2; k += 1024) d.psd[k] = 0.f;
+  for (int k = tid; k < d.N / 2; k += 1024) d.psd[k] = 0.0;
   if (tid == 0) {
-    d.acc->C[0] = 0.f;
-    d.acc->C[1] = 0.f;
-    d.acc->P = 0.f;
+    d.acc->C[0] = 0.0;
+    d.acc->C[1] = 0.0;
+    d.acc->P = 0.0;
   }
 }
 
@@ -241,15 +252,30 @@ static cudaError_t launch_cd_n(const RxDev& d, const FrameArgs& fa, cudaStream_t
   const size_t smem = sizeof(float2) * N;
   dim3 grid(nblk, 2);
   if (d.storage == 2) {
-    auto k = cd_ols_kernel<N, NT, 2>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<grid, NT, smem, s>>>(d, fa);
+    cd_ols_kernel<N, NT, 2><<<grid, NT, smem, s>>>(d, fa);
   } else {
-    auto k = cd_ols_kernel<N, NT, 1>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<grid, NT, smem, s>>>(d, fa);
+    cd_ols_kernel<N, NT, 1><<<grid, NT, smem, s>>>(d, fa);
   }
   return cudaGetLastError();
+}
+
+template <int N, int NT>
+static cudaError_t cd_attr_n() {
+  const int smem = (int)(sizeof(float2) * N);
+  cudaError_t e = cudaFuncSetAttribute(cd_ols_kernel<N, NT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(cd_ols_kernel<N, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
+
+// Opt-in to the dynamic shared memory of every FFT size (once per process).
+cudaError_t cd_set_attributes() {
+  cudaError_t e = cd_attr_n<1024, 256>();
+  if (e == cudaSuccess) e = cd_attr_n<2048, 256>();
+  if (e == cudaSuccess) e = cd_attr_n<4096, 256>();
+  if (e == cudaSuccess) e = cd_attr_n<8192, 512>();
+  if (e == cudaSuccess) e = cd_attr_n<16384, 1024>();
+  return e;
 }
 
 cudaError_t launch_cd(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {

@@ -180,74 +180,176 @@ __device__ __forceinline__ void store_taps(const ChainSmem<T>& sm, float2* dst) 
   }
 }
 
-// Sequential acquisition of the first frame (one warp).
+// Sequential acquisition of the first frame, one block of 256 threads
+// (the chain is inherently sequential, so its latency is spread over a
+// block).  FIR: thread (k, p, q) = (t >> 2, (t >> 1) & 1, t & 1) forms
+// sum_t w[p][q][t] r_q[2k + t] and the q pair is added with a shuffle.
+// Gradient: thread (combo, quarter) sums e_p[k] conj(r_q[2k + t]) over a
+// quarter of the sub-block, quarters are added with shuffles.  The next
+// sub-block's samples are loaded into registers while the gradient runs.
 template <int T>
-__global__ void __launch_bounds__(32) acq_kernel(RxDev d, FrameArgs fa) {
-  __shared__ ChainSmem<T> sm;
-  const int lane = threadIdx.x;
+__global__ void __launch_bounds__(256) acq_kernel(RxDev d, FrameArgs fa) {
+  constexpr int NS = 2 * kK + T - 1;      // samples per pol per sub-block
+  constexpr int NLD = (2 * NS + 255) / 256;
+  __shared__ float2 r_s[2][NS + 1];
+  __shared__ float2 w_s[2][2][T];         // [p][q][t]
+  __shared__ float2 e_s[2][kK];
+  __shared__ float red_s[8][4];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int zlen_f = 2 * fa.Ff + 2 * d.c;
   const int n_acq = min(d.acq_syms, fa.Ff);
-  // centre spike
-  for (int pr = lane; pr < 2 * T; pr += 32) {
-    const int q = pr / T, t = pr - q * T;
-    const float one = (t == (T - 1) / 2) ? 1.f : 0.f;
-    sm.w[q][t] = make_float4(q == 0 ? one : 0.f, 0.f, q == 1 ? one : 0.f, 0.f);
+  for (int i = tid; i < 4 * T; i += 256) {
+    const int p = i / (2 * T), q = (i / T) & 1, t = i % T;
+    w_s[p][q][t] = make_float2((p == q && t == (T - 1) / 2) ? 1.f : 0.f, 0.f);
   }
-  __syncwarp();
+  // prefetch registers for one sub-block's samples
+  float2 pre[NLD];
+  auto load = [&](int kf0, int nk) {
+    const int ns = 2 * nk + T - 1;
+#pragma unroll
+    for (int j = 0; j < NLD; ++j) {
+      const int i = tid + j * 256;
+      const int q = i / NS, s = i - q * NS;
+      float2 v = make_float2(0.f, 0.f);
+      if (q < 2 && s < ns) {
+        const int n = 2 * kf0 + s;
+        if (n < zlen_f) {
+          const float2 rot = cmul(__ldg(&d.rot_hi[n >> 10]), __ldg(&d.rot_lo[n & (kRotLo - 1)]));
+          v = cmul(d.z[(long long)q * d.zlen + n], rot);
+        }
+      }
+      pre[j] = v;
+    }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int j = 0; j < NLD; ++j) {
+      const int i = tid + j * 256;
+      const int q = i / NS, s = i - q * NS;
+      if (q < 2) r_s[q][s] = pre[j];
+    }
+  };
   const int cma_end = min(((d.cma_syms + kK - 1) / kK) * kK, n_acq);
   const int corr_lo = max(cma_end - 1024, 0);
   float cxr = 0.f, cxi = 0.f, pxx = 0.f, pyy = 0.f;
   bool was_cma = false;
+  load(0, min(kK, n_acq));
+  store();
+  __syncthreads();
+  const int kk = tid >> 2, pp = (tid >> 1) & 1, qq = tid & 1;
   for (int k0 = 0; k0 < n_acq; k0 += kK) {
     const int nk = min(kK, n_acq - k0);
     const int mode = k0 < d.cma_syms ? 0 : 1;
     if (mode == 1 && was_cma) {
-      const float sxy = warp_sum(cxr), syx = warp_sum(cxi);
-      const float sxx = warp_sum(pxx), syy = warp_sum(pyy);
+      // singularity check over the last CMA outputs
+      float v0 = warp_sum(cxr), v1 = warp_sum(cxi), v2 = warp_sum(pxx), v3 = warp_sum(pyy);
+      if (lane == 0) { red_s[warp][0] = v0; red_s[warp][1] = v1; red_s[warp][2] = v2; red_s[warp][3] = v3; }
+      __syncthreads();
+      float sxy = 0.f, syx = 0.f, sxx = 0.f, syy = 0.f;
+      for (int w = 0; w < 8; ++w) { sxy += red_s[w][0]; syx += red_s[w][1]; sxx += red_s[w][2]; syy += red_s[w][3]; }
       const float den = sqrtf(sxx * syy);
       const float rho = den > 0.f ? sqrtf(sxy * sxy + syx * syx) / den : 0.f;
       if (rho > 0.5f) {
-        float4 old0[1], old1[1];
-        const int t = lane;
-        if (t < T) {
-          old0[0] = sm.w[0][T - 1 - t];
-          old1[0] = sm.w[1][T - 1 - t];
+        float2 a = make_float2(0.f, 0.f), b2 = a;
+        if (tid < T) {
+          a = w_s[0][1][T - 1 - tid];  // w_xy reversed
+          b2 = w_s[0][0][T - 1 - tid];  // w_xx reversed
         }
-        __syncwarp();
-        if (t < T) {
-          // w[1][0][t] = -conj(w[0][1][T-1-t]);  w[1][1][t] = conj(w[0][0][T-1-t])
-          float4 a = sm.w[0][t], b = sm.w[1][t];
-          a.z = -old1[0].x;
-          a.w = old1[0].y;
-          b.z = old0[0].x;
-          b.w = -old0[0].y;
-          sm.w[0][t] = a;
-          sm.w[1][t] = b;
+        __syncthreads();
+        if (tid < T) {
+          w_s[1][0][tid] = make_float2(-a.x, a.y);   // -conj(w_xy[T-1-t])
+          w_s[1][1][tid] = make_float2(b2.x, -b2.y);  // conj(w_xx[T-1-t])
         }
-        __syncwarp();
-        if (lane == 0) d.st->reinit = 1;
+        if (tid == 0) d.st->reinit = 1;
+      }
+      __syncthreads();
+    }
+    // ---- FIR
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      const float2 w = w_s[pp][qq][t], x = r_s[qq][2 * kk + t];
+      acc.x = fmaf(w.x, x.x, fmaf(-w.y, x.y, acc.x));
+      acc.y = fmaf(w.x, x.y, fmaf(w.y, x.x, acc.y));
+    }
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+    const float2 y = acc;  // y_pp[kk]
+    const bool valid = kk < nk;
+    // ---- error
+    float2 e;
+    if (mode == 0) {
+      e = cscale(y, y.x * y.x + y.y * y.y - d.R2);
+      // correlation of the two outputs for the singularity check
+      const float2 yo = make_float2(__shfl_xor_sync(0xffffffffu, y.x, 2), __shfl_xor_sync(0xffffffffu, y.y, 2));
+      const int k = k0 + kk;
+      if (valid && pp == 0 && qq == 0 && k >= corr_lo && k < cma_end) {
+        cxr += y.x * yo.x + y.y * yo.y;
+        cxi += y.y * yo.x - y.x * yo.y;
+        pxx += y.x * y.x + y.y * y.y;
+        pyy += yo.x * yo.x + yo.y * yo.y;
+      }
+    } else {
+      float s0x = 0.f, s0y = 0.f, s1x = 0.f, s1y = 0.f;
+      if (valid && qq == 0) {
+        const float2 a2 = make_float2(y.x * y.x - y.y * y.y, 2.f * y.x * y.y);
+        const float a4x = a2.x * a2.x - a2.y * a2.y, a4y = 2.f * a2.x * a2.y;
+        if (pp == 0) { s0x = a4x; s0y = a4y; } else { s1x = a4x; s1y = a4y; }
+      }
+      s0x = warp_sum(s0x); s0y = warp_sum(s0y); s1x = warp_sum(s1x); s1y = warp_sum(s1y);
+      if (lane == 0) { red_s[warp][0] = s0x; red_s[warp][1] = s0y; red_s[warp][2] = s1x; red_s[warp][3] = s1y; }
+      __syncthreads();
+      float sx = 0.f, sy = 0.f;
+      for (int w = 0; w < 8; ++w) { sx += red_s[w][2 * pp]; sy += red_s[w][2 * pp + 1]; }
+      float ph = 0.f;
+      if (sx != 0.f || sy != 0.f) ph = 0.25f * atan2f(-sy, -sx);
+      float sn, cs;
+      sincosf(ph, &sn, &cs);
+      const float2 zr = make_float2(y.x * cs + y.y * sn, y.y * cs - y.x * sn);
+      const float dx = level_val(level_of(zr.x, d.nl), d.nl), dy = level_val(level_of(zr.y, d.nl), d.nl);
+      e = csub(y, make_float2(dx * cs - dy * sn, dx * sn + dy * cs));
+    }
+    if (qq == 0) e_s[pp][kk] = valid ? e : make_float2(0.f, 0.f);
+    __syncthreads();
+    // prefetch the next sub-block while the gradient runs
+    const int k1 = k0 + kK;
+    if (k1 < n_acq) load(k1, min(kK, n_acq - k1));
+    // ---- gradient: combo = (p, q, t), quarter of the sub-block
+    const float step = (mode == 0 ? d.mu_cma : d.mu_dd) / (float)nk;
+    for (int c0 = 0; c0 < 16 * T; c0 += 256) {  // every lane runs every iteration (shuffles)
+      const int c = c0 + tid;
+      const bool act = c < 16 * T;
+      const int combo = act ? c >> 2 : 0, quarter = c & 3;
+      const int p = combo / (2 * T), q = (combo / T) & 1, t = combo % T;
+      float gx = 0.f, gy = 0.f;
+      const int ka = quarter * 16, kb = act ? min(ka + 16, nk) : ka;
+      for (int k = ka; k < kb; ++k) {
+        const float2 ee = e_s[p][k], x = r_s[q][2 * k + t];
+        gx = fmaf(ee.x, x.x, fmaf(ee.y, x.y, gx));
+        gy = fmaf(ee.y, x.x, fmaf(-ee.x, x.y, gy));
+      }
+      gx += __shfl_xor_sync(0xffffffffu, gx, 1);
+      gy += __shfl_xor_sync(0xffffffffu, gy, 1);
+      gx += __shfl_xor_sync(0xffffffffu, gx, 2);
+      gy += __shfl_xor_sync(0xffffffffu, gy, 2);
+      if (act && quarter == 0) {
+        float2 w = w_s[p][q][t];
+        w.x -= step * gx;
+        w.y -= step * gy;
+        w_s[p][q][t] = w;
       }
     }
-    stage_samples<T>(sm, d, k0, nk, zlen_f);
-    __syncwarp();
-    float2 y[2][2];
-    sub_block<T>(sm, nk, mode, mode == 0 ? d.mu_cma : d.mu_dd, d.R2, d.nl, y);
-    if (mode == 0) {
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int k = k0 + 2 * lane + j;
-        if (2 * lane + j < nk && k >= corr_lo && k < cma_end) {
-          const float2 a = y[0][j], b = y[1][j];
-          cxr += a.x * b.x + a.y * b.y;  // a conj(b)
-          cxi += a.y * b.x - a.x * b.y;
-          pxx += a.x * a.x + a.y * a.y;
-          pyy += b.x * b.x + b.y * b.y;
-        }
-      }
+    __syncthreads();
+    if (k1 < n_acq) {
+      store();
+      __syncthreads();
     }
     was_cma = mode == 0;
   }
-  store_taps<T>(sm, d.w_acq);
+  for (int i = tid; i < 4 * T; i += 256) {
+    const int p = i / (2 * T), q = (i / T) & 1, t = i % T;
+    d.w_acq[(p * 2 + q) * T + t] = w_s[p][q][t];
+  }
 }
 
 // All segments of one frame, one warp per segment.
@@ -262,7 +364,18 @@ __global__ void __launch_bounds__(128) mimo_kernel(RxDev d, FrameArgs fa, long l
   const int zlen_f = 2 * fa.Ff + 2 * d.c;
   float2* chain = d.chains + (long long)j * 4 * T;
   load_taps<T>(sm, fa.f == 0 ? d.w_acq : chain);
-  float2* yb = d.y + (long long)(fa.f & 1) * 2 * d.F;
+  // frame f's equalised symbols go to buffer f % 2 after a copy of the last
+  // kYHist symbols of frame f-1 (zeros for the first frame)
+  float2* yb = d.y + (long long)(fa.f & 1) * 2 * (kYHist + d.F);
+  if (blockIdx.x == 0 && wib == 0) {
+    const float2* yp = d.y + (long long)((fa.f + 1) & 1) * 2 * (kYHist + d.F);
+    for (int i = lane; i < 2 * kYHist; i += 32) {
+      const int p = i / kYHist, t = i % kYHist;
+      yb[(long long)p * (kYHist + d.F) + t] =
+          fa.f == 0 ? make_float2(0.f, 0.f) : yp[(long long)p * (kYHist + d.F) + d.F + t];
+    }
+  }
+  yb += kYHist;
   const int a = j * d.S, e = min(a + d.S, fa.Ff);
   for (int k0 = a; k0 < e; k0 += kK) {
     const int nk = min(kK, e - k0);
@@ -274,9 +387,9 @@ __global__ void __launch_bounds__(128) mimo_kernel(RxDev d, FrameArgs fa, long l
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
       if (2 * lane + 1 < nk) {
-        *reinterpret_cast<float4*>(&yb[(long long)p * d.F + k]) = make_float4(y[p][0].x, y[p][0].y, y[p][1].x, y[p][1].y);
+        *reinterpret_cast<float4*>(&yb[(long long)p * (kYHist + d.F) + k]) = make_float4(y[p][0].x, y[p][0].y, y[p][1].x, y[p][1].y);
       } else if (2 * lane < nk) {
-        yb[(long long)p * d.F + k] = y[p][0];
+        yb[(long long)p * (kYHist + d.F) + k] = y[p][0];
       }
       if (d.hist_syms > 0) {
 #pragma unroll
@@ -294,7 +407,7 @@ __global__ void __launch_bounds__(128) mimo_kernel(RxDev d, FrameArgs fa, long l
 
 template <int T>
 static cudaError_t launch_acq_t(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
-  acq_kernel<T><<<1, 32, 0, s>>>(d, fa);
+  acq_kernel<T><<<1, 256, 0, s>>>(d, fa);
   return cudaGetLastError();
 }
 

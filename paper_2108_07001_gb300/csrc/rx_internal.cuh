@@ -4,7 +4,8 @@
 //   ring   [2][ring_cap]       pushed samples, storage dtype, index n mod cap
 //   z      [2][zlen]           CD output of the frame, complex float; index
 //                              i <-> absolute sample 2fF - c + i
-//   y      [2 buf][2][F]       equaliser output, frame f in buffer f % 2
+//   y      [2 buf][2][64 + F]  equaliser output, frame f in buffer f % 2 after
+//                              the last 64 symbols of frame f-1
 //   bl     [2][F + 2W]         per decided symbol: BPS angle | levels << 8
 //   taps   [G][2][2][T]        adaptive chains, complex float
 #pragma once
@@ -18,7 +19,8 @@ constexpr int kMaxTaps = 31;
 constexpr int kRotLo = 1024;          // FO rotation table split: n = hi*1024 + lo
 constexpr int kRun = 256;             // BPS run / demap tile length (symbols)
 constexpr int kMaxTrace = 4096;       // per-frame estimate records kept
-constexpr int kWinRing = 64;          // BER slip windows in flight
+constexpr int kYHist = 64;            // equalised-symbol history kept before each frame (>= 2W)
+constexpr int kFoeMinSyms = 4096;     // shorter frames reuse the previous FO estimate
 
 // Per-frame estimates written by the estimator kernel (also the trace).
 struct FrameRec {
@@ -29,17 +31,20 @@ struct FrameRec {
 };
 
 // Accumulators filled by the CD kernel, consumed and cleared by the
-// estimator kernel.
+// estimator kernel.  Block partials are FP32; the sums are FP64, so their
+// value does not depend on the order the blocks finish in (the partials
+// are exactly representable and the sums stay far from 53-bit rounding).
 struct FrameAcc {
-  float C[2];      // Godard sum (re, im), both polarisations
-  float P;         // sum |z|^2 of in-frame samples, both polarisations
-  float pad;
+  double C[2];     // Godard sum (re, im), both polarisations
+  double P;        // sum |z|^2 of in-frame samples, both polarisations
+  double pad;
 };
 
 // Scalars carried from frame to frame (device resident).
 struct StreamState {
   double tau;          // timing advance for the next CD pass (s)
   double theta;        // FO phase at the next frame start
+  double dfo_prev;     // FO estimate of the previous frame (Hz)
   int bhat_last[2];    // BPS angle of the last decided symbol (-1: none)
   int m_last[2];       // unwrap counter of the last decided symbol
   int synced;
@@ -71,19 +76,23 @@ struct RxDev {
   float2* Hs;                  // static CD x RRC response, 1/N folded in
   float2* Hf;                  // Hs x timing phase of the coming pass
   float2* tw;                  // tw[k] = exp(-2 pi i k / N)
+  float2* tw2;                 // [256]: exp(-2 pi i 128 h / N) for h < 128, then exp(-2 pi i l / N), l < 128
   float2* z;
   float2* rot_hi;              // [ceil(zlen/1024)]  gain * exp(-j(theta + w (hi*1024 - c)))
   float2* rot_lo;              // [1024]             exp(-j w lo)
   FrameAcc* acc;
-  float* psd;                  // [N/2] FOE periodogram
+  double* psd;                 // [N/2] FOE periodogram (FP64 sums of FP32 block terms)
   FrameRec* rec;               // [kMaxTrace]
   StreamState* st;
   float2* w_acq;               // [2][2][T]
   float2* chains;              // [G][2][2][T]
-  float2* y;                   // [2][2][F]
+  float2* y;                   // [2][2][kYHist + F]
   uint16_t* bl;                // [2][F + 2W]
   int* run_int;                // [2][nruns] internal unwrap increment sums
   int* run_m0;                 // [2][nruns] unwrap counter at each run's first symbol
+  int* run_edge;               // [2][nruns][2] BPS angle of each run's first and last symbol
+  unsigned* bps_done;          // [2] finished-block counters of the BPS kernel
+  unsigned* ber_done;          // [2] finished-block counters: sync, count
   uint8_t* dec;                // decision ring [dec_cap]: x levels | y levels << 4
   uint8_t* out;                // output bit ring (bytes)
   uint32_t* prbs_jump;         // [64][31] columns of A^(2^i)

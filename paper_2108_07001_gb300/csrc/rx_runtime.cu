@@ -30,6 +30,9 @@ cudaError_t launch_sync(const RxDev& d, cudaStream_t s);
 cudaError_t launch_ber(const RxDev& d, long long ka, long long kb, long long w_from, long long w_to,
                        long long k_lim, int n_win_ring, cudaStream_t s);
 cudaError_t launch_ingest(const RxDev& d, const void* src, int dtype, long long n, long long w0, cudaStream_t s);
+cudaError_t cd_set_attributes();
+cudaError_t bps_set_attributes();
+cudaError_t ber_set_attributes();
 }  // namespace rx
 
 using namespace rx;
@@ -80,6 +83,7 @@ struct rx_handle {
   cudaEvent_t ev_reset = nullptr;  // last rx_reset (recorded on the compute stream)
   bool reset_pending = false;
   cudaStream_t last_cs = nullptr;  // stream of the last push (input arrival events)
+  bool copy_dirty = false;         // ingests queued since ev_copy was last recorded
   long long pushed = 0;       // samples per pol written to the ring
   long long n_total = -1;     // samples per pol in the stream (after end)
   bool ended = false;
@@ -177,8 +181,8 @@ int dalloc(T** p, size_t n) {
 
 void free_all(rx_handle* h) {
   RxDev& d = h->d;
-  void* ptrs[] = {d.ring, d.Hs, d.Hf, d.tw, d.z, d.rot_hi, d.rot_lo, d.acc, d.psd, d.rec, d.st, d.w_acq,
-                  d.chains, d.y, d.bl, d.run_int, d.run_m0, d.dec, d.out, d.prbs_jump, d.ref,
+  void* ptrs[] = {d.ring, d.Hs, d.Hf, d.tw, d.tw2, d.z, d.rot_hi, d.rot_lo, d.acc, d.psd, d.rec, d.st, d.w_acq,
+                  d.chains, d.y, d.bl, d.run_int, d.run_m0, d.run_edge, d.bps_done, d.ber_done, d.dec, d.out, d.prbs_jump, d.ref,
                   d.sync_err, d.win_err, d.hist_y, d.hist_bhat, d.hist_m, h->stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -263,6 +267,13 @@ int staged(rx_handle* h, PendingFrame& pf, int stage, Fn&& fn) {
     h->stage_n[st] += (nk);                                                      \
   } while (0)
 
+// Records ev_copy after the ingests queued so far (on the last push stream).
+cudaError_t mark_copy(rx_handle* h) {
+  if (!h->copy_dirty) return cudaSuccess;
+  h->copy_dirty = false;
+  return cudaEventRecord(h->ev_copy, h->last_cs);
+}
+
 // Launch the decision stages (BPS .. BER) for decided range [k_a, k_b).
 int launch_decide(rx_handle* h, PendingFrame& pf, const FrameArgs& fa, bool final_) {
   const RxDev& d = h->d;
@@ -276,7 +287,7 @@ int launch_decide(rx_handle* h, PendingFrame& pf, const FrameArgs& fa, bool fina
       const int nb = (d.sync_syms + 2 * d.sync_dmax) * d.bps;
       RX_CK(launch_ref_gen(d, ks - d.sync_dmax, nb, 0, h->s_comp));
       RX_CK(launch_sync(d, h->s_comp));
-      h->stage_n[RX_STAGE_BER] += 3;
+      h->stage_n[RX_STAGE_BER] += 2;
       h->synced = true;
       h->w_next = 0;
     }
@@ -288,13 +299,13 @@ int launch_decide(rx_handle* h, PendingFrame& pf, const FrameArgs& fa, bool fina
       if (hi > ka) {
         const int nbits = (int)((hi - ka) * d.bps);
         RX_CK(launch_ref_gen(d, ka, nbits, 1, h->s_comp));
-        h->stage_n[RX_STAGE_BER] += 2;  // reference + count
+        h->stage_n[RX_STAGE_BER] += 1;
       }
       const long long klim = final_ ? fa.k_end : fa.k_b;
       long long w_to = klim > ks ? (final_ ? (klim - ks + d.slip_win - 1) / d.slip_win : (klim - ks) / d.slip_win) : 0;
       if (w_to < h->w_next) w_to = h->w_next;
+      if (hi > ka || w_to > h->w_next) h->stage_n[RX_STAGE_BER] += 1;  // count (+ slip pass in its last block)
       RX_CK(launch_ber(d, ka, std::max(hi, ka), h->w_next, w_to, klim, h->n_win_ring, h->s_comp));
-      if (w_to > h->w_next) h->stage_n[RX_STAGE_BER] += 1;  // slip pass
       h->w_next = w_to;
     }
     return RX_OK;
@@ -326,6 +337,7 @@ int launch_frame(rx_handle* h, long long f, bool final_) {
   pf.ev_in = get_event(h);
   pf.ev_start = get_event(h);
   pf.ev_done = get_event(h);
+  RX_CK(mark_copy(h));
   RX_CK(cudaEventRecord(pf.ev_in, h->last_cs));
   RX_CK(cudaStreamWaitEvent(h->s_comp, h->ev_copy, 0));
   RX_CK(cudaEventRecord(pf.ev_start, h->s_comp));
@@ -369,6 +381,7 @@ int launch_tail(rx_handle* h) {
   pf.ev_in = get_event(h);
   pf.ev_start = get_event(h);
   pf.ev_done = get_event(h);
+  RX_CK(mark_copy(h));
   RX_CK(cudaEventRecord(pf.ev_in, h->last_cs));
   RX_CK(cudaStreamWaitEvent(h->s_comp, h->ev_copy, 0));
   RX_CK(cudaEventRecord(pf.ev_start, h->s_comp));
@@ -514,7 +527,9 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   d.hist_syms = cfg->history_syms;
 
   h->tail = (d.h + 1) / 2 + d.T + d.W;
-  h->la = std::max(d.c + d.h + 2, 2 * (h->tail + d.W + 2));
+  // look-ahead: the last overlap-save block of a frame reads up to L + h + c
+  // samples beyond the frame end; the BER end rule needs tail + W symbols
+  h->la = std::max(d.L + d.h + d.c + 2, 2 * (h->tail + d.W + 2));
   const long long mb = (long long)cfg->max_block_samples;
   d.ring_cap = 2LL * d.F + 2LL * h->la + d.c + d.h + mb + 1024;
   d.out_cap_bytes = std::max<long long>(1 << 20, 32LL * d.F * 2 * d.bps / 8);
@@ -534,6 +549,7 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   RX_AL(d.Hs, N);
   RX_AL(d.Hf, N);
   RX_AL(d.tw, N);
+  RX_AL(d.tw2, 256);
   RX_AL(d.z, 2LL * d.zlen);
   RX_AL(d.rot_hi, d.zlen / kRotLo + 2);
   RX_AL(d.rot_lo, kRotLo);
@@ -543,10 +559,13 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   RX_AL(d.st, 1);
   RX_AL(d.w_acq, 4 * d.T);
   RX_AL(d.chains, (size_t)d.G * 4 * d.T);
-  RX_AL(d.y, 4LL * d.F);
+  RX_AL(d.y, 4LL * (kYHist + d.F));
   RX_AL(d.bl, 2LL * (d.F + 2 * d.W));
   RX_AL(d.run_int, 2LL * nruns);
   RX_AL(d.run_m0, 2LL * nruns);
+  RX_AL(d.run_edge, 4LL * nruns);
+  RX_AL(d.bps_done, 2);
+  RX_AL(d.ber_done, 2);
   RX_AL(d.dec, d.dec_cap);
   RX_AL(d.out, d.out_cap_bytes);
   RX_AL(d.prbs_jump, 64 * 31);
@@ -579,6 +598,13 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
     cudaMemcpy(d.Hs, Hs.data(), N * sizeof(float2), cudaMemcpyHostToDevice);
     cudaMemcpy(d.Hf, Hs.data(), N * sizeof(float2), cudaMemcpyHostToDevice);
     cudaMemcpy(d.tw, tw.data(), N * sizeof(float2), cudaMemcpyHostToDevice);
+    std::vector<float2> tw2(256);
+    for (int i = 0; i < 128; ++i) {
+      const double ah = -2.0 * M_PI * (double)(i * 128) / N, al = -2.0 * M_PI * (double)i / N;
+      tw2[i] = make_float2((float)std::cos(ah), (float)std::sin(ah));
+      tw2[128 + i] = make_float2((float)std::cos(al), (float)std::sin(al));
+    }
+    cudaMemcpy(d.tw2, tw2.data(), 256 * sizeof(float2), cudaMemcpyHostToDevice);
   }
   // PRBS jump matrices A^(2^i): A shifts the window down one bit and sets
   // bit 30 = bit 3 ^ bit 0.
@@ -602,6 +628,14 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_reset, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev_copy, h->s_copy);
+  if (e == cudaSuccess) e = cd_set_attributes();
+  if (e == cudaSuccess) e = bps_set_attributes();
+  if (e == cudaSuccess) e = ber_set_attributes();
+  for (int i = 0; i < 512 && e == cudaSuccess; ++i) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreate(&ev);
+    if (e == cudaSuccess) h->ev_pool.push_back(ev);
+  }
   h->cd_done.assign(64, nullptr);
   for (auto& ev : h->cd_done)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -651,6 +685,10 @@ int rx_push_block(rx_handle* h, const void* samples, size_t n_per_pol, int dtype
       return fail(RX_EAGAIN, "output ring full: pull bits first");
   }
   cudaStream_t cs = (cudaStream_t)cuda_stream;
+  if (h->copy_dirty && cs != h->last_cs) {  // keep all ingests ordered on one stream's event
+    RX_CK(mark_copy(h));
+    RX_CK(cudaStreamWaitEvent(cs, h->ev_copy, 0));
+  }
   // The copy runs on the caller's stream, so it is ordered after the
   // caller's queued work and the caller's later work is ordered after it.
   // Ring slots being overwritten must no longer be read by launched frames.
@@ -681,9 +719,12 @@ int rx_push_block(rx_handle* h, const void* samples, size_t n_per_pol, int dtype
     RX_CK(launch_ingest(d, src, dtype, n, h->pushed, cs));
   }
   h->stage_n[RX_STAGE_INGEST] += 1;
-  RX_CK(cudaEventRecord(h->ev_copy, cs));
   h->last_cs = cs;
-  if (!on_device) RX_CK(cudaEventSynchronize(h->ev_copy));  // host buffer and staging reusable
+  h->copy_dirty = true;
+  if (!on_device) {  // host buffer and staging reusable on return
+    RX_CK(mark_copy(h));
+    RX_CK(cudaEventSynchronize(h->ev_copy));
+  }
   h->pushed += n;
   while (h->pushed >= 2 * (h->f_next + 1) * F + h->la) {
     int rc = launch_frame(h, h->f_next, false);
@@ -790,13 +831,14 @@ int rx_reset(rx_handle* h) {
   RxDev& d = h->d;
   cudaStream_t s = h->s_comp;
   // stream-ordered: runs after all queued frames, before the next stream's work
+  RX_CK(mark_copy(h));
   RX_CK(cudaStreamWaitEvent(s, h->ev_copy, 0));
   StreamState st{};
   st.bhat_last[0] = st.bhat_last[1] = -1;
   RX_CK(cudaMemcpyAsync(d.st, &h->st_init, sizeof(st), cudaMemcpyHostToDevice, s));
   RX_CK(cudaMemcpyAsync(d.Hf, d.Hs, d.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
   RX_CK(cudaMemsetAsync(d.acc, 0, sizeof(FrameAcc), s));
-  RX_CK(cudaMemsetAsync(d.psd, 0, (d.N / 2) * sizeof(float), s));
+  RX_CK(cudaMemsetAsync(d.psd, 0, (d.N / 2) * sizeof(double), s));
   RX_CK(cudaMemsetAsync(d.win_err, 0, (size_t)h->n_win_ring * 8 * sizeof(unsigned), s));
   RX_CK(cudaMemsetAsync(d.rec, 0, kMaxTrace * sizeof(FrameRec), s));
   if (d.hist_syms > 0) {

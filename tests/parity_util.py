@@ -93,7 +93,16 @@ def compare(gpu: dict, ref: dict, rx_kw: dict, check_bits=True) -> dict:
     rep = {}
     y_err = rel_rms(gpu["y"], ref["y"])
     rep["y_rel_rms"] = y_err
-    assert y_err <= Y_TOL, f"equalised symbols: rel RMS {y_err:.3e} > {Y_TOL}"
+    if y_err > Y_TOL:
+        F = rx_kw.get("frame_syms", 1 << 16)
+        n = ref["y"].shape[1]
+        per = [rel_rms(gpu["y"][:, a:a + F], ref["y"][:, a:a + F]) for a in range(0, n, F)]
+        worst = np.argsort(-np.abs(gpu["y"] - ref["y"]).max(axis=0))[:8]
+        tr = gpu.get("trace")
+        msg = (f"equalised symbols: rel RMS {y_err:.3e} > {Y_TOL}; per frame {np.round(per, 7).tolist()}; "
+               f"worst symbols {worst.tolist()}; gpu trace {None if tr is None else tr.tolist()}; "
+               f"oracle tau {ref['trace']['tau']} dfo {ref['trace']['dfo']} gain {ref['trace']['gain']}")
+        raise AssertionError(msg)
 
     # BPS angles: equal, or a near-tie under the oracle's own metric
     bh_g = gpu["bhat"].astype(np.int64)
@@ -109,22 +118,36 @@ def compare(gpu: dict, ref: dict, rx_kw: dict, check_bits=True) -> dict:
             assert ok.all(), f"pol {p}: {np.sum(~ok)} BPS angles are not near-ties"
             tie[p, diff] = True
     rep["bps_ties"] = int(tie.sum())
-    # unwrapped phase: angles equal -> phase equal (same unwrap counter modulo the
-    # branch shift a near-tie across the grid edge produces)
+    # unwrap counters: m_gpu - m_oracle may change only at a near-tie symbol or
+    # the one after it (a tie can move the unwrap branch by a multiple of pi/2;
+    # both branches are valid outputs); elsewhere the phases are identical.
+    delta = gpu["m"].astype(np.int64) - ref["m"]
+    for p in range(2):
+        jumps = np.nonzero(np.diff(delta[p]))[0] + 1
+        ok = tie[p, jumps] | tie[p, jumps - 1]
+        assert ok.all(), f"pol {p}: unwrap branch changes at {jumps[~ok][:5]} without a near-tie"
     phi = O.bps_angles(B)
-    ph_g = phi[bh_g] + gpu["m"] * (math.pi / 2)
+    ph_g = phi[bh_g] + (gpu["m"] - delta) * (math.pi / 2)
     ph_o = phi[bh_o] + ref["m"] * (math.pi / 2)
-    dph = np.abs(ph_g - ph_o)
-    assert np.all(dph[~tie] < 1e-9), "unwrap counters differ where the BPS angles agree"
-    assert np.all(dph <= math.pi / 2 / B + 1e-9), "unwrapped phase differs by more than one grid step"
+    assert np.all(np.abs(ph_g - ph_o)[~tie] < 1e-9), "phases differ where the BPS angles agree"
+    rep["branch_shift_syms"] = int(np.count_nonzero(delta))
 
     if check_bits:
-        # bits: symbol-major, pol x then y, I bits then Q bits
+        # bits: symbol-major, pol x then y, I bits then Q bits; the oracle's
+        # decisions are moved to the GPU's unwrap branch ((-j)^delta) first
         n_sym = ref["y"].shape[1]
-        sb = 2 * bps
-        gb = gpu["bits"][:n_sym * sb].reshape(n_sym, 2, bps)
-        ob = np.stack([ref["bits"][0], ref["bits"][1]], axis=1)  # [n, 2, bps]
-        assert gb.shape == ob.shape, (gb.shape, ob.shape)
+        nl = 2 if bps == 2 else 4
+        lb = O.level_bits(bps)
+        gb = gpu["bits"][:n_sym * 2 * bps].reshape(n_sym, 2, bps)
+        ob = np.zeros_like(gb)
+        for p in range(2):
+            lI, lQ = ref["levels"][p][0].copy(), ref["levels"][p][1].copy()
+            q = np.mod(delta[p], 4)
+            for _ in range(3):
+                rot = q > 0
+                lI[rot], lQ[rot] = lQ[rot], nl - 1 - lI[rot]
+                q = np.where(rot, q - 1, q)
+            ob[:, p, :] = np.concatenate([lb[lI], lb[lQ]], axis=1)
         mism = np.any(gb != ob, axis=2)  # [n, 2]
         lv = O.levels(bps)
         thr = 0.5 * (lv[1:] + lv[:-1])
