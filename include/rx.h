@@ -207,6 +207,36 @@ int rx_get_equalised(rx_handle* h, int64_t first, int64_t n, float* out);
  * history.  Waits for queued work.  RX_EINVAL outside the history. */
 int rx_get_phase(rx_handle* h, int64_t first, int64_t n, uint8_t* bhat, int32_t* m);
 
+/* ---- allocation-free block decisions ----------------------------------
+ * The paper has no counterpart to this call; it exists for callers that
+ * must not enter the CUDA allocator: for example a capture thread with a
+ * hard deadline, where cudaMalloc's latency and implicit synchronisation
+ * are not acceptable, or a process whose device memory is already held by
+ * another pool allocator, so a cudaMalloc would fail.
+ *
+ * Blind phase search, unwrap, decisions and Gray demapping of one block of
+ * n equalised symbols y (device, complex float, planar [2][n], re/im
+ * interleaved), exactly as the streaming receiver decides a stream that
+ * consists of this one block (window truncated at both ends, unwrap
+ * counter starting at 0).  Decided bits go to the device buffer bits
+ * (caller owned, at least ceil(n * 2 * modulation / 8) bytes) in the
+ * rx_pull_bits order.  Work is queued on cuda_stream; nothing is allocated:
+ * all working memory is one static device array of about 1.4 MB that every
+ * device which loads the library holds until the process exits.
+ *   n                 1 .. RX_NOALLOC_MAX_SYMS, else RX_EINVAL
+ *   modulation        RX_QPSK or RX_QAM16; bps_angles 32 or 64;
+ *   bps_half_window   8, 12, 16, 24 or 32
+ * The first call on a device (the device current at the call) looks up
+ * that array's device address and sets kernel attributes; make that first
+ * call before any stream capture.  All calls share the one array and it
+ * keeps the last call's contents: calls whose work overlaps on the GPU
+ * (different streams, or several host threads) race and must be ordered
+ * by the caller.  Returns RX_OK, RX_EINVAL or RX_EDEVICE (message via
+ * rx_last_error()). */
+#define RX_NOALLOC_MAX_SYMS 65536
+int rx_decide_block_noalloc(const void* y, int64_t n, int modulation, int bps_angles,
+                            int bps_half_window, uint8_t* bits, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -423,6 +423,11 @@ int validate(const rx_config* c, std::string& why) {
 
 }  // namespace
 
+namespace rx {
+// Message for rx_last_error() from code outside this file.
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace rx
+
 extern "C" {
 
 const char* rx_last_error(void) { return g_err.c_str(); }

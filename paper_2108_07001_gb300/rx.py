@@ -24,7 +24,8 @@ STAGES = ["ingest", "cd", "est", "acquire", "mimo", "bps", "demap", "ber"]
 # every function declared in include/rx.h
 EXPORTS = ["rx_config_default", "rx_create", "rx_push_block", "rx_pull_bits", "rx_stats",
            "rx_destroy", "rx_reset", "rx_join", "rx_stage_times", "rx_last_error",
-           "rx_frame_trace", "rx_get_taps", "rx_get_equalised", "rx_get_phase"]
+           "rx_frame_trace", "rx_get_taps", "rx_get_equalised", "rx_get_phase",
+           "rx_decide_block_noalloc"]
 
 
 class RxConfig(ctypes.Structure):
@@ -117,9 +118,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rx_get_taps.argtypes = [P, I, ctypes.POINTER(ctypes.c_float)]
     lib.rx_get_equalised.argtypes = [P, I64, I64, ctypes.POINTER(ctypes.c_float)]
     lib.rx_get_phase.argtypes = [P, I64, I64, ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_int32)]
+    lib.rx_decide_block_noalloc.argtypes = [P, I64, I, I, I, P, P]
     for name in ["rx_create", "rx_push_block", "rx_pull_bits", "rx_stats", "rx_destroy", "rx_reset",
                  "rx_join", "rx_stage_times", "rx_frame_trace", "rx_get_taps", "rx_get_equalised",
-                 "rx_get_phase"]:
+                 "rx_get_phase", "rx_decide_block_noalloc"]:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
