@@ -141,10 +141,24 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* __restrict__
     if ((NB % NT) == 0 || j < NB) {
       const int k = j & (NS - 1);
       if (NS > 1) {
+        // w^r for r < R from the table entries w, w^2, w^4, w^8 (each power
+        // is a product of at most four correctly rounded table values)
         constexpr int STEP = N / (NS * R);
+        const int m = k * STEP * tws;
+        float2 wp[R];
+        wp[1] = twiddle(tw, m);
+        if (R > 2) wp[2] = twiddle(tw, 2 * m);
+        if (R > 4) wp[4] = twiddle(tw, 4 * m);
+        if (R > 8) wp[8] = twiddle(tw, 8 * m);
+#pragma unroll
+        for (int r = 3; r < R; ++r) {
+          if (r == 4 || r == 8) continue;
+          const int hb = r >= 8 ? 8 : (r >= 4 ? 4 : 2);
+          wp[r] = cmul(wp[hb], wp[r - hb]);
+        }
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          float2 w = twiddle(tw, (r * k * STEP) * tws);
+          float2 w = wp[r];
           if (INV) w.y = -w.y;
           v[u][r] = cmul(v[u][r], w);
         }

@@ -175,49 +175,85 @@ __global__ void __launch_bounds__(256) sync_kernel(RxDev d) {
 __device__ void slip_pass(const RxDev& d, long long w_from, long long w_to, long long k_lim, int n_win_ring,
                           unsigned* win_s);
 
+constexpr int kBerSyms = 4;  // symbols per thread
+
 __global__ void __launch_bounds__(256) ber_count_kernel(RxDev d, long long ka, long long kb, long long w_from,
                                                         long long w_to, long long k_lim, int n_win_ring) {
+  __shared__ uint8_t lut[4][16];  // bits of level code (lI | lQ << 2) rotated by q
   __shared__ unsigned red[8][9];
   __shared__ int am_last;
+  if (threadIdx.x < 64) {
+    const int q = threadIdx.x >> 4, lv = threadIdx.x & 15;
+    lut[q][lv] = (uint8_t)rx_sym_bits(lv & 3, lv >> 2, q, d.nl);
+  }
+  __syncthreads();
   const long long ks = d.ber_skip;
-  const long long kal = ks + ((ka - ks) / 32) * 32;
-  const long long k = kal + (long long)blockIdx.x * 256 + threadIdx.x;
-  const int perm = d.st->sync_perm;
+  const long long kal = ks + ((ka - ks) / (32 * kBerSyms)) * (32 * kBerSyms);
+  // thread t of block b handles symbols k0 + 32 j + lane (j < kBerSyms) of its warp's span
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const long long kw = kal + ((long long)blockIdx.x * 8 + w) * 32 * kBerSyms;  // warp span start
+  const int perm = d.st->sync_perm;
   unsigned err[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-  if (k >= ka && k < kb) {
-    const uint8_t v = d.dec[k % d.dec_cap];
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-      const int tx = p ^ perm;
-      const uint32_t rb = ref_bits(d.ref + (long long)tx * d.ref_words, (k - ka) * d.bps, d.bps);
-      const int lv = (v >> (4 * p)) & 15;
+  for (int j = 0; j < kBerSyms; ++j) {
+    const long long k = kw + 32 * j + l;
+    if (k >= ka && k < kb) {
+      const uint8_t v = d.dec[k % d.dec_cap];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) err[p][q] = __popc(rx_sym_bits(lv & 3, lv >> 2, q, d.nl) ^ rb);
+      for (int p = 0; p < 2; ++p) {
+        const uint32_t rb = ref_bits(d.ref + (long long)(p ^ perm) * d.ref_words, (k - ka) * d.bps, d.bps);
+        const int lv = (v >> (4 * p)) & 15;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) err[p][q] += __popc((uint32_t)lut[q][lv] ^ rb);
+      }
     }
   }
-  const long long kw = kal + (long long)blockIdx.x * 256 + (threadIdx.x & ~31);
-  const long long win = (kw - ks) / d.slip_win;
+  // a warp span (32 kBerSyms symbols, aligned to ks) lies in one window
+  // unless slip_win is not a multiple of the span; then per-symbol atomics
+  const bool one_window = ((kw - ks) / d.slip_win) == ((kw + 32 * kBerSyms - 1 - ks) / d.slip_win);
+  if (one_window) {
 #pragma unroll
-  for (int p = 0; p < 2; ++p)
+    for (int p = 0; p < 2; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      unsigned s = err[p][q];
+      for (int q = 0; q < 4; ++q) {
+        unsigned s = err[p][q];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (l == 0) red[w][p * 4 + q] = s;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (l == 0) red[w][p * 4 + q] = s;
+      }
+    if (l == 0) red[w][8] = (unsigned)((kw - ks) / d.slip_win);
+  } else {
+    // rare (small windows): per-symbol atomics
+    if (l == 0) red[w][8] = 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < kBerSyms; ++j) {
+      const long long k = kw + 32 * j + l;
+      if (k >= ka && k < kb) {
+        const long long win = (k - ks) / d.slip_win;
+        const uint8_t v = d.dec[k % d.dec_cap];
+        for (int p = 0; p < 2; ++p) {
+          const uint32_t rb = ref_bits(d.ref + (long long)(p ^ perm) * d.ref_words, (k - ka) * d.bps, d.bps);
+          const int lv = (v >> (4 * p)) & 15;
+          for (int q = 0; q < 4; ++q) {
+            const unsigned e = __popc((uint32_t)lut[q][lv] ^ rb);
+            if (e) atomicAdd(&d.win_err[(win % n_win_ring) * 8 + p * 4 + q], e);
+          }
+        }
+      }
     }
-  if (l == 0) red[w][8] = (unsigned)win;  // windows differ by block only when SW < 256
+  }
   __syncthreads();
   if (threadIdx.x < 8) {
     const int j = threadIdx.x;
     unsigned acc = 0;
-    unsigned cur = red[0][8];
+    unsigned cur = 0xffffffffu;
     for (int ww = 0; ww < 8; ++ww) {
-      if (red[ww][8] != cur) {
+      const unsigned wnd = red[ww][8];
+      if (wnd == 0xffffffffu) continue;
+      if (wnd != cur) {
         if (acc) atomicAdd(&d.win_err[(cur % n_win_ring) * 8 + j], acc);
         acc = 0;
-        cur = red[ww][8];
+        cur = wnd;
       }
       acc += red[ww][j];
     }
@@ -358,9 +394,10 @@ cudaError_t launch_ber(const RxDev& d, long long ka, long long kb, long long w_f
                        long long k_lim, int n_win_ring, cudaStream_t s) {
   if (kb <= ka && w_to <= w_from) return cudaSuccess;
   const long long ks = d.ber_skip;
-  const long long kal = ks + ((max(ka, ks) - ks) / 32) * 32;
+  const long long kal = ks + ((max(ka, ks) - ks) / (32 * kBerSyms)) * (32 * kBerSyms);
   const long long n = max(kb - kal, 1LL);
-  ber_count_kernel<<<(unsigned)((n + 255) / 256), 256, kSlipChunk * 8 * sizeof(unsigned), s>>>(
+  const long long per_block = 256LL * kBerSyms;
+  ber_count_kernel<<<(unsigned)((n + per_block - 1) / per_block), 256, kSlipChunk * 8 * sizeof(unsigned), s>>>(
       d, ka, kb, w_from, w_to, k_lim, n_win_ring);
   return cudaGetLastError();
 }

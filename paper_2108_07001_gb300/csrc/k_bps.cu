@@ -8,83 +8,66 @@
 // integers as floor((2 (b_{k-1} - b_k) + B) / 2B); the decision is
 // dec(y_k e^{-j(phi_b + m pi/2)}) = dec(y_k e^{-j phi_b}) (-j)^m.
 //
-// Kernel layout: lane = test angle, a group of B/32 warps slides a
-// (2W+1)-symbol window along a run of kRun symbols of one polarisation,
-// keeping the last 2W+1 metrics in registers (the loop is unrolled by 2W+1
-// so the ring index is static).  After every 2W+1 steps the group has
-// written the window sums of those steps to shared memory as
-// order-preserving keys (float bits with the low 6 bits replaced by the
-// angle) and reduces each symbol's B keys with an integer min.  Runs that
-// touch no stream edge take an unpredicated path.  The last block of each
+// Kernel layout: one warp per run of kRun symbols of one polarisation;
+// lane l holds the test angles l + 32a (B/32 per lane) and slides a
+// (2W+1)-symbol window with the last 2W+1 metrics in registers (the loop is
+// unrolled by 2W+1 so the ring index is static).  Each step the lane writes
+// the smaller of its angles' order-preserving keys (float bits with the
+// low 6 bits replaced by the angle) to a shared-memory row; after 2W+1
+// steps the rows are reduced with an integer min.  Runs that touch no
+// stream edge take no per-step predicate.  The last block of each
 // polarisation (found with an atomic counter after a fence; nothing waits)
-// turns the runs' unwrap sums into each run's starting counter.  The metric is the squared
-// distance in scaled units where the levels are odd integers: QPSK
-// (x sqrt2, levels +-1): per dimension |u| - 1; 16QAM (x sqrt10, levels
-// +-1, +-3): ||u| - 2| - 1.  Keeping the (small) distance itself, rather
-// than an equivalent large correlation, keeps the key's 17-bit resolution
-// relative to the quantity being minimised.
+// turns the runs' unwrap sums into each run's starting counter.
 #include "rx_internal.cuh"
 
 namespace rx {
-
-template <int B>
-__device__ __forceinline__ void group_sync(int g) {
-  if constexpr (B == 32) {
-    __syncwarp();
-  } else {
-    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(B) : "memory");
-  }
-}
 
 __device__ __forceinline__ int unwrap_inc(int a, int b, int B) {  // floor((2(a-b)+B)/(2B))
   const int x = 2 * (a - b) + B;
   return (x >= 2 * B) - (x < 0);
 }
 
-template <int B, int W, bool QAM16, bool EDGE>
-__device__ __forceinline__ void bps_window_step(const float2* __restrict__ yb, int u, int s, int sv_lo, int sv_hi,
-                                                float c_s, float s_s, float& D, float& ring_u) {
-  float m = 0.f;
-  if (!EDGE || (s >= sv_lo && s < sv_hi)) {
-    const float2 yv = yb[u];
-    const float zx = fmaf(yv.x, c_s, yv.y * s_s);
-    const float zy = fmaf(yv.y, c_s, -yv.x * s_s);
-    float ex, ey;
-    if (QAM16) {
-      ex = fabsf(fabsf(zx) - 2.f) - 1.f;
-      ey = fabsf(fabsf(zy) - 2.f) - 1.f;
-    } else {
-      ex = fabsf(zx) - 1.f;
-      ey = fabsf(zy) - 1.f;
-    }
-    m = fmaf(ex, ex, ey * ey);
+// Metric of one symbol at one test angle (scaled squared distance).
+template <bool QAM16>
+__device__ __forceinline__ float bps_metric(float2 yv, float c_s, float s_s) {
+  const float zx = fmaf(yv.x, c_s, yv.y * s_s);
+  const float zy = fmaf(yv.y, c_s, -yv.x * s_s);
+  float ex, ey;
+  if (QAM16) {
+    ex = fabsf(fabsf(zx) - 2.f) - 1.f;
+    ey = fabsf(fabsf(zy) - 2.f) - 1.f;
+  } else {
+    ex = fabsf(zx) - 1.f;
+    ey = fabsf(zy) - 1.f;
   }
-  D += m;
-  D -= ring_u;
-  ring_u = m;
+  return fmaf(ex, ex, ey * ey);
 }
 
-// One block = 8 warps = 256/B runs of kRun symbols of one polarisation.
+// One warp = one run of kRun symbols of one polarisation; lane l holds the
+// test angles l + 32 a (a < APL = B/32), each with its own register ring of
+// the last 2W+1 metrics.  Per window step the lane packs its angles' window
+// sums into keys and keeps the smaller, so a row of 32 keys per output is
+// reduced afterwards.  The run's symbols (with the window halo) are staged
+// in shared memory once.
 template <int B, int W, bool QAM16>
-__global__ void __launch_bounds__(256) bps_kernel(RxDev d, FrameArgs fa) {
-  constexpr int HALVES = B / 32;         // warps per group
-  constexpr int GROUPS = 8 / HALVES;     // runs per block
+__global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
+  constexpr int APL = B / 32;            // angles per lane
   constexpr int WIN = 2 * W + 1;
-  constexpr int ROW = B + 4;             // padded key row (words)
-  extern __shared__ __align__(16) uint32_t keys_smem[];  // [GROUPS][WIN][ROW]
-  __shared__ int bh_s[GROUPS][WIN];
+  constexpr int ROW = 36;                // padded key row (words)
+  constexpr int YS = kRun + 2 * W;       // staged symbols per run
+  extern __shared__ __align__(16) uint32_t keys_smem[];  // [8 warps][WIN][ROW]
+  __shared__ float2 y_s[8][kRun + 64];
+  __shared__ uint8_t bh_s[8][kRun];
   __shared__ float2 cs_s[B];
   __shared__ float red_s[8][3];
   __shared__ int part[256];
   __shared__ int am_last;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = warp / HALVES, wg = warp % HALVES;
-  const int tg = wg * 32 + lane;  // thread index within the group
   const int pol = blockIdx.y;
   const long long n_dec = fa.k_b - fa.k_a;
   const int nruns = (int)((n_dec + kRun - 1) / kRun);
-  const int run = blockIdx.x * GROUPS + g;
+  const int run = blockIdx.x * 8 + warp;
   const long long kr = fa.k_a + (long long)run * kRun;
   const int ract = run < nruns ? (int)min((long long)kRun, fa.k_b - kr) : 0;
 
@@ -93,118 +76,124 @@ __global__ void __launch_bounds__(256) bps_kernel(RxDev d, FrameArgs fa) {
     sincospif(((float)threadIdx.x / (float)B - 0.5f) * 0.5f, &sb, &cb);
     cs_s[threadIdx.x] = make_float2(cb, sb);
   }
-  const int b = tg;  // this lane's test angle
-  float cs, sn;
-  sincospif(((float)b / (float)B - 0.5f) * 0.5f, &sn, &cs);
   const float sc = QAM16 ? 3.16227766016837933f : 1.41421356237309505f;
-  const float c_s = cs * sc, s_s = sn * sc;
+  float c_s[APL], s_s[APL];
+#pragma unroll
+  for (int a = 0; a < APL; ++a) {
+    float cs, sn;
+    sincospif(((float)(lane + 32 * a) / (float)B - 0.5f) * 0.5f, &sn, &cs);
+    c_s[a] = cs * sc;
+    s_s[a] = sn * sc;
+  }
 
-  // y of the frame with its history: symbol i is yf[i - fbase] for i >= fbase - kYHist
+  // stage the run's symbols kr - W .. kr + ract + W (zero outside the stream)
   const long long fbase = fa.f * (long long)d.F;
   const float2* yf = d.y + ((long long)(fa.f & 1) * 2 + pol) * (kYHist + d.F) + kYHist;
   const long long ylim = min(fa.n_sym, fbase + fa.Ff);  // symbols beyond do not exist (yet)
-  // window step s reads symbol kr - W + s; valid steps [sv_lo, sv_hi)
   const int total = ract + 2 * W;
-  const float2* yrun = yf + (kr - W - fbase);
   const int sv_lo = (int)max(0LL, (long long)W - kr);
   const int sv_hi = (int)min((long long)total, ylim - (kr - W));
+  float2* ys = y_s[warp];
+  for (int i = lane; i < total; i += 32)
+    ys[i] = (i >= sv_lo && i < sv_hi) ? yf[kr - W - fbase + i] : make_float2(0.f, 0.f);
   const bool edge = sv_lo > 0 || sv_hi < total;
-  __syncthreads();  // cs_s
+  __syncthreads();  // cs_s, y_s
 
-  float ring[WIN];
+  float ring[APL][WIN];
 #pragma unroll
-  for (int u = 0; u < WIN; ++u) ring[u] = 0.f;
-  float D = 0.f;
-  float evn = 0.f, evd = 0.f;
-  int inc_sum = 0;
-  int bh_prev = -1, bh_first = -1;
-  uint16_t* blp = d.bl + (long long)pol * (d.F + 2 * d.W);
-  uint32_t* krow = keys_smem + (g * WIN) * ROW + b;
+  for (int a = 0; a < APL; ++a)
+#pragma unroll
+    for (int u = 0; u < WIN; ++u) ring[a][u] = 0.f;
+  float D[APL];
+#pragma unroll
+  for (int a = 0; a < APL; ++a) D[a] = 0.f;
+  uint32_t* kw = keys_smem + warp * WIN * ROW;
   for (int base = 0; base < total; base += WIN) {
-    const float2* yb = yrun + base;
+    const float2* yb = ys + base;
     if (!edge && base + WIN <= total) {
+      // interior: every step is a real symbol
 #pragma unroll
       for (int u = 0; u < WIN; ++u) {
-        bps_window_step<B, W, QAM16, false>(yb, u, base + u, sv_lo, sv_hi, c_s, s_s, D, ring[u]);
-        krow[u * ROW] = (__float_as_uint(fmaxf(D, 0.f)) & ~63u) | (uint32_t)b;
+        const float2 yv = yb[u];
+        uint32_t key = 0xffffffffu;
+#pragma unroll
+        for (int a = 0; a < APL; ++a) {
+          const float m = bps_metric<QAM16>(yv, c_s[a], s_s[a]);
+          D[a] += m;
+          D[a] -= ring[a][u];
+          ring[a][u] = m;
+          key = min(key, (__float_as_uint(D[a]) & ~63u) | (uint32_t)(lane + 32 * a));
+        }
+        kw[u * ROW + lane] = key;
       }
     } else {
 #pragma unroll
       for (int u = 0; u < WIN; ++u) {
-        if (base + u < total) {
-          bps_window_step<B, W, QAM16, true>(yb, u, base + u, sv_lo, sv_hi, c_s, s_s, D, ring[u]);
-          krow[u * ROW] = (__float_as_uint(fmaxf(D, 0.f)) & ~63u) | (uint32_t)b;
+        const int s = base + u;
+        if (s < total) {
+          const bool ok = s >= sv_lo && s < sv_hi;
+          const float2 yv = yb[u];
+          uint32_t key = 0xffffffffu;
+#pragma unroll
+          for (int a = 0; a < APL; ++a) {
+            const float m = ok ? bps_metric<QAM16>(yv, c_s[a], s_s[a]) : 0.f;
+            D[a] += m;
+            D[a] -= ring[a][u];
+            ring[a][u] = m;
+            key = min(key, (__float_as_uint(fmaxf(D[a], 0.f)) & ~63u) | (uint32_t)(lane + 32 * a));
+          }
+          kw[u * ROW + lane] = key;
         }
       }
     }
-    // outputs of this super-step: steps s in [max(base, 2W), min(base + WIN, total))
+    // reduce the super-step's outputs: steps [max(base, 2W), min(base + WIN, total))
     const int s_lo = max(base, 2 * W), s_hi = min(base + WIN, total);
-    if (s_hi > s_lo) {
-      group_sync<B>(g);
-      const int half = tg % HALVES;
-      for (int s = s_lo + tg / HALVES; s < s_lo + 32 * ((s_hi - s_lo + 31) / 32); s += 32) {
-        const int u = s - base;
-        const bool act = s < s_hi;
-        uint32_t best = 0xffffffffu;
-        if (act) {
-          const uint4* row = reinterpret_cast<const uint4*>(keys_smem + (g * WIN + u) * ROW + half * 32);
+    __syncwarp();
+    for (int s = s_lo + lane; s < s_hi; s += 32) {
+      const uint4* row = reinterpret_cast<const uint4*>(kw + (s - base) * ROW);
+      uint32_t best = 0xffffffffu;
 #pragma unroll
-          for (int c4 = 0; c4 < 8; ++c4) {
-            const uint4 v = row[c4];
-            best = min(best, min(min(v.x, v.y), min(v.z, v.w)));
-          }
-        }
-        if (HALVES == 2) best = min(best, __shfl_xor_sync(0xffffffffu, best, 1));
-        if (act && half == 0) bh_s[g][u] = (int)(best & 63u);
+      for (int c4 = 0; c4 < 8; ++c4) {
+        const uint4 v = row[c4];
+        best = min(best, min(min(v.x, v.y), min(v.z, v.w)));
       }
-      group_sync<B>(g);
-      // decisions, unwrap increments and EVM of the super-step's outputs
-      for (int s = s_lo + tg; s < s_hi; s += B) {
-        const int u = s - base;
-        const int ko = s - 2 * W;  // output index in the run
-        const long long k = kr + ko;
-        const int bh = bh_s[g][u];
-        const int bprev = (s == s_lo) ? (s == 2 * W ? -1 : bh_prev) : bh_s[g][u - 1];
-        if (bprev >= 0) inc_sum += unwrap_inc(bprev, bh, B);
-        const float2 yv = yrun[W + ko];
-        const float2 csb = cs_s[bh];
-        const float zx = fmaf(yv.x, csb.x, yv.y * csb.y), zy = fmaf(yv.y, csb.x, -yv.x * csb.y);
-        const int lI = level_of(zx, d.nl), lQ = level_of(zy, d.nl);
-        blp[k - fa.k_a] = (uint16_t)(bh | (lI << 8) | (lQ << 12));
-        if (k >= d.ber_skip && k < fa.k_end) {
-          const float dx = level_val(lI, d.nl), dy = level_val(lQ, d.nl);
-          evn += (zx - dx) * (zx - dx) + (zy - dy) * (zy - dy);
-          evd += dx * dx + dy * dy;
-        }
-      }
-      if (s_lo == 2 * W) bh_first = bh_s[g][s_lo - base];
-      bh_prev = bh_s[g][s_hi - 1 - base];
+      bh_s[warp][s - 2 * W] = (uint8_t)(best & 63u);
+    }
+    __syncwarp();
+  }
+  // decisions, unwrap increments and EVM of the run
+  float evn = 0.f, evd = 0.f;
+  int inc_sum = 0;
+  uint16_t* blp = d.bl + (long long)pol * (d.F + 2 * d.W);
+  for (int ko = lane; ko < ract; ko += 32) {
+    const int bh = bh_s[warp][ko];
+    if (ko > 0) inc_sum += unwrap_inc(bh_s[warp][ko - 1], bh, B);
+    const float2 yv = ys[W + ko];
+    const float2 csb = cs_s[bh];
+    const float zx = fmaf(yv.x, csb.x, yv.y * csb.y), zy = fmaf(yv.y, csb.x, -yv.x * csb.y);
+    const int lI = level_of(zx, d.nl), lQ = level_of(zy, d.nl);
+    const long long k = kr + ko;
+    blp[k - fa.k_a] = (uint16_t)(bh | (lI << 8) | (lQ << 12));
+    if (k >= d.ber_skip && k < fa.k_end) {
+      const float dx = level_val(lI, d.nl), dy = level_val(lQ, d.nl);
+      evn += (zx - dx) * (zx - dx) + (zy - dy) * (zy - dy);
+      evd += dx * dx + dy * dy;
     }
   }
-  // run results: internal unwrap sum, first and last angle
   const float incf = warp_sum((float)inc_sum);
   evn = warp_sum(evn);
   evd = warp_sum(evd);
+  const int stride = d.F / kRun + 4;
   if (lane == 0) {
-    red_s[warp][0] = incf;
     red_s[warp][1] = evn;
     red_s[warp][2] = evd;
-  }
-  __syncthreads();
-  const int stride = d.F / kRun + 4;
-  if (threadIdx.x < GROUPS) {
-    const int gg = threadIdx.x;
-    const int rr = blockIdx.x * GROUPS + gg;
-    if (rr < nruns) {
-      float si = 0.f;
-      for (int w = 0; w < HALVES; ++w) si += red_s[gg * HALVES + w][0];
-      d.run_int[pol * stride + rr] = (int)lrintf(si);
+    if (run < nruns) {
+      d.run_int[pol * stride + run] = (int)lrintf(incf);
+      d.run_edge[(pol * stride + run) * 2 + 0] = bh_s[warp][0];
+      d.run_edge[(pol * stride + run) * 2 + 1] = bh_s[warp][ract - 1];
     }
   }
-  if (tg == 0 && run < nruns) {
-    d.run_edge[(pol * stride + run) * 2 + 0] = bh_first;
-    d.run_edge[(pol * stride + run) * 2 + 1] = bh_prev;
-  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     float a = 0.f, c = 0.f;
     for (int w = 0; w < 8; ++w) { a += red_s[w][1]; c += red_s[w][2]; }
@@ -352,18 +341,16 @@ __global__ void __launch_bounds__(128) demap_kernel(RxDev d, FrameArgs fa) {
 
 template <int B, int W, bool Q>
 static void launch_bps_t(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
-  constexpr int GROUPS = 8 / (B / 32);
   const long long n_dec = fa.k_b - fa.k_a;
   const int nruns = (int)((n_dec + kRun - 1) / kRun);
-  dim3 grid((nruns + GROUPS - 1) / GROUPS, 2);
-  const size_t smem = sizeof(uint32_t) * GROUPS * (2 * W + 1) * (B + 4);
+  dim3 grid((nruns + 7) / 8, 2);
+  const size_t smem = sizeof(uint32_t) * 8 * (2 * W + 1) * 36;
   bps_kernel<B, W, Q><<<grid, 256, smem, s>>>(d, fa);
 }
 
 template <int B, int W>
 static cudaError_t bps_attr_t() {
-  constexpr int GROUPS = 8 / (B / 32);
-  const int smem = (int)(sizeof(uint32_t) * GROUPS * (2 * W + 1) * (B + 4));
+  const int smem = (int)(sizeof(uint32_t) * 8 * (2 * W + 1) * 36);
   cudaError_t e = cudaFuncSetAttribute(bps_kernel<B, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(bps_kernel<B, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -75,8 +75,9 @@ __global__ void __launch_bounds__(NT) cd_ols_kernel(RxDev d, FrameArgs fa) {
   gi = block_sum<NT>(gi, scratch);
   if (threadIdx.x == 0) {
     const float sg = (lo & 1) ? -1.f : 1.f;
-    atomicAdd(&d.acc->C[0], (double)(sg * gr));
-    atomicAdd(&d.acc->C[1], (double)(sg * gi));
+    FrameAcc* acc = d.acc + fa.acc_slot;
+    atomicAdd(&acc->C[0], (double)(sg * gr));
+    atomicAdd(&acc->C[1], (double)(sg * gi));
   }
   if (fa.est_only) return;
   __syncthreads();
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(NT) cd_ols_kernel(RxDev d, FrameArgs fa) {
     if (n >= fa.f0 && n < fa.f1) pw += v.x * v.x + v.y * v.y;
   }
   pw = block_sum<NT>(pw, scratch);
-  if (threadIdx.x == 0) atomicAdd(&d.acc->P, (double)pw);
+  if (threadIdx.x == 0) atomicAdd(&d.acc[fa.acc_slot].P, (double)pw);
 
   // 4th power of the even in-frame samples, zero padded to N/2
   const long long lo_n = max(a, fa.f0), hi_n = min(a + keep, fa.f1);
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(NT) cd_ols_kernel(RxDev d, FrameArgs fa) {
   fft_smem<N / 2, NT, false>(buf, tw_s, 2);
   for (int k = threadIdx.x; k < N / 2; k += NT) {
     const float2 v = buf[swz(k)];
-    atomicAdd(&d.psd[k], (double)(v.x * v.x + v.y * v.y));
+    atomicAdd(&d.psd[(long long)fa.acc_slot * (N / 2) + k], (double)(v.x * v.x + v.y * v.y));
   }
 }
 
@@ -133,29 +134,36 @@ __device__ __forceinline__ double wrap_pi(double x) {
   return fma(-kTwoPi, rint(x * kInvTwoPi), x);
 }
 
-// Per-frame estimator (one block of 1024 threads).
+// Per-frame estimator, nb blocks of 1024 threads.  Every block recomputes
+// the frame's scalars from the FP64 sums (same values in every block) and
+// fills its slice of the next H and of the rotation tables; block 0 writes
+// the estimator state of the next frame and the trace record.
 // mode 0 (timing acquisition of the first frame): tau = -arg(C)/(2 pi Rs).
 // mode 1 (after the frame's CD pass): FO from the periodogram (argmax, lowest
 //   index on ties; parabola through the logs of the peak and its cyclic
-//   neighbours), AGC gain 1/sqrt(mean |z|^2), the frame's rotation tables,
+//   neighbours; frames shorter than kFoeMinSyms keep the previous estimate),
+//   AGC gain 1/sqrt(mean |z|^2), the frame's rotation tables,
 //   tau <- tau + gain_t * residual, theta <- theta + w * 2 F_f.
-// Both modes then rebuild Hf = Hs * exp(+j 2 pi f_k tau) for the next CD
-// pass and clear the accumulators.  Phases are formed in FP64 and reduced
-// before the single-precision sine/cosine.
+// Accumulators and estimator state are double-buffered by frame parity:
+// frame f reads acc/psd slot fa.acc_slot and state es[f & 1], clears the
+// other accumulator slot and writes es[(f + 1) & 1].
 __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mode) {
   __shared__ double sv[32];
   __shared__ int si[32];
   __shared__ double sh[4];
   const int tid = threadIdx.x;
-  StreamState* st = d.st;
-  const double C_re = d.acc->C[0], C_im = d.acc->C[1];
+  const FrameAcc* acc = d.acc + fa.acc_slot;
+  const double* psd = d.psd + (long long)fa.acc_slot * (d.N / 2);
+  const double C_re = acc->C[0], C_im = acc->C[1];
   const double resid = (C_re == 0.0 && C_im == 0.0) ? 0.0 : -atan2(C_im, C_re) / (2.0 * M_PI * d.Rs);
+  double tau_next;
   if (mode == 1) {
+    const EstState es = d.es[fa.f & 1];
     const int n2 = d.N / 2;
     double best = -1.0;
     int bi = 0;
     for (int k = tid; k < n2; k += 1024) {
-      const double v = d.psd[k];
+      const double v = psd[k];
       if (v > best) { best = v; bi = k; }
     }
 #pragma unroll
@@ -177,7 +185,7 @@ __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mo
       }
     }
     if (tid == 0) {
-      const double pm = d.psd[(bi - 1 + n2) % n2], p0 = d.psd[bi], pp = d.psd[(bi + 1) % n2];
+      const double pm = psd[(bi - 1 + n2) % n2], p0 = psd[bi], pp = psd[(bi + 1) % n2];
       double dl = 0.0;
       if (pm > 0.0 && pp > 0.0 && p0 > 0.0) {
         const double lm = log(pm), l0 = log(p0), lp = log(pp);
@@ -187,59 +195,72 @@ __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mo
       const int ks = bi < n2 / 2 ? bi : bi - n2;
       double dfo = (ks + dl) * (d.Rs / n2) / 4.0;
       // a frame shorter than kFoeMinSyms keeps the previous frame's estimate
-      if (fa.f > 0 && fa.Ff < kFoeMinSyms) dfo = st->dfo_prev;
-      st->dfo_prev = dfo;
-      const double P = d.acc->P / (2.0 * (double)(fa.f1 - fa.f0));
+      if (fa.f > 0 && fa.Ff < kFoeMinSyms) dfo = es.dfo_prev;
+      const double P = acc->P / (2.0 * (double)(fa.f1 - fa.f0));
       const double gain = P > 0.0 ? 1.0 / sqrt(P) : 1.0;
       const double om = 2.0 * M_PI * dfo / d.fs;
-      const double theta = st->theta;
-      if (fa.f < kMaxTrace) {
-        FrameRec r;
-        r.tau = st->tau;
-        r.dfo = dfo;
-        r.gain = gain;
-        r.theta = theta;
-        d.rec[fa.f] = r;
-      }
       sh[0] = om;
-      sh[1] = theta;
-      sh[2] = gain;
-      st->theta = wrap_pi(theta + om * (double)(fa.f1 - fa.f0));
-      st->tau = st->tau + (double)d.timing_gain * resid;
+      sh[1] = gain;
+      sh[2] = es.tau + (double)d.timing_gain * resid;
+      if (blockIdx.x == 0) {
+        if (fa.f < kMaxTrace) {
+          FrameRec r;
+          r.tau = es.tau;
+          r.dfo = dfo;
+          r.gain = gain;
+          r.theta = es.theta;
+          d.rec[fa.f] = r;
+        }
+        EstState nx;
+        nx.tau = sh[2];
+        nx.theta = wrap_pi(es.theta + om * (double)(fa.f1 - fa.f0));
+        nx.dfo_prev = dfo;
+        nx.pad = 0.0;
+        d.es[(fa.f + 1) & 1] = nx;
+      }
     }
     __syncthreads();
-    const double om = sh[0], theta = sh[1], gain = sh[2];
+    const double om = sh[0], gain = sh[1], theta = es.theta;
+    tau_next = sh[2];
     const float omf = (float)om;  // |w l| < 1024 |w|: FP32 phase is exact to ~1e-6 rad
-    for (int l = tid; l < kRotLo; l += 1024) {
+    for (int l = blockIdx.x * 1024 + tid; l < kRotLo; l += gridDim.x * 1024) {
       float s, c;
       sincosf(omf * (float)l, &s, &c);
       d.rot_lo[l] = make_float2(c, -s);
     }
     const int nhi = (d.zlen + kRotLo - 1) / kRotLo;
-    for (int hh = tid; hh < nhi; hh += 1024) {
+    for (int hh = blockIdx.x * 1024 + tid; hh < nhi; hh += gridDim.x * 1024) {
       const double ph = wrap_pi(theta + om * (double)(hh * kRotLo - d.c));
       float s, c;
       sincosf((float)ph, &s, &c);
       d.rot_hi[hh] = make_float2((float)gain * c, -(float)gain * s);
     }
+    // clear the other accumulator slot for the next frame's CD pass
+    double* psd_n = d.psd + (long long)((fa.f + 1) & 1) * (d.N / 2);
+    for (int k = blockIdx.x * 1024 + tid; k < n2; k += gridDim.x * 1024) psd_n[k] = 0.0;
+    if (blockIdx.x == 0 && tid == 0) {
+      FrameAcc* an = d.acc + ((fa.f + 1) & 1);
+      an->C[0] = an->C[1] = an->P = 0.0;
+    }
   } else {
-    if (tid == 0) st->tau = resid;
+    tau_next = resid;
+    if (blockIdx.x == 0 && tid == 0) {
+      EstState nx;
+      nx.tau = resid;
+      nx.theta = 0.0;
+      nx.dfo_prev = 0.0;
+      nx.pad = 0.0;
+      d.es[0] = nx;
+    }
   }
-  __syncthreads();
   // exp(+j 2 pi f_k tau) = sincospi(2 (k'/N) fs tau), k' = k or k - N: the
   // scalar fs tau is formed in FP64, the per-bin product (k'/N exact) in FP32
-  const float u2 = (float)(2.0 * d.fs * st->tau) / (float)d.N;
-  for (int k = tid; k < d.N; k += 1024) {
+  const float u2 = (float)(2.0 * d.fs * tau_next) / (float)d.N;
+  for (int k = blockIdx.x * 1024 + tid; k < d.N; k += gridDim.x * 1024) {
     const int kk = k < d.N / 2 ? k : k - d.N;
     float s, c;
     sincospif((float)kk * u2, &s, &c);
     d.Hf[k] = cmul(d.Hs[k], make_float2(c, s));
-  }
-  for (int k = tid; k < d.N / 2; k += 1024) d.psd[k] = 0.0;
-  if (tid == 0) {
-    d.acc->C[0] = 0.0;
-    d.acc->C[1] = 0.0;
-    d.acc->P = 0.0;
   }
 }
 
@@ -290,7 +311,8 @@ cudaError_t launch_cd(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
 }
 
 cudaError_t launch_est(const RxDev& d, const FrameArgs& fa, int mode, cudaStream_t s) {
-  est_kernel<<<1, 1024, 0, s>>>(d, fa, mode);
+  const int nb = max(1, min(16, (d.N + 1023) / 1024));
+  est_kernel<<<nb, 1024, 0, s>>>(d, fa, mode);
   return cudaGetLastError();
 }
 

@@ -377,10 +377,41 @@ __global__ void __launch_bounds__(128) mimo_kernel(RxDev d, FrameArgs fa, long l
   }
   yb += kYHist;
   const int a = j * d.S, e = min(a + d.S, fa.Ff);
+  // the next sub-block's CD samples are loaded into registers while the
+  // current one computes; rotation (L1-resident tables) is applied on store
+  constexpr int NSP = 2 * kK + T - 1;
+  constexpr int PF = (NSP + 31) / 32;
+  float2 pz[2][PF];
+  auto prefetch = [&](int kf0, int nk) {
+    const int ns = 2 * nk + T - 1;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int r = 0; r < PF; ++r) {
+        const int s = lane + 32 * r;
+        const int i = 2 * kf0 + s;
+        pz[q][r] = (s < ns && i < zlen_f) ? d.z[(long long)q * d.zlen + i] : make_float2(0.f, 0.f);
+      }
+  };
+  auto store = [&](int kf0) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int r = 0; r < PF; ++r) {
+        const int s = lane + 32 * r;
+        if (s < NSP) {
+          const int i = 2 * kf0 + s;
+          const float2 rot = cmul(__ldg(&d.rot_hi[i >> 10]), __ldg(&d.rot_lo[i & (kRotLo - 1)]));
+          sm.r[q][(s & 3) * ChainSmem<T>::P4 + (s >> 2)] = cmul(pz[q][r], rot);
+        }
+      }
+  };
+  if (a < e) prefetch(a, min(kK, e - a));
   for (int k0 = a; k0 < e; k0 += kK) {
     const int nk = min(kK, e - k0);
-    stage_samples<T>(sm, d, k0, nk, zlen_f);
+    store(k0);
     __syncwarp();
+    if (k0 + kK < e) prefetch(k0 + kK, min(kK, e - k0 - kK));
     float2 y[2][2];
     sub_block<T>(sm, nk, 1, d.mu_dd, d.R2, d.nl, y);
     const int k = k0 + 2 * lane;

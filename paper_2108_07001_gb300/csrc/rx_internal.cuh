@@ -40,11 +40,16 @@ struct FrameAcc {
   double pad;
 };
 
+// Estimator state entering a frame (double-buffered by frame parity).
+struct EstState {
+  double tau;          // timing advance of the frame's CD pass (s)
+  double theta;        // FO phase at the frame start
+  double dfo_prev;     // FO estimate of the previous frame (Hz)
+  double pad;
+};
+
 // Scalars carried from frame to frame (device resident).
 struct StreamState {
-  double tau;          // timing advance for the next CD pass (s)
-  double theta;        // FO phase at the next frame start
-  double dfo_prev;     // FO estimate of the previous frame (Hz)
   int bhat_last[2];    // BPS angle of the last decided symbol (-1: none)
   int m_last[2];       // unwrap counter of the last decided symbol
   int synced;
@@ -80,8 +85,9 @@ struct RxDev {
   float2* z;
   float2* rot_hi;              // [ceil(zlen/1024)]  gain * exp(-j(theta + w (hi*1024 - c)))
   float2* rot_lo;              // [1024]             exp(-j w lo)
-  FrameAcc* acc;
-  double* psd;                 // [N/2] FOE periodogram (FP64 sums of FP32 block terms)
+  FrameAcc* acc;               // [3]: frame parity slots + the timing-acquisition pass
+  double* psd;                 // [3][N/2] FOE periodogram (FP64 sums of FP32 block terms)
+  EstState* es;                // [2]
   FrameRec* rec;               // [kMaxTrace]
   StreamState* st;
   float2* w_acq;               // [2][2][T]
@@ -118,6 +124,7 @@ struct FrameArgs {
   long long k_end;     // BER count limit (exclusive); LLONG_MAX before end of stream
   long long n_sym;     // symbols in the stream if known (final), else LLONG_MAX
   int est_only;        // CD pass that only accumulates the Godard sum
+  int acc_slot;        // accumulator slot of this CD pass (f & 1; 2 for est_only)
 };
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {

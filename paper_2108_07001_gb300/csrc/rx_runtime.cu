@@ -58,6 +58,7 @@ int cuda_fail(cudaError_t e, const char* where) {
   } while (0)
 
 constexpr double kC = 299792458.0;
+constexpr int kZSlots = 3;  // frames in flight between the front and back streams
 
 struct StageEv {
   int stage;
@@ -78,7 +79,15 @@ struct PendingFrame {
 struct rx_handle {
   rx_config cfg;
   RxDev d;
-  cudaStream_t s_copy = nullptr, s_comp = nullptr;
+  cudaStream_t s_copy = nullptr;
+  cudaStream_t s_front = nullptr;  // CD + estimator of each frame
+  cudaStream_t s_comp = nullptr;   // acquisition, MIMO, BPS, demap, BER ("back")
+  cudaEvent_t ev_front[kZSlots] = {};  // front work of the frame in slot done
+  cudaEvent_t ev_mimo[kZSlots] = {};   // MIMO of the frame in slot done (slot reusable)
+  cudaStream_t s_ber = nullptr;        // BER counting (metrics), off the decision path
+  cudaEvent_t ev_dem[2] = {};          // demap of a frame done (decisions in the ring)
+  cudaEvent_t ev_berd[2] = {};         // BER work of a frame done (its ring slots reusable)
+  long long n_decide = 0;              // decision passes launched in this stream
   cudaEvent_t ev_copy = nullptr;   // last ingest (recorded on the pushing stream)
   cudaEvent_t ev_reset = nullptr;  // last rx_reset (recorded on the compute stream)
   bool reset_pending = false;
@@ -181,7 +190,7 @@ int dalloc(T** p, size_t n) {
 
 void free_all(rx_handle* h) {
   RxDev& d = h->d;
-  void* ptrs[] = {d.ring, d.Hs, d.Hf, d.tw, d.tw2, d.z, d.rot_hi, d.rot_lo, d.acc, d.psd, d.rec, d.st, d.w_acq,
+  void* ptrs[] = {d.ring, d.Hs, d.Hf, d.tw, d.tw2, d.z, d.rot_hi, d.rot_lo, d.acc, d.psd, d.es, d.rec, d.st, d.w_acq,
                   d.chains, d.y, d.bl, d.run_int, d.run_m0, d.run_edge, d.bps_done, d.ber_done, d.dec, d.out, d.prbs_jump, d.ref,
                   d.sync_err, d.win_err, d.hist_y, d.hist_bhat, d.hist_m, h->stage};
   for (void* p : ptrs)
@@ -206,6 +215,16 @@ void free_all(rx_handle* h) {
   if (h->ev_reset) cudaEventDestroy(h->ev_reset);
   if (h->s_copy) cudaStreamDestroy(h->s_copy);
   if (h->s_comp) cudaStreamDestroy(h->s_comp);
+  if (h->s_front) cudaStreamDestroy(h->s_front);
+  if (h->s_ber) cudaStreamDestroy(h->s_ber);
+  for (int i = 0; i < 2; ++i) {
+    if (h->ev_dem[i]) cudaEventDestroy(h->ev_dem[i]);
+    if (h->ev_berd[i]) cudaEventDestroy(h->ev_berd[i]);
+  }
+  for (int i = 0; i < kZSlots; ++i) {
+    if (h->ev_front[i]) cudaEventDestroy(h->ev_front[i]);
+    if (h->ev_mimo[i]) cudaEventDestroy(h->ev_mimo[i]);
+  }
 }
 
 // Harvest completed frames (in order): latency, device time, bits.
@@ -247,25 +266,33 @@ void harvest(rx_handle* h) {
 // Runs fn (which enqueues work on the compute stream) between two timing
 // events when profiling is on.
 template <typename Fn>
-int staged(rx_handle* h, PendingFrame& pf, int stage, Fn&& fn) {
+int staged(rx_handle* h, PendingFrame& pf, int stage, cudaStream_t strm, Fn&& fn) {
   if (!h->cfg.profile) return fn();
   StageEv se{stage, get_event(h), get_event(h)};
-  RX_CK(cudaEventRecord(se.a, h->s_comp));
+  RX_CK(cudaEventRecord(se.a, strm));
   int rc = fn();
-  RX_CK(cudaEventRecord(se.b, h->s_comp));
+  RX_CK(cudaEventRecord(se.b, strm));
   pf.sev.push_back(se);
   return rc;
 }
 
-#define RX_STAGE(st, nk, call)                                                   \
+#define RX_STAGE(st, nk, strm, call)                                             \
   do {                                                                           \
-    int rc_ = staged(h, pf, st, [&]() -> int {                                   \
+    int rc_ = staged(h, pf, st, strm, [&]() -> int {                             \
       cudaError_t e_ = (call);                                                   \
       return e_ == cudaSuccess ? RX_OK : cuda_fail(e_, #call);                   \
     });                                                                          \
     if (rc_ != RX_OK) return rc_;                                                \
     h->stage_n[st] += (nk);                                                      \
   } while (0)
+
+// Waits for everything the library has queued.
+cudaError_t sync_all(rx_handle* h) {
+  cudaError_t e = cudaStreamSynchronize(h->s_front);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_comp);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_ber);
+  return e;
+}
 
 // Records ev_copy after the ingests queued so far (on the last push stream).
 cudaError_t mark_copy(rx_handle* h) {
@@ -277,16 +304,23 @@ cudaError_t mark_copy(rx_handle* h) {
 // Launch the decision stages (BPS .. BER) for decided range [k_a, k_b).
 int launch_decide(rx_handle* h, PendingFrame& pf, const FrameArgs& fa, bool final_) {
   const RxDev& d = h->d;
-  RX_STAGE(RX_STAGE_BPS, 1, launch_bps(d, fa, h->s_comp));
-  RX_STAGE(RX_STAGE_DEMAP, 2, launch_unwrap_demap(d, fa, h->s_comp));
+  RX_STAGE(RX_STAGE_BPS, 1, h->s_comp, launch_bps(d, fa, h->s_comp));
+  // the decision ring slots of pass n were read by the BER work of pass n-2
+  const int par = (int)(h->n_decide & 1);
+  if (d.ber_on && h->n_decide >= 2) RX_CK(cudaStreamWaitEvent(h->s_comp, h->ev_berd[par], 0));
+  RX_STAGE(RX_STAGE_DEMAP, 1, h->s_comp, launch_unwrap_demap(d, fa, h->s_comp));
+  h->n_decide++;
   if (d.ber_on) {
-    return staged(h, pf, RX_STAGE_BER, [&]() -> int {
+    RX_CK(cudaEventRecord(h->ev_dem[par], h->s_comp));
+    RX_CK(cudaStreamWaitEvent(h->s_ber, h->ev_dem[par], 0));
+    cudaStream_t sb = h->s_ber;
+    int rcb = staged(h, pf, RX_STAGE_BER, sb, [&]() -> int {
     const long long ks = d.ber_skip;
     const long long need = ks + d.sync_syms;
     if (!h->synced && fa.k_b >= need && need <= fa.k_end && ks > d.sync_dmax) {
       const int nb = (d.sync_syms + 2 * d.sync_dmax) * d.bps;
-      RX_CK(launch_ref_gen(d, ks - d.sync_dmax, nb, 0, h->s_comp));
-      RX_CK(launch_sync(d, h->s_comp));
+      RX_CK(launch_ref_gen(d, ks - d.sync_dmax, nb, 0, sb));
+      RX_CK(launch_sync(d, sb));
       h->stage_n[RX_STAGE_BER] += 2;
       h->synced = true;
       h->w_next = 0;
@@ -298,18 +332,20 @@ int launch_decide(rx_handle* h, PendingFrame& pf, const FrameArgs& fa, bool fina
       const long long hi = std::min(fa.k_b, fa.k_end);
       if (hi > ka) {
         const int nbits = (int)((hi - ka) * d.bps);
-        RX_CK(launch_ref_gen(d, ka, nbits, 1, h->s_comp));
+        RX_CK(launch_ref_gen(d, ka, nbits, 1, sb));
         h->stage_n[RX_STAGE_BER] += 1;
       }
       const long long klim = final_ ? fa.k_end : fa.k_b;
       long long w_to = klim > ks ? (final_ ? (klim - ks + d.slip_win - 1) / d.slip_win : (klim - ks) / d.slip_win) : 0;
       if (w_to < h->w_next) w_to = h->w_next;
       if (hi > ka || w_to > h->w_next) h->stage_n[RX_STAGE_BER] += 1;  // count (+ slip pass in its last block)
-      RX_CK(launch_ber(d, ka, std::max(hi, ka), h->w_next, w_to, klim, h->n_win_ring, h->s_comp));
+      RX_CK(launch_ber(d, ka, std::max(hi, ka), h->w_next, w_to, klim, h->n_win_ring, sb));
       h->w_next = w_to;
     }
     return RX_OK;
     });
+    if (rcb != RX_OK) return rcb;
+    RX_CK(cudaEventRecord(h->ev_berd[par], sb));
   }
   return RX_OK;
 }
@@ -330,6 +366,7 @@ int launch_frame(rx_handle* h, long long f, bool final_) {
   fa.k_end = h->ended ? n_sym - h->tail : LLONG_MAX;
   fa.n_sym = n_sym;
   fa.est_only = 0;
+  fa.acc_slot = (int)(f & 1);
 
   PendingFrame pf;
   pf.f = f;
@@ -337,21 +374,35 @@ int launch_frame(rx_handle* h, long long f, bool final_) {
   pf.ev_in = get_event(h);
   pf.ev_start = get_event(h);
   pf.ev_done = get_event(h);
+  // frame slot: CD output and rotation tables of frames f and f + kZSlots share it
+  const int slot = (int)(f % kZSlots);
+  RxDev df = d;
+  df.z = d.z + (long long)slot * 2 * d.zlen;
+  df.rot_hi = d.rot_hi + (long long)slot * (d.zlen / kRotLo + 2);
+  df.rot_lo = d.rot_lo + (long long)slot * kRotLo;
+  cudaStream_t sf = h->s_front;
   RX_CK(mark_copy(h));
   RX_CK(cudaEventRecord(pf.ev_in, h->last_cs));
-  RX_CK(cudaStreamWaitEvent(h->s_comp, h->ev_copy, 0));
-  RX_CK(cudaEventRecord(pf.ev_start, h->s_comp));
+  // front: CD + estimator, after the input and after the slot's previous user
+  RX_CK(cudaStreamWaitEvent(sf, h->ev_copy, 0));
+  if (f >= kZSlots) RX_CK(cudaStreamWaitEvent(sf, h->ev_mimo[slot], 0));
+  RX_CK(cudaEventRecord(pf.ev_start, sf));
   if (f == 0) {
     FrameArgs fe = fa;
     fe.est_only = 1;
-    RX_STAGE(RX_STAGE_CD, 1, launch_cd(d, fe, h->s_comp));
-    RX_STAGE(RX_STAGE_EST, 1, launch_est(d, fe, 0, h->s_comp));
+    fe.acc_slot = 2;
+    RX_STAGE(RX_STAGE_CD, 1, sf, launch_cd(df, fe, sf));
+    RX_STAGE(RX_STAGE_EST, 1, sf, launch_est(df, fe, 0, sf));
   }
-  RX_STAGE(RX_STAGE_CD, 1, launch_cd(d, fa, h->s_comp));
-  RX_CK(cudaEventRecord(h->cd_done[f % h->cd_done.size()], h->s_comp));
-  RX_STAGE(RX_STAGE_EST, 1, launch_est(d, fa, 1, h->s_comp));
-  if (f == 0) RX_STAGE(RX_STAGE_ACQUIRE, 1, launch_acquire(d, fa, h->s_comp));
-  RX_STAGE(RX_STAGE_MIMO, 1, launch_mimo(d, fa, h->s_comp));
+  RX_STAGE(RX_STAGE_CD, 1, sf, launch_cd(df, fa, sf));
+  RX_CK(cudaEventRecord(h->cd_done[f % h->cd_done.size()], sf));
+  RX_STAGE(RX_STAGE_EST, 1, sf, launch_est(df, fa, 1, sf));
+  RX_CK(cudaEventRecord(h->ev_front[slot], sf));
+  // back: equaliser and decisions
+  RX_CK(cudaStreamWaitEvent(h->s_comp, h->ev_front[slot], 0));
+  if (f == 0) RX_STAGE(RX_STAGE_ACQUIRE, 1, h->s_comp, launch_acquire(df, fa, h->s_comp));
+  RX_STAGE(RX_STAGE_MIMO, 1, h->s_comp, launch_mimo(df, fa, h->s_comp));
+  RX_CK(cudaEventRecord(h->ev_mimo[slot], h->s_comp));
   int rc = launch_decide(h, pf, fa, final_);
   if (rc != RX_OK) return rc;
   RX_CK(cudaEventRecord(pf.ev_done, h->s_comp));
@@ -555,11 +606,12 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   RX_AL(d.Hf, N);
   RX_AL(d.tw, N);
   RX_AL(d.tw2, 256);
-  RX_AL(d.z, 2LL * d.zlen);
-  RX_AL(d.rot_hi, d.zlen / kRotLo + 2);
-  RX_AL(d.rot_lo, kRotLo);
-  RX_AL(d.acc, 1);
-  RX_AL(d.psd, N / 2);
+  RX_AL(d.z, (long long)kZSlots * 2 * d.zlen);
+  RX_AL(d.rot_hi, (long long)kZSlots * (d.zlen / kRotLo + 2));
+  RX_AL(d.rot_lo, (long long)kZSlots * kRotLo);
+  RX_AL(d.acc, 3);
+  RX_AL(d.psd, 3LL * (N / 2));
+  RX_AL(d.es, 2);
   RX_AL(d.rec, kMaxTrace);
   RX_AL(d.st, 1);
   RX_AL(d.w_acq, 4 * d.T);
@@ -630,6 +682,16 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   if (cudaMalloc(&h->stage, h->stage_bytes) != cudaSuccess) { free_all(h); delete h; return fail(RX_ENOMEM, "staging allocation failed"); }
   cudaError_t e = cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_comp, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_front, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_ber, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&h->ev_dem[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_berd[i], cudaEventDisableTiming);
+  }
+  for (int i = 0; i < kZSlots && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&h->ev_front[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_mimo[i], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_reset, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev_copy, h->s_copy);
@@ -744,7 +806,7 @@ int rx_pull_bits(rx_handle* h, uint8_t* out, size_t cap_bytes, size_t* n_bits, i
   *n_bits = 0;
   int rc = RX_OK;
   if (timeout_ms < 0) {
-    RX_CK(cudaStreamSynchronize(h->s_comp));
+    RX_CK(sync_all(h));
   } else if (timeout_ms > 0) {
     auto t0 = std::chrono::steady_clock::now();
     while (true) {
@@ -779,7 +841,7 @@ int rx_pull_bits(rx_handle* h, uint8_t* out, size_t cap_bytes, size_t* n_bits, i
 int rx_stats(rx_handle* h, rx_stats_t* out) {
   if (!h || !out) return fail(RX_EINVAL, "null argument");
   RX_CK(cudaSetDevice(h->cfg.device));
-  RX_CK(cudaStreamSynchronize(h->s_comp));
+  RX_CK(sync_all(h));
   harvest(h);
   StreamState st;
   RX_CK(cudaMemcpy(&st, h->d.st, sizeof(st), cudaMemcpyDeviceToHost));
@@ -821,7 +883,9 @@ int rx_stats(rx_handle* h, rx_stats_t* out) {
 int rx_destroy(rx_handle* h) {
   if (!h) return RX_OK;
   cudaSetDevice(h->cfg.device);
+  if (h->s_front) cudaStreamSynchronize(h->s_front);
   if (h->s_comp) cudaStreamSynchronize(h->s_comp);
+  if (h->s_ber) cudaStreamSynchronize(h->s_ber);
   if (h->s_copy) cudaStreamSynchronize(h->s_copy);
   free_all(h);
   delete h;
@@ -835,15 +899,21 @@ int rx_reset(rx_handle* h) {
   harvest(h);
   RxDev& d = h->d;
   cudaStream_t s = h->s_comp;
-  // stream-ordered: runs after all queued frames, before the next stream's work
+  // stream-ordered: runs after all queued frames (front and back), before the
+  // next stream's work
   RX_CK(mark_copy(h));
   RX_CK(cudaStreamWaitEvent(s, h->ev_copy, 0));
+  RX_CK(cudaEventRecord(h->ev_front[0], h->s_front));
+  RX_CK(cudaStreamWaitEvent(s, h->ev_front[0], 0));
+  RX_CK(cudaEventRecord(h->ev_berd[0], h->s_ber));
+  RX_CK(cudaStreamWaitEvent(s, h->ev_berd[0], 0));
   StreamState st{};
   st.bhat_last[0] = st.bhat_last[1] = -1;
   RX_CK(cudaMemcpyAsync(d.st, &h->st_init, sizeof(st), cudaMemcpyHostToDevice, s));
   RX_CK(cudaMemcpyAsync(d.Hf, d.Hs, d.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
-  RX_CK(cudaMemsetAsync(d.acc, 0, sizeof(FrameAcc), s));
-  RX_CK(cudaMemsetAsync(d.psd, 0, (d.N / 2) * sizeof(double), s));
+  RX_CK(cudaMemsetAsync(d.acc, 0, 3 * sizeof(FrameAcc), s));
+  RX_CK(cudaMemsetAsync(d.psd, 0, 3LL * (d.N / 2) * sizeof(double), s));
+  RX_CK(cudaMemsetAsync(d.es, 0, 2 * sizeof(EstState), s));
   RX_CK(cudaMemsetAsync(d.win_err, 0, (size_t)h->n_win_ring * 8 * sizeof(unsigned), s));
   RX_CK(cudaMemsetAsync(d.rec, 0, kMaxTrace * sizeof(FrameRec), s));
   if (d.hist_syms > 0) {
@@ -852,6 +922,9 @@ int rx_reset(rx_handle* h) {
     RX_CK(cudaMemsetAsync(d.hist_m, 0, 2 * d.hist_syms * sizeof(int), s));
   }
   RX_CK(cudaEventRecord(h->ev_reset, s));
+  RX_CK(cudaStreamWaitEvent(h->s_front, h->ev_reset, 0));
+  RX_CK(cudaStreamWaitEvent(h->s_ber, h->ev_reset, 0));
+  h->n_decide = 0;
   h->reset_pending = true;
   h->gen++;
   h->pushed = 0;
@@ -870,10 +943,16 @@ int rx_reset(rx_handle* h) {
 int rx_join(rx_handle* h, void* cuda_stream) {
   if (!h) return fail(RX_EINVAL, "null handle");
   RX_CK(cudaSetDevice(h->cfg.device));
-  cudaEvent_t e = get_event(h);
+  cudaEvent_t e = get_event(h), e2 = get_event(h), e3 = get_event(h);
   RX_CK(cudaEventRecord(e, h->s_comp));
+  RX_CK(cudaEventRecord(e2, h->s_front));
+  RX_CK(cudaEventRecord(e3, h->s_ber));
   RX_CK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, e, 0));
+  RX_CK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, e2, 0));
+  RX_CK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, e3, 0));
   h->ev_pool.push_back(e);
+  h->ev_pool.push_back(e2);
+  h->ev_pool.push_back(e3);
   return RX_OK;
 }
 
@@ -881,7 +960,7 @@ int rx_stage_times(rx_handle* h, double* ms, int64_t* launches) {
   if (!h || !ms || !launches) return fail(RX_EINVAL, "null argument");
   RX_CK(cudaSetDevice(h->cfg.device));
   RX_CK(cudaStreamSynchronize(h->s_copy));
-  RX_CK(cudaStreamSynchronize(h->s_comp));
+  RX_CK(sync_all(h));
   harvest(h);
   for (int i = 0; i < RX_NSTAGES; ++i) {
     ms[i] = h->stage_ms[i];
@@ -893,7 +972,7 @@ int rx_stage_times(rx_handle* h, double* ms, int64_t* launches) {
 int rx_frame_trace(rx_handle* h, double* out, int cap_frames) {
   if (!h || !out) return fail(RX_EINVAL, "null argument");
   RX_CK(cudaSetDevice(h->cfg.device));
-  RX_CK(cudaStreamSynchronize(h->s_comp));
+  RX_CK(sync_all(h));
   const int n = (int)std::min<long long>(std::min<long long>(h->f_next, kMaxTrace), cap_frames);
   std::vector<FrameRec> r(n);
   if (n > 0) RX_CK(cudaMemcpy(r.data(), h->d.rec, n * sizeof(FrameRec), cudaMemcpyDeviceToHost));
@@ -910,7 +989,7 @@ int rx_get_taps(rx_handle* h, int which, float* out) {
   if (!h || !out) return fail(RX_EINVAL, "null argument");
   if (which < -1 || which >= h->d.G) return fail(RX_EINVAL, "no such chain");
   RX_CK(cudaSetDevice(h->cfg.device));
-  RX_CK(cudaStreamSynchronize(h->s_comp));
+  RX_CK(sync_all(h));
   const float2* src = which < 0 ? h->d.w_acq : h->d.chains + (size_t)which * 4 * h->d.T;
   RX_CK(cudaMemcpy(out, src, 4 * h->d.T * sizeof(float2), cudaMemcpyDeviceToHost));
   return RX_OK;
@@ -921,7 +1000,7 @@ int rx_get_equalised(rx_handle* h, int64_t first, int64_t n, float* out) {
   const long long H = h->d.hist_syms;
   if (first < 0 || n < 0 || first + n > H) return fail(RX_EINVAL, "range outside the inspection history");
   RX_CK(cudaSetDevice(h->cfg.device));
-  RX_CK(cudaStreamSynchronize(h->s_comp));
+  RX_CK(sync_all(h));
   for (int p = 0; p < 2; ++p)
     RX_CK(cudaMemcpy(out + 2 * p * n, h->d.hist_y + p * H + first, n * sizeof(float2), cudaMemcpyDeviceToHost));
   return RX_OK;
@@ -932,7 +1011,7 @@ int rx_get_phase(rx_handle* h, int64_t first, int64_t n, uint8_t* bhat, int32_t*
   const long long H = h->d.hist_syms;
   if (first < 0 || n < 0 || first + n > H) return fail(RX_EINVAL, "range outside the inspection history");
   RX_CK(cudaSetDevice(h->cfg.device));
-  RX_CK(cudaStreamSynchronize(h->s_comp));
+  RX_CK(sync_all(h));
   for (int p = 0; p < 2; ++p) {
     RX_CK(cudaMemcpy(bhat + p * n, h->d.hist_bhat + p * H + first, n, cudaMemcpyDeviceToHost));
     RX_CK(cudaMemcpy(m + p * n, h->d.hist_m + p * H + first, n * 4, cudaMemcpyDeviceToHost));
