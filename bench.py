@@ -56,7 +56,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -65,9 +65,17 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([v.strip() for v in line.split(",")])
+            self.rows.append((time.perf_counter(), [v.strip() for v in line.split(",")]))
 
-    def stop(self):
+    def wait_first(self, timeout=5.0):
+        t = time.perf_counter() + timeout
+        while self.proc is not None and not self.rows and time.perf_counter() < t:
+            time.sleep(0.01)
+
+    def stop(self, t0=None, t1=None):
+        """Summary of the samples taken in [t0, t1] (host perf_counter
+        times); when the window is shorter than the sampling period, the
+        samples within one period of it."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -75,13 +83,40 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = [r for r in self.rows if len(r) >= 7]
+        rows = [(t, r) for t, r in self.rows if len(r) >= 7]
+        if t0 is not None:
+            inside = [r for t, r in rows if t0 <= t <= t1]
+            rows = inside or [r for t, r in rows if t0 - 0.15 <= t <= t1 + 0.15]
+        else:
+            rows = [r for _, r in rows]
         sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
         mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, or
+    None when the kernel's sources changed since that capture."""
+    import hashlib
+    try:
+        lines = open(os.path.join(ROOT, "profiles", "traffic.txt")).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        f = ln.split()
+        if not f or f[0].startswith("#") or f[0] != kernel:
+            continue
+        h = hashlib.sha256()
+        for src in f[3].split(","):
+            with open(os.path.join(ROOT, "paper_2108_07001_gb300", "csrc", src), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest()[:16] != f[4]:
+            return None
+        return int(f[1]) + int(f[2])
+    return None
 
 
 def workload():
@@ -159,15 +194,16 @@ def run_ours(args):
         torch.cuda.synchronize()
         return ev0.elapsed_time(ev1), h0, h1
 
+    clk = ClockSampler()
+    clk.start()
     for rr in (r, rp):
         for _ in range(args.warmup):
             step(rr)
             rr.pull_bytes(outbuf)
     torch.cuda.synchronize()
-    clk = ClockSampler()
-    clk.start()
+    clk.wait_first()
     total_ms, host0, host1 = timed(r, args.steps)
-    clocks = clk.stop()
+    clocks = clk.stop(host0, time.perf_counter())
     stats = r.stats()
     before = rp.stage_times()
     prof_ms, _, _ = timed(rp, args.steps)
@@ -204,7 +240,9 @@ def run_ours(args):
     dom = max(stages, key=lambda k: stages[k]["ms_per_step"])
     roof = dict(stages[dom])
     roof["kernel"] = dom
-    roof["traffic"] = None
+    roof["traffic"] = profiled_traffic(dom)
+    if roof["traffic"] is not None:
+        roof["traffic_unit"] = "bytes per launch (ncu dram read+write, profiles/traffic.txt)"
     roof.pop("launches_per_step", None)
     roof["peak_source"] = ("measured MEASURED_PEAKS.json hbm_gbs" if roof["bound"] == "hbm" and hbm_peak
                            else "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz")
@@ -245,7 +283,7 @@ def run_ours(args):
 
 def finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, other_ms,
            gpu_launches, clocks, host0, host1, gen_s, e2e):
-    cpu = cpu_baseline(wl) if args.cpu_baseline else None
+    cpu = cpu_baseline() if args.cpu_baseline else None
     line = {
         "metric": "gsamples_per_s", "value": round(value, 3), "unit": "Gsamples/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
@@ -268,37 +306,60 @@ def finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, o
     return line
 
 
-def oracle_sample(wl, n_sym):
-    """Run the oracle on the first n_sym symbols of the workload's link."""
+ORACLE_THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS")
+
+
+def oracle_child(n_sym, reps):
+    """Runs in a child process with one BLAS/OpenMP thread: simulates the
+    first n_sym symbols of the workload's link once, then times the FP64
+    oracle on them reps times.  Prints {"times": [...]} as JSON."""
     import rxsim
     from oracle import rx_oracle as O
     from paper_2108_07001_gb300.workloads import oracle_kwargs
+    wl = workload()
     lk = dict(wl["link"])
     lk["n_sym"] = n_sym
     sim = rxsim.simulate(rxsim.LinkConfig(**lk))
     x = sim["rx"].astype(np.complex128)
+    del sim
     kw = oracle_kwargs(wl["rx"])
-    t0 = time.perf_counter()
-    O.Receiver(O.RxConfig(**kw)).run(x)
-    return time.perf_counter() - t0
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        O.Receiver(O.RxConfig(**kw)).run(x)
+        times.append(time.perf_counter() - t0)
+    print(json.dumps({"times": times}), flush=True)
 
 
-def cpu_baseline(wl, n_sym=1 << 16):
-    t = oracle_sample(wl, n_sym)
-    v = 4 * n_sym / t / 1e9
+def oracle_times(n_sym, reps):
+    """Oracle run times on the host cores, measured in a fresh single-threaded
+    process (fork+exec, so safe after CUDA initialisation)."""
+    env = dict(os.environ)
+    for k in ORACLE_THREAD_ENV:
+        env[k] = "1"
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", str(n_sym), str(reps)],
+                         env=env, capture_output=True, text=True, check=True, cwd=ROOT)
+    return json.loads(out.stdout.strip().splitlines()[-1])["times"]
+
+
+CPU_BASELINE_SYMS = 1 << 20  # one full frame, acquisition included (10-30 s of one core)
+
+
+def cpu_baseline():
+    t = oracle_times(CPU_BASELINE_SYMS, 1)[0]
+    v = 4 * CPU_BASELINE_SYMS / t / 1e9
     return {"value": round(v, 6), "unit": "Gsamples/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {n_sym} symbols/pol of the workload (one partial frame incl. acquisition), "
-                      f"FP64 numpy, {t:.1f} s"}
+            "sample": f"first {CPU_BASELINE_SYMS} symbols/pol of the workload (one whole frame incl. "
+                      f"acquisition), FP64 numpy oracle, one thread, {t:.1f} s"}
+
+
+REFERENCE_STEP_SYMS = 1 << 18
 
 
 def run_reference(args):
     wl = workload()
-    n_sym = 1 << 15
-    times = []
-    for i in range(args.warmup + args.steps):
-        t = oracle_sample(wl, n_sym)
-        if i >= args.warmup:
-            times.append(t)
+    n_sym = REFERENCE_STEP_SYMS
+    times = oracle_times(n_sym, args.warmup + args.steps)[args.warmup:]
     t = sum(times) / len(times)
     v = 4 * n_sym / t / 1e9
     return {"impl": "reference", "metric": "gsamples_per_s", "value": round(v, 6), "unit": "Gsamples/s",
@@ -307,20 +368,24 @@ def run_reference(args):
             "data": "synthetic (seeded link simulator)",
             "config": {"workload": wl["name"], "sample_symbols_per_pol": n_sym},
             "cpu_baseline": {"value": round(v, 6), "unit": "Gsamples/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {n_sym} symbols/pol per step"},
+                             "sample": f"first {n_sym} symbols/pol of the workload per step, one thread"},
             "e2e": {"value": round(v, 6), "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--symbols", type=int, default=0, help="stream length per pol (default: the workload's 2^24)")
+    ap.add_argument("--oracle-child", nargs=2, type=int, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_child:
+        oracle_child(*args.oracle_child)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
@@ -335,13 +400,20 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
         dist.barrier()
+        args.cpu_baseline = False  # the CPU baseline is taken on one rank at N=1 only
         line = run_ours(args)
-        t = torch.tensor([line["ms_per_step"]], device="cuda")
+        e2e_ms = line["e2e"]["ms_per_step"] if line.get("e2e") else 0.0
+        t = torch.tensor([line["ms_per_step"], e2e_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         if rank == 0:
             line["n_gpus"] = world
-            line["ms_per_step"] = float(t.item())
-            line["value"] = round(world * 2 * (1 << 25) / (line["ms_per_step"] * 1e-3) / 1e9, 3)
+            line["ms_per_step"] = float(t[0].item())
+            if line.get("e2e"):
+                line["e2e"]["ms_per_step"] = float(t[1].item())
+                line["e2e"]["value"] = round(world * 4 * line["config"]["symbols_per_pol"] / (t[1].item() * 1e-3) / 1e9, 3)
+                line["e2e"]["h2d_bytes_per_step"] *= world
+                line["e2e"]["d2h_bytes_per_step"] *= world
+            line["value"] = round(world * 4 * line["config"]["symbols_per_pol"] / (line["ms_per_step"] * 1e-3) / 1e9, 3)
             line["config"]["parallelism"] = f"replicas x{world}"
             print(json.dumps(line), flush=True)
         dist.destroy_process_group()
