@@ -120,7 +120,47 @@ __device__ __forceinline__ float2 twiddle(const float2* tw_s, int m) {
   return cmul(tw_s[m / kTwSplit], tw_s[kTwSplit + (m % kTwSplit)]);
 }
 
-// One Stockham pass.  Inverse passes conjugate the twiddles.
+// Sub-transform length of the last pass (passes use radix 16 while at
+// least 16 remain) and its radix.
+template <int N>
+constexpr int last_ns() {
+  int ns = 1;
+  while (N / ns > 16) ns *= 16;
+  return ns;
+}
+
+// Twiddles and R-point DFT of butterfly j of the pass with sub-transform
+// length NS: inputs v[r] = element j + r N/R, outputs v[r] = element
+// (j / NS) NS R + (j mod NS) + r NS.  Inverse passes conjugate the twiddles.
+template <int N, int R, int NS, bool INV>
+__device__ __forceinline__ void pass_butterfly(float2 (&v)[R], int j, const float2* __restrict__ tw, int tws) {
+  if (NS > 1) {
+    // w^r for r < R from the table entries w, w^2, w^4, w^8 (each power is
+    // a product of at most four correctly rounded table values)
+    constexpr int STEP = N / (NS * R);
+    const int m = (j & (NS - 1)) * STEP * tws;
+    float2 wp[R];
+    wp[1] = twiddle(tw, m);
+    if (R > 2) wp[2] = twiddle(tw, 2 * m);
+    if (R > 4) wp[4] = twiddle(tw, 4 * m);
+    if (R > 8) wp[8] = twiddle(tw, 8 * m);
+#pragma unroll
+    for (int r = 3; r < R; ++r) {
+      if (r == 4 || r == 8) continue;
+      const int hb = r >= 8 ? 8 : (r >= 4 ? 4 : 2);
+      wp[r] = cmul(wp[hb], wp[r - hb]);
+    }
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      float2 w = wp[r];
+      if (INV) w.y = -w.y;
+      v[r] = cmul(v[r], w);
+    }
+  }
+  dft<R, INV>(v);
+}
+
+// One Stockham pass through shared memory.
 template <int N, int NT, int R, int NS, bool INV>
 __device__ __forceinline__ void fft_pass(float2* buf, const float2* __restrict__ tw, int tws) {
   constexpr int NB = N / R;
@@ -139,32 +179,8 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* __restrict__
   for (int u = 0; u < PER; ++u) {
     const int j = threadIdx.x + u * NT;
     if ((NB % NT) == 0 || j < NB) {
-      const int k = j & (NS - 1);
-      if (NS > 1) {
-        // w^r for r < R from the table entries w, w^2, w^4, w^8 (each power
-        // is a product of at most four correctly rounded table values)
-        constexpr int STEP = N / (NS * R);
-        const int m = k * STEP * tws;
-        float2 wp[R];
-        wp[1] = twiddle(tw, m);
-        if (R > 2) wp[2] = twiddle(tw, 2 * m);
-        if (R > 4) wp[4] = twiddle(tw, 4 * m);
-        if (R > 8) wp[8] = twiddle(tw, 8 * m);
-#pragma unroll
-        for (int r = 3; r < R; ++r) {
-          if (r == 4 || r == 8) continue;
-          const int hb = r >= 8 ? 8 : (r >= 4 ? 4 : 2);
-          wp[r] = cmul(wp[hb], wp[r - hb]);
-        }
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          float2 w = wp[r];
-          if (INV) w.y = -w.y;
-          v[u][r] = cmul(v[u][r], w);
-        }
-      }
-      dft<R, INV>(v[u]);
-      const int idxD = (j / NS) * NS * R + k;
+      pass_butterfly<N, R, NS, INV>(v[u], j, tw, tws);
+      const int idxD = (j / NS) * NS * R + (j & (NS - 1));
 #pragma unroll
       for (int r = 0; r < R; ++r) buf[swz(idxD + r * NS)] = v[u][r];
     }
@@ -172,13 +188,14 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* __restrict__
   __syncthreads();
 }
 
-template <int N, int NT, int NS, bool INV>
+// The passes with sub-transform lengths NS, 16 NS, ... below NS_END.
+template <int N, int NT, int NS, int NS_END, bool INV>
 __device__ __forceinline__ void fft_passes(float2* buf, const float2* __restrict__ tw, int tws) {
-  if constexpr (NS < N) {
+  if constexpr (NS < NS_END) {
     constexpr int REM = N / NS;
     constexpr int R = REM >= 16 ? 16 : REM;
     fft_pass<N, NT, R, NS, INV>(buf, tw, tws);
-    fft_passes<N, NT, NS * R, INV>(buf, tw, tws);
+    fft_passes<N, NT, NS * R, NS_END, INV>(buf, tw, tws);
   }
 }
 
@@ -186,7 +203,7 @@ __device__ __forceinline__ void fft_passes(float2* buf, const float2* __restrict
 // Requires a __syncthreads() between the last write of buf and this call.
 template <int N, int NT, bool INV>
 __device__ __forceinline__ void fft_smem(float2* buf, const float2* __restrict__ tw, int tws) {
-  fft_passes<N, NT, 1, INV>(buf, tw, tws);
+  fft_passes<N, NT, 1, N, INV>(buf, tw, tws);
 }
 
 }  // namespace rx

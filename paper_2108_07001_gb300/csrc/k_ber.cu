@@ -15,6 +15,9 @@
 // sequential pass then keeps the current quadrant unless its errors exceed
 // a quarter of the window's bits, in which case the window's best quadrant
 // is taken and a slip is counted.
+#include <algorithm>
+#include <cstdint>
+
 #include "rx_internal.cuh"
 
 namespace rx {
@@ -260,7 +263,9 @@ __global__ void __launch_bounds__(256) ber_count_kernel(RxDev d, long long ka, l
     if (acc) atomicAdd(&d.win_err[(cur % n_win_ring) * 8 + j], acc);
   }
   if (w_to <= w_from) return;
-  __threadfence();
+  // threads that added to the window counters make them visible before the
+  // block takes its ticket
+  if (threadIdx.x < 8 || !one_window) __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) am_last = atomicAdd(&d.ber_done[1], 1u) == gridDim.x - 1;
   __syncthreads();
@@ -371,6 +376,24 @@ __global__ void ingest_kernel(RxDev d, const void* __restrict__ src, int dtype, 
   else reinterpret_cast<float2*>(d.ring)[dst] = v;
 }
 
+// c64 input into a c64 ring, two samples (16 bytes) per access: pair j of
+// polarisation p is src4[p n2 + j] -> ring slot j0 + 2j (mod cap).  Needs
+// n, j0 and cap even and a 16-byte aligned source, so a pair never
+// straddles the polarisations or the ring's wrap.
+__global__ void __launch_bounds__(256) ingest_pairs_kernel(RxDev d, const float4* __restrict__ src, long long n2,
+                                                            long long j0) {
+  float4* ring4 = reinterpret_cast<float4*>(d.ring);
+  const long long cap2 = d.ring_cap / 2;
+  const long long s0 = j0 / 2;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n2; i += (long long)gridDim.x * blockDim.x) {
+    const int pol = i >= n2;
+    const long long j = i - pol * n2;
+    long long slot = s0 + j;
+    if (slot >= cap2) slot -= cap2;
+    ring4[pol * cap2 + slot] = __ldcs(&src[i]);
+  }
+}
+
 // ---- launchers ------------------------------------------------------------
 
 cudaError_t launch_ref_gen(const RxDev& d, long long sym0, int nbits, int use_delay, cudaStream_t s) {
@@ -405,7 +428,15 @@ cudaError_t launch_ber(const RxDev& d, long long ka, long long kb, long long w_f
 cudaError_t launch_ingest(const RxDev& d, const void* src, int dtype, long long n, long long w0, cudaStream_t s) {
   const long long tot = 2 * n;
   if (tot == 0) return cudaSuccess;
-  ingest_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d, src, dtype, n, w0 % d.ring_cap);
+  const long long j0 = w0 % d.ring_cap;
+  if (dtype == 1 && d.storage == 1 && (n & 1) == 0 && (j0 & 1) == 0 && (d.ring_cap & 1) == 0 &&
+      (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+    const long long pairs = n;  // 2 pols x n/2 pairs
+    const long long blocks = std::min<long long>((pairs + 255) / 256, 152LL * 8);
+    ingest_pairs_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, static_cast<const float4*>(src), n / 2, j0);
+    return cudaGetLastError();
+  }
+  ingest_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d, src, dtype, n, j0);
   return cudaGetLastError();
 }
 

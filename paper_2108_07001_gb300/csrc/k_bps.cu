@@ -13,8 +13,10 @@
 // (2W+1)-symbol window with the last 2W+1 metrics in registers (the loop is
 // unrolled by 2W+1 so the ring index is static).  Each step the lane writes
 // the smaller of its angles' order-preserving keys (float bits with the
-// low 6 bits replaced by the angle) to a shared-memory row; after 2W+1
-// steps the rows are reduced with an integer min.  Runs that touch no
+// low 6 bits replaced by the angle) to a shared-memory row; the rows are
+// reduced with an integer min once per super-step of 2W+1 steps (QPSK with
+// 64 angles derives a lane's second angle from the rotation of its first,
+// see bps_kernel).  Runs that touch no
 // stream edge take no per-step predicate.  The last block of each
 // polarisation (found with an atomic counter after a fence; nothing waits)
 // turns the runs' unwrap sums into each run's starting counter.
@@ -43,20 +45,48 @@ __device__ __forceinline__ float bps_metric(float2 yv, float c_s, float s_s) {
   return fmaf(ex, ex, ey * ey);
 }
 
+// Dynamic shared memory of one block: per warp, WIN - 1 + NSUP key rows of
+// ROW words, then the staged symbols (float4 {x, y, h, 0} in the paired
+// QPSK form, float2 otherwise).
+template <int B, int W, bool QAM16>
+struct BpsSmem {
+  static constexpr bool PAIR = !QAM16 && B == 64;
+  static constexpr int WIN = 2 * W + 1;
+  static constexpr int ROW = 36;                         // padded key row (words)
+  static constexpr int YS = kRun + 2 * W;                // staged symbols per run
+  static constexpr int NSUP = (YS + WIN - 1) / WIN;      // super-steps per run
+  static constexpr int ROWS = WIN - 1 + NSUP;            // key rows per warp
+  static constexpr int YSP = (NSUP * WIN + 7) / 8 * 8;     // staged entries (whole super-steps)
+  static constexpr size_t KEY_BYTES = sizeof(uint32_t) * 8 * ROWS * ROW;
+  static constexpr size_t Y_BYTES = (size_t)8 * YSP * (PAIR ? 16 : 8);
+  static constexpr size_t BYTES = KEY_BYTES + Y_BYTES;
+};
+
 // One warp = one run of kRun symbols of one polarisation; lane l holds the
-// test angles l + 32 a (a < APL = B/32), each with its own register ring of
-// the last 2W+1 metrics.  Per window step the lane packs its angles' window
+// test angles l + 32 a (a < B/32), each with its own register ring of the
+// last 2W+1 metrics.  Per window step the lane packs its angles' window
 // sums into keys and keeps the smaller, so a row of 32 keys per output is
-// reduced afterwards.  The run's symbols (with the window halo) are staged
-// in shared memory once.
+// reduced afterwards: rows 0..2W-1 of a super-step of 2W+1 steps are
+// reduced at its end (one pass of 32 lanes for W = 16), the last row of
+// every super-step goes to a row of its own, reduced once per run.
+//
+// QPSK with B = 64 (the paired form): angle l + 32 is angle l + pi/4, and
+// with z = sc y e^{-j phi_l} (sc = sqrt 2, points at +-1 +-j) the metric
+// halves are d_l / 2 = h - (|z_x| + |z_y|) and
+// d_{l+32} / 2 = h - sqrt2 max(|z_x|, |z_y|), h = |y|^2 + 1 (|z|^2 = 2|y|^2
+// and rotating z by -pi/4 maps |z_x| + |z_y| to sqrt2 max(|z_x|, |z_y|)).
+// One rotation then serves both angles of a lane.  h carries a relative
+// bias of 2^-17 (common to all angles of a symbol, so the argmin is that of
+// d) that keeps every metric positive under rounding; symbols outside the
+// stream are staged as y = 0, h = 0 and contribute exactly 0.
 template <int B, int W, bool QAM16>
 __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
+  using SM = BpsSmem<B, W, QAM16>;
+  constexpr bool PAIR = SM::PAIR;
   constexpr int APL = B / 32;            // angles per lane
-  constexpr int WIN = 2 * W + 1;
-  constexpr int ROW = 36;                // padded key row (words)
-  constexpr int YS = kRun + 2 * W;       // staged symbols per run
-  extern __shared__ __align__(16) uint32_t keys_smem[];  // [8 warps][WIN][ROW]
-  __shared__ float2 y_s[8][kRun + 64];
+  constexpr int WIN = SM::WIN;
+  constexpr int ROW = SM::ROW;
+  extern __shared__ __align__(16) uint32_t keys_smem[];
   __shared__ uint8_t bh_s[8][kRun];
   __shared__ float2 cs_s[B];
   __shared__ float red_s[8][3];
@@ -93,11 +123,25 @@ __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
   const int total = ract + 2 * W;
   const int sv_lo = (int)max(0LL, (long long)W - kr);
   const int sv_hi = (int)min((long long)total, ylim - (kr - W));
-  float2* ys = y_s[warp];
-  for (int i = lane; i < total; i += 32)
-    ys[i] = (i >= sv_lo && i < sv_hi) ? yf[kr - W - fbase + i] : make_float2(0.f, 0.f);
+  uint32_t* kw = keys_smem + warp * SM::ROWS * ROW;
+  unsigned char* ybase = reinterpret_cast<unsigned char*>(keys_smem) + SM::KEY_BYTES;
+  float4* ys4 = reinterpret_cast<float4*>(ybase) + warp * SM::YSP;
+  float2* ys2 = reinterpret_cast<float2*>(ybase) + warp * SM::YSP;
+  // the paired form stages whole super-steps (zeros past the run) and so
+  // runs every super-step, the partial last one included, without predicates
+  const int staged = PAIR ? SM::NSUP * WIN : total;
+  for (int i = lane; i < staged; i += 32) {
+    const bool in = i >= sv_lo && i < sv_hi;
+    const float2 v = in ? yf[kr - W - fbase + i] : make_float2(0.f, 0.f);
+    if (PAIR) {
+      const float h = in ? fmaf(v.x, v.x, fmaf(v.y, v.y, 1.f)) * (1.f + 0x1p-17f) : 0.f;
+      ys4[i] = make_float4(v.x, v.y, h, 0.f);
+    } else {
+      ys2[i] = v;
+    }
+  }
   const bool edge = sv_lo > 0 || sv_hi < total;
-  __syncthreads();  // cs_s, y_s
+  __syncthreads();  // cs_s, staged symbols
 
   float ring[APL][WIN];
 #pragma unroll
@@ -107,47 +151,78 @@ __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
   float D[APL];
 #pragma unroll
   for (int a = 0; a < APL; ++a) D[a] = 0.f;
-  uint32_t* kw = keys_smem + warp * WIN * ROW;
-  for (int base = 0; base < total; base += WIN) {
-    const float2* yb = ys + base;
-    if (!edge && base + WIN <= total) {
-      // interior: every step is a real symbol
+
+  // metrics of the lane's angles for staged symbol i (in == false: zero)
+  auto metrics_v = [&](const float4 v, float (&m)[APL]) {
+    const float zx = fmaf(v.x, c_s[0], v.y * s_s[0]);
+    const float zy = fmaf(v.y, c_s[0], -v.x * s_s[0]);
+    const float ax = fabsf(zx), ay = fabsf(zy);
+    m[0] = (v.z - ax) - ay;
+    m[1] = fmaf(-1.41421356237309505f, fmaxf(ax, ay), v.z);
+  };
+  auto metrics = [&](int i, bool in, float (&m)[APL]) {
+    if constexpr (PAIR) {
+      const float4 v = ys4[i];
+      const float zx = fmaf(v.x, c_s[0], v.y * s_s[0]);
+      const float zy = fmaf(v.y, c_s[0], -v.x * s_s[0]);
+      const float ax = fabsf(zx), ay = fabsf(zy);
+      m[0] = (v.z - ax) - ay;
+      m[1] = fmaf(-1.41421356237309505f, fmaxf(ax, ay), v.z);
+    } else {
+      const float2 yv = ys2[i];
+#pragma unroll
+      for (int a = 0; a < APL; ++a) m[a] = in ? bps_metric<QAM16>(yv, c_s[a], s_s[a]) : 0.f;
+    }
+  };
+
+  int sup = 0;
+  for (int base = 0; base < total; base += WIN, ++sup) {
+    if (PAIR || (!edge && base + WIN <= total)) {
+      // interior: every step is a real symbol (paired form: or a staged zero);
+      // the paired form loads the staged symbols two steps ahead
+      float4 vn0 = PAIR ? ys4[base] : make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 vn1 = PAIR ? ys4[base + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int u = 0; u < WIN; ++u) {
-        const float2 yv = yb[u];
+        float m[APL];
+        if constexpr (PAIR) {
+          const float4 v = vn0;
+          vn0 = vn1;
+          if (u + 2 < WIN) vn1 = ys4[base + u + 2];
+          metrics_v(v, m);
+        } else {
+          metrics(base + u, true, m);
+        }
         uint32_t key = 0xffffffffu;
 #pragma unroll
         for (int a = 0; a < APL; ++a) {
-          const float m = bps_metric<QAM16>(yv, c_s[a], s_s[a]);
-          D[a] += m;
-          D[a] -= ring[a][u];
-          ring[a][u] = m;
+          D[a] += m[a] - ring[a][u];
+          ring[a][u] = m[a];
           key = min(key, (__float_as_uint(D[a]) & ~63u) | (uint32_t)(lane + 32 * a));
         }
-        kw[u * ROW + lane] = key;
+        kw[(u < WIN - 1 ? u : WIN - 1 + sup) * ROW + lane] = key;
       }
     } else {
 #pragma unroll
       for (int u = 0; u < WIN; ++u) {
         const int s = base + u;
         if (s < total) {
-          const bool ok = s >= sv_lo && s < sv_hi;
-          const float2 yv = yb[u];
+          float m[APL];
+          metrics(s, s >= sv_lo && s < sv_hi, m);
           uint32_t key = 0xffffffffu;
 #pragma unroll
           for (int a = 0; a < APL; ++a) {
-            const float m = ok ? bps_metric<QAM16>(yv, c_s[a], s_s[a]) : 0.f;
-            D[a] += m;
+            D[a] += m[a];
             D[a] -= ring[a][u];
-            ring[a][u] = m;
+            ring[a][u] = m[a];
             key = min(key, (__float_as_uint(fmaxf(D[a], 0.f)) & ~63u) | (uint32_t)(lane + 32 * a));
           }
-          kw[u * ROW + lane] = key;
+          kw[(u < WIN - 1 ? u : WIN - 1 + sup) * ROW + lane] = key;
         }
       }
     }
-    // reduce the super-step's outputs: steps [max(base, 2W), min(base + WIN, total))
-    const int s_lo = max(base, 2 * W), s_hi = min(base + WIN, total);
+    // reduce rows 0..WIN-2 of the super-step: steps [max(base, 2W), min(base + WIN - 1, total))
+    const int s_lo = max(base, 2 * W), s_hi = min(base + WIN - 1, total);
     __syncwarp();
     for (int s = s_lo + lane; s < s_hi; s += 32) {
       const uint4* row = reinterpret_cast<const uint4*>(kw + (s - base) * ROW);
@@ -161,6 +236,21 @@ __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
     }
     __syncwarp();
   }
+  // the last row of every super-step: step base_t + WIN - 1 of super-step t
+  for (int t = lane; t < sup; t += 32) {
+    const int s = t * WIN + WIN - 1;
+    if (s >= 2 * W && s < total) {
+      const uint4* row = reinterpret_cast<const uint4*>(kw + (WIN - 1 + t) * ROW);
+      uint32_t best = 0xffffffffu;
+#pragma unroll
+      for (int c4 = 0; c4 < 8; ++c4) {
+        const uint4 v = row[c4];
+        best = min(best, min(min(v.x, v.y), min(v.z, v.w)));
+      }
+      bh_s[warp][s - 2 * W] = (uint8_t)(best & 63u);
+    }
+  }
+  __syncwarp();
   // decisions, unwrap increments and EVM of the run
   float evn = 0.f, evd = 0.f;
   int inc_sum = 0;
@@ -168,7 +258,7 @@ __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
   for (int ko = lane; ko < ract; ko += 32) {
     const int bh = bh_s[warp][ko];
     if (ko > 0) inc_sum += unwrap_inc(bh_s[warp][ko - 1], bh, B);
-    const float2 yv = ys[W + ko];
+    const float2 yv = PAIR ? make_float2(ys4[W + ko].x, ys4[W + ko].y) : ys2[W + ko];
     const float2 csb = cs_s[bh];
     const float zx = fmaf(yv.x, csb.x, yv.y * csb.y), zy = fmaf(yv.y, csb.x, -yv.x * csb.y);
     const int lI = level_of(zx, d.nl), lQ = level_of(zy, d.nl);
@@ -202,8 +292,9 @@ __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
       atomicAdd(&d.st->evm_den, (double)c);
     }
   }
-  // the last block of this polarisation turns run sums into run start counters
-  __threadfence();
+  // the last block of this polarisation turns run sums into run start
+  // counters (the lane-0 threads wrote the run sums and edges)
+  if (lane == 0) __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) am_last = atomicAdd(&d.bps_done[pol], 1u) == gridDim.x - 1;
   __syncthreads();
@@ -344,16 +435,16 @@ static void launch_bps_t(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
   const long long n_dec = fa.k_b - fa.k_a;
   const int nruns = (int)((n_dec + kRun - 1) / kRun);
   dim3 grid((nruns + 7) / 8, 2);
-  const size_t smem = sizeof(uint32_t) * 8 * (2 * W + 1) * 36;
-  bps_kernel<B, W, Q><<<grid, 256, smem, s>>>(d, fa);
+  bps_kernel<B, W, Q><<<grid, 256, BpsSmem<B, W, Q>::BYTES, s>>>(d, fa);
 }
 
 template <int B, int W>
 static cudaError_t bps_attr_t() {
-  const int smem = (int)(sizeof(uint32_t) * 8 * (2 * W + 1) * 36);
-  cudaError_t e = cudaFuncSetAttribute(bps_kernel<B, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(bps_kernel<B, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)BpsSmem<B, W, true>::BYTES);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(bps_kernel<B, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(bps_kernel<B, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BpsSmem<B, W, false>::BYTES);
   return e;
 }
 

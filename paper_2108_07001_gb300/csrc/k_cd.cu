@@ -17,7 +17,12 @@
 // sum_{k<N/2} Y[k] conj(Y[k+N/2]) (times (-1)^window_start) to the frame
 // accumulator; after the inverse transform it adds the in-frame power and
 // the periodogram |FFT_{N/2}(z^4)|^2 of its symbol-spaced in-frame samples
-// (Welch average over blocks and polarisations).
+// (Welch average over blocks and polarisations, FP64 sums of the FP32 block
+// terms, so the result does not depend on the order of the blocks).  The first
+// forward pass reads the window from the ring into registers, the filter
+// and the Godard sum ride on the last forward pass, and the last inverse
+// pass writes z and the periodogram input directly, so each transform
+// makes one shared-memory round trip fewer per end.
 #include "fft_smem.cuh"
 
 namespace rx {
@@ -49,27 +54,74 @@ __global__ void __launch_bounds__(NT) cd_ols_kernel(RxDev d, FrameArgs fa) {
   const int keep = (int)min((long long)d.L, fa.s0 + zlen_f - a);
   const long long lo = a - d.h;
   const long long rbase = (long long)pol * d.ring_cap;
+  // ring slot of window sample 0 (the window is shorter than the ring, so
+  // it wraps at most once)
+  long long r0 = lo % d.ring_cap;
+  if (r0 < 0) r0 += d.ring_cap;
 
-  // load the window (halo included) from the ring
-  for (int i = threadIdx.x; i < N; i += NT) {
-    const long long n = lo + i;
-    float2 v = make_float2(0.f, 0.f);
-    if (n >= 0 && n < fa.n_valid) v = load_sample(d.ring, STOR, rbase + (n % d.ring_cap));
-    buf[swz(i)] = v;
+  // first forward pass (radix 16, no twiddles) straight from the ring:
+  // butterfly j takes window samples j + r N/16
+  {
+    constexpr int NB = N / 16;
+    constexpr int PER = (NB + NT - 1) / NT;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int j = threadIdx.x + u * NT;
+      if ((NB % NT) == 0 || j < NB) {
+        float2 v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int i = j + r * NB;
+          const long long n = lo + i;
+          long long slot = r0 + i;
+          if (slot >= d.ring_cap) slot -= d.ring_cap;
+          v[r] = (n >= 0 && n < fa.n_valid) ? load_sample(d.ring, STOR, rbase + slot) : make_float2(0.f, 0.f);
+        }
+        dft<16, false>(v);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) buf[swz(16 * j + r)] = v[r];
+      }
+    }
   }
   __syncthreads();
-  fft_smem<N, NT, false>(buf, tw_s, 1);
+  constexpr int NSL = last_ns<N>();  // sub-transform length of the last pass
+  constexpr int RL = N / NSL;        // its radix; its butterfly j (< NSL) outputs bins j + r NSL
+  constexpr int PERL = (NSL + NT - 1) / NT;
+  fft_passes<N, NT, 16, NSL, false>(buf, tw_s, 1);
 
-  // filter; Godard sum over bin pairs Rs apart
+  // last forward pass, filter and Godard sum over bin pairs (k, k + N/2) =
+  // outputs (r, r + RL/2) of one butterfly
   float gr = 0.f, gi = 0.f;
-  for (int k = threadIdx.x; k < N / 2; k += NT) {
-    float2 y0 = cmul(buf[swz(k)], __ldg(&d.Hf[k]));
-    float2 y1 = cmul(buf[swz(k + N / 2)], __ldg(&d.Hf[k + N / 2]));
-    const float2 p = cmulc(y0, y1);
-    gr += p.x;
-    gi += p.y;
-    buf[swz(k)] = y0;
-    buf[swz(k + N / 2)] = y1;
+  {
+    float2 v[PERL][RL];
+#pragma unroll
+    for (int u = 0; u < PERL; ++u) {
+      const int j = threadIdx.x + u * NT;
+      if ((NSL % NT) == 0 || j < NSL) {
+#pragma unroll
+        for (int r = 0; r < RL; ++r) v[u][r] = buf[swz(j + r * NSL)];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PERL; ++u) {
+      const int j = threadIdx.x + u * NT;
+      if ((NSL % NT) == 0 || j < NSL) {
+        pass_butterfly<N, RL, NSL, false>(v[u], j, tw_s, 1);
+#pragma unroll
+        for (int r = 0; r < RL; ++r) v[u][r] = cmul(v[u][r], __ldg(&d.Hf[j + r * NSL]));
+#pragma unroll
+        for (int r = 0; r < RL / 2; ++r) {
+          const float2 p = cmulc(v[u][r], v[u][r + RL / 2]);
+          gr += p.x;
+          gi += p.y;
+        }
+        if (!fa.est_only) {
+#pragma unroll
+          for (int r = 0; r < RL; ++r) buf[swz(j + r * NSL)] = v[u][r];
+        }
+      }
+    }
   }
   gr = block_sum<NT>(gr, scratch);
   gi = block_sum<NT>(gi, scratch);
@@ -80,51 +132,86 @@ __global__ void __launch_bounds__(NT) cd_ols_kernel(RxDev d, FrameArgs fa) {
     atomicAdd(&acc->C[1], (double)(sg * gi));
   }
   if (fa.est_only) return;
-  __syncthreads();
-  fft_smem<N, NT, true>(buf, tw_s, 1);
+  fft_passes<N, NT, 1, NSL, true>(buf, tw_s, 1);  // block_sum ended with a barrier
 
-  // kept samples -> z; in-frame power
+  // last inverse pass: output o = j + r NSL is window sample o; the kept
+  // ones (h <= o < h + keep) go to z, their in-frame power is summed, and
+  // the 4th powers of the even in-frame samples are placed as the input of
+  // the N/2-point periodogram transform (slot (n - e0)/2)
   float2* zp = d.z + (long long)pol * d.zlen + (a - fa.s0);
-  float pw = 0.f;
-  for (int i = threadIdx.x; i < keep; i += NT) {
-    const float2 v = buf[swz(d.h + i)];
-    zp[i] = v;
-    const long long n = a + i;
-    if (n >= fa.f0 && n < fa.f1) pw += v.x * v.x + v.y * v.y;
-  }
-  pw = block_sum<NT>(pw, scratch);
-  if (threadIdx.x == 0) atomicAdd(&d.acc[fa.acc_slot].P, (double)pw);
-
-  // 4th power of the even in-frame samples, zero padded to N/2
   const long long lo_n = max(a, fa.f0), hi_n = min(a + keep, fa.f1);
   const long long e0 = lo_n + (lo_n & 1);
   const int cnt = hi_n > e0 ? (int)((hi_n - e0 + 1) / 2) : 0;
-  if (cnt == 0) return;
-  constexpr int PER = (N / 2 + NT - 1) / NT;
-  float2 u[PER];
-  const int off = d.h + (int)(e0 - a);
+  const int off = d.h + (int)(e0 - a);  // window index of sample e0
+  float pw = 0.f;
+  {
+    float2 v[PERL][RL];
 #pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int idx = threadIdx.x + q * NT;
-    float2 v = make_float2(0.f, 0.f);
-    if (idx < cnt) {
-      const float2 x = buf[swz(off + 2 * idx)];
-      const float2 x2 = make_float2(x.x * x.x - x.y * x.y, 2.f * x.x * x.y);
-      v = make_float2(x2.x * x2.x - x2.y * x2.y, 2.f * x2.x * x2.y);
+    for (int u = 0; u < PERL; ++u) {
+      const int j = threadIdx.x + u * NT;
+      if ((NSL % NT) == 0 || j < NSL) {
+#pragma unroll
+        for (int r = 0; r < RL; ++r) v[u][r] = buf[swz(j + r * NSL)];
+      }
     }
-    u[q] = v;
-  }
-  __syncthreads();
+    __syncthreads();
 #pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int idx = threadIdx.x + q * NT;
-    if (idx < N / 2) buf[swz(idx)] = u[q];
+    for (int u = 0; u < PERL; ++u) {
+      const int j = threadIdx.x + u * NT;
+      if ((NSL % NT) == 0 || j < NSL) {
+        pass_butterfly<N, RL, NSL, true>(v[u], j, tw_s, 1);
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const int o = j + r * NSL;
+          const float2 x = v[u][r];
+          if (o >= d.h && o < d.h + keep) {
+            zp[o - d.h] = x;
+            const long long n = a + (o - d.h);
+            if (n >= fa.f0 && n < fa.f1) pw += x.x * x.x + x.y * x.y;
+            const int q = o - off;
+            if (q >= 0 && (q & 1) == 0 && (q >> 1) < cnt) {
+              const float2 x2 = make_float2(x.x * x.x - x.y * x.y, 2.f * x.x * x.y);
+              buf[swz(q >> 1)] = make_float2(x2.x * x2.x - x2.y * x2.y, 2.f * x2.x * x2.y);
+            }
+          }
+        }
+      }
+    }
   }
-  __syncthreads();
-  fft_smem<N / 2, NT, false>(buf, tw_s, 2);
-  for (int k = threadIdx.x; k < N / 2; k += NT) {
-    const float2 v = buf[swz(k)];
-    atomicAdd(&d.psd[(long long)fa.acc_slot * (N / 2) + k], (double)(v.x * v.x + v.y * v.y));
+  // zero padding of the periodogram input (slots no output was placed in)
+  for (int i = cnt + threadIdx.x; i < N / 2; i += NT) buf[swz(i)] = make_float2(0.f, 0.f);
+  pw = block_sum<NT>(pw, scratch);  // ends with a barrier
+  if (threadIdx.x == 0) atomicAdd(&d.acc[fa.acc_slot].P, (double)pw);
+  if (cnt == 0) return;
+
+  // N/2-point transform of the 4th powers; |.|^2 of its last pass is added
+  // to the frame's periodogram (Welch sum over blocks and polarisations)
+  constexpr int N2 = N / 2;
+  constexpr int NSL2 = last_ns<N2>();
+  constexpr int RL2 = N2 / NSL2;
+  constexpr int PERL2 = (NSL2 + NT - 1) / NT;
+  fft_passes<N2, NT, 1, NSL2, false>(buf, tw_s, 2);
+  double* psd = d.psd + (long long)fa.acc_slot * N2;
+  {
+    float2 v[PERL2][RL2];
+#pragma unroll
+    for (int u = 0; u < PERL2; ++u) {
+      const int j = threadIdx.x + u * NT;
+      if ((NSL2 % NT) == 0 || j < NSL2) {
+#pragma unroll
+        for (int r = 0; r < RL2; ++r) v[u][r] = buf[swz(j + r * NSL2)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PERL2; ++u) {
+      const int j = threadIdx.x + u * NT;
+      if ((NSL2 % NT) == 0 || j < NSL2) {
+        pass_butterfly<N2, RL2, NSL2, false>(v[u], j, tw_s, 2);
+#pragma unroll
+        for (int r = 0; r < RL2; ++r)
+          atomicAdd(&psd[j + r * NSL2], (double)(v[u][r].x * v[u][r].x + v[u][r].y * v[u][r].y));
+      }
+    }
   }
 }
 
@@ -154,8 +241,13 @@ __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mo
   const int tid = threadIdx.x;
   const FrameAcc* acc = d.acc + fa.acc_slot;
   const double* psd = d.psd + (long long)fa.acc_slot * (d.N / 2);
-  const double C_re = acc->C[0], C_im = acc->C[1];
-  const double resid = (C_re == 0.0 && C_im == 0.0) ? 0.0 : -atan2(C_im, C_re) / (2.0 * M_PI * d.Rs);
+  // FP64 transcendentals run on one thread only (the FP64 pipe is narrow)
+  if (tid == 0) {
+    const double C_re = acc->C[0], C_im = acc->C[1];
+    sh[3] = (C_re == 0.0 && C_im == 0.0) ? 0.0 : -atan2(C_im, C_re) / (2.0 * M_PI * d.Rs);
+  }
+  __syncthreads();
+  const double resid = sh[3];
   double tau_next;
   if (mode == 1) {
     const EstState es = d.es[fa.f & 1];

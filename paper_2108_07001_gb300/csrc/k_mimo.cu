@@ -182,64 +182,76 @@ __device__ __forceinline__ void store_taps(const ChainSmem<T>& sm, float2* dst) 
 
 // Sequential acquisition of the first frame, one block of 256 threads
 // (the chain is inherently sequential, so its latency is spread over a
-// block).  FIR: thread (k, p, q) = (t >> 2, (t >> 1) & 1, t & 1) forms
-// sum_t w[p][q][t] r_q[2k + t] and the q pair is added with a shuffle.
-// Gradient: thread (combo, quarter) sums e_p[k] conj(r_q[2k + t]) over a
-// quarter of the sub-block, quarters are added with shuffles.  The next
-// sub-block's samples are loaded into registers while the gradient runs.
+// block).  The rotated samples pass through a shared ring of four
+// 128-sample blocks per polarisation, kept as even/odd planes (with the
+// first 80 entries mirrored past the end, so window reads never wrap);
+// blocks are loaded into registers two sub-blocks ahead.
+// FIR: thread (q, k, p) = (t & 1, (t >> 1) & 63, t >> 7) forms
+// sum_t w[p][q][t] r_q[2k + t]; the q pair is added with a shuffle.
+// Gradient: thread (combo, quarter) = (t >> 2, t & 3) sums e_p[k] conj(r_q[2k + t])
+// over the sub-block's symbols k = quarter mod 4; the quarters are added
+// with shuffles and the quarter-0 thread updates the tap.
 template <int T>
 __global__ void __launch_bounds__(256) acq_kernel(RxDev d, FrameArgs fa) {
-  constexpr int NS = 2 * kK + T - 1;      // samples per pol per sub-block
-  constexpr int NLD = (2 * NS + 255) / 256;
-  __shared__ float2 r_s[2][NS + 1];
+  constexpr int PL = 344;   // plane stride (float2): 256 + 80 mirror, = 64 B mod 128 B
+  __shared__ float2 r_s[4 * PL + 8];
   __shared__ float2 w_s[2][2][T];         // [p][q][t]
   __shared__ float2 e_s[2][kK];
+  __shared__ float2 y1_s[kK];             // y_y outputs for the singularity check
   __shared__ float red_s[8][4];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int zlen_f = 2 * fa.Ff + 2 * d.c;
   const int n_acq = min(d.acq_syms, fa.Ff);
+  const int nsub = (n_acq + kK - 1) / kK;
   for (int i = tid; i < 4 * T; i += 256) {
     const int p = i / (2 * T), q = (i / T) & 1, t = i % T;
     w_s[p][q][t] = make_float2((p == q && t == (T - 1) / 2) ? 1.f : 0.f, 0.f);
   }
-  // prefetch registers for one sub-block's samples
-  float2 pre[NLD];
-  auto load = [&](int kf0, int nk) {
-    const int ns = 2 * nk + T - 1;
-#pragma unroll
-    for (int j = 0; j < NLD; ++j) {
-      const int i = tid + j * 256;
-      const int q = i / NS, s = i - q * NS;
-      float2 v = make_float2(0.f, 0.f);
-      if (q < 2 && s < ns) {
-        const int n = 2 * kf0 + s;
-        if (n < zlen_f) {
-          const float2 rot = cmul(__ldg(&d.rot_hi[n >> 10]), __ldg(&d.rot_lo[n & (kRotLo - 1)]));
-          v = cmul(d.z[(long long)q * d.zlen + n], rot);
-        }
-      }
-      pre[j] = v;
+  auto plane = [&](int q, int par) -> float2* { return r_s + (2 * q + par) * PL + q * 8; };
+  // one 128-sample block per polarisation: thread (q, s) = (tid >> 7, tid & 127).
+  // The raw loads stay in registers until the block is stored (rotation
+  // applied then), so nothing waits for them earlier.
+  struct Raw { float2 z, h, l; };
+  auto load_blk = [&](int b) -> Raw {
+    const int q = tid >> 7, n = 128 * b + (tid & 127);
+    Raw r{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    if (b < nsub + 2 && n < zlen_f) {
+      r.z = d.z[(long long)q * d.zlen + n];
+      r.h = __ldg(&d.rot_hi[n >> 10]);
+      r.l = __ldg(&d.rot_lo[n & (kRotLo - 1)]);
     }
+    return r;
   };
-  auto store = [&]() {
-#pragma unroll
-    for (int j = 0; j < NLD; ++j) {
-      const int i = tid + j * 256;
-      const int q = i / NS, s = i - q * NS;
-      if (q < 2) r_s[q][s] = pre[j];
-    }
+  auto store_blk = [&](int b, const Raw& r) {
+    const int q = tid >> 7, s = tid & 127;
+    const int idx = ((64 * b) & 255) + (s >> 1);
+    const float2 v = cmul(r.z, cmul(r.h, r.l));
+    float2* pl = plane(q, s & 1);
+    pl[idx] = v;
+    if (idx < 80) pl[idx + 256] = v;
   };
   const int cma_end = min(((d.cma_syms + kK - 1) / kK) * kK, n_acq);
   const int corr_lo = max(cma_end - 1024, 0);
   float cxr = 0.f, cxi = 0.f, pxx = 0.f, pyy = 0.f;
   bool was_cma = false;
-  load(0, min(kK, n_acq));
-  store();
+  Raw pre0 = load_blk(2), pre1 = load_blk(3);
+  store_blk(0, load_blk(0));
+  store_blk(1, load_blk(1));
   __syncthreads();
-  const int kk = tid >> 2, pp = (tid >> 1) & 1, qq = tid & 1;
-  for (int k0 = 0; k0 < n_acq; k0 += kK) {
+  const int qq = tid & 1, kk = (tid >> 1) & 63, pp = tid >> 7;
+  constexpr int NG = 16 * T;  // gradient (combo, quarter) pairs
+  for (int i = 0; i < nsub; ++i) {
+    const int k0 = i * kK;
     const int nk = min(kK, n_acq - k0);
     const int mode = k0 < d.cma_syms ? 0 : 1;
+    // block i + 2 into the ring (slot of block i - 2), block i + 4 into registers
+    if (i & 1) {
+      store_blk(i + 2, pre1);
+      pre1 = load_blk(i + 4);
+    } else {
+      store_blk(i + 2, pre0);
+      pre0 = load_blk(i + 4);
+    }
     if (mode == 1 && was_cma) {
       // singularity check over the last CMA outputs
       float v0 = warp_sum(cxr), v1 = warp_sum(cxi), v2 = warp_sum(pxx), v3 = warp_sum(pyy);
@@ -252,55 +264,64 @@ __global__ void __launch_bounds__(256) acq_kernel(RxDev d, FrameArgs fa) {
       if (rho > 0.5f) {
         float2 a = make_float2(0.f, 0.f), b2 = a;
         if (tid < T) {
-          a = w_s[0][1][T - 1 - tid];  // w_xy reversed
+          a = w_s[0][1][T - 1 - tid];   // w_xy reversed
           b2 = w_s[0][0][T - 1 - tid];  // w_xx reversed
         }
         __syncthreads();
         if (tid < T) {
-          w_s[1][0][tid] = make_float2(-a.x, a.y);   // -conj(w_xy[T-1-t])
+          w_s[1][0][tid] = make_float2(-a.x, a.y);    // -conj(w_xy[T-1-t])
           w_s[1][1][tid] = make_float2(b2.x, -b2.y);  // conj(w_xx[T-1-t])
         }
         if (tid == 0) d.st->reinit = 1;
       }
       __syncthreads();
     }
-    // ---- FIR
-    float2 acc = make_float2(0.f, 0.f);
+    // ---- FIR over one input polarisation, two accumulators (even/odd taps)
+    const int base = (64 * i) & 255;
+    const float2* rp0 = plane(qq, 0) + base + kk;
+    const float2* rp1 = plane(qq, 1) + base + kk;
+    float2 a0 = make_float2(0.f, 0.f), a1 = a0;
 #pragma unroll
     for (int t = 0; t < T; ++t) {
-      const float2 w = w_s[pp][qq][t], x = r_s[qq][2 * kk + t];
+      const float2 w = w_s[pp][qq][t];
+      const float2 x = (t & 1) ? rp1[t >> 1] : rp0[t >> 1];
+      float2& acc = (t & 1) ? a1 : a0;
       acc.x = fmaf(w.x, x.x, fmaf(-w.y, x.y, acc.x));
       acc.y = fmaf(w.x, x.y, fmaf(w.y, x.x, acc.y));
     }
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
-    const float2 y = acc;  // y_pp[kk]
+    float2 y = make_float2(a0.x + a1.x, a0.y + a1.y);
+    y.x += __shfl_xor_sync(0xffffffffu, y.x, 1);
+    y.y += __shfl_xor_sync(0xffffffffu, y.y, 1);
     const bool valid = kk < nk;
     // ---- error
     float2 e;
     if (mode == 0) {
       e = cscale(y, y.x * y.x + y.y * y.y - d.R2);
-      // correlation of the two outputs for the singularity check
-      const float2 yo = make_float2(__shfl_xor_sync(0xffffffffu, y.x, 2), __shfl_xor_sync(0xffffffffu, y.y, 2));
-      const int k = k0 + kk;
-      if (valid && pp == 0 && qq == 0 && k >= corr_lo && k < cma_end) {
-        cxr += y.x * yo.x + y.y * yo.y;
-        cxi += y.y * yo.x - y.x * yo.y;
-        pxx += y.x * y.x + y.y * y.y;
-        pyy += yo.x * yo.x + yo.y * yo.y;
+      if (k0 + nk > corr_lo && k0 < cma_end) {  // sub-block overlaps the correlation range
+        if (pp == 1 && qq == 0) y1_s[kk] = y;
+        __syncthreads();
+        const int k = k0 + kk;
+        if (valid && pp == 0 && qq == 0 && k >= corr_lo && k < cma_end) {
+          const float2 yo = y1_s[kk];
+          cxr += y.x * yo.x + y.y * yo.y;
+          cxi += y.y * yo.x - y.x * yo.y;
+          pxx += y.x * y.x + y.y * y.y;
+          pyy += yo.x * yo.x + yo.y * yo.y;
+        }
       }
     } else {
-      float s0x = 0.f, s0y = 0.f, s1x = 0.f, s1y = 0.f;
+      float sx = 0.f, sy = 0.f;
       if (valid && qq == 0) {
         const float2 a2 = make_float2(y.x * y.x - y.y * y.y, 2.f * y.x * y.y);
-        const float a4x = a2.x * a2.x - a2.y * a2.y, a4y = 2.f * a2.x * a2.y;
-        if (pp == 0) { s0x = a4x; s0y = a4y; } else { s1x = a4x; s1y = a4y; }
+        sx = a2.x * a2.x - a2.y * a2.y;
+        sy = 2.f * a2.x * a2.y;
       }
-      s0x = warp_sum(s0x); s0y = warp_sum(s0y); s1x = warp_sum(s1x); s1y = warp_sum(s1y);
-      if (lane == 0) { red_s[warp][0] = s0x; red_s[warp][1] = s0y; red_s[warp][2] = s1x; red_s[warp][3] = s1y; }
+      sx = warp_sum(sx);
+      sy = warp_sum(sy);
+      if (lane == 0) { red_s[warp][0] = sx; red_s[warp][1] = sy; }
       __syncthreads();
-      float sx = 0.f, sy = 0.f;
-      for (int w = 0; w < 8; ++w) { sx += red_s[w][2 * pp]; sy += red_s[w][2 * pp + 1]; }
+      sx = red_s[4 * pp][0] + red_s[4 * pp + 1][0] + red_s[4 * pp + 2][0] + red_s[4 * pp + 3][0];
+      sy = red_s[4 * pp][1] + red_s[4 * pp + 1][1] + red_s[4 * pp + 2][1] + red_s[4 * pp + 3][1];
       float ph = 0.f;
       if (sx != 0.f || sy != 0.f) ph = 0.25f * atan2f(-sy, -sx);
       float sn, cs;
@@ -311,39 +332,44 @@ __global__ void __launch_bounds__(256) acq_kernel(RxDev d, FrameArgs fa) {
     }
     if (qq == 0) e_s[pp][kk] = valid ? e : make_float2(0.f, 0.f);
     __syncthreads();
-    // prefetch the next sub-block while the gradient runs
-    const int k1 = k0 + kK;
-    if (k1 < n_acq) load(k1, min(kK, n_acq - k1));
-    // ---- gradient: combo = (p, q, t), quarter of the sub-block
-    const float step = (mode == 0 ? d.mu_cma : d.mu_dd) / (float)nk;
-    for (int c0 = 0; c0 < 16 * T; c0 += 256) {  // every lane runs every iteration (shuffles)
-      const int c = c0 + tid;
-      const bool act = c < 16 * T;
-      const int combo = act ? c >> 2 : 0, quarter = c & 3;
-      const int p = combo / (2 * T), q = (combo / T) & 1, t = combo % T;
-      float gx = 0.f, gy = 0.f;
-      const int ka = quarter * 16, kb = act ? min(ka + 16, nk) : ka;
-      for (int k = ka; k < kb; ++k) {
-        const float2 ee = e_s[p][k], x = r_s[q][2 * k + t];
-        gx = fmaf(ee.x, x.x, fmaf(ee.y, x.y, gx));
-        gy = fmaf(ee.y, x.x, fmaf(-ee.x, x.y, gy));
-      }
-      gx += __shfl_xor_sync(0xffffffffu, gx, 1);
-      gy += __shfl_xor_sync(0xffffffffu, gy, 1);
-      gx += __shfl_xor_sync(0xffffffffu, gx, 2);
-      gy += __shfl_xor_sync(0xffffffffu, gy, 2);
-      if (act && quarter == 0) {
-        float2 w = w_s[p][q][t];
-        w.x -= step * gx;
-        w.y -= step * gy;
-        w_s[p][q][t] = w;
+    // ---- gradient: thread (combo, quarter) sums over k = quarter mod 4
+    // (every lane runs every iteration: shuffles)
+    {
+      const float step = (mode == 0 ? d.mu_cma : d.mu_dd) / (float)nk;
+#pragma unroll
+      for (int c0 = 0; c0 < NG; c0 += 256) {
+        const int c = c0 + tid;
+        const bool act = c < NG;
+        const int cg = act ? c >> 2 : 0, qt = c & 3;
+        const int gp = cg / (2 * T), gq = (cg / T) & 1, gt = cg % T;
+        const float2* rq = plane(gq, gt & 1) + base + qt + (gt >> 1);  // r_q[2k + t] at k = qt + 4m: rq[4m]
+        const float2* eq = &e_s[gp][qt];
+        float gx0 = 0.f, gy0 = 0.f, gx1 = 0.f, gy1 = 0.f;
+        if (act) {
+#pragma unroll
+          for (int m = 0; m < kK / 4; m += 2) {
+            const float2 ea = eq[4 * m], xa = rq[4 * m];
+            const float2 eb = eq[4 * m + 4], xb = rq[4 * m + 4];
+            gx0 = fmaf(ea.x, xa.x, fmaf(ea.y, xa.y, gx0));
+            gy0 = fmaf(ea.y, xa.x, fmaf(-ea.x, xa.y, gy0));
+            gx1 = fmaf(eb.x, xb.x, fmaf(eb.y, xb.y, gx1));
+            gy1 = fmaf(eb.y, xb.x, fmaf(-eb.x, xb.y, gy1));
+          }
+        }
+        float gx = gx0 + gx1, gy = gy0 + gy1;
+        gx += __shfl_xor_sync(0xffffffffu, gx, 1);
+        gy += __shfl_xor_sync(0xffffffffu, gy, 1);
+        gx += __shfl_xor_sync(0xffffffffu, gx, 2);
+        gy += __shfl_xor_sync(0xffffffffu, gy, 2);
+        if (act && qt == 0) {
+          float2 w = w_s[gp][gq][gt];
+          w.x -= step * gx;
+          w.y -= step * gy;
+          w_s[gp][gq][gt] = w;
+        }
       }
     }
     __syncthreads();
-    if (k1 < n_acq) {
-      store();
-      __syncthreads();
-    }
     was_cma = mode == 0;
   }
   for (int i = tid; i < 4 * T; i += 256) {

@@ -58,7 +58,8 @@ int cuda_fail(cudaError_t e, const char* where) {
   } while (0)
 
 constexpr double kC = 299792458.0;
-constexpr int kZSlots = 3;  // frames in flight between the front and back streams
+constexpr int kZSlots = 6;      // frames in flight between the front and back streams
+constexpr int kStageSlots = 3;  // device staging buffers of host pushes
 
 struct StageEv {
   int stage;
@@ -114,7 +115,10 @@ struct rx_handle {
   std::vector<double> lat_ms;
   double gpu_ms = 0.0;
   long long frames_done = 0;
-  void* stage = nullptr;      // device staging for host pushes
+  void* stage[kStageSlots] = {};              // device staging for host pushes
+  cudaEvent_t ev_stage_in[kStageSlots] = {};   // H2D copy into the slot done (copy stream)
+  cudaEvent_t ev_stage_free[kStageSlots] = {}; // ingest of the slot done (pushing stream)
+  long long stage_i = 0;
   size_t stage_bytes = 0;
   std::deque<StageEv> ingest_ev;
   long long gen = 0;
@@ -192,7 +196,9 @@ void free_all(rx_handle* h) {
   RxDev& d = h->d;
   void* ptrs[] = {d.ring, d.Hs, d.Hf, d.tw, d.tw2, d.z, d.rot_hi, d.rot_lo, d.acc, d.psd, d.es, d.rec, d.st, d.w_acq,
                   d.chains, d.y, d.bl, d.run_int, d.run_m0, d.run_edge, d.bps_done, d.ber_done, d.dec, d.out, d.prbs_jump, d.ref,
-                  d.sync_err, d.win_err, d.hist_y, d.hist_bhat, d.hist_m, h->stage};
+                  d.sync_err, d.win_err, d.hist_y, d.hist_bhat, d.hist_m,
+                  h->stage[0], h->stage[1], h->stage[2]};
+  static_assert(kStageSlots == 3, "staging slots listed above");
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->cd_done)
@@ -212,6 +218,10 @@ void free_all(rx_handle* h) {
   }
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->ev_copy) cudaEventDestroy(h->ev_copy);
+  for (int i = 0; i < kStageSlots; ++i) {
+    if (h->ev_stage_in[i]) cudaEventDestroy(h->ev_stage_in[i]);
+    if (h->ev_stage_free[i]) cudaEventDestroy(h->ev_stage_free[i]);
+  }
   if (h->ev_reset) cudaEventDestroy(h->ev_reset);
   if (h->s_copy) cudaStreamDestroy(h->s_copy);
   if (h->s_comp) cudaStreamDestroy(h->s_comp);
@@ -288,7 +298,8 @@ int staged(rx_handle* h, PendingFrame& pf, int stage, cudaStream_t strm, Fn&& fn
 
 // Waits for everything the library has queued.
 cudaError_t sync_all(rx_handle* h) {
-  cudaError_t e = cudaStreamSynchronize(h->s_front);
+  cudaError_t e = cudaStreamSynchronize(h->s_copy);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_front);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_comp);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_ber);
   return e;
@@ -587,7 +598,7 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   // samples beyond the frame end; the BER end rule needs tail + W symbols
   h->la = std::max(d.L + d.h + d.c + 2, 2 * (h->tail + d.W + 2));
   const long long mb = (long long)cfg->max_block_samples;
-  d.ring_cap = 2LL * d.F + 2LL * h->la + d.c + d.h + mb + 1024;
+  d.ring_cap = (2LL * d.F + 2LL * h->la + d.c + d.h + mb + 1024 + 255) / 256 * 256;  // even: paired ingest
   d.out_cap_bytes = std::max<long long>(1 << 20, 32LL * d.F * 2 * d.bps / 8);
   d.dec_cap = 2LL * d.F + 8192;
   h->n_win_ring = d.F / std::max(d.slip_win, 32) + 8;
@@ -679,8 +690,14 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   h->st_init.bhat_last[0] = h->st_init.bhat_last[1] = -1;
   cudaMemcpy(d.st, &h->st_init, sizeof(StreamState), cudaMemcpyHostToDevice);
   h->stage_bytes = (size_t)mb * 2 * 16;
-  if (cudaMalloc(&h->stage, h->stage_bytes) != cudaSuccess) { free_all(h); delete h; return fail(RX_ENOMEM, "staging allocation failed"); }
+  for (int i = 0; i < kStageSlots; ++i)
+    if (cudaMalloc(&h->stage[i], h->stage_bytes) != cudaSuccess) { free_all(h); delete h; return fail(RX_ENOMEM, "staging allocation failed"); }
   cudaError_t e = cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking);
+  for (int i = 0; i < kStageSlots && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&h->ev_stage_in[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_stage_free[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_stage_free[i], h->s_copy);
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_comp, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_front, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_ber, cudaStreamNonBlocking);
@@ -772,9 +789,17 @@ int rx_push_block(rx_handle* h, const void* samples, size_t n_per_pol, int dtype
   }
   const size_t esz = dtype == RX_C128 ? 16 : (dtype == RX_C64 ? 8 : 4);
   const void* src = samples;
+  int sl = -1;
   if (!on_device) {
-    RX_CK(cudaMemcpyAsync(h->stage, samples, 2 * n * esz, cudaMemcpyHostToDevice, cs));
-    src = h->stage;
+    // The host->device copy runs on the copy stream into a staging slot, so
+    // it does not wait for the ring-slot dependencies of the ingest; the
+    // call returns once the copy (not the ingest) is done.
+    sl = (int)(h->stage_i++ % kStageSlots);
+    RX_CK(cudaStreamWaitEvent(h->s_copy, h->ev_stage_free[sl], 0));
+    RX_CK(cudaMemcpyAsync(h->stage[sl], samples, 2 * n * esz, cudaMemcpyHostToDevice, h->s_copy));
+    RX_CK(cudaEventRecord(h->ev_stage_in[sl], h->s_copy));
+    RX_CK(cudaStreamWaitEvent(cs, h->ev_stage_in[sl], 0));
+    src = h->stage[sl];
   }
   if (h->cfg.profile) {
     StageEv se{RX_STAGE_INGEST, get_event(h), get_event(h)};
@@ -788,9 +813,9 @@ int rx_push_block(rx_handle* h, const void* samples, size_t n_per_pol, int dtype
   h->stage_n[RX_STAGE_INGEST] += 1;
   h->last_cs = cs;
   h->copy_dirty = true;
-  if (!on_device) {  // host buffer and staging reusable on return
-    RX_CK(mark_copy(h));
-    RX_CK(cudaEventSynchronize(h->ev_copy));
+  if (!on_device) {  // the host buffer is reusable on return
+    RX_CK(cudaEventRecord(h->ev_stage_free[sl], cs));
+    RX_CK(cudaEventSynchronize(h->ev_stage_in[sl]));
   }
   h->pushed += n;
   while (h->pushed >= 2 * (h->f_next + 1) * F + h->la) {
