@@ -58,7 +58,7 @@ struct BpsSmem {
   static constexpr int ROWS = WIN - 1 + NSUP;            // key rows per warp
   static constexpr int YSP = (NSUP * WIN + 7) / 8 * 8;     // staged entries (whole super-steps)
   static constexpr size_t KEY_BYTES = sizeof(uint32_t) * 8 * ROWS * ROW;
-  static constexpr size_t Y_BYTES = (size_t)8 * YSP * (PAIR ? 16 : 8);
+  static constexpr size_t Y_BYTES = (size_t)8 * YSP * (PAIR ? 24 : 8);
   static constexpr size_t BYTES = KEY_BYTES + Y_BYTES;
 };
 
@@ -79,6 +79,37 @@ struct BpsSmem {
 // bias of 2^-17 (common to all angles of a symbol, so the argmin is that of
 // d) that keeps every metric positive under rounding; symbols outside the
 // stream are staged as y = 0, h = 0 and contribute exactly 0.
+// Packed FP32 pairs (two IEEE single-precision lanes in one 64-bit register,
+// element 0 in the low half): add/sub/mul/fma .rn.f32x2.
+__device__ __forceinline__ unsigned long long f2pk(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2up(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2mul(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
 template <int B, int W, bool QAM16>
 __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
   using SM = BpsSmem<B, W, QAM16>;
@@ -125,7 +156,8 @@ __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
   const int sv_hi = (int)min((long long)total, ylim - (kr - W));
   uint32_t* kw = keys_smem + warp * SM::ROWS * ROW;
   unsigned char* ybase = reinterpret_cast<unsigned char*>(keys_smem) + SM::KEY_BYTES;
-  float4* ys4 = reinterpret_cast<float4*>(ybase) + warp * SM::YSP;
+  float4* ys4 = reinterpret_cast<float4*>(ybase) + warp * SM::YSP;            // paired: {x, y, y, x}
+  float2* hs2 = reinterpret_cast<float2*>(ybase + (size_t)8 * SM::YSP * 16) + warp * SM::YSP;  // paired: {h, h}
   float2* ys2 = reinterpret_cast<float2*>(ybase) + warp * SM::YSP;
   // the paired form stages whole super-steps (zeros past the run) and so
   // runs every super-step, the partial last one included, without predicates
@@ -135,7 +167,8 @@ __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
     const float2 v = in ? yf[kr - W - fbase + i] : make_float2(0.f, 0.f);
     if (PAIR) {
       const float h = in ? fmaf(v.x, v.x, fmaf(v.y, v.y, 1.f)) * (1.f + 0x1p-17f) : 0.f;
-      ys4[i] = make_float4(v.x, v.y, h, 0.f);
+      ys4[i] = make_float4(v.x, v.y, v.y, v.x);
+      hs2[i] = make_float2(h, h);
     } else {
       ys2[i] = v;
     }
@@ -175,32 +208,62 @@ __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
     }
   };
 
+  // paired form: packed window sums and ring (angle l low, l + 32 high)
+  unsigned long long ring2[PAIR ? WIN : 1];
+  unsigned long long D2 = 0ull;
+#pragma unroll
+  for (int u = 0; u < (PAIR ? WIN : 1); ++u) ring2[u] = 0ull;
+  const unsigned long long CC2 = f2pk(c_s[0], c_s[0]), SS2 = f2pk(s_s[0], -s_s[0]);
+  const unsigned long long NG2 = f2pk(-1.f, -1.41421356237309505f);
   int sup = 0;
   for (int base = 0; base < total; base += WIN, ++sup) {
     if (PAIR || (!edge && base + WIN <= total)) {
       // interior: every step is a real symbol (paired form: or a staged zero);
       // the paired form loads the staged symbols two steps ahead
-      float4 vn0 = PAIR ? ys4[base] : make_float4(0.f, 0.f, 0.f, 0.f);
-      float4 vn1 = PAIR ? ys4[base + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+      if constexpr (PAIR) {
+        // packed pairs: (zx, zy) = (x, y) c + (y, x) (s, -s); (g0, g1) =
+        // (h, h) + (|zx| + |zy|, max(|zx|, |zy|)) (-1, -sqrt2); D += g - ring
+        const ulonglong2* pq_s = reinterpret_cast<const ulonglong2*>(ys4);
+        const unsigned long long* hh_s = reinterpret_cast<const unsigned long long*>(hs2);
+        ulonglong2 q0 = pq_s[base], q1 = pq_s[base + 1];
+        unsigned long long h0 = hh_s[base], h1 = hh_s[base + 1];
 #pragma unroll
-      for (int u = 0; u < WIN; ++u) {
-        float m[APL];
-        if constexpr (PAIR) {
-          const float4 v = vn0;
-          vn0 = vn1;
-          if (u + 2 < WIN) vn1 = ys4[base + u + 2];
-          metrics_v(v, m);
-        } else {
+        for (int u = 0; u < WIN; ++u) {
+          const ulonglong2 pq = q0;
+          const unsigned long long hh = h0;
+          q0 = q1;
+          h0 = h1;
+          if (u + 2 < WIN) {
+            q1 = pq_s[base + u + 2];
+            h1 = hh_s[base + u + 2];
+          }
+          const unsigned long long zz = f2fma(pq.y, SS2, f2mul(pq.x, CC2));
+          float zx, zy;
+          f2up(zz, zx, zy);
+          const float ax = fabsf(zx), ay = fabsf(zy);
+          const unsigned long long g = f2fma(f2pk(ax + ay, fmaxf(ax, ay)), NG2, hh);
+          D2 = f2add(D2, f2sub(g, ring2[u]));
+          ring2[u] = g;
+          float d0, d1;
+          f2up(D2, d0, d1);
+          const uint32_t key = min((__float_as_uint(d0) & ~63u) | (uint32_t)lane,
+                                   (__float_as_uint(d1) & ~63u) | (uint32_t)(lane + 32));
+          kw[(u < WIN - 1 ? u : WIN - 1 + sup) * ROW + lane] = key;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < WIN; ++u) {
+          float m[APL];
           metrics(base + u, true, m);
-        }
-        uint32_t key = 0xffffffffu;
+          uint32_t key = 0xffffffffu;
 #pragma unroll
-        for (int a = 0; a < APL; ++a) {
-          D[a] += m[a] - ring[a][u];
-          ring[a][u] = m[a];
-          key = min(key, (__float_as_uint(D[a]) & ~63u) | (uint32_t)(lane + 32 * a));
+          for (int a = 0; a < APL; ++a) {
+            D[a] += m[a] - ring[a][u];
+            ring[a][u] = m[a];
+            key = min(key, (__float_as_uint(D[a]) & ~63u) | (uint32_t)(lane + 32 * a));
+          }
+          kw[(u < WIN - 1 ? u : WIN - 1 + sup) * ROW + lane] = key;
         }
-        kw[(u < WIN - 1 ? u : WIN - 1 + sup) * ROW + lane] = key;
       }
     } else {
 #pragma unroll
