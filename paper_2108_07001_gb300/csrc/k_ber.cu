@@ -197,11 +197,14 @@ __global__ void __launch_bounds__(256) ber_count_kernel(RxDev d, long long ka, l
   const long long kw = kal + ((long long)blockIdx.x * 8 + w) * 32 * kBerSyms;  // warp span start
   const int perm = d.st->sync_perm;
   unsigned err[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  const long long r0 = (kw + l) % d.dec_cap;  // decision ring slot of the lane's first symbol
 #pragma unroll
   for (int j = 0; j < kBerSyms; ++j) {
     const long long k = kw + 32 * j + l;
     if (k >= ka && k < kb) {
-      const uint8_t v = d.dec[k % d.dec_cap];
+      long long slot = r0 + 32 * j;
+      if (slot >= d.dec_cap) slot -= d.dec_cap;
+      const uint8_t v = d.dec[slot];
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         const uint32_t rb = ref_bits(d.ref + (long long)(p ^ perm) * d.ref_words, (k - ka) * d.bps, d.bps);
@@ -278,75 +281,116 @@ __global__ void __launch_bounds__(256) ber_count_kernel(RxDev d, long long ka, l
 
 // Slip pass over windows [w_from, w_to); window w covers symbols
 // [ks + w SW, ks + (w+1) SW) clipped to k_lim.  A 4-state automaton (state =
-// quadrant in use) per polarisation: windows are staged in shared memory in
-// chunks of kSlipChunk, each lane of warp p runs its 32 windows of a chunk
-// from all four start states at once, and the lanes are chained in order,
-// which gives exactly the sequential result.  Window slots are cleared.
+// quadrant in use) per polarisation.  Windows are staged in shared memory in
+// chunks of kSlipChunk; each of the 128 threads of a polarisation runs a
+// contiguous slice of a chunk from all four start states at once, which
+// gives a map start state -> (end state, errors, slips); the maps are
+// composed in window order (shuffles within a warp, then the warps in
+// order) and the composition is applied to the current state, which gives
+// exactly the sequential result.  Window slots are cleared.
 constexpr int kSlipChunk = 1024;
+
+struct SlipMap {
+  int q[4];
+  unsigned e[4], s[4];
+};
+
+// a then b: start state i -> b applied to a's end state.
+__device__ __forceinline__ void slip_compose(SlipMap& a, const SlipMap& b) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = a.q[i];
+    const int bq = m == 0 ? b.q[0] : m == 1 ? b.q[1] : m == 2 ? b.q[2] : b.q[3];
+    const unsigned be = m == 0 ? b.e[0] : m == 1 ? b.e[1] : m == 2 ? b.e[2] : b.e[3];
+    const unsigned bs = m == 0 ? b.s[0] : m == 1 ? b.s[1] : m == 2 ? b.s[2] : b.s[3];
+    a.q[i] = bq;
+    a.e[i] += be;
+    a.s[i] += bs;
+  }
+}
 
 __device__ void slip_pass(const RxDev& d, long long w_from, long long w_to, long long k_lim, int n_win_ring,
                           unsigned* win_s) {
-  const int p = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ SlipMap wmap[8];
+  const int pol = threadIdx.x >> 7, lp = threadIdx.x & 127, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   StreamState* st = d.st;
   const long long ks = d.ber_skip;
-  int qc = p < 2 ? st->q_cur[p] : 0;
+  int qc = st->q_cur[pol];  // used by the first thread of each polarisation
   unsigned long long E = 0, SL = 0;
   for (long long c0 = w_from; c0 < w_to; c0 += kSlipChunk) {
     const int nw = (int)min((long long)kSlipChunk, w_to - c0);
+    const int r0 = (int)(c0 % n_win_ring);  // ring slot of the chunk's first window (nw <= ring size)
+    // stage the chunk's counters (all loads first), then clear their slots
     for (int i = threadIdx.x; i < nw * 8; i += blockDim.x) {
-      const long long w = c0 + i / 8;
-      unsigned* e = d.win_err + (w % n_win_ring) * 8 + (i % 8);
-      win_s[i] = __ldcg(e);
-      *e = 0;
+      int slot = r0 + (i >> 3);
+      if (slot >= n_win_ring) slot -= n_win_ring;
+      win_s[i] = __ldcg(d.win_err + (long long)slot * 8 + (i & 7));
     }
     __syncthreads();
-    if (p < 2) {
-      const int per = (nw + 31) / 32;
-      const int a0 = lane * per, a1 = min(a0 + per, nw);
-      int q[4] = {0, 1, 2, 3};
-      unsigned long long err[4] = {0, 0, 0, 0}, slp[4] = {0, 0, 0, 0};
-      for (int i = a0; i < a1; ++i) {
-        const long long a = ks + (c0 + i) * d.slip_win;
-        const long long nb = (min(a + d.slip_win, k_lim) - a) * d.bps;
-        const unsigned* ev = win_s + i * 8 + p * 4;
-        int qb = 0;
+    for (int i = threadIdx.x; i < nw * 8; i += blockDim.x) {
+      int slot = r0 + (i >> 3);
+      if (slot >= n_win_ring) slot -= n_win_ring;
+      d.win_err[(long long)slot * 8 + (i & 7)] = 0;
+    }
+    // this thread's slice of windows, from every start state
+    const int per = (nw + 127) / 128;
+    const int a0 = min(lp * per, nw), a1 = min(a0 + per, nw);
+    SlipMap m;
 #pragma unroll
-        for (int qq = 1; qq < 4; ++qq)
-          if (ev[qq] < ev[qb]) qb = qq;
+    for (int i = 0; i < 4; ++i) { m.q[i] = i; m.e[i] = 0u; m.s[i] = 0u; }
+    for (int i = a0; i < a1; ++i) {
+      const long long a = ks + (c0 + i) * d.slip_win;
+      const long long nb = (min(a + d.slip_win, k_lim) - a) * d.bps;
+      const unsigned* ev = win_s + i * 8 + pol * 4;
+      const unsigned e0 = ev[0], e1 = ev[1], e2 = ev[2], e3 = ev[3];
+      int qb = 0;
+      unsigned eb = e0;
+      if (e1 < eb) { qb = 1; eb = e1; }
+      if (e2 < eb) { qb = 2; eb = e2; }
+      if (e3 < eb) { qb = 3; eb = e3; }
 #pragma unroll
-        for (int s0 = 0; s0 < 4; ++s0) {
-          if ((long long)ev[q[s0]] * 4 > nb) {
-            q[s0] = qb;
-            ++slp[s0];
-          }
-          err[s0] += ev[q[s0]];
+      for (int s0 = 0; s0 < 4; ++s0) {
+        const int qs = m.q[s0];
+        unsigned ec = qs == 0 ? e0 : qs == 1 ? e1 : qs == 2 ? e2 : e3;
+        if ((long long)ec * 4 > nb) {
+          m.q[s0] = qb;
+          ec = eb;
+          ++m.s[s0];
         }
+        m.e[s0] += ec;
       }
-      for (int ln = 0; ln < 32; ++ln) {
-        int nq[4];
-        unsigned long long re[4], rs[4];
+    }
+    // compose the 32 maps of the warp in order: lane l takes lane l + o's
+    // composition when l is a multiple of 2o
 #pragma unroll
-        for (int s0 = 0; s0 < 4; ++s0) {
-          nq[s0] = __shfl_sync(0xffffffffu, q[s0], ln);
-          re[s0] = __shfl_sync(0xffffffffu, err[s0], ln);
-          rs[s0] = __shfl_sync(0xffffffffu, slp[s0], ln);
-        }
-        int nqc = nq[0];
-        unsigned long long ee = re[0], ss = rs[0];
+    for (int o = 1; o < 32; o <<= 1) {
+      SlipMap nb;
 #pragma unroll
-        for (int s0 = 1; s0 < 4; ++s0)
-          if (qc == s0) { nqc = nq[s0]; ee = re[s0]; ss = rs[s0]; }
-        E += ee;
-        SL += ss;
-        qc = nqc;
+      for (int i = 0; i < 4; ++i) {
+        nb.q[i] = __shfl_down_sync(0xffffffffu, m.q[i], o);
+        nb.e[i] = __shfl_down_sync(0xffffffffu, m.e[i], o);
+        nb.s[i] = __shfl_down_sync(0xffffffffu, m.s[i], o);
+      }
+      if ((lane & (2 * o - 1)) == 0) slip_compose(m, nb);
+    }
+    if (lane == 0) wmap[warp] = m;
+    __syncthreads();
+    if (lp == 0) {
+#pragma unroll 1
+      for (int w = 4 * pol; w < 4 * pol + 4; ++w) {
+        const SlipMap& mw = wmap[w];
+        const int i = qc;
+        E += i == 0 ? mw.e[0] : i == 1 ? mw.e[1] : i == 2 ? mw.e[2] : mw.e[3];
+        SL += i == 0 ? mw.s[0] : i == 1 ? mw.s[1] : i == 2 ? mw.s[2] : mw.s[3];
+        qc = i == 0 ? mw.q[0] : i == 1 ? mw.q[1] : i == 2 ? mw.q[2] : mw.q[3];
       }
     }
     __syncthreads();
   }
-  if (p < 2 && lane == 0) {
+  if (lp == 0) {
     const long long a = ks + w_from * d.slip_win;
     const long long b = min(ks + w_to * (long long)d.slip_win, k_lim);
-    st->q_cur[p] = qc;
+    st->q_cur[pol] = qc;
     atomicAdd(&st->errors, E);
     atomicAdd(&st->bits, (unsigned long long)(max(b - a, 0LL) * d.bps));
     atomicAdd(&st->slips, SL);

@@ -79,37 +79,6 @@ struct BpsSmem {
 // bias of 2^-17 (common to all angles of a symbol, so the argmin is that of
 // d) that keeps every metric positive under rounding; symbols outside the
 // stream are staged as y = 0, h = 0 and contribute exactly 0.
-// Packed FP32 pairs (two IEEE single-precision lanes in one 64-bit register,
-// element 0 in the low half): add/sub/mul/fma .rn.f32x2.
-__device__ __forceinline__ unsigned long long f2pk(float lo, float hi) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void f2up(unsigned long long v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b, unsigned long long c) {
-  unsigned long long r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
-__device__ __forceinline__ unsigned long long f2mul(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-
 template <int B, int W, bool QAM16>
 __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
   using SM = BpsSmem<B, W, QAM16>;

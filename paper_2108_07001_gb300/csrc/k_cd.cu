@@ -235,7 +235,7 @@ __device__ __forceinline__ double wrap_pi(double x) {
 // frame f reads acc/psd slot fa.acc_slot and state es[f & 1], clears the
 // other accumulator slot and writes es[(f + 1) & 1].
 __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mode) {
-  __shared__ double sv[32];
+  __shared__ long long sv[32];
   __shared__ int si[32];
   __shared__ double sh[4];
   const int tid = threadIdx.x;
@@ -252,15 +252,17 @@ __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mo
   if (mode == 1) {
     const EstState es = d.es[fa.f & 1];
     const int n2 = d.N / 2;
-    double best = -1.0;
+    // argmax (lowest index on ties) on the bit patterns: the sums are >= 0,
+    // and non-negative doubles order like their bits as integers
+    long long best = -1;
     int bi = 0;
     for (int k = tid; k < n2; k += 1024) {
-      const double v = psd[k];
+      const long long v = __double_as_longlong(psd[k]);
       if (v > best) { best = v; bi = k; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
     }
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mo
       bi = si[tid];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
       }

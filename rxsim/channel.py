@@ -133,6 +133,7 @@ class LinkConfig:
     prbs_seed: int = 1
     seed: int = 1000
     out_dtype: str = "c128"          # c128 | c64 | c16 (interleaved float16 re/im)
+    phase_jumps: tuple = ()          # ((sample index, radians), ...) carrier phase steps
 
 
 def simulate(cfg: LinkConfig) -> dict:
@@ -179,6 +180,8 @@ def simulate(cfg: LinkConfig) -> dict:
         inc = rng.standard_normal(ns) * math.sqrt(2.0 * math.pi * cfg.linewidth_hz / fs)
         inc[0] = 0.0
         ph = ph + np.cumsum(inc)
+    for n_j, rad in cfg.phase_jumps:
+        ph[int(n_j):] += float(rad)
     x = x * np.exp(1j * ph)[None, :]
 
     if cfg.snr_db is not None:

@@ -326,6 +326,27 @@ def test_chain_noiseless_all_impairments_is_error_free():
     assert b["errors"] == 0 and b["slips"] == 0 and b["bits"] > 100000
 
 
+def test_quarter_turn_phase_jumps_are_counted_as_slips():
+    """Abrupt +-pi/2 carrier steps (no dispersion, so nothing smears them)
+    leave the 4th-power phase references and the pi/2-periodic BPS metric
+    unchanged, so later decisions are a quarter turn off.  The slip rule (a
+    1024-symbol window with more than a quarter of its bits wrong switches to
+    its best quadrant) then gives, per polarisation, one slip per step; a
+    rotated Gray QPSK symbol has exactly one wrong bit, so the counted errors
+    follow by hand: the step at symbol 20003.5 leaves 476 rotated symbols in
+    window [19456, 20480) (under a quarter: counted, slip in the next window);
+    the step at symbol 26800 rotates 848 of window [26624, 27648) (over a
+    quarter: slip in that window, its 176 unrotated symbols counted)."""
+    n_sym = 1 << 15
+    sim = rxsim.simulate(rxsim.LinkConfig(n_sym=n_sym, snr_db=None, fiber_len_m=1e3, prbs_seed=5, seed=23,
+                                          phase_jumps=((2 * 20000 + 7, math.pi / 2), (53600, -math.pi / 2))))
+    cfg = O.RxConfig(fiber_len_m=1e3, prbs_seed=5, frame_syms=1 << 14)
+    b = O.Receiver(cfg).run(sim["rx"])["ber"]
+    assert b["sync"]["errors"] == 0
+    assert b["slips"] == 4
+    assert abs(b["errors"] - 2 * (476 + 176)) <= 8  # a few symbols at each step are in transition
+
+
 @pytest.mark.slow
 def test_chain_ber_within_half_db_of_theory():
     """All impairments of the 1,000 km QPSK workload at 10 dB: the BER is
