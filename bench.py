@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import ctypes
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -309,37 +310,56 @@ def finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, o
 ORACLE_THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS")
 
 
-def oracle_child(n_sym, reps):
+def workload_by_name(name):
+    from paper_2108_07001_gb300 import workloads
+    for wl in workloads.ALL:
+        if wl["name"] == name:
+            return wl
+    raise KeyError(name)
+
+
+def oracle_child(name, n_sym, reps):
     """Runs in a child process with one BLAS/OpenMP thread: simulates the
-    first n_sym symbols of the workload's link once, then times the FP64
-    oracle on them reps times.  Prints {"times": [...]} as JSON."""
+    first n_sym symbols of the named workload's link once (complex64
+    samples, as the GPU forms receive them), then times the FP64 oracle on
+    them reps times.  Prints {"times": [...], "ber": {...}} as JSON."""
     import rxsim
     from oracle import rx_oracle as O
     from paper_2108_07001_gb300.workloads import oracle_kwargs
-    wl = workload()
+    wl = workload_by_name(name)
     lk = dict(wl["link"])
     lk["n_sym"] = n_sym
+    lk["out_dtype"] = "c64"
     sim = rxsim.simulate(rxsim.LinkConfig(**lk))
     x = sim["rx"].astype(np.complex128)
     del sim
     kw = oracle_kwargs(wl["rx"])
-    times = []
+    times, res = [], None
     for _ in range(reps):
         t0 = time.perf_counter()
-        O.Receiver(O.RxConfig(**kw)).run(x)
+        res = O.Receiver(O.RxConfig(**kw)).run(x)
         times.append(time.perf_counter() - t0)
-    print(json.dumps({"times": times}), flush=True)
+    b = res["ber"]
+    print(json.dumps({"times": times, "ber": {"errors": int(b["errors"]), "bits": int(b["bits"]),
+                                              "slips": int(b["slips"]), "ber": float(b["ber"]),
+                                              "evm": float(b["evm"])}}), flush=True)
 
 
-def oracle_times(n_sym, reps):
-    """Oracle run times on the host cores, measured in a fresh single-threaded
-    process (fork+exec, so safe after CUDA initialisation)."""
+def oracle_run(n_sym, reps, name=None):
+    """Oracle run times (and the last run's BER counters) on the host cores,
+    measured in a fresh single-threaded process (fork+exec, so safe after
+    CUDA initialisation)."""
     env = dict(os.environ)
     for k in ORACLE_THREAD_ENV:
         env[k] = "1"
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", str(n_sym), str(reps)],
+    name = name or workload()["name"]
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", name, str(n_sym), str(reps)],
                          env=env, capture_output=True, text=True, check=True, cwd=ROOT)
-    return json.loads(out.stdout.strip().splitlines()[-1])["times"]
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_times(n_sym, reps):
+    return oracle_run(n_sym, reps)["times"]
 
 
 CPU_BASELINE_SYMS = 1 << 20  # one full frame, acquisition included (10-30 s of one core)
@@ -372,6 +392,102 @@ def run_reference(args):
             "e2e": {"value": round(v, 6), "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_qam16(args):
+    """DP-16QAM 32 GBd, 2^22 symbols, 5,000 km, 18 dB: the same complex64
+    samples through the FP32-storage path and the FP16-storage path (FP32
+    arithmetic), pushed in 2^18-symbol blocks from HBM, against the FP64
+    oracle on the same samples: throughput, BER and EVM of each form and
+    the EVM penalty of each GPU form over the oracle."""
+    import torch
+    import rxsim
+    from paper_2108_07001_gb300 import rx, workloads
+    wl = workloads.DP_16QAM_5000KM
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    lk = dict(wl["link"])
+    lk["out_dtype"] = "c64"
+    if args.symbols:
+        lk["n_sym"] = args.symbols
+    x = rxsim.simulate(rxsim.LinkConfig(**lk))["rx"]
+    n_samp = x.shape[1]
+    n_sym = n_samp // 2
+    push_syms = min(1 << 18, n_sym)
+    m = 2 * push_syms
+    nb = n_samp // m
+    blocks = np.ascontiguousarray(x[:, :nb * m].reshape(2, nb, m).transpose(1, 0, 2))
+    dx64 = torch.from_numpy(blocks).to(dev)
+    dx16 = torch.from_numpy(np.stack([blocks.real, blocks.imag], axis=-1).astype(np.float16)).to(dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    forms = {}
+    for form, storage, dtype, data, esz in (("fp32_storage", rx.RX_C64, rx.RX_C64, dx64, 8),
+                                            ("fp16_storage", rx.RX_C16, rx.RX_C16, dx16, 4)):
+        cfg = rx.default_config(**wl["rx"], storage_dtype=storage, max_block_samples=m)
+        r = rx.Receiver(cfg)
+        base, bbytes = data.data_ptr(), 2 * m * esz
+
+        def step():
+            r.reset()
+            for b in range(nb):
+                rc = r.lib.rx_push_block(r.h, ctypes.c_void_p(base + b * bbytes), m, dtype, 1, ctypes.c_void_p(stream))
+                if rc:
+                    raise rx.RxError(rc, r.lib.rx_last_error().decode())
+            r.end()
+            r.join(stream)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            step()
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        st = r.stats()
+        forms[form] = {"value": round(2 * n_samp / (ms * 1e-3) / 1e9, 3), "unit": "Gsamples/s",
+                       "ms_per_step": round(ms, 3), "ber": st["ber"], "bit_errors": st["bit_errors"],
+                       "bits": st["bits"], "cycle_slips": st["cycle_slips"], "evm": st["evm"],
+                       "evm_db": round(20 * math.log10(st["evm"]), 3) if st["evm"] > 0 else None}
+        r.close()
+    orc = oracle_run(n_sym, 1, wl["name"])
+    ob = orc["ber"]
+    oracle = {"ber": ob["ber"], "bit_errors": ob["errors"], "bits": ob["bits"], "cycle_slips": ob["slips"],
+              "evm": ob["evm"], "evm_db": round(20 * math.log10(ob["evm"]), 3), "cores": 1,
+              "seconds": round(orc["times"][0], 1)}
+    for f in forms.values():
+        f["evm_penalty_db"] = round(f["evm_db"] - oracle["evm_db"], 4) if f["evm_db"] is not None else None
+    return {"metric": "gsamples_per_s", "value": forms["fp16_storage"]["value"], "unit": "Gsamples/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "workload": "qam16", "dtype": "f16 storage, f32 arithmetic", "data": "synthetic (seeded link simulator)",
+            "config": {"workload": wl["name"], "symbols_per_pol": n_sym, "push_syms": push_syms,
+                       "mimo_taps": wl["rx"]["mimo_taps"], "bps_angles": wl["rx"]["bps_angles"],
+                       "bps_half_window": wl["rx"]["bps_half_window"]},
+            "forms": forms, "oracle": oracle, "cpu_baseline": {
+                "value": round(4 * n_sym / orc["times"][0] / 1e9, 6), "unit": "Gsamples/s", "cores": 1,
+                "kind": "oracle", "sample": f"the whole {n_sym}-symbol stream, FP64 numpy oracle, one thread"}}
+
+
+def combine_replicas(line, world, reduce_max):
+    """Whole-job line of N independent replicas: the step time (and the
+    end-to-end step time) is the maximum over ranks (reduce_max: list of
+    floats -> element-wise max over ranks, a collective every rank calls)
+    and the value counts the samples of every rank."""
+    e2e = line.get("e2e")
+    ms, e2e_ms = reduce_max([float(line["ms_per_step"]), float(e2e["ms_per_step"]) if e2e else 0.0])
+    out = dict(line)
+    samples = world * 4 * line["config"]["symbols_per_pol"]
+    out["n_gpus"] = world
+    out["ms_per_step"] = ms
+    out["value"] = round(samples / (ms * 1e-3) / 1e9, 3)
+    out["config"] = dict(line["config"], parallelism=f"replicas x{world}")
+    if e2e:
+        out["e2e"] = dict(e2e, ms_per_step=e2e_ms, value=round(samples / (e2e_ms * 1e-3) / 1e9, 3),
+                          h2d_bytes_per_step=e2e["h2d_bytes_per_step"] * world,
+                          d2h_bytes_per_step=e2e["d2h_bytes_per_step"] * world)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,10 +497,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--symbols", type=int, default=0, help="stream length per pol (default: the workload's 2^24)")
-    ap.add_argument("--oracle-child", nargs=2, type=int, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-child", nargs=3, help=argparse.SUPPRESS)
+    ap.add_argument("--workload", default="stream", choices=["stream", "qam16"],
+                    help="stream: the 2^24-symbol DP-QPSK stream (default line); qam16: DP-16QAM 5,000 km "
+                         "with FP16 and FP32 sample storage against the FP64 oracle")
     args = ap.parse_args()
     if args.oracle_child:
-        oracle_child(*args.oracle_child)
+        name, n_sym, reps = args.oracle_child
+        oracle_child(name, int(n_sym), int(reps))
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -402,21 +522,19 @@ def main():
         dist.barrier()
         args.cpu_baseline = False  # the CPU baseline is taken on one rank at N=1 only
         line = run_ours(args)
-        e2e_ms = line["e2e"]["ms_per_step"] if line.get("e2e") else 0.0
-        t = torch.tensor([line["ms_per_step"], e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+
+        def reduce_max(vals):
+            t = torch.tensor(vals, device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return t.tolist()
+
+        line = combine_replicas(line, world, reduce_max)
         if rank == 0:
-            line["n_gpus"] = world
-            line["ms_per_step"] = float(t[0].item())
-            if line.get("e2e"):
-                line["e2e"]["ms_per_step"] = float(t[1].item())
-                line["e2e"]["value"] = round(world * 4 * line["config"]["symbols_per_pol"] / (t[1].item() * 1e-3) / 1e9, 3)
-                line["e2e"]["h2d_bytes_per_step"] *= world
-                line["e2e"]["d2h_bytes_per_step"] *= world
-            line["value"] = round(world * 4 * line["config"]["symbols_per_pol"] / (line["ms_per_step"] * 1e-3) / 1e9, 3)
-            line["config"]["parallelism"] = f"replicas x{world}"
             print(json.dumps(line), flush=True)
         dist.destroy_process_group()
+        return
+    if args.workload == "qam16":
+        print(json.dumps(run_qam16(args)), flush=True)
         return
     print(json.dumps(run_ours(args)), flush=True)
 
