@@ -237,6 +237,99 @@ int rx_get_phase(rx_handle* h, int64_t first, int64_t n, uint8_t* bhat, int32_t*
 int rx_decide_block_noalloc(const void* y, int64_t n, int modulation, int bps_angles,
                             int bps_half_window, uint8_t* bits, void* cuda_stream);
 
+/* ---- serving: many channel streams on one GPU ---------------------------
+ * The paper runs several CUDA streams so that buffers are processed
+ * concurrently (Sec. II); a server extends this to many independent channel
+ * streams.  It owns one receiver per channel stream, each with its state
+ * (ring, equaliser taps, phase, timing, BER counters) resident on the
+ * device between blocks, and a worker thread that admits submitted capture
+ * blocks in arrival order, round-robin over streams, as soon as the
+ * stream's receiver can take them (its output ring has room), so blocks of
+ * different streams are on the GPU at the same time and their work
+ * overlaps.  Results of a stream do not depend on the other streams.
+ *
+ * Streams are admitted by device memory: rx_server_open creates the
+ * stream's receiver and keeps it only if the device memory it holds fits
+ * in what is left of the server's budget; otherwise it frees it again and
+ * returns RX_EAGAIN (retry after closing a stream).
+ *
+ * Latency of a frame = time from the submission of the block that
+ * completed the frame's input (its look-ahead included) to the frame's
+ * bits being ready, host clock, queueing inside the server included.
+ */
+typedef struct rx_server rx_server;
+
+typedef struct rx_server_config {
+  int64_t mem_budget_bytes; /* device memory for streams; <= 0: free memory at create minus 1 GiB */
+  int max_streams;          /* 1 .. 1024 */
+  int device;               /* CUDA device of every stream (their rx_config.device must match) */
+  int64_t bits_cap_bytes;   /* per-stream host buffer of decided bits not yet pulled (>= 4096);
+                               when full the stream's blocks wait (backpressure) */
+} rx_server_config;
+
+typedef struct rx_server_stats_t {
+  int64_t blocks_submitted, blocks_pushed, blocks_queued;
+  int64_t samples_pushed;    /* samples per polarisation, all streams */
+  int64_t frames_done;
+  double latency_p50_ms, latency_p99_ms, latency_max_ms;
+  int64_t latency_samples;
+  int64_t mem_in_use_bytes, mem_budget_bytes;
+  int streams_open;
+  int worker_error;          /* first error of the worker (RX_* code), 0 if none */
+} rx_server_stats_t;
+
+void rx_server_config_default(rx_server_config* cfg);
+
+/* Starts the worker thread.  RX_EINVAL on a bad config, RX_EDEVICE if the
+ * device does not exist. */
+int rx_server_create(const rx_server_config* cfg, rx_server** out);
+
+/* Opens a channel stream with receiver configuration cfg (as rx_create);
+ * *stream_id receives its id.  RX_EAGAIN when the stream does not fit in
+ * the remaining memory budget or max_streams are open. */
+int rx_server_open(rx_server* s, const rx_config* cfg, int* stream_id);
+
+/* Queues one capture block of stream_id: planar [2][n_per_pol] samples of
+ * dtype (as rx_push_block).  A host block is copied before the call
+ * returns.  A device block (on_device) must hold its data when submitted
+ * (it is read on the server's own CUDA streams, unordered with the
+ * caller's) and stay valid and unchanged until rx_server_sync(s,
+ * stream_id) returns.  Returns the block's sequence number (>= 0) or an
+ * RX_* error (RX_EINVAL: bad stream, null or empty block, bad dtype;
+ * RX_ESTATE: after rx_server_end). */
+int64_t rx_server_submit(rx_server* s, int stream_id, const void* samples, size_t n_per_pol, int dtype,
+                         int on_device);
+
+/* Marks the end of stream_id's input: its remaining frames are processed
+ * after its queued blocks. */
+int rx_server_end(rx_server* s, int stream_id);
+
+/* Waits until every block of stream_id submitted so far has been pushed
+ * and all launched frames are done (and, after rx_server_end, the stream
+ * is flushed).  timeout_ms < 0 waits without limit; RX_ETIMEDOUT when the
+ * limit passes first.  Returns the worker's error if it stopped. */
+int rx_server_sync(rx_server* s, int stream_id, int timeout_ms);
+
+/* Moves up to cap_bytes of stream_id's decided bits (rx_pull_bits order)
+ * out of the server's host buffer; *n_bits receives the count. */
+int rx_server_pull_bits(rx_server* s, int stream_id, uint8_t* out, size_t cap_bytes, size_t* n_bits);
+
+/* Statistics of stream_id's receiver (as rx_stats; waits for its queued
+ * device work). */
+int rx_server_stream_stats(rx_server* s, int stream_id, rx_stats_t* out);
+
+/* The receiver of stream_id, for inspection calls (rx_get_equalised,
+ * rx_frame_trace, ...) after rx_server_sync; NULL for a bad id. */
+rx_handle* rx_server_handle(rx_server* s, int stream_id);
+
+/* Waits for stream_id's queued work, frees its receiver and its budget. */
+int rx_server_close(rx_server* s, int stream_id);
+
+int rx_server_stats(rx_server* s, rx_server_stats_t* out);
+
+/* Stops the worker, closes every stream and frees the server. */
+int rx_server_destroy(rx_server* s);
+
 #ifdef __cplusplus
 }
 #endif

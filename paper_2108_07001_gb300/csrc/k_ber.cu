@@ -423,18 +423,31 @@ __global__ void ingest_kernel(RxDev d, const void* __restrict__ src, int dtype, 
 // c64 input into a c64 ring, two samples (16 bytes) per access: pair j of
 // polarisation p is src4[p n2 + j] -> ring slot j0 + 2j (mod cap).  Needs
 // n, j0 and cap even and a 16-byte aligned source, so a pair never
-// straddles the polarisations or the ring's wrap.
+// straddles the polarisations or the ring's wrap.  Each thread moves four
+// pairs, all four loads issued before the stores.
 __global__ void __launch_bounds__(256) ingest_pairs_kernel(RxDev d, const float4* __restrict__ src, long long n2,
                                                             long long j0) {
   float4* ring4 = reinterpret_cast<float4*>(d.ring);
   const long long cap2 = d.ring_cap / 2;
   const long long s0 = j0 / 2;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n2; i += (long long)gridDim.x * blockDim.x) {
-    const int pol = i >= n2;
-    const long long j = i - pol * n2;
-    long long slot = s0 + j;
-    if (slot >= cap2) slot -= cap2;
-    ring4[pol * cap2 + slot] = __ldcs(&src[i]);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float4 v[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const long long i = i0 + u * stride;
+    if (i < 2 * n2) v[u] = __ldcs(&src[i]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const long long i = i0 + u * stride;
+    if (i < 2 * n2) {
+      const int pol = i >= n2;
+      const long long j = i - pol * n2;
+      long long slot = s0 + j;
+      if (slot >= cap2) slot -= cap2;
+      ring4[pol * cap2 + slot] = v[u];
+    }
   }
 }
 
@@ -476,7 +489,7 @@ cudaError_t launch_ingest(const RxDev& d, const void* src, int dtype, long long 
   if (dtype == 1 && d.storage == 1 && (n & 1) == 0 && (j0 & 1) == 0 && (d.ring_cap & 1) == 0 &&
       (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
     const long long pairs = n;  // 2 pols x n/2 pairs
-    const long long blocks = std::min<long long>((pairs + 255) / 256, 152LL * 8);
+    const long long blocks = (pairs + 1023) / 1024;
     ingest_pairs_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, static_cast<const float4*>(src), n / 2, j0);
     return cudaGetLastError();
   }

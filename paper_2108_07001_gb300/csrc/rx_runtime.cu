@@ -125,6 +125,7 @@ struct rx_handle {
   StreamState st_init{};             // initial device state (host copy for resets)
   double stage_ms[RX_NSTAGES] = {0};
   long long stage_n[RX_NSTAGES] = {0};   // kernel launches per stage
+  size_t dev_bytes = 0;                  // device memory held by the handle
 };
 
 namespace {
@@ -183,10 +184,11 @@ double erfcinv_host(double y) {  // solve erfc(x) = y, 0 < y < 1, Newton from a 
 }
 
 template <typename T>
-int dalloc(T** p, size_t n) {
+int dalloc(T** p, size_t n, size_t* total) {
   if (n == 0) n = 1;
   cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
   if (e != cudaSuccess) return fail(RX_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  *total += n * sizeof(T);
   e = cudaMemset(*p, 0, n * sizeof(T));
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
   return RX_OK;
@@ -488,6 +490,18 @@ int validate(const rx_config* c, std::string& why) {
 namespace rx {
 // Message for rx_last_error() from code outside this file.
 void set_last_error(const char* msg) { g_err = msg; }
+
+// Library-internal accessors for the serving layer (not part of the C ABI).
+size_t handle_dev_bytes(const rx_handle* h) { return h->dev_bytes; }
+
+// Frames launched and completed so far, and launched work not yet complete
+// (frames and end-of-stream passes); completion is polled, nothing waits.
+void handle_progress(rx_handle* h, long long* launched, long long* done, long long* pending) {
+  harvest(h);
+  *launched = h->f_next;
+  *done = h->frames_done;
+  *pending = (long long)h->pend.size();
+}
 }  // namespace rx
 
 extern "C" {
@@ -610,9 +624,10 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   {
     cudaError_t e = cudaMalloc(&d.ring, 2 * d.ring_cap * elt);
     if (e != cudaSuccess) { free_all(h); delete h; return fail(RX_ENOMEM, "ring allocation failed"); }
+    h->dev_bytes += 2 * d.ring_cap * elt;
     cudaMemset(d.ring, 0, 2 * d.ring_cap * elt);
   }
-#define RX_AL(p, n) if ((rc = dalloc(&p, n)) != RX_OK) { free_all(h); delete h; return rc; }
+#define RX_AL(p, n) if ((rc = dalloc(&p, n, &h->dev_bytes)) != RX_OK) { free_all(h); delete h; return rc; }
   RX_AL(d.Hs, N);
   RX_AL(d.Hf, N);
   RX_AL(d.tw, N);
@@ -690,8 +705,10 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   h->st_init.bhat_last[0] = h->st_init.bhat_last[1] = -1;
   cudaMemcpy(d.st, &h->st_init, sizeof(StreamState), cudaMemcpyHostToDevice);
   h->stage_bytes = (size_t)mb * 2 * 16;
-  for (int i = 0; i < kStageSlots; ++i)
+  for (int i = 0; i < kStageSlots; ++i) {
     if (cudaMalloc(&h->stage[i], h->stage_bytes) != cudaSuccess) { free_all(h); delete h; return fail(RX_ENOMEM, "staging allocation failed"); }
+    h->dev_bytes += h->stage_bytes;
+  }
   cudaError_t e = cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking);
   for (int i = 0; i < kStageSlots && e == cudaSuccess; ++i) {
     e = cudaEventCreateWithFlags(&h->ev_stage_in[i], cudaEventDisableTiming);

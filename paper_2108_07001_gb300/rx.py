@@ -25,7 +25,10 @@ STAGES = ["ingest", "cd", "est", "acquire", "mimo", "bps", "demap", "ber"]
 EXPORTS = ["rx_config_default", "rx_create", "rx_push_block", "rx_pull_bits", "rx_stats",
            "rx_destroy", "rx_reset", "rx_join", "rx_stage_times", "rx_last_error",
            "rx_frame_trace", "rx_get_taps", "rx_get_equalised", "rx_get_phase",
-           "rx_decide_block_noalloc"]
+           "rx_decide_block_noalloc",
+           "rx_server_config_default", "rx_server_create", "rx_server_open", "rx_server_submit",
+           "rx_server_end", "rx_server_sync", "rx_server_pull_bits", "rx_server_stream_stats",
+           "rx_server_handle", "rx_server_close", "rx_server_stats", "rx_server_destroy"]
 
 
 class RxConfig(ctypes.Structure):
@@ -90,6 +93,36 @@ class RxStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [
+        ("mem_budget_bytes", ctypes.c_int64),
+        ("max_streams", ctypes.c_int),
+        ("device", ctypes.c_int),
+        ("bits_cap_bytes", ctypes.c_int64),
+    ]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [
+        ("blocks_submitted", ctypes.c_int64),
+        ("blocks_pushed", ctypes.c_int64),
+        ("blocks_queued", ctypes.c_int64),
+        ("samples_pushed", ctypes.c_int64),
+        ("frames_done", ctypes.c_int64),
+        ("latency_p50_ms", ctypes.c_double),
+        ("latency_p99_ms", ctypes.c_double),
+        ("latency_max_ms", ctypes.c_double),
+        ("latency_samples", ctypes.c_int64),
+        ("mem_in_use_bytes", ctypes.c_int64),
+        ("mem_budget_bytes", ctypes.c_int64),
+        ("streams_open", ctypes.c_int),
+        ("worker_error", ctypes.c_int),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -119,9 +152,26 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rx_get_equalised.argtypes = [P, I64, I64, ctypes.POINTER(ctypes.c_float)]
     lib.rx_get_phase.argtypes = [P, I64, I64, ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_int32)]
     lib.rx_decide_block_noalloc.argtypes = [P, I64, I, I, I, P, P]
+    lib.rx_server_config_default.argtypes = [ctypes.POINTER(ServerConfig)]
+    lib.rx_server_config_default.restype = None
+    lib.rx_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]
+    lib.rx_server_open.argtypes = [P, ctypes.POINTER(RxConfig), ctypes.POINTER(I)]
+    lib.rx_server_submit.argtypes = [P, I, P, SZ, I, I]
+    lib.rx_server_submit.restype = I64
+    lib.rx_server_end.argtypes = [P, I]
+    lib.rx_server_sync.argtypes = [P, I, I]
+    lib.rx_server_pull_bits.argtypes = [P, I, P, SZ, ctypes.POINTER(SZ)]
+    lib.rx_server_stream_stats.argtypes = [P, I, ctypes.POINTER(RxStats)]
+    lib.rx_server_handle.argtypes = [P, I]
+    lib.rx_server_handle.restype = P
+    lib.rx_server_close.argtypes = [P, I]
+    lib.rx_server_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
+    lib.rx_server_destroy.argtypes = [P]
     for name in ["rx_create", "rx_push_block", "rx_pull_bits", "rx_stats", "rx_destroy", "rx_reset",
                  "rx_join", "rx_stage_times", "rx_frame_trace", "rx_get_taps", "rx_get_equalised",
-                 "rx_get_phase", "rx_decide_block_noalloc"]:
+                 "rx_get_phase", "rx_decide_block_noalloc", "rx_server_create", "rx_server_open",
+                 "rx_server_end", "rx_server_sync", "rx_server_pull_bits", "rx_server_stream_stats",
+                 "rx_server_close", "rx_server_stats", "rx_server_destroy"]:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -260,6 +310,103 @@ class Receiver:
         if getattr(self, "h", None):
             self.lib.rx_destroy(self.h)
             self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def default_server_config(**overrides) -> ServerConfig:
+    cfg = ServerConfig()
+    load().rx_server_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+class _Borrowed(Receiver):
+    """A receiver owned by a server (inspection calls only; never destroyed here)."""
+
+    def __init__(self, lib, h, cfg):
+        self.lib, self.h, self.cfg = lib, h, cfg
+
+    def close(self) -> None:
+        self.h = None
+
+
+class Server:
+    """Many channel streams on one GPU (rx_server_*): a worker thread admits
+    submitted capture blocks as each stream's receiver can take them."""
+
+    def __init__(self, cfg: ServerConfig | None = None, **overrides):
+        self.lib = load()
+        self.cfg = cfg if cfg is not None else default_server_config(**overrides)
+        s = ctypes.c_void_p()
+        _check(self.lib.rx_server_create(ctypes.byref(self.cfg), ctypes.byref(s)))
+        self.s = s
+        self._cfgs = {}
+
+    def open(self, cfg: RxConfig | None = None, **overrides) -> int:
+        """Opens a stream; raises RxError (code RX_EAGAIN) when it does not fit."""
+        cfg = cfg if cfg is not None else default_config(**overrides)
+        sid = ctypes.c_int()
+        _check(self.lib.rx_server_open(self.s, ctypes.byref(cfg), ctypes.byref(sid)))
+        self._cfgs[sid.value] = cfg
+        return sid.value
+
+    def submit_device(self, sid: int, ptr: int, n_per_pol: int, dtype: int) -> int:
+        return _check(self.lib.rx_server_submit(self.s, sid, ctypes.c_void_p(ptr), n_per_pol, dtype, 1))
+
+    def submit_host(self, sid: int, x: np.ndarray) -> int:
+        x = np.ascontiguousarray(x)
+        dt = RX_C16 if x.dtype == np.float16 else _DT[x.dtype]
+        return _check(self.lib.rx_server_submit(self.s, sid, x.ctypes.data_as(ctypes.c_void_p), x.shape[1], dt, 0))
+
+    def end(self, sid: int) -> None:
+        _check(self.lib.rx_server_end(self.s, sid))
+
+    def sync(self, sid: int, timeout_ms: int = -1) -> None:
+        _check(self.lib.rx_server_sync(self.s, sid, timeout_ms))
+
+    def pull_bytes(self, sid: int, cap_bytes: int = 1 << 26) -> tuple[np.ndarray, int]:
+        out = np.empty(cap_bytes, dtype=np.uint8)
+        nb = ctypes.c_size_t()
+        _check(self.lib.rx_server_pull_bits(self.s, sid, out.ctypes.data_as(ctypes.c_void_p), cap_bytes,
+                                            ctypes.byref(nb)))
+        return out[:(nb.value + 7) // 8].copy(), nb.value
+
+    def stream_stats(self, sid: int) -> dict:
+        st = RxStats()
+        _check(self.lib.rx_server_stream_stats(self.s, sid, ctypes.byref(st)))
+        return st.as_dict()
+
+    def receiver(self, sid: int) -> Receiver:
+        h = self.lib.rx_server_handle(self.s, sid)
+        if not h:
+            raise RxError(RX_EINVAL, "no such stream")
+        return _Borrowed(self.lib, ctypes.c_void_p(h), self._cfgs[sid])
+
+    def close_stream(self, sid: int) -> None:
+        _check(self.lib.rx_server_close(self.s, sid))
+        self._cfgs.pop(sid, None)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(self.lib.rx_server_stats(self.s, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self) -> None:
+        if getattr(self, "s", None):
+            self.lib.rx_server_destroy(self.s)
+            self.s = None
 
     def __enter__(self):
         return self

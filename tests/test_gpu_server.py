@@ -1,0 +1,148 @@
+"""Serving layer on the GPU: streams served together give exactly what each
+gives alone (and what a plain receiver gives), admission by device memory,
+latency statistics."""
+import numpy as np
+import pytest
+
+import rxsim
+from paper_2108_07001_gb300 import rx
+
+pytestmark = pytest.mark.gpu
+
+
+def stream_case(kind, seed):
+    """A short stream of one of three channel types and its receiver config."""
+    F = 1 << 13
+    if kind == "qpsk1000":
+        link = dict(baud_hz=28e9, bits_per_sym=2, n_sym=4 * F + 999, fiber_len_m=1000e3, snr_db=12.0)
+        cfg = dict(baud_hz=28e9, modulation=2, fiber_len_m=1000e3)
+    elif kind == "qpsk2000":
+        link = dict(baud_hz=32e9, bits_per_sym=2, n_sym=3 * F + 77, fiber_len_m=2000e3, snr_db=11.0)
+        cfg = dict(baud_hz=32e9, modulation=2, fiber_len_m=2000e3)
+    else:
+        link = dict(baud_hz=32e9, bits_per_sym=4, n_sym=3 * F + 500, fiber_len_m=500e3, snr_db=18.0)
+        cfg = dict(baud_hz=32e9, modulation=4, fiber_len_m=500e3, mimo_taps=25, bps_angles=32, bps_half_window=32,
+                   mu_dd=2e-3)
+    sim = rxsim.simulate(rxsim.LinkConfig(**link, prbs_seed=seed, seed=seed, out_dtype="c64"))
+    n_sym = link["n_sym"]
+    cfg.update(frame_syms=F, acq_syms=F, cma_syms=4096, prbs_seed=seed, ber_skip_syms=2048, sync_syms=2048,
+               history_syms=n_sym, max_block_samples=1 << 15)
+    x = sim["rx"]
+    rng = np.random.default_rng(seed)
+    cuts, left = [], x.shape[1]
+    while left:
+        m = int(min(left, rng.integers(1000, 1 << 15)))
+        cuts.append(m)
+        left -= m
+    blocks, a = [], 0
+    for m in cuts:
+        blocks.append(np.ascontiguousarray(x[:, a:a + m]))
+        a += m
+    return cfg, blocks, n_sym
+
+
+def serve(cases, interleave=True):
+    """Runs the given streams through one server; returns per-stream
+    (bits, n_bits, y, stats) and the server statistics."""
+    out = {}
+    with rx.Server(max_streams=16) as srv:
+        sids = {k: srv.open(**cfg) for k, (cfg, _, _) in cases.items()}
+        queues = {k: list(blocks) for k, (_, blocks, _) in cases.items()}
+        if interleave:
+            while any(queues.values()):
+                for k in cases:
+                    if queues[k]:
+                        srv.submit_host(sids[k], queues[k].pop(0))
+        else:
+            for k in cases:
+                for b in queues[k]:
+                    srv.submit_host(sids[k], b)
+        for k in cases:
+            srv.end(sids[k])
+        for k in cases:
+            srv.sync(sids[k], timeout_ms=120000)
+        for k, (cfg, _, n_sym) in cases.items():
+            bits, nb = srv.pull_bytes(sids[k])
+            y = srv.receiver(sids[k]).equalised(0, n_sym)
+            out[k] = (bits, nb, y, srv.stream_stats(sids[k]))
+        sst = srv.stats()
+    return out, sst
+
+
+CASES = ("qpsk1000", "qpsk2000", "qam16")
+
+
+@pytest.fixture(scope="module")
+def cases():
+    return {k: stream_case(k, 700 + i) for i, k in enumerate(CASES)}
+
+
+@pytest.fixture(scope="module")
+def mixed(cases):
+    return serve(cases, interleave=True)
+
+
+def test_each_stream_alone_equals_the_mix(cases, mixed):
+    mix, _ = mixed
+    for k in CASES:
+        alone, _ = serve({k: cases[k]})
+        b0, n0, y0, s0 = alone[k]
+        b1, n1, y1, s1 = mix[k]
+        assert n0 == n1 > 0
+        assert np.array_equal(b0, b1), k
+        assert np.array_equal(y0, y1), k
+        for f in ("bits", "bit_errors", "cycle_slips", "synced", "frames"):
+            assert s0[f] == s1[f], (k, f)
+
+
+def test_served_stream_equals_a_plain_receiver(cases, mixed):
+    mix, _ = mixed
+    k = "qpsk1000"
+    cfg, blocks, n_sym = cases[k]
+    r = rx.Receiver(**cfg)
+    for b in blocks:
+        r.push_host(b)
+    r.end()
+    buf = np.empty(1 << 22, dtype=np.uint8)
+    nb = r.pull_bytes(buf, timeout_ms=-1)
+    bits = buf[:(nb + 7) // 8]
+    y = r.equalised(0, n_sym)
+    st = r.stats()
+    r.close()
+    b1, n1, y1, s1 = mix[k]
+    assert nb == n1
+    assert np.array_equal(bits, b1)
+    assert np.array_equal(y, y1)
+    assert st["bit_errors"] == s1["bit_errors"] and st["bits"] == s1["bits"]
+
+
+def test_server_statistics(cases, mixed):
+    mix, sst = mixed
+    n_blocks = sum(len(cases[k][1]) for k in CASES)
+    assert sst["blocks_submitted"] == sst["blocks_pushed"] == n_blocks
+    assert sst["blocks_queued"] == 0 and sst["worker_error"] == 0
+    assert sst["samples_pushed"] == sum(2 * cases[k][2] for k in CASES)
+    assert sst["frames_done"] == sum(mix[k][3]["frames"] for k in CASES)
+    assert sst["latency_samples"] > 0
+    assert 0 < sst["latency_p50_ms"] <= sst["latency_p99_ms"] <= sst["latency_max_ms"]
+    for k in CASES:
+        st = mix[k][3]
+        assert st["synced"] == 1 and st["bits"] > 0 and st["ber"] < 1e-2
+
+
+def test_streams_are_admitted_by_device_memory(cases):
+    cfg = cases["qpsk1000"][0]
+    with rx.Server(max_streams=8) as probe:
+        probe.open(**cfg)
+        one = probe.stats()["mem_in_use_bytes"]
+    assert one > 0
+    with rx.Server(max_streams=8, mem_budget_bytes=2 * one + one // 2) as srv:
+        a = srv.open(**cfg)
+        srv.open(**cfg)
+        with pytest.raises(rx.RxError) as e:
+            srv.open(**cfg)
+        assert e.value.code == rx.RX_EAGAIN
+        assert srv.stats()["streams_open"] == 2
+        srv.close_stream(a)
+        srv.open(**cfg)  # room again
+        assert srv.stats()["mem_in_use_bytes"] == 2 * one
