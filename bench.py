@@ -448,12 +448,12 @@ def run_qam16(args):
         forms[form] = {"value": round(2 * n_samp / (ms * 1e-3) / 1e9, 3), "unit": "Gsamples/s",
                        "ms_per_step": round(ms, 3), "ber": st["ber"], "bit_errors": st["bit_errors"],
                        "bits": st["bits"], "cycle_slips": st["cycle_slips"], "evm": st["evm"],
-                       "evm_db": round(20 * math.log10(st["evm"]), 3) if st["evm"] > 0 else None}
+                       "evm_db": round(10 * math.log10(st["evm"]), 3) if st["evm"] > 0 else None}
         r.close()
     orc = oracle_run(n_sym, 1, wl["name"])
     ob = orc["ber"]
     oracle = {"ber": ob["ber"], "bit_errors": ob["errors"], "bits": ob["bits"], "cycle_slips": ob["slips"],
-              "evm": ob["evm"], "evm_db": round(20 * math.log10(ob["evm"]), 3), "cores": 1,
+              "evm": ob["evm"], "evm_db": round(10 * math.log10(ob["evm"]), 3), "cores": 1,
               "seconds": round(orc["times"][0], 1)}
     for f in forms.values():
         f["evm_penalty_db"] = round(f["evm_db"] - oracle["evm_db"], 4) if f["evm_db"] is not None else None
@@ -488,6 +488,121 @@ def combine_replicas(line, world, reduce_max):
     return out
 
 
+SERVING_STREAMS = 16
+SERVING_SYMS = 1 << 21       # symbols per polarisation per stream
+SERVING_FRAME = 1 << 18
+
+
+def serving_streams(n_streams, n_sym):
+    """16 channel streams: DP-QPSK and DP-16QAM alternating, baud rates
+    28-64 GBd, 10,000 km of D = 17 ps/(nm km), capture blocks of 2^16-2^20
+    symbols.  Seeds: 1004 * 1000 + stream index."""
+    rng = np.random.default_rng(1004)
+    bauds = [28e9, 32e9, 40e9, 48e9, 56e9, 64e9]
+    out = []
+    for i in range(n_streams):
+        qam = i % 2 == 1
+        baud = bauds[int(rng.integers(len(bauds)))]
+        seed = 1004 * 1000 + i
+        link = dict(baud_hz=baud, bits_per_sym=4 if qam else 2, n_sym=n_sym, fiber_len_m=10000e3,
+                    snr_db=18.0 if qam else 11.0, prbs_seed=seed, seed=seed, out_dtype="c64")
+        rxc = dict(baud_hz=baud, modulation=4 if qam else 2, fiber_len_m=10000e3,
+                   mimo_taps=25 if qam else 15, bps_angles=32 if qam else 64, bps_half_window=32 if qam else 16,
+                   frame_syms=SERVING_FRAME, prbs_seed=seed, max_block_samples=2 << 20)
+        if qam:
+            rxc["mu_dd"] = 2e-3
+        sizes, left = [], n_sym
+        while left:
+            m = min(left, 1 << int(rng.integers(16, 21)))
+            sizes.append(m)
+            left -= m
+        out.append((link, rxc, sizes))
+    return out
+
+
+def run_serving(args):
+    """The serving layer under load: 16 mixed channel streams (configs as in
+    serving_streams) on one GPU.  First the capacity (every block submitted
+    at once), then blocks arriving as one Poisson process at 80 % of that
+    capacity (arrival order interleaves the streams, each stream's blocks
+    in order): sustained throughput and p50/p99 frame latency, for FP32 and
+    FP16 sample storage."""
+    import torch
+    import rxsim
+    from paper_2108_07001_gb300 import rx
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    n_sym = args.symbols or SERVING_SYMS
+    streams = serving_streams(SERVING_STREAMS, n_sym)
+    data = []
+    t0 = time.time()
+    for link, rxc, sizes in streams:
+        x = rxsim.simulate(rxsim.LinkConfig(**link))["rx"]
+        blocks, a = [], 0
+        for m in sizes:
+            blocks.append(torch.from_numpy(np.ascontiguousarray(x[:, 2 * a:2 * (a + m)])).to(dev))
+            a += m
+        data.append(blocks)
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    total_samples = 4 * n_sym * len(streams)
+    bits_per_pass = sum(2 * rxc["modulation"] * n_sym for _, rxc, _ in streams)
+    order = [(i, j) for j in range(max(len(b) for b in data)) for i in range(len(streams)) if j < len(data[i])]
+
+    def one_pass(storage, arrivals):
+        with rx.Server(max_streams=64) as srv:
+            sids = [srv.open(**dict(rxc, storage_dtype=storage)) for _, rxc, _ in streams]
+            t_start = time.perf_counter()
+            for k, (i, j) in enumerate(order):
+                if arrivals is not None:
+                    while time.perf_counter() - t_start < arrivals[k]:
+                        pass
+                b = data[i][j]
+                srv.submit_device(sids[i], b.data_ptr(), b.shape[1], rx.RX_C64)
+            for sid in sids:
+                srv.end(sid)
+            for sid in sids:
+                srv.sync(sid, timeout_ms=600000)
+            wall = time.perf_counter() - t_start
+            st = srv.stats()
+            ber = [srv.stream_stats(sid) for sid in sids]
+        return wall, st, ber
+
+    forms = {}
+    for form, storage in (("fp32_storage", rx.RX_C64), ("fp16_storage", rx.RX_C16)):
+        one_pass(storage, None)  # warm-up
+        wall, st, ber = one_pass(storage, None)
+        cap = total_samples / wall / 1e9
+        rate = 0.8 * cap * 1e9  # samples/s offered
+        rng = np.random.default_rng(7)
+        sizes = [4 * streams[i][2][j] for i, j in order]
+        gaps = rng.exponential(np.asarray(sizes, dtype=np.float64) / rate)
+        arrivals = np.cumsum(gaps) - gaps[0]
+        wall_l, st_l, ber_l = one_pass(storage, arrivals)
+        forms[form] = {
+            "capacity_gsamples_s": round(cap, 3),
+            "offered_gsamples_s": round(0.8 * cap, 3),
+            "sustained_gsamples_s": round(total_samples / wall_l / 1e9, 3),
+            "sustained_decoded_gbps": round(bits_per_pass / wall_l / 1e9, 3),
+            "latency_p50_ms": round(st_l["latency_p50_ms"], 3), "latency_p99_ms": round(st_l["latency_p99_ms"], 3),
+            "latency_max_ms": round(st_l["latency_max_ms"], 3), "latency_samples": st_l["latency_samples"],
+            "capacity_latency_p50_ms": round(st["latency_p50_ms"], 3),
+            "capacity_latency_p99_ms": round(st["latency_p99_ms"], 3),
+            "ber_max": max(b["ber"] for b in ber_l), "cycle_slips": int(sum(b["cycle_slips"] for b in ber_l)),
+            "synced_streams": int(sum(b["synced"] for b in ber_l)),
+            "mem_gib": round(st_l["mem_in_use_bytes"] / 2 ** 30, 2) if st_l["mem_in_use_bytes"] else None,
+        }
+    return {"metric": "gsamples_per_s", "value": forms["fp16_storage"]["sustained_gsamples_s"], "unit": "Gsamples/s",
+            "n_gpus": 1, "higher_is_better": True, "workload": "serving", "dtype": "f32 arithmetic",
+            "data": "synthetic (seeded link simulator)",
+            "config": {"streams": len(streams), "symbols_per_pol_per_stream": n_sym,
+                       "baud_gbd": [s[0]["baud_hz"] / 1e9 for s in streams],
+                       "modulation": ["16qam" if s[1]["modulation"] == 4 else "qpsk" for s in streams],
+                       "fiber_km": 10000, "blocks": len(order), "block_syms": "2^16..2^20",
+                       "frame_syms": SERVING_FRAME, "arrivals": "Poisson at 0.8 x capacity"},
+            "forms": forms, "sim_seconds": round(gen_s, 1)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -498,9 +613,10 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--symbols", type=int, default=0, help="stream length per pol (default: the workload's 2^24)")
     ap.add_argument("--oracle-child", nargs=3, help=argparse.SUPPRESS)
-    ap.add_argument("--workload", default="stream", choices=["stream", "qam16"],
+    ap.add_argument("--workload", default="stream", choices=["stream", "qam16", "serving"],
                     help="stream: the 2^24-symbol DP-QPSK stream (default line); qam16: DP-16QAM 5,000 km "
-                         "with FP16 and FP32 sample storage against the FP64 oracle")
+                         "with FP16 and FP32 sample storage against the FP64 oracle; serving: 16 mixed "
+                         "channel streams through the serving layer at 80 %% of its capacity")
     args = ap.parse_args()
     if args.oracle_child:
         name, n_sym, reps = args.oracle_child
@@ -535,6 +651,9 @@ def main():
         return
     if args.workload == "qam16":
         print(json.dumps(run_qam16(args)), flush=True)
+        return
+    if args.workload == "serving":
+        print(json.dumps(run_serving(args)), flush=True)
         return
     print(json.dumps(run_ours(args)), flush=True)
 
