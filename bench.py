@@ -603,6 +603,101 @@ def run_serving(args):
             "forms": forms, "sim_seconds": round(gen_s, 1)}
 
 
+BATCH_STREAMS = 64
+BATCH_SYMS = 1 << 19
+BATCH_FRAME = 1 << 16
+
+
+def batched_streams(n_streams, n_sym):
+    """64 independent DP-QPSK streams: 28-64 GBd, 1,000-10,000 km, SNR
+    9-14 dB, capture blocks of 2^12-2^18 symbols.  Seeds 1003 * 1000 + i."""
+    rng = np.random.default_rng(1003)
+    bauds = [28e9, 32e9, 40e9, 48e9, 56e9, 64e9]
+    out = []
+    for i in range(n_streams):
+        baud = bauds[int(rng.integers(len(bauds)))]
+        L = float(rng.uniform(1000e3, 10000e3))
+        snr = float(rng.uniform(9.0, 14.0))
+        seed = 1003 * 1000 + i
+        link = dict(baud_hz=baud, bits_per_sym=2, n_sym=n_sym, fiber_len_m=L, snr_db=snr, prbs_seed=seed,
+                    seed=seed, out_dtype="c64")
+        rxc = dict(baud_hz=baud, modulation=2, fiber_len_m=L, frame_syms=BATCH_FRAME, prbs_seed=seed,
+                   max_block_samples=1 << 19)
+        sizes, left = [], n_sym
+        while left:
+            m = min(left, 1 << int(rng.integers(12, 19)))
+            sizes.append(m)
+            left -= m
+        out.append((link, rxc, sizes))
+    return out
+
+
+def run_batched(args):
+    """64 independent streams with uneven capture blocks through the serving
+    layer, every block submitted at once: throughput and frame latency with
+    the FFT size of the default rule (N >= 4 halo) and with the size the
+    autotuner picks per stream."""
+    import torch
+    import rxsim
+    from paper_2108_07001_gb300 import rx
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    n_sym = args.symbols or BATCH_SYMS
+    streams = batched_streams(BATCH_STREAMS, n_sym)
+    data = []
+    t0 = time.time()
+    for link, rxc, sizes in streams:
+        x = rxsim.simulate(rxsim.LinkConfig(**link))["rx"]
+        blocks, a = [], 0
+        for m in sizes:
+            blocks.append(torch.from_numpy(np.ascontiguousarray(x[:, 2 * a:2 * (a + m)])).to(dev))
+            a += m
+        data.append(blocks)
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    t0 = time.time()
+    tuned = [rx.autotune_fft(rx.default_config(**rxc), frames=8)[0] for _, rxc, _ in streams]
+    tune_s = time.time() - t0
+    total_samples = 4 * n_sym * len(streams)
+    order = [(i, j) for j in range(max(len(b) for b in data)) for i in range(len(streams)) if j < len(data[i])]
+
+    def one_pass(fft):
+        with rx.Server(max_streams=128) as srv:
+            sids = [srv.open(**dict(rxc, fft_n=fft[i])) for i, (_, rxc, _) in enumerate(streams)]
+            t_start = time.perf_counter()
+            for i, j in order:
+                b = data[i][j]
+                srv.submit_device(sids[i], b.data_ptr(), b.shape[1], rx.RX_C64)
+            for sid in sids:
+                srv.end(sid)
+            for sid in sids:
+                srv.sync(sid, timeout_ms=600000)
+            wall = time.perf_counter() - t_start
+            st = srv.stats()
+            per = [srv.stream_stats(sid) for sid in sids]
+        return wall, st, per
+
+    forms = {}
+    for form, fft in (("default_fft", [0] * len(streams)), ("autotuned_fft", tuned)):
+        one_pass(fft)
+        wall, st, per = one_pass(fft)
+        forms[form] = {"gsamples_s": round(total_samples / wall / 1e9, 3), "wall_ms": round(wall * 1e3, 1),
+                       "latency_p50_ms": round(st["latency_p50_ms"], 3),
+                       "latency_p99_ms": round(st["latency_p99_ms"], 3),
+                       "synced_streams": int(sum(p["synced"] for p in per)),
+                       "ber_max": max(p["ber"] for p in per), "cycle_slips": int(sum(p["cycle_slips"] for p in per)),
+                       "mem_gib": round(st["mem_in_use_bytes"] / 2 ** 30, 2) if st["mem_in_use_bytes"] else None}
+    return {"metric": "gsamples_per_s", "value": forms["autotuned_fft"]["gsamples_s"], "unit": "Gsamples/s",
+            "n_gpus": 1, "higher_is_better": True, "workload": "batched", "dtype": "f32",
+            "data": "synthetic (seeded link simulator)",
+            "config": {"streams": len(streams), "symbols_per_pol_per_stream": n_sym, "blocks": len(order),
+                       "block_syms": "2^12..2^18", "frame_syms": BATCH_FRAME,
+                       "baud_gbd": [s[0]["baud_hz"] / 1e9 for s in streams],
+                       "fiber_km": [round(s[0]["fiber_len_m"] / 1e3) for s in streams],
+                       "autotuned_fft": tuned, "submission": "every block at once"},
+            "forms": forms, "autotune_seconds": round(tune_s, 1), "sim_seconds": round(gen_s, 1)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -613,10 +708,11 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--symbols", type=int, default=0, help="stream length per pol (default: the workload's 2^24)")
     ap.add_argument("--oracle-child", nargs=3, help=argparse.SUPPRESS)
-    ap.add_argument("--workload", default="stream", choices=["stream", "qam16", "serving"],
+    ap.add_argument("--workload", default="stream", choices=["stream", "qam16", "serving", "batched"],
                     help="stream: the 2^24-symbol DP-QPSK stream (default line); qam16: DP-16QAM 5,000 km "
                          "with FP16 and FP32 sample storage against the FP64 oracle; serving: 16 mixed "
-                         "channel streams through the serving layer at 80 %% of its capacity")
+                         "channel streams through the serving layer at 80 %% of its capacity; batched: 64 "
+                         "streams with uneven blocks, FFT sizes from the heuristic and from the autotuner")
     args = ap.parse_args()
     if args.oracle_child:
         name, n_sym, reps = args.oracle_child
@@ -654,6 +750,9 @@ def main():
         return
     if args.workload == "serving":
         print(json.dumps(run_serving(args)), flush=True)
+        return
+    if args.workload == "batched":
+        print(json.dumps(run_batched(args)), flush=True)
         return
     print(json.dumps(run_ours(args)), flush=True)
 

@@ -117,7 +117,8 @@ typedef struct rx_handle rx_handle;
 
 /* Defaults: QPSK at 28 GBd over 1,000 km of D = 17 ps/(nm km) at 1550 nm,
  * RRC 0.1, T = 15, B = 64, W = 16, K = 64, S = 512, F = 65536,
- * CMA 8192 of 12288 acquisition symbols, mu_cma 3e-2, mu_dd 5e-3, timing
+ * CMA 16384 of 20480 acquisition symbols, BER sync from symbol 16384 (the
+ * CMA -> DD switch), mu_cma 3e-2, mu_dd 5e-3, timing
  * gain 0.5, complex64 storage, no BER, 2^17-sample pushes, no history,
  * device 0. */
 void rx_config_default(rx_config* cfg);
@@ -236,6 +237,18 @@ int rx_get_phase(rx_handle* h, int64_t first, int64_t n, uint8_t* bhat, int32_t*
 #define RX_NOALLOC_MAX_SYMS 65536
 int rx_decide_block_noalloc(const void* y, int64_t n, int modulation, int bps_angles,
                             int bps_half_window, uint8_t* bits, void* cuda_stream);
+
+/* ---- autotuner ----------------------------------------------------------
+ * Picks the overlap-save FFT size for cfg on this GPU.  A larger N wastes a
+ * smaller halo fraction h / N but costs more per output sample; the paper
+ * fixes its block geometry for its own GPU (Sec. II).  Every admissible N
+ * (a power of two in [1024, 16384] with N - halo >= 256) runs cfg's whole
+ * chain on a zero stream (BER off): two frames untimed (the first, with the
+ * acquisition, completes), then `frames` frames (1..64) timed; the fastest goes to *fft_n and its
+ * time per 2^20 samples per polarisation to *ms_per_msample (may be NULL).  Creates and frees one
+ * receiver per candidate; errors as rx_create, RX_EINVAL on bad arguments
+ * or when no N is admissible. */
+int rx_autotune_fft(const rx_config* cfg, int frames, int* fft_n, double* ms_per_msample);
 
 /* ---- serving: many channel streams on one GPU ---------------------------
  * The paper runs several CUDA streams so that buffers are processed

@@ -80,13 +80,13 @@ class RxConfig:
     sub_block_syms: int = 64
     seg_syms: int = 512
     frame_syms: int = 1 << 16
-    cma_syms: int = 8192
-    acq_syms: int = 12288
+    cma_syms: int = 16384
+    acq_syms: int = 20480
     mu_cma: float = 3e-2
     mu_dd: float = 5e-3
     timing_gain: float = 0.5
     prbs_seed: int = 0                    # 0: no BER counting
-    ber_skip_syms: int = 4096
+    ber_skip_syms: int = 16384
     sync_syms: int = 4096
     sync_max_delay: int = 32
     slip_window: int = 1024

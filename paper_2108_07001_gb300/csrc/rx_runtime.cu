@@ -77,6 +77,10 @@ struct PendingFrame {
 
 }  // namespace
 
+namespace rx {
+int cd_halo_samples(const rx_config* cfg);
+}  // namespace rx
+
 struct rx_handle {
   rx_config cfg;
   RxDev d;
@@ -488,6 +492,20 @@ int validate(const rx_config* c, std::string& why) {
 }  // namespace
 
 namespace rx {
+// Overlap-save halo M - 1 in samples: ceil(1.1 x CD memory) rounded up to
+// even (or the configured cd_halo); CD memory = |D| L lambda^2 Rs (1 + rho) / c
+// seconds of spread at fs = 2 Rs.
+int cd_halo_samples(const rx_config* cfg) {
+  const double Rs = cfg->baud_hz, fs = 2.0 * Rs;
+  const double rho = std::max(cfg->rrc_rolloff, 0.0);
+  const double Dsm = std::fabs(cfg->D_ps_nm_km) * 1e-6;
+  const double dlam = cfg->lambda_m * cfg->lambda_m * Rs * (1.0 + rho) / kC;
+  const double mem = Dsm * cfg->fiber_len_m * dlam * fs;
+  int halo = cfg->cd_halo > 0 ? cfg->cd_halo : (int)std::ceil(1.1 * mem);
+  halo += halo & 1;
+  return std::max(halo, 2);
+}
+
 // Message for rx_last_error() from code outside this file.
 void set_last_error(const char* msg) { g_err = msg; }
 
@@ -524,14 +542,14 @@ void rx_config_default(rx_config* c) {
   c->sub_block_syms = 64;
   c->seg_syms = 512;
   c->frame_syms = 1 << 16;
-  c->cma_syms = 8192;
-  c->acq_syms = 12288;
+  c->cma_syms = 16384;
+  c->acq_syms = 20480;
   c->mu_cma = 3e-2f;
   c->mu_dd = 5e-3f;
   c->timing_gain = 0.5f;
   c->storage_dtype = RX_C64;
   c->prbs_seed = 0;
-  c->ber_skip_syms = 4096;
+  c->ber_skip_syms = 16384;
   c->sync_syms = 4096;
   c->sync_max_delay = 32;
   c->slip_window = 1024;
@@ -552,13 +570,7 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   std::memset(&d, 0, sizeof(d));
   // geometry (FP64)
   const double Rs = cfg->baud_hz, fs = 2.0 * Rs;
-  const double rho = std::max(cfg->rrc_rolloff, 0.0);
-  const double Dsm = std::fabs(cfg->D_ps_nm_km) * 1e-6;
-  const double dlam = cfg->lambda_m * cfg->lambda_m * Rs * (1.0 + rho) / kC;
-  const double mem = Dsm * cfg->fiber_len_m * dlam * fs;
-  int halo = cfg->cd_halo > 0 ? cfg->cd_halo : (int)std::ceil(1.1 * mem);
-  halo += halo & 1;
-  halo = std::max(halo, 2);
+  const int halo = rx::cd_halo_samples(cfg);
   int N = cfg->fft_n;
   if (N <= 0) {
     N = 1024;

@@ -28,7 +28,8 @@ EXPORTS = ["rx_config_default", "rx_create", "rx_push_block", "rx_pull_bits", "r
            "rx_decide_block_noalloc",
            "rx_server_config_default", "rx_server_create", "rx_server_open", "rx_server_submit",
            "rx_server_end", "rx_server_sync", "rx_server_pull_bits", "rx_server_stream_stats",
-           "rx_server_handle", "rx_server_close", "rx_server_stats", "rx_server_destroy"]
+           "rx_server_handle", "rx_server_close", "rx_server_stats", "rx_server_destroy",
+           "rx_autotune_fft"]
 
 
 class RxConfig(ctypes.Structure):
@@ -167,11 +168,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rx_server_close.argtypes = [P, I]
     lib.rx_server_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
     lib.rx_server_destroy.argtypes = [P]
+    lib.rx_autotune_fft.argtypes = [ctypes.POINTER(RxConfig), I, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double)]
     for name in ["rx_create", "rx_push_block", "rx_pull_bits", "rx_stats", "rx_destroy", "rx_reset",
                  "rx_join", "rx_stage_times", "rx_frame_trace", "rx_get_taps", "rx_get_equalised",
                  "rx_get_phase", "rx_decide_block_noalloc", "rx_server_create", "rx_server_open",
                  "rx_server_end", "rx_server_sync", "rx_server_pull_bits", "rx_server_stream_stats",
-                 "rx_server_close", "rx_server_stats", "rx_server_destroy"]:
+                 "rx_server_close", "rx_server_stats", "rx_server_destroy", "rx_autotune_fft"]:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -419,3 +421,13 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def autotune_fft(cfg: RxConfig | None = None, frames: int = 3, **overrides) -> tuple[int, float]:
+    """The fastest overlap-save FFT size for cfg on this GPU and its time
+    per 2^20 samples per polarisation (rx_autotune_fft)."""
+    cfg = cfg if cfg is not None else default_config(**overrides)
+    n = ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(load().rx_autotune_fft(ctypes.byref(cfg), frames, ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value

@@ -154,3 +154,14 @@ def test_server_config_checks_without_device(lib):
         lib.rx_server_destroy(s)
     assert lib.rx_server_submit(None, 0, None, 0, rx.RX_C64, 1) == rx.RX_EINVAL
     assert lib.rx_server_stats(None, None) == rx.RX_EINVAL
+
+
+def test_autotune_argument_checks_without_device(lib):
+    from paper_2108_07001_gb300 import rx
+    n, ms = ctypes.c_int(), ctypes.c_double()
+    cfg = rx.default_config()
+    assert lib.rx_autotune_fft(None, 3, ctypes.byref(n), None) == rx.RX_EINVAL
+    assert lib.rx_autotune_fft(ctypes.byref(cfg), 0, ctypes.byref(n), None) == rx.RX_EINVAL
+    far = rx.default_config(fiber_len_m=100000e3)  # halo longer than any FFT size
+    assert lib.rx_autotune_fft(ctypes.byref(far), 3, ctypes.byref(n), None) == rx.RX_EINVAL
+    assert b"halo" in lib.rx_last_error()

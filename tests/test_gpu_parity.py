@@ -133,7 +133,7 @@ def test_c128_input_equals_c64_input_rounded():
 def test_noiseless_stream_is_error_free():
     sim = rxsim.simulate(link(n_sym=1 << 16, snr_db=None, fiber_len_m=3000e3, prbs_seed=8, seed=8,
                               out_dtype="c64"))
-    rx_kw = dict(fiber_len_m=3000e3, frame_syms=1 << 14, acq_syms=8192, prbs_seed=8)
+    rx_kw = dict(fiber_len_m=3000e3, frame_syms=1 << 14, acq_syms=8192, prbs_seed=8, ber_skip_syms=4096)
     gpu, r = run_gpu(sim["rx"], rx_kw, pushes=[1 << 15] * 4, history=False)
     st = gpu["stats"]
     # counted: symbols [4096, 2^16 - tail) of both polarisations, 2 bits each
@@ -198,7 +198,7 @@ def test_backpressure_when_bits_are_not_pulled():
 def test_reset_reproduces_the_stream():
     sim = rxsim.simulate(link(n_sym=1 << 14, snr_db=12.0, fiber_len_m=600e3, prbs_seed=4, seed=4,
                               out_dtype="c64"))
-    rx_kw = dict(fiber_len_m=600e3, frame_syms=1 << 14, acq_syms=8192, prbs_seed=4)
+    rx_kw = dict(fiber_len_m=600e3, frame_syms=1 << 14, acq_syms=8192, prbs_seed=4, ber_skip_syms=4096)
     g1, r = run_gpu(sim["rx"], rx_kw)
     r.reset()
     import torch
@@ -222,3 +222,20 @@ def test_host_push_equals_device_push():
     assert np.array_equal(bits, g1["bits"])
     r1.close()
     r2.close()
+
+
+def test_autotuned_fft_size_is_admissible_and_keeps_parity():
+    """The autotuner's FFT size is admissible for the CD length and the chain
+    with it still matches the oracle (the OLS result does not depend on N
+    beyond rounding)."""
+    from paper_2108_07001_gb300 import rx
+    rx_kw = dict(fiber_len_m=3000e3, frame_syms=1 << 14, prbs_seed=41, cma_syms=8192, acq_syms=12288,
+                 ber_skip_syms=4096)
+    n, ms = rx.autotune_fft(rx.default_config(**rx_kw), frames=2)
+    assert n in (1024, 2048, 4096, 8192, 16384) and ms > 0
+    sim = rxsim.simulate(link(n_sym=1 << 15, snr_db=12.0, fiber_len_m=3000e3, prbs_seed=41, seed=41))
+    kw = dict(rx_kw, fft_n=n)
+    gpu, r = run_gpu(sim["rx"], kw)
+    ref = run_oracle(sim["rx"], kw)
+    compare(gpu, ref, kw)
+    r.close()

@@ -321,7 +321,8 @@ def test_awgn_ber_matches_closed_form(bps_, snr_db):
 def test_chain_noiseless_all_impairments_is_error_free():
     sim = rxsim.simulate(rxsim.LinkConfig(n_sym=1 << 15, snr_db=None, fiber_len_m=1000e3,
                                           prbs_seed=5, seed=21))
-    cfg = O.RxConfig(fiber_len_m=1000e3, prbs_seed=5, frame_syms=1 << 14)
+    cfg = O.RxConfig(fiber_len_m=1000e3, prbs_seed=5, frame_syms=1 << 14, cma_syms=8192, acq_syms=12288,
+                     ber_skip_syms=4096)
     b = O.Receiver(cfg).run(sim["rx"])["ber"]
     assert b["errors"] == 0 and b["slips"] == 0 and b["bits"] > 100000
 
@@ -340,7 +341,8 @@ def test_quarter_turn_phase_jumps_are_counted_as_slips():
     n_sym = 1 << 15
     sim = rxsim.simulate(rxsim.LinkConfig(n_sym=n_sym, snr_db=None, fiber_len_m=1e3, prbs_seed=5, seed=23,
                                           phase_jumps=((2 * 20000 + 7, math.pi / 2), (53600, -math.pi / 2))))
-    cfg = O.RxConfig(fiber_len_m=1e3, prbs_seed=5, frame_syms=1 << 14)
+    cfg = O.RxConfig(fiber_len_m=1e3, prbs_seed=5, frame_syms=1 << 14, cma_syms=8192, acq_syms=12288,
+                     ber_skip_syms=4096)
     b = O.Receiver(cfg).run(sim["rx"])["ber"]
     assert b["sync"]["errors"] == 0
     assert b["slips"] == 4
