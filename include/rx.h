@@ -255,7 +255,7 @@ int rx_autotune_fft(const rx_config* cfg, int frames, int* fft_n, double* ms_per
  * concurrently (Sec. II); a server extends this to many independent channel
  * streams.  It owns one receiver per channel stream, each with its state
  * (ring, equaliser taps, phase, timing, BER counters) resident on the
- * device between blocks, and a worker thread that admits submitted capture
+ * device between blocks, and worker threads that admit submitted capture
  * blocks in arrival order, round-robin over streams, as soon as the
  * stream's receiver can take them (its output ring has room), so blocks of
  * different streams are on the GPU at the same time and their work
@@ -278,6 +278,7 @@ typedef struct rx_server_config {
   int device;               /* CUDA device of every stream (their rx_config.device must match) */
   int64_t bits_cap_bytes;   /* per-stream host buffer of decided bits not yet pulled (>= 4096);
                                when full the stream's blocks wait (backpressure) */
+  int workers;              /* worker threads, 1..64; worker k serves the streams with id % workers == k */
 } rx_server_config;
 
 typedef struct rx_server_stats_t {

@@ -78,9 +78,9 @@ struct Stream {
 struct rx_server {
   rx_server_config cfg{};
   std::mutex mu;
-  std::condition_variable cv;       // wakes the worker
+  std::condition_variable cv;       // wakes the workers
   std::condition_variable done_cv;  // wakes sync/close waiters
-  std::thread worker;
+  std::vector<std::thread> workers; // worker k serves the streams with id % workers == k
   bool stop = false;
   std::map<int, Stream*> streams;
   int next_id = 0;
@@ -89,7 +89,6 @@ struct rx_server {
   int64_t submitted = 0, pushed = 0, samples = 0, frames_done = 0;
   int werr = 0;
   std::string werr_msg;
-  std::vector<uint8_t> scratch;  // worker's pull buffer
 };
 
 namespace {
@@ -97,8 +96,9 @@ namespace {
 const size_t kPullChunk = 1 << 20;
 
 // Moves decided bytes of one stream into its host buffer (worker, stream
-// lock held).  Returns RX_OK or the receiver's error.
-int drain_bits(rx_server* s, Stream* st) {
+// lock held; scratch is the worker's own buffer).  Returns RX_OK or the
+// receiver's error.
+int drain_bits(rx_server* s, Stream* st, std::vector<uint8_t>& scratch) {
   for (;;) {
     size_t room;
     {
@@ -107,13 +107,13 @@ int drain_bits(rx_server* s, Stream* st) {
     }
     if (room == 0) return RX_OK;
     const size_t want = std::min(room, kPullChunk);
-    if (s->scratch.size() < want) s->scratch.resize(want);
+    if (scratch.size() < want) scratch.resize(want);
     size_t nb = 0;
-    const int rc = rx_pull_bits(st->h, s->scratch.data(), want, &nb, 0);
+    const int rc = rx_pull_bits(st->h, scratch.data(), want, &nb, 0);
     if (rc != RX_OK) return rc;
     if (nb == 0) return RX_OK;
     std::lock_guard<std::mutex> lk(s->mu);
-    st->bits.insert(st->bits.end(), s->scratch.begin(), s->scratch.begin() + (nb + 7) / 8);
+    st->bits.insert(st->bits.end(), scratch.begin(), scratch.begin() + (nb + 7) / 8);
     if (nb % 8) st->bits_tail = nb % 8;
     if (nb < want * 8) return RX_OK;
   }
@@ -144,21 +144,22 @@ void set_worker_error(rx_server* s, int rc) {
   }
 }
 
-// One pass of the worker over the streams; true if anything was pushed.
-bool worker_pass(rx_server* s) {
+// One pass of worker k over its streams; true if anything was pushed.
+bool worker_pass(rx_server* s, int k, std::vector<uint8_t>& scratch) {
   bool progressed = false;
   std::vector<Stream*> order;
+  const int nw = (int)s->workers.size();
   {
     std::lock_guard<std::mutex> lk(s->mu);
     for (auto& kv : s->streams)
-      if (!kv.second->closing) {
+      if (!kv.second->closing && kv.first % nw == k) {
         kv.second->busy = true;
         order.push_back(kv.second);
       }
   }
   for (Stream* st : order) {
     std::lock_guard<std::mutex> hl(st->hm);
-    int rc = drain_bits(s, st);
+    int rc = drain_bits(s, st, scratch);
     // push queued blocks while the receiver takes them
     while (rc == RX_OK) {
       Block* b = nullptr;
@@ -172,7 +173,7 @@ bool worker_pass(rx_server* s) {
       const int prc = b->end ? rx_push_block(st->h, nullptr, 0, RX_C64, 1, st->cs)
                              : rx_push_block(st->h, b->p, b->n, b->dtype, b->on_device, st->cs);
       if (prc == RX_EAGAIN) {  // output ring full: make room, try again next pass
-        rc = drain_bits(s, st);
+        rc = drain_bits(s, st, scratch);
         break;
       }
       if (prc != RX_OK) {
@@ -195,7 +196,7 @@ bool worker_pass(rx_server* s) {
     }
     if (rc == RX_OK) {
       poll_frames(s, st);
-      rc = drain_bits(s, st);
+      rc = drain_bits(s, st, scratch);
     }
     if (rc != RX_OK) set_worker_error(s, rc);
   }
@@ -207,8 +208,10 @@ bool worker_pass(rx_server* s) {
   return progressed;
 }
 
-void worker_main(rx_server* s) {
+void worker_main(rx_server* s, int k) {
   cudaSetDevice(s->cfg.device);
+  std::vector<uint8_t> scratch;
+  const int nw = (int)s->workers.size();
   for (;;) {
     bool work;
     {
@@ -216,11 +219,11 @@ void worker_main(rx_server* s) {
       if (s->stop) return;
       work = false;
       for (auto& kv : s->streams)
-        if (!kv.second->q.empty() || kv.second->pending > 0) work = true;
+        if (kv.first % nw == k && (!kv.second->q.empty() || kv.second->pending > 0)) work = true;
       if (!work) s->cv.wait_for(lk, std::chrono::microseconds(200));
       if (s->stop) return;
     }
-    if (!worker_pass(s)) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    if (!worker_pass(s, k, scratch)) std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
 }
 
@@ -246,6 +249,7 @@ void rx_server_config_default(rx_server_config* c) {
   c->max_streams = 64;
   c->device = 0;
   c->bits_cap_bytes = 64LL << 20;
+  c->workers = 4;
 }
 
 int rx_server_create(const rx_server_config* cfg, rx_server** out) {
@@ -253,6 +257,7 @@ int rx_server_create(const rx_server_config* cfg, rx_server** out) {
   *out = nullptr;
   if (cfg->max_streams < 1 || cfg->max_streams > 1024) return err(RX_EINVAL, "max_streams must be in 1..1024");
   if (cfg->bits_cap_bytes < 4096) return err(RX_EINVAL, "bits_cap_bytes must be >= 4096");
+  if (cfg->workers < 1 || cfg->workers > 64) return err(RX_EINVAL, "workers must be in 1..64");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
     cudaGetLastError();
@@ -269,7 +274,8 @@ int rx_server_create(const rx_server_config* cfg, rx_server** out) {
     }
     s->cfg.mem_budget_bytes = std::max<int64_t>((int64_t)fr - (1LL << 30), 0);
   }
-  s->worker = std::thread(worker_main, s);
+  s->workers.resize(s->cfg.workers);
+  for (int k = 0; k < s->cfg.workers; ++k) s->workers[k] = std::thread(worker_main, s, k);
   *out = s;
   return RX_OK;
 }
@@ -334,7 +340,7 @@ int64_t rx_server_submit(rx_server* s, int stream_id, const void* samples, size_
     s->submitted++;
     st->q.push_back(std::move(b));
   }
-  s->cv.notify_one();
+  s->cv.notify_all();
   return seq;
 }
 
@@ -351,7 +357,7 @@ int rx_server_end(rx_server* s, int stream_id) {
     b.t_submit = now_ms();
     st->q.push_back(std::move(b));
   }
-  s->cv.notify_one();
+  s->cv.notify_all();
   return RX_OK;
 }
 
@@ -368,7 +374,7 @@ int rx_server_sync(rx_server* s, int stream_id, int timeout_ms) {
     }
     if (st->q.empty() && st->pending == 0 && !st->busy) break;
     if (timeout_ms >= 0 && Clock::now() >= t_end) return err(RX_ETIMEDOUT, "sync timed out");
-    s->cv.notify_one();
+    s->cv.notify_all();
     s->done_cv.wait_for(lk, std::chrono::microseconds(200));
   }
   return RX_OK;
@@ -386,7 +392,7 @@ int rx_server_pull_bits(rx_server* s, int stream_id, uint8_t* out, size_t cap_by
   if (nb == st->bits.size()) st->bits_tail = 0;
   st->bits.erase(st->bits.begin(), st->bits.begin() + nb);
   *n_bits = bits;
-  s->cv.notify_one();
+  s->cv.notify_all();
   return RX_OK;
 }
 
@@ -460,7 +466,8 @@ int rx_server_destroy(rx_server* s) {
     s->stop = true;
   }
   s->cv.notify_all();
-  if (s->worker.joinable()) s->worker.join();
+  for (auto& w : s->workers)
+    if (w.joinable()) w.join();
   int rc = RX_OK;
   for (auto& kv : s->streams) {
     const int r = rx_destroy(kv.second->h);

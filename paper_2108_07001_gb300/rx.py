@@ -100,6 +100,7 @@ class ServerConfig(ctypes.Structure):
         ("max_streams", ctypes.c_int),
         ("device", ctypes.c_int),
         ("bits_cap_bytes", ctypes.c_int64),
+        ("workers", ctypes.c_int),
     ]
 
 

@@ -128,24 +128,26 @@ def test_server_struct_layout_matches_c(tmp_path, lib):
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "rx.h"\n'
         "int main(void){printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(rx_server_config), sizeof(rx_server_stats_t),"
-        " offsetof(rx_server_config, bits_cap_bytes), offsetof(rx_server_stats_t, latency_p99_ms),"
+        " offsetof(rx_server_config, workers), offsetof(rx_server_stats_t, latency_p99_ms),"
         " offsetof(rx_server_stats_t, worker_error)); return 0;}\n")
     exe = tmp_path / "slayout"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
-    assert vals == [ctypes.sizeof(rx.ServerConfig), ctypes.sizeof(rx.ServerStats), rx.ServerConfig.bits_cap_bytes.offset,
+    assert vals == [ctypes.sizeof(rx.ServerConfig), ctypes.sizeof(rx.ServerStats), rx.ServerConfig.workers.offset,
                     rx.ServerStats.latency_p99_ms.offset, rx.ServerStats.worker_error.offset]
 
 
 def test_server_config_checks_without_device(lib):
     from paper_2108_07001_gb300 import rx
     c = rx.default_server_config()
-    assert c.max_streams == 64 and c.bits_cap_bytes == 64 << 20 and c.mem_budget_bytes == 0
+    assert c.max_streams == 64 and c.bits_cap_bytes == 64 << 20 and c.mem_budget_bytes == 0 and c.workers == 4
     s = ctypes.c_void_p()
     bad = rx.default_server_config(max_streams=0)
     assert lib.rx_server_create(ctypes.byref(bad), ctypes.byref(s)) == rx.RX_EINVAL
     assert b"max_streams" in lib.rx_last_error()
     bad = rx.default_server_config(bits_cap_bytes=100)
+    assert lib.rx_server_create(ctypes.byref(bad), ctypes.byref(s)) == rx.RX_EINVAL
+    bad = rx.default_server_config(workers=0)
     assert lib.rx_server_create(ctypes.byref(bad), ctypes.byref(s)) == rx.RX_EINVAL
     # no GPU in this container: a valid config stops at the device check
     rc = lib.rx_server_create(ctypes.byref(rx.default_server_config()), ctypes.byref(s))
