@@ -28,6 +28,12 @@ import time
 
 import numpy as np
 
+# Hardware work queues for concurrent streams (read when the CUDA context is
+# created): each receiver runs four CUDA streams, and many receivers share
+# the GPU in the serving workloads; with the default 8 queues their kernels
+# serialise.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 

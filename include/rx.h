@@ -269,6 +269,11 @@ int rx_autotune_fft(const rx_config* cfg, int frames, int* fft_n, double* ms_per
  * Latency of a frame = time from the submission of the block that
  * completed the frame's input (its look-ahead included) to the frame's
  * bits being ready, host clock, queueing inside the server included.
+ *
+ * Each receiver runs four CUDA streams; set CUDA_DEVICE_MAX_CONNECTIONS=32
+ * in the environment before the process creates its CUDA context, or the
+ * default 8 hardware queues serialise the streams' kernels (64 streams:
+ * 4.0 vs 11.4 Gsamples/s on a GB300).
  */
 typedef struct rx_server rx_server;
 

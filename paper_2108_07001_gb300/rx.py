@@ -19,6 +19,12 @@ LIB_PATH = os.path.join(HERE, "librx.so")
 RX_OK, RX_EINVAL, RX_ENOMEM, RX_EAGAIN, RX_ETIMEDOUT, RX_EDEVICE, RX_ESTATE = 0, -1, -2, -3, -4, -5, -6
 RX_QPSK, RX_QAM16 = 2, 4
 RX_C128, RX_C64, RX_C16 = 0, 1, 2
+
+# Each receiver drives four CUDA streams and a server many receivers; with
+# the default 8 hardware work queues their kernels serialise.  The count is
+# read when the process creates its CUDA context, so this only takes effect
+# if the binding is imported before CUDA is initialised.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 STAGES = ["ingest", "cd", "est", "acquire", "mimo", "bps", "demap", "ber"]
 
 # every function declared in include/rx.h
