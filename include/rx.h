@@ -131,18 +131,22 @@ int rx_create(const rx_config* cfg, rx_handle** out);
 
 /* Appends n_per_pol samples of both polarisations.  Layout: planar
  * [pol][n_per_pol], each sample re/im interleaved, element type dtype
- * (RX_C128 / RX_C64 / RX_C16).  samples is a device pointer if on_device,
- * else a host pointer.  The call is asynchronous: the copy into the
+ * (RX_C128 / RX_C64 / RX_C16).  on_device: 1 = samples is a device
+ * pointer; 0 = a host pointer, copied before the call returns; 2 = a
+ * pointer to page-locked host memory, copied to the device by a copy
+ * engine in stream order without a host wait: the caller keeps the buffer
+ * unchanged until the work on cuda_stream has passed it (RX_EINVAL if the
+ * memory is not page-locked).  The call is asynchronous: the copy into the
  * library's ring is a kernel launched on cuda_stream (a cudaStream_t, NULL =
  * legacy default stream), so it follows the work already queued there and
  * later work on cuda_stream follows it; the caller may reuse a device
- * buffer in stream order.  A host buffer is copied before the call returns.
+ * buffer in stream order.
  * When the ring is full, cuda_stream is made to wait for the frames that
  * still read the overwritten slots.
  * Complete frames are processed on the library's own stream.
  * samples == NULL with n_per_pol == 0 marks the end of the stream: the
  * remaining samples are processed with zeros beyond the end.
- * Returns RX_EINVAL (size > max_block_samples, bad dtype), RX_ESTATE (after
+ * Returns RX_EINVAL (size > max_block_samples, bad dtype or on_device), RX_ESTATE (after
  * end of stream), RX_EAGAIN (decided bits not pulled and the output ring
  * is full) or RX_EDEVICE. */
 int rx_push_block(rx_handle* h, const void* samples, size_t n_per_pol, int dtype,

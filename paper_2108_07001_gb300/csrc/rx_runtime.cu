@@ -59,7 +59,7 @@ int cuda_fail(cudaError_t e, const char* where) {
 
 constexpr double kC = 299792458.0;
 constexpr int kZSlots = 6;      // frames in flight between the front and back streams
-constexpr int kStageSlots = 3;  // device staging buffers of host pushes
+constexpr int kStageSlots = 8;  // device staging buffers of host pushes
 
 struct StageEv {
   int stage;
@@ -203,9 +203,10 @@ void free_all(rx_handle* h) {
   void* ptrs[] = {d.ring, d.Hs, d.Hf, d.tw, d.tw2, d.z, d.rot_hi, d.rot_lo, d.acc, d.psd, d.es, d.rec, d.st, d.w_acq,
                   d.chains, d.y, d.bl, d.run_int, d.run_m0, d.run_edge, d.bps_done, d.ber_done, d.dec, d.out, d.prbs_jump, d.ref,
                   d.sync_err, d.win_err, d.hist_y, d.hist_bhat, d.hist_m,
-                  h->stage[0], h->stage[1], h->stage[2]};
-  static_assert(kStageSlots == 3, "staging slots listed above");
+                  nullptr};
   for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (void* p : h->stage)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->cd_done)
     if (e) cudaEventDestroy(e);
@@ -783,7 +784,22 @@ int rx_push_block(rx_handle* h, const void* samples, size_t n_per_pol, int dtype
   if (samples == nullptr) return fail(RX_EINVAL, "samples is NULL");
   if (dtype < RX_C128 || dtype > RX_C16) return fail(RX_EINVAL, "bad dtype");
   if (n_per_pol > h->cfg.max_block_samples) return fail(RX_EINVAL, "n_per_pol exceeds max_block_samples");
+  if (on_device < 0 || on_device > 2) return fail(RX_EINVAL, "on_device must be 0, 1 or 2");
   if (n_per_pol == 0) return RX_OK;
+  bool async_host = false;
+  if (on_device == 2) {
+    // page-locked host memory: copied by a copy engine into a staging slot
+    // in stream order, without a host wait (the caller keeps the buffer
+    // until the stream has passed it)
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, samples) != cudaSuccess || pa.type != cudaMemoryTypeHost ||
+        pa.devicePointer == nullptr) {
+      cudaGetLastError();
+      return fail(RX_EINVAL, "on_device = 2 needs page-locked host memory mapped for the device");
+    }
+    async_host = true;
+    on_device = 0;
+  }
   const long long n = (long long)n_per_pol;
   // output ring room for the frames this push completes
   {
@@ -844,7 +860,7 @@ int rx_push_block(rx_handle* h, const void* samples, size_t n_per_pol, int dtype
   h->copy_dirty = true;
   if (!on_device) {  // the host buffer is reusable on return
     RX_CK(cudaEventRecord(h->ev_stage_free[sl], cs));
-    RX_CK(cudaEventSynchronize(h->ev_stage_in[sl]));
+    if (!async_host) RX_CK(cudaEventSynchronize(h->ev_stage_in[sl]));
   }
   h->pushed += n;
   while (h->pushed >= 2 * (h->f_next + 1) * F + h->la) {

@@ -239,3 +239,42 @@ def test_autotuned_fft_size_is_admissible_and_keeps_parity():
     ref = run_oracle(sim["rx"], kw)
     compare(gpu, ref, kw)
     r.close()
+
+
+def test_pinned_host_push_equals_device_push():
+    """Page-locked host blocks read by the device in stream order (on_device
+    = 2) give exactly the device-push result; unpinned memory is refused."""
+    import torch
+    from paper_2108_07001_gb300 import rx
+    sim = rxsim.simulate(link(n_sym=1 << 15, snr_db=12.0, fiber_len_m=600e3, seed=88, out_dtype="c64"))
+    rx_kw = dict(fiber_len_m=600e3, frame_syms=1 << 14, acq_syms=8192, history_syms=1 << 15, max_block_samples=1 << 14)
+    x = np.ascontiguousarray(sim["rx"])
+    blocks = [np.ascontiguousarray(x[:, a:a + (1 << 14)]) for a in range(0, x.shape[1], 1 << 14)]
+    out = []
+    for mode in ("device", "pinned"):
+        r = rx.Receiver(**rx_kw)
+        stream = torch.cuda.current_stream().cuda_stream
+        keep = []
+        for b in blocks:
+            if mode == "device":
+                t = torch.from_numpy(b).to("cuda:0")
+                keep.append(t)
+                r.push_device(t.data_ptr(), b.shape[1], rx.RX_C64, stream)
+            else:
+                t = torch.from_numpy(b).pin_memory()
+                keep.append(t)
+                r.push_pinned(t.data_ptr(), b.shape[1], rx.RX_C64, stream)
+        r.end()
+        buf = np.empty(1 << 20, dtype=np.uint8)
+        nb = r.pull_bytes(buf, timeout_ms=-1)
+        out.append((buf[:(nb + 7) // 8].copy(), r.equalised(0, 1 << 15)))
+        if mode == "pinned":
+            with pytest.raises(rx.RxError):
+                r2 = rx.Receiver(**rx_kw)
+                try:
+                    r2.push_pinned(blocks[0].ctypes.data, blocks[0].shape[1], rx.RX_C64, stream)
+                finally:
+                    r2.close()
+        r.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
