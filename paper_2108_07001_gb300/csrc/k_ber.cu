@@ -37,20 +37,44 @@ __device__ uint32_t prbs_window_at(const uint32_t* jump, uint32_t s, long long P
 
 // Bits [B0, B0 + nbits) of each polarisation's PRBS into d.ref (LSB first).
 // B0 = (sym0 - delay) * bps, delay read from the device state if use_delay.
-// The jump matrices are staged in shared memory.
+// The jump matrices are staged in shared memory.  Warp 0 jumps the state to
+// the block's first chunk (lane j holds column j of each matrix; a product
+// is an XOR reduction over the lanes), then every thread jumps the few
+// chunks from there to its own (at most log2(blockDim) products).  A chunk
+// is kRefChunk bits.
+constexpr int kRefChunk = 256;
+
 __global__ void __launch_bounds__(128) ref_gen_kernel(RxDev d, long long sym0, int nbits, int use_delay) {
   __shared__ uint32_t jump_s[48 * 31];
+  __shared__ uint32_t base_s;
   for (int i = threadIdx.x; i < 48 * 31; i += blockDim.x) jump_s[i] = d.prbs_jump[i];
   __syncthreads();
   const int pol = blockIdx.y;
-  const int chunk = blockIdx.x * blockDim.x + threadIdx.x;
-  const int start = chunk * 1024;
-  if (start >= nbits) return;
+  const int chunk0 = blockIdx.x * blockDim.x;
+  if ((long long)chunk0 * kRefChunk >= nbits) return;  // whole block past the end (uniform)
   const long long delay = use_delay ? d.st->sync_delay : 0;
   const long long B0 = (sym0 - delay) * d.bps;
-  uint32_t s = prbs_window_at(jump_s, d.prbs_state0[pol], B0 + start);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    uint32_t st = d.prbs_state0[pol];
+    long long P = B0 + (long long)chunk0 * kRefChunk;
+    for (int i = 0; P > 0; ++i, P >>= 1) {
+      if (P & 1) {
+        uint32_t v = (lane < 31 && ((st >> lane) & 1u)) ? jump_s[i * 31 + lane] : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v ^= __shfl_xor_sync(0xffffffffu, v, o);
+        st = v;
+      }
+    }
+    if (lane == 0) base_s = st;
+  }
+  __syncthreads();
+  const int chunk = chunk0 + threadIdx.x;
+  const int start = chunk * kRefChunk;
+  if (start >= nbits) return;
+  uint32_t s = prbs_window_at(jump_s, base_s, (long long)threadIdx.x * kRefChunk);
   uint32_t* out = d.ref + (long long)pol * d.ref_words + start / 32;
-  const int nw = min(32, (nbits - start + 31) / 32);
+  const int nw = min(kRefChunk / 32, (nbits - start + 31) / 32);
   unsigned long long acc = 0;
   int nacc = 0, wc = 0;
   while (wc < nw) {
@@ -170,105 +194,79 @@ __global__ void __launch_bounds__(256) sync_kernel(RxDev d) {
 }
 
 // Errors of symbols [ka, kb) under the four quadrants, per slip window.
-// Blocks of 256 symbols are aligned to ks, so each lies inside one window
-// (slip_window is a multiple of 256 or 256 a multiple of it is not needed:
-// windows are multiples of 32 and warps reduce separately when a block
-// straddles windows).  The reference holds tx symbols [ka - delay, kb - delay).
-// The last block to finish runs the slip pass over windows [w_from, w_to).
+// The symbols are cut into pieces of at most kBerPiece symbols that never
+// cross a window; one warp counts one piece (lane l takes symbols k0 + l of
+// each 32-symbol step, so decision bytes load coalesced and the reference
+// words are shared by the lanes), reduces its counters with shuffles and
+// adds them to its window's slot.  The reference holds tx symbols
+// [ka - delay, kb - delay).  The last block to finish runs the slip pass
+// over windows [w_from, w_to).
 __device__ void slip_pass(const RxDev& d, long long w_from, long long w_to, long long k_lim, int n_win_ring,
                           unsigned* win_s);
 
-constexpr int kBerSyms = 4;  // symbols per thread
+constexpr int kBerPiece = 256;  // symbols per warp work item
+
+__host__ __device__ inline long long ber_items(long long ka, long long kb, long long ks, long long sw) {
+  const long long k_lo = ka > ks ? ka : ks;
+  if (kb <= k_lo) return 0;
+  const long long wa = (k_lo - ks) / sw, wb = (kb - 1 - ks) / sw;
+  return (wb - wa + 1) * ((sw + kBerPiece - 1) / kBerPiece);
+}
 
 __global__ void __launch_bounds__(256) ber_count_kernel(RxDev d, long long ka, long long kb, long long w_from,
                                                         long long w_to, long long k_lim, int n_win_ring) {
   __shared__ uint8_t lut[4][16];  // bits of level code (lI | lQ << 2) rotated by q
-  __shared__ unsigned red[8][9];
   __shared__ int am_last;
   if (threadIdx.x < 64) {
     const int q = threadIdx.x >> 4, lv = threadIdx.x & 15;
     lut[q][lv] = (uint8_t)rx_sym_bits(lv & 3, lv >> 2, q, d.nl);
   }
   __syncthreads();
-  const long long ks = d.ber_skip;
-  const long long kal = ks + ((ka - ks) / (32 * kBerSyms)) * (32 * kBerSyms);
-  // thread t of block b handles symbols k0 + 32 j + lane (j < kBerSyms) of its warp's span
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const long long kw = kal + ((long long)blockIdx.x * 8 + w) * 32 * kBerSyms;  // warp span start
-  const int perm = d.st->sync_perm;
-  unsigned err[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-  const long long r0 = (kw + l) % d.dec_cap;  // decision ring slot of the lane's first symbol
+  const long long ks = d.ber_skip, sw = d.slip_win;
+  const long long ppw = (sw + kBerPiece - 1) / kBerPiece;  // pieces per window
+  const long long k_lo = ka > ks ? ka : ks;
+  const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const long long item = (long long)blockIdx.x * 8 + warp;
+  bool wrote = false;
+  if (item < ber_items(ka, kb, ks, sw)) {  // warp-uniform
+    const long long w = (k_lo - ks) / sw + item / ppw;
+    const long long pc = item % ppw;
+    const long long p0 = max(k_lo, ks + w * sw + pc * kBerPiece);
+    const long long p1 = min(kb, min(ks + (w + 1) * sw, ks + w * sw + (pc + 1) * kBerPiece));
+    const int perm = d.st->sync_perm;
+    unsigned err[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    long long slot = (p0 + l) % d.dec_cap;
+#pragma unroll 2
+    for (long long k0 = p0; k0 < p1; k0 += 32) {
+      const long long k = k0 + l;
+      if (k < p1) {
+        const uint8_t v = d.dec[slot];
 #pragma unroll
-  for (int j = 0; j < kBerSyms; ++j) {
-    const long long k = kw + 32 * j + l;
-    if (k >= ka && k < kb) {
-      long long slot = r0 + 32 * j;
-      if (slot >= d.dec_cap) slot -= d.dec_cap;
-      const uint8_t v = d.dec[slot];
-#pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        const uint32_t rb = ref_bits(d.ref + (long long)(p ^ perm) * d.ref_words, (k - ka) * d.bps, d.bps);
-        const int lv = (v >> (4 * p)) & 15;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) err[p][q] += __popc((uint32_t)lut[q][lv] ^ rb);
-      }
-    }
-  }
-  // a warp span (32 kBerSyms symbols, aligned to ks) lies in one window
-  // unless slip_win is not a multiple of the span; then per-symbol atomics
-  const bool one_window = ((kw - ks) / d.slip_win) == ((kw + 32 * kBerSyms - 1 - ks) / d.slip_win);
-  if (one_window) {
-#pragma unroll
-    for (int p = 0; p < 2; ++p)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        unsigned s = err[p][q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (l == 0) red[w][p * 4 + q] = s;
-      }
-    if (l == 0) red[w][8] = (unsigned)((kw - ks) / d.slip_win);
-  } else {
-    // rare (small windows): per-symbol atomics
-    if (l == 0) red[w][8] = 0xffffffffu;
-#pragma unroll
-    for (int j = 0; j < kBerSyms; ++j) {
-      const long long k = kw + 32 * j + l;
-      if (k >= ka && k < kb) {
-        const long long win = (k - ks) / d.slip_win;
-        const uint8_t v = d.dec[k % d.dec_cap];
         for (int p = 0; p < 2; ++p) {
           const uint32_t rb = ref_bits(d.ref + (long long)(p ^ perm) * d.ref_words, (k - ka) * d.bps, d.bps);
           const int lv = (v >> (4 * p)) & 15;
-          for (int q = 0; q < 4; ++q) {
-            const unsigned e = __popc((uint32_t)lut[q][lv] ^ rb);
-            if (e) atomicAdd(&d.win_err[(win % n_win_ring) * 8 + p * 4 + q], e);
-          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) err[p][q] += __popc((uint32_t)lut[q][lv] ^ rb);
         }
       }
+      slot += 32;
+      if (slot >= d.dec_cap) slot -= d.dec_cap;
     }
-  }
-  __syncthreads();
-  if (threadIdx.x < 8) {
-    const int j = threadIdx.x;
-    unsigned acc = 0;
-    unsigned cur = 0xffffffffu;
-    for (int ww = 0; ww < 8; ++ww) {
-      const unsigned wnd = red[ww][8];
-      if (wnd == 0xffffffffu) continue;
-      if (wnd != cur) {
-        if (acc) atomicAdd(&d.win_err[(cur % n_win_ring) * 8 + j], acc);
-        acc = 0;
-        cur = wnd;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      unsigned e = err[j >> 2][j & 3];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+      if (l == 0 && e) {
+        atomicAdd(&d.win_err[(w % n_win_ring) * 8 + j], e);
+        wrote = true;
       }
-      acc += red[ww][j];
     }
-    if (acc) atomicAdd(&d.win_err[(cur % n_win_ring) * 8 + j], acc);
   }
   if (w_to <= w_from) return;
   // threads that added to the window counters make them visible before the
   // block takes its ticket
-  if (threadIdx.x < 8 || !one_window) __threadfence();
+  if (wrote) __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) am_last = atomicAdd(&d.ber_done[1], 1u) == gridDim.x - 1;
   __syncthreads();
@@ -320,11 +318,22 @@ __device__ void slip_pass(const RxDev& d, long long w_from, long long w_to, long
   for (long long c0 = w_from; c0 < w_to; c0 += kSlipChunk) {
     const int nw = (int)min((long long)kSlipChunk, w_to - c0);
     const int r0 = (int)(c0 % n_win_ring);  // ring slot of the chunk's first window (nw <= ring size)
-    // stage the chunk's counters (all loads first), then clear their slots
-    for (int i = threadIdx.x; i < nw * 8; i += blockDim.x) {
-      int slot = r0 + (i >> 3);
-      if (slot >= n_win_ring) slot -= n_win_ring;
-      win_s[i] = __ldcg(d.win_err + (long long)slot * 8 + (i & 7));
+    // stage the chunk's counters (eight loads in flight per thread), then
+    // clear their slots
+    for (int i0 = threadIdx.x; i0 < nw * 8; i0 += 8 * blockDim.x) {
+      unsigned v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u * blockDim.x;
+        int slot = r0 + (i >> 3);
+        if (slot >= n_win_ring) slot -= n_win_ring;
+        v[u] = i < nw * 8 ? __ldcg(d.win_err + (long long)slot * 8 + (i & 7)) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i < nw * 8) win_s[i] = v[u];
+      }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nw * 8; i += blockDim.x) {
@@ -454,7 +463,7 @@ __global__ void __launch_bounds__(256) ingest_pairs_kernel(RxDev d, const float4
 // ---- launchers ------------------------------------------------------------
 
 cudaError_t launch_ref_gen(const RxDev& d, long long sym0, int nbits, int use_delay, cudaStream_t s) {
-  const int chunks = (nbits + 1023) / 1024;
+  const int chunks = (nbits + kRefChunk - 1) / kRefChunk;
   dim3 grid((chunks + 127) / 128, 2);
   ref_gen_kernel<<<grid, 128, 0, s>>>(d, sym0, nbits, use_delay);
   return cudaGetLastError();
@@ -473,12 +482,10 @@ cudaError_t ber_set_attributes() {
 cudaError_t launch_ber(const RxDev& d, long long ka, long long kb, long long w_from, long long w_to,
                        long long k_lim, int n_win_ring, cudaStream_t s) {
   if (kb <= ka && w_to <= w_from) return cudaSuccess;
-  const long long ks = d.ber_skip;
-  const long long kal = ks + ((max(ka, ks) - ks) / (32 * kBerSyms)) * (32 * kBerSyms);
-  const long long n = max(kb - kal, 1LL);
-  const long long per_block = 256LL * kBerSyms;
-  ber_count_kernel<<<(unsigned)((n + per_block - 1) / per_block), 256, kSlipChunk * 8 * sizeof(unsigned), s>>>(
-      d, ka, kb, w_from, w_to, k_lim, n_win_ring);
+  const long long items = ber_items(ka, kb, d.ber_skip, d.slip_win);
+  const long long blocks = std::max(1LL, (items + 7) / 8);
+  ber_count_kernel<<<(unsigned)blocks, 256, kSlipChunk * 8 * sizeof(unsigned), s>>>(d, ka, kb, w_from, w_to, k_lim,
+                                                                                    n_win_ring);
   return cudaGetLastError();
 }
 

@@ -366,14 +366,13 @@ __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
   }
 }
 
-// Quadrant rotation by -m (multiply by (-j)^m): (lI, lQ) -> (lQ, nl-1-lI).
+// Quadrant rotation by -m (multiply by (-j)^m); one quarter turn maps
+// (lI, lQ) -> (lQ, nl-1-lI), so q = m mod 4 turns give the cases below.
 __device__ __forceinline__ void rot_minus(int& lI, int& lQ, int m, int nl) {
-  const int q = ((m % 4) + 4) % 4;
-  for (int i = 0; i < q; ++i) {
-    const int t = lI;
-    lI = lQ;
-    lQ = nl - 1 - t;
-  }
+  const int q = m & 3;  // m mod 4 in [0, 4) for negative m too
+  const int a = lI, b = lQ, ra = nl - 1 - lI, rb = nl - 1 - lQ;
+  lI = q == 0 ? a : q == 1 ? b : q == 2 ? ra : rb;
+  lQ = q == 0 ? b : q == 1 ? ra : q == 2 ? rb : a;
 }
 
 __device__ __forceinline__ uint32_t gray_bits(int l, int nl) {  // MSB first
@@ -384,7 +383,7 @@ __device__ __forceinline__ uint32_t gray_bits(int l, int nl) {  // MSB first
 // of both polarisations.  Writes the output bits, the decision ring and
 // the inspection history.
 __global__ void __launch_bounds__(128) demap_kernel(RxDev d, FrameArgs fa) {
-  __shared__ int sc[2][128];
+  __shared__ int wt[2][4];
   const int r = blockIdx.x;
   const long long kr = fa.k_a + (long long)r * kRun;
   const int t = threadIdx.x;
@@ -405,17 +404,31 @@ __global__ void __launch_bounds__(128) demap_kernel(RxDev d, FrameArgs fa) {
     lev[pol][1] = v1 >> 8;
     if (val[0] && t > 0) c0 = unwrap_inc(blp[i0 - 1] & 63, bh[pol][0], B);
     if (val[1]) c1 = unwrap_inc(bh[pol][0], bh[pol][1], B);
-    sc[pol][t] = c0 + c1;
     mm[pol][0] = c0;
     mm[pol][1] = c0 + c1;
   }
+  // exclusive prefix over the block's threads of c0 + c1 (both polarisations):
+  // warp scans, then the warps' totals
+  const int lane = t & 31, w = t >> 5;
+  int incl[2] = {mm[0][1], mm[1][1]};
+#pragma unroll
+  for (int pol = 0; pol < 2; ++pol)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int a = __shfl_up_sync(0xffffffffu, incl[pol], o);
+      if (lane >= o) incl[pol] += a;
+    }
+  if (lane == 31) {
+    wt[0][w] = incl[0];
+    wt[1][w] = incl[1];
+  }
   __syncthreads();
-  for (int o = 1; o < 128; o <<= 1) {
-    int a0 = t >= o ? sc[0][t - o] : 0, a1 = t >= o ? sc[1][t - o] : 0;
-    __syncthreads();
-    sc[0][t] += a0;
-    sc[1][t] += a1;
-    __syncthreads();
+  int excl[2];
+#pragma unroll
+  for (int pol = 0; pol < 2; ++pol) {
+    int base = 0;
+    for (int ww = 0; ww < w; ++ww) base += wt[pol][ww];
+    excl[pol] = base + incl[pol] - mm[pol][1];
   }
   const int nl = d.nl, hb = d.bps / 2;
   uint32_t bits = 0;
@@ -424,8 +437,7 @@ __global__ void __launch_bounds__(128) demap_kernel(RxDev d, FrameArgs fa) {
   for (int j = 0; j < 2; ++j) {
     const long long k = kr + 2 * t + j;
     for (int pol = 0; pol < 2; ++pol) {
-      const int excl = t > 0 ? sc[pol][t - 1] : 0;
-      const int m = d.run_m0[pol * stride + r] + excl + mm[pol][j];
+      const int m = d.run_m0[pol * stride + r] + excl[pol] + mm[pol][j];
       int lI = lev[pol][j] & 15, lQ = lev[pol][j] >> 4;
       rot_minus(lI, lQ, m, nl);
       bits = (bits << hb) | gray_bits(lI, nl);

@@ -13,8 +13,10 @@
 // overlap, so each lane loads T+2 samples per polarisation), then owns the
 // tap pairs (q, t) = divmod(l, T) (and l + 32) for the gradient.  The
 // sub-block's samples live in shared memory split into 4 planes by index
-// mod 4 (conflict-free for the lane stride of 4); taps are stored as
-// float4 {w[0][q][t], w[1][q][t]} and read as broadcasts.
+// mod 4 (conflict-free for the lane stride of 4), the two input
+// polarisations' planes 64 bytes apart modulo 128 (conflict-free gradient
+// reads); taps are stored as float4 {w[0][q][t], w[1][q][t]} and read as
+// broadcasts.
 //
 // Schedule (both kernels together): the first frame is preceded by one
 // sequential acquisition chain over its first acq_syms symbols (CMA while a
@@ -33,33 +35,15 @@ template <int T>
 struct ChainSmem {
   static constexpr int NEED = (2 * kK + T - 1 + 3) / 4;
   static constexpr int P4 = NEED + ((4 - NEED % 16) + 16) % 16;  // P4 = 4 mod 16
-  float2 r[2][4 * P4];
+  static constexpr int QS = 4 * P4 + 8;  // q stride: the q planes 64 bytes apart mod 128
+  float2 r[2 * QS];
   float4 w[2][T];
   float4 e[kK];
 };
 
 template <int T>
 __device__ __forceinline__ float2 sm_r(const ChainSmem<T>& sm, int q, int s) {
-  return sm.r[q][(s & 3) * ChainSmem<T>::P4 + (s >> 2)];
-}
-
-// Stage samples [2 kf0, 2 kf0 + 2 nk + T - 1) of the frame buffer, rotated.
-template <int T>
-__device__ __forceinline__ void stage_samples(ChainSmem<T>& sm, const RxDev& d, int kf0, int nk, int zlen_f) {
-  const int lane = threadIdx.x & 31;
-  const int ns = 2 * nk + T - 1;
-  for (int q = 0; q < 2; ++q) {
-    const float2* zq = d.z + (long long)q * d.zlen;
-    for (int s = lane; s < ns; s += 32) {
-      const int i = 2 * kf0 + s;
-      float2 v = make_float2(0.f, 0.f);
-      if (i < zlen_f) {
-        const float2 rot = cmul(__ldg(&d.rot_hi[i >> 10]), __ldg(&d.rot_lo[i & (kRotLo - 1)]));
-        v = cmul(zq[i], rot);
-      }
-      sm.r[q][(s & 3) * ChainSmem<T>::P4 + (s >> 2)] = v;
-    }
-  }
+  return sm.r[q * ChainSmem<T>::QS + (s & 3) * ChainSmem<T>::P4 + (s >> 2)];
 }
 
 // One sub-block update of nk (<= 64) symbols.  mode 0 = CMA, 1 = DD.
@@ -428,7 +412,7 @@ __global__ void __launch_bounds__(128) mimo_kernel(RxDev d, FrameArgs fa, long l
         if (s < NSP) {
           const int i = 2 * kf0 + s;
           const float2 rot = cmul(__ldg(&d.rot_hi[i >> 10]), __ldg(&d.rot_lo[i & (kRotLo - 1)]));
-          sm.r[q][(s & 3) * ChainSmem<T>::P4 + (s >> 2)] = cmul(pz[q][r], rot);
+          sm.r[q * ChainSmem<T>::QS + (s & 3) * ChainSmem<T>::P4 + (s >> 2)] = cmul(pz[q][r], rot);
         }
       }
   };
