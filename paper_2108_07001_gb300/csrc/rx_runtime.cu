@@ -86,7 +86,10 @@ struct rx_handle {
   RxDev d;
   cudaStream_t s_copy = nullptr;
   cudaStream_t s_front = nullptr;  // CD + estimator of each frame
-  cudaStream_t s_comp = nullptr;   // acquisition, MIMO, BPS, demap, BER ("back")
+  cudaStream_t s_mid = nullptr;    // acquisition and MIMO
+  cudaStream_t s_comp = nullptr;   // BPS and demap ("back")
+  cudaEvent_t ev_mid[2] = {};      // MIMO of a frame done (its y buffer written), by frame parity
+  cudaEvent_t ev_bpsd[2] = {};     // BPS of a frame done (its y buffer free again), by frame parity
   cudaEvent_t ev_front[kZSlots] = {};  // front work of the frame in slot done
   cudaEvent_t ev_mimo[kZSlots] = {};   // MIMO of the frame in slot done (slot reusable)
   cudaStream_t s_ber = nullptr;        // BER counting (metrics), off the decision path
@@ -232,6 +235,11 @@ void free_all(rx_handle* h) {
   if (h->ev_reset) cudaEventDestroy(h->ev_reset);
   if (h->s_copy) cudaStreamDestroy(h->s_copy);
   if (h->s_comp) cudaStreamDestroy(h->s_comp);
+  if (h->s_mid) cudaStreamDestroy(h->s_mid);
+  for (int i = 0; i < 2; ++i) {
+    if (h->ev_mid[i]) cudaEventDestroy(h->ev_mid[i]);
+    if (h->ev_bpsd[i]) cudaEventDestroy(h->ev_bpsd[i]);
+  }
   if (h->s_front) cudaStreamDestroy(h->s_front);
   if (h->s_ber) cudaStreamDestroy(h->s_ber);
   for (int i = 0; i < 2; ++i) {
@@ -307,6 +315,7 @@ int staged(rx_handle* h, PendingFrame& pf, int stage, cudaStream_t strm, Fn&& fn
 cudaError_t sync_all(rx_handle* h) {
   cudaError_t e = cudaStreamSynchronize(h->s_copy);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_front);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_mid);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_comp);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_ber);
   return e;
@@ -323,6 +332,7 @@ cudaError_t mark_copy(rx_handle* h) {
 int launch_decide(rx_handle* h, PendingFrame& pf, const FrameArgs& fa, bool final_) {
   const RxDev& d = h->d;
   RX_STAGE(RX_STAGE_BPS, 1, h->s_comp, launch_bps(d, fa, h->s_comp));
+  if (fa.f >= 0) RX_CK(cudaEventRecord(h->ev_bpsd[fa.f & 1], h->s_comp));
   // the decision ring slots of pass n were read by the BER work of pass n-2
   const int par = (int)(h->n_decide & 1);
   if (d.ber_on && h->n_decide >= 2) RX_CK(cudaStreamWaitEvent(h->s_comp, h->ev_berd[par], 0));
@@ -416,11 +426,18 @@ int launch_frame(rx_handle* h, long long f, bool final_) {
   RX_CK(cudaEventRecord(h->cd_done[f % h->cd_done.size()], sf));
   RX_STAGE(RX_STAGE_EST, 1, sf, launch_est(df, fa, 1, sf));
   RX_CK(cudaEventRecord(h->ev_front[slot], sf));
-  // back: equaliser and decisions
-  RX_CK(cudaStreamWaitEvent(h->s_comp, h->ev_front[slot], 0));
-  if (f == 0) RX_STAGE(RX_STAGE_ACQUIRE, 1, h->s_comp, launch_acquire(df, fa, h->s_comp));
-  RX_STAGE(RX_STAGE_MIMO, 1, h->s_comp, launch_mimo(df, fa, h->s_comp));
-  RX_CK(cudaEventRecord(h->ev_mimo[slot], h->s_comp));
+  // middle: equaliser, after the frame's front work and after the decisions
+  // of frame f - 2 have read the y buffer it reuses
+  cudaStream_t sm = h->s_mid;
+  RX_CK(cudaStreamWaitEvent(sm, h->ev_front[slot], 0));
+  if (f >= 2) RX_CK(cudaStreamWaitEvent(sm, h->ev_bpsd[f & 1], 0));
+  if (f == 0) RX_STAGE(RX_STAGE_ACQUIRE, 1, sm, launch_acquire(df, fa, sm));
+  RX_STAGE(RX_STAGE_MIMO, 1, sm, launch_mimo(df, fa, sm));
+  RX_CK(cudaEventRecord(h->ev_mimo[slot], sm));
+  RX_CK(cudaEventRecord(h->ev_mid[f & 1], sm));
+  // back: decisions, after the frame's equaliser (the MIMO of frame f + 1
+  // runs meanwhile)
+  RX_CK(cudaStreamWaitEvent(h->s_comp, h->ev_mid[f & 1], 0));
   int rc = launch_decide(h, pf, fa, final_);
   if (rc != RX_OK) return rc;
   RX_CK(cudaEventRecord(pf.ev_done, h->s_comp));
@@ -729,6 +746,11 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_stage_free[i], h->s_copy);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_comp, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_mid, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&h->ev_mid[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_bpsd[i], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_front, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_ber, cudaStreamNonBlocking);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
@@ -954,6 +976,7 @@ int rx_destroy(rx_handle* h) {
   if (!h) return RX_OK;
   cudaSetDevice(h->cfg.device);
   if (h->s_front) cudaStreamSynchronize(h->s_front);
+  if (h->s_mid) cudaStreamSynchronize(h->s_mid);
   if (h->s_comp) cudaStreamSynchronize(h->s_comp);
   if (h->s_ber) cudaStreamSynchronize(h->s_ber);
   if (h->s_copy) cudaStreamSynchronize(h->s_copy);
@@ -977,6 +1000,8 @@ int rx_reset(rx_handle* h) {
   RX_CK(cudaStreamWaitEvent(s, h->ev_front[0], 0));
   RX_CK(cudaEventRecord(h->ev_berd[0], h->s_ber));
   RX_CK(cudaStreamWaitEvent(s, h->ev_berd[0], 0));
+  RX_CK(cudaEventRecord(h->ev_mid[0], h->s_mid));
+  RX_CK(cudaStreamWaitEvent(s, h->ev_mid[0], 0));
   StreamState st{};
   st.bhat_last[0] = st.bhat_last[1] = -1;
   RX_CK(cudaMemcpyAsync(d.st, &h->st_init, sizeof(st), cudaMemcpyHostToDevice, s));
@@ -994,6 +1019,7 @@ int rx_reset(rx_handle* h) {
   RX_CK(cudaEventRecord(h->ev_reset, s));
   RX_CK(cudaStreamWaitEvent(h->s_front, h->ev_reset, 0));
   RX_CK(cudaStreamWaitEvent(h->s_ber, h->ev_reset, 0));
+  RX_CK(cudaStreamWaitEvent(h->s_mid, h->ev_reset, 0));
   h->n_decide = 0;
   h->reset_pending = true;
   h->gen++;
@@ -1013,16 +1039,19 @@ int rx_reset(rx_handle* h) {
 int rx_join(rx_handle* h, void* cuda_stream) {
   if (!h) return fail(RX_EINVAL, "null handle");
   RX_CK(cudaSetDevice(h->cfg.device));
-  cudaEvent_t e = get_event(h), e2 = get_event(h), e3 = get_event(h);
+  cudaEvent_t e = get_event(h), e2 = get_event(h), e3 = get_event(h), e4 = get_event(h);
   RX_CK(cudaEventRecord(e, h->s_comp));
   RX_CK(cudaEventRecord(e2, h->s_front));
   RX_CK(cudaEventRecord(e3, h->s_ber));
+  RX_CK(cudaEventRecord(e4, h->s_mid));
   RX_CK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, e, 0));
   RX_CK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, e2, 0));
   RX_CK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, e3, 0));
+  RX_CK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, e4, 0));
   h->ev_pool.push_back(e);
   h->ev_pool.push_back(e2);
   h->ev_pool.push_back(e3);
+  h->ev_pool.push_back(e4);
   return RX_OK;
 }
 
