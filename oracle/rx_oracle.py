@@ -26,7 +26,9 @@ The chain (per stream, both polarisations processed jointly):
       stream; afterwards every frame is cut into segments of S symbols and
       segment j continues the chain of segment j of the previous frame.
   a6  blind phase search over B test angles with a (2W+1)-symbol window and
-      pi/2 unwrapping.
+      pi/2 unwrapping; reduced-cost form: the same window costs at the B/S
+      coarse angles only, the fine index from the parabola through the
+      coarse minimum and its two neighbours.
   a7  hard decision and Gray demapping (paper Sec. II: decisions demapped).
   a8  BER against the known PRBS-31 payload after a one-time sync (delay,
       polarisation order, quadrant), with cycle-slip re-resolution; Q-factor
@@ -53,6 +55,8 @@ PIN_STATUS = {
     "mimo_fir": "pinned: brute-force convolution sums; inverse of a known unitary",
     "sub_block_update": "pinned: CMA converges to the inverse of a known unitary",
     "bps": "pinned: constant injected phase recovered modulo pi/2 to grid resolution",
+    "two_stage_index": "pinned: vertex of exact parabolas (wrapping included) recovered to the nearest fine index",
+    "bps_two_stage": "pinned: equals bps for S = 1; off-grid constant phase recovered to one fine step",
     "unwrap_increments": "pinned: phase ramp across quadrants tracked without slips",
     "decide/demap": "pinned: exhaustive constellation round trip, Gray neighbour property",
     "prbs31_bits": "pinned: independent generator agreement, recurrence, balance",
@@ -77,6 +81,7 @@ class RxConfig:
     mimo_taps: int = 15
     bps_angles: int = 64
     bps_half_window: int = 16
+    bps_coarse_stride: int = 1            # S > 1: two-stage search over B/S coarse angles
     sub_block_syms: int = 64
     seg_syms: int = 512
     frame_syms: int = 1 << 16
@@ -411,26 +416,65 @@ def bps_angles(B: int) -> np.ndarray:
     return (np.arange(B) / B - 0.5) * (math.pi / 2.0)
 
 
+def bps_costs(y: np.ndarray, phi: np.ndarray, W: int, bits_per_sym: int, a: int, b: int) -> np.ndarray:
+    """D_{k,i} = sum_{|m|<=W, 0<=k+m<n} |z - dec(z)|^2, z = y_{k+m} exp(-j phi_i),
+    for the symbols a <= k < b (rows) and the listed test angles (columns)."""
+    n = y.size
+    lo, hi = max(a - W, 0), min(b + W, n)
+    z = y[lo:hi, None] * np.exp(-1j * phi)[None, :]
+    d = np.abs(z - decide(z, bits_per_sym)) ** 2
+    D = np.zeros((b - a, phi.size))
+    for i in range(-W, W + 1):
+        src_lo, src_hi = a + i, b + i
+        clo, chi = max(src_lo, 0), min(src_hi, n)
+        if chi > clo:
+            D[clo - src_lo:chi - src_lo] += d[clo - lo:chi - lo]
+    return D
+
+
 def bps(y: np.ndarray, B: int, W: int, bits_per_sym: int, chunk: int = 1 << 15) -> np.ndarray:
     """b_k = argmin_b sum_{|i|<=W, 0<=k+i<n} |z_{k+i,b} - dec(z_{k+i,b})|^2,
     z_{k,b} = y_k exp(-j phi_b); lowest b on exact ties.  Computed in chunks
     of symbols (each output is the same sum, in the same order)."""
     n = y.size
     phi = bps_angles(B)
-    rot = np.exp(-1j * phi)
     out = np.empty(n, dtype=np.int64)
     for a in range(0, n, chunk):
         b = min(a + chunk, n)
-        lo, hi = max(a - W, 0), min(b + W, n)
-        z = y[lo:hi, None] * rot[None, :]
-        d = np.abs(z - decide(z, bits_per_sym)) ** 2
-        D = np.zeros((b - a, B))
-        for i in range(-W, W + 1):
-            src_lo, src_hi = a + i, b + i
-            clo, chi = max(src_lo, 0), min(src_hi, n)
-            if chi > clo:
-                D[clo - src_lo:chi - src_lo] += d[clo - lo:chi - lo]
-        out[a:b] = np.argmin(D, axis=1)
+        out[a:b] = np.argmin(bps_costs(y, phi, W, bits_per_sym, a, b), axis=1)
+    return out
+
+
+def two_stage_index(Dc: np.ndarray, S: int, B: int) -> np.ndarray:
+    """Fine angle index from the window costs Dc[k, j] of the C = B/S coarse
+    angles b = S j: j* = argmin_j (lowest j on ties); with the cyclic
+    neighbours D-, D0, D+ of j* (the cost is pi/2-periodic in the angle, so
+    coarse index C wraps to 0), c = D- - 2 D0 + D+ (>= 0 at a minimum) and
+    delta = (D- - D+) / (2c) in [-1/2, 1/2] (0 if c = 0) is the vertex of
+    the parabola through the three costs in units of the coarse step;
+    b = (S j* + floor(S delta + 1/2)) mod B."""
+    C = Dc.shape[1]
+    k = np.arange(Dc.shape[0])
+    j = np.argmin(Dc, axis=1)
+    Dm, D0, Dp = Dc[k, (j - 1) % C], Dc[k, j], Dc[k, (j + 1) % C]
+    c = Dm - 2.0 * D0 + Dp
+    delta = np.where(c > 0, (Dm - Dp) / (2.0 * np.where(c > 0, c, 1.0)), 0.0)
+    delta = np.clip(delta, -0.5, 0.5)
+    r = np.floor(S * delta + 0.5).astype(np.int64)
+    return (S * j + r) % B
+
+
+def bps_two_stage(y: np.ndarray, B: int, W: int, bits_per_sym: int, S: int,
+                  chunk: int = 1 << 15) -> np.ndarray:
+    """Reduced-cost blind phase search: the window costs of the same
+    definition as bps() at the B/S coarse angles b = S j only, then the fine
+    index on the B-angle grid from two_stage_index (S = 1 is bps())."""
+    n = y.size
+    phi = bps_angles(B)[::S]
+    out = np.empty(n, dtype=np.int64)
+    for a in range(0, n, chunk):
+        b = min(a + chunk, n)
+        out[a:b] = two_stage_index(bps_costs(y, phi, W, bits_per_sym, a, b), S, B)
     return out
 
 
@@ -645,7 +689,10 @@ class Receiver:
         # a6/a7
         B, W = cfg.bps_angles, cfg.bps_half_window
         phi = bps_angles(B)
-        bh = np.stack([bps(y_all[p], B, W, cfg.bits_per_sym) for p in range(2)])
+        if cfg.bps_coarse_stride > 1:
+            bh = np.stack([bps_two_stage(y_all[p], B, W, cfg.bits_per_sym, cfg.bps_coarse_stride) for p in range(2)])
+        else:
+            bh = np.stack([bps(y_all[p], B, W, cfg.bits_per_sym) for p in range(2)])
         m = np.stack([unwrap_increments(bh[p], B) for p in range(2)])
         phat = phi[bh] + m * (math.pi / 2.0)
         zc = y_all * np.exp(-1j * phat)

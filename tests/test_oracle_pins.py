@@ -211,6 +211,58 @@ def test_bps_recovers_constant_phase_mod_half_pi(bps_):
         assert np.all(branch == branch[0])
 
 
+def test_two_stage_refinement_finds_the_vertex_of_a_parabola():
+    """Coarse costs sampled from an exact parabola (cyclic in the angle index)
+    put the fine index at the vertex, rounded to the nearest fine angle; the
+    vertex positions include ones whose coarse minimum or neighbours wrap."""
+    B = 64
+    for S in (2, 4, 8):
+        C = B // S
+        b0 = np.array([0.3, -1.4, 17.2, 17.6, 33.49, 62.9, 63.7, 40.0, 8.5 + 1e-6, -0.51])
+        j = np.arange(C)
+        dist = (S * j[None, :] - b0[:, None] + B / 2) % B - B / 2  # cyclic offset from the vertex
+        Dc = 5.0 + 0.25 * dist ** 2
+        got = O.two_stage_index(Dc, S, B)
+        want = np.floor(b0 + 0.5).astype(np.int64) % B
+        assert np.array_equal(got, want), (S, got, want)
+
+
+def test_two_stage_with_stride_one_is_the_full_search():
+    rng = np.random.default_rng(21)
+    for bps_, B in ((2, 64), (4, 32)):
+        bits = rng.integers(0, 2, 3000 * bps_).astype(np.uint8)
+        s = rxsim.gray_map(bits, bps_)
+        y = s * np.exp(1j * np.cumsum(0.02 * rng.standard_normal(s.size)))
+        y = y + 0.15 * (rng.standard_normal(s.size) + 1j * rng.standard_normal(s.size))
+        assert np.array_equal(O.bps_two_stage(y, B, 16, bps_, 1), O.bps(y, B, 16, bps_))
+
+
+@pytest.mark.parametrize("bps_", [2, 4])
+def test_two_stage_recovers_an_off_grid_phase_to_one_fine_step(bps_):
+    """A constant phase between two coarse angles: the coarse angle alone is
+    up to S/2 = 2 fine steps off; the refined index is as close as the full
+    search's (at most one step past the two grid angles around the phase)."""
+    rng = np.random.default_rng(22)
+    B, W, S = 64, 16, 4
+    bits = rng.integers(0, 2, 4000 * bps_).astype(np.uint8)
+    s = rxsim.gray_map(bits, bps_)
+    noise = 0.02 * (rng.standard_normal(s.size) + 1j * rng.standard_normal(s.size))
+    step = math.pi / 2 / B
+    for theta in (0.3, -1.2, 2.9, 0.7853, O.bps_angles(B)[21] + 1.6 * step, O.bps_angles(B)[0] - 1.3 * step):
+        y = (s + noise) * np.exp(1j * theta)
+        errs = []
+        for SS in (S, 1):
+            bh = O.bps_two_stage(y, B, W, bps_, SS)
+            ph = O.bps_angles(B)[bh] + O.unwrap_increments(bh, B) * math.pi / 2
+            errs.append(np.abs((ph - theta + math.pi / 4) % (math.pi / 2) - math.pi / 4))
+            branch = np.round((ph - theta) / (math.pi / 2))
+            assert np.all(branch == branch[0])
+        err, full = errs
+        assert np.max(err) <= 1.5 * step
+        assert np.median(err) <= step / 2 + 1e-3
+        assert np.mean(err) <= np.mean(full) + 0.05 * step
+
+
 def test_unwrap_follows_a_ramp_across_quadrants():
     rng = np.random.default_rng(10)
     n, B = 20000, 64
