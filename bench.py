@@ -126,23 +126,28 @@ def profiled_traffic(kernel):
     return None
 
 
-def workload():
+def workload(stride=1):
+    """The stream workload; stride > 1 selects the two-stage blind phase
+    search over bps_angles / stride coarse angles."""
     from paper_2108_07001_gb300 import workloads
-    return workloads.DP_QPSK_10000KM_STREAM
+    wl = workloads.DP_QPSK_10000KM_STREAM
+    if stride > 1:
+        wl = dict(wl, rx=dict(wl["rx"], bps_coarse_stride=stride))
+    return wl
 
 
 def stage_work(wl, n_sym):
     """Algorithmic work per step of each stage (flops or bytes).  One step
     processes n_sym symbols per polarisation = 4 n_sym complex samples."""
     rx = wl["rx"]
-    B, T = rx["bps_angles"], rx["mimo_taps"]
+    B, T = rx["bps_angles"] // rx.get("bps_coarse_stride", 1), rx["mimo_taps"]
     samples = 4 * n_sym
     return {
         # CD: each complex64 sample read once from the ring, written once
         "cd": ("hbm", samples * 16.0),
         # FIR (2 outputs x 2 inputs x T complex MACs) + gradient (same), 8 flops per CMAC
         "mimo": ("alu", n_sym * 2 * (4 * T) * 8.0),
-        # per symbol, polarisation and angle: rotation 6, |Re|+|Im| 1, window add/sub 2
+        # per symbol, polarisation and searched angle: rotation 6, |Re|+|Im| 1, window add/sub 2
         "bps": ("alu", n_sym * 2 * B * 9.0),
     }
 
@@ -151,7 +156,7 @@ def run_ours(args):
     import torch
     from paper_2108_07001_gb300 import rx
 
-    wl = workload()
+    wl = workload(args.bps_coarse_stride)
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
     import rxsim
@@ -247,7 +252,7 @@ def run_ours(args):
     dom = max(stages, key=lambda k: stages[k]["ms_per_step"])
     roof = dict(stages[dom])
     roof["kernel"] = dom
-    roof["traffic"] = profiled_traffic(dom)
+    roof["traffic"] = profiled_traffic("bps2" if dom == "bps" and args.bps_coarse_stride > 1 else dom)
     if roof["traffic"] is not None:
         roof["traffic_unit"] = "bytes per launch (ncu dram read+write, profiles/traffic.txt)"
     roof.pop("launches_per_step", None)
@@ -309,7 +314,7 @@ def run_ours(args):
 
 def finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, other_ms,
            gpu_launches, clocks, host0, host1, gen_s, e2e):
-    cpu = cpu_baseline() if args.cpu_baseline else None
+    cpu = cpu_baseline(args.bps_coarse_stride) if args.cpu_baseline else None
     line = {
         "metric": "gsamples_per_s", "value": round(value, 3), "unit": "Gsamples/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
@@ -317,7 +322,9 @@ def finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, o
         "data": "synthetic (seeded link simulator)",
         "config": {"workload": wl["name"], "symbols_per_pol": n_sym, "push_syms": wl["push_syms"],
                    "frame_syms": cfg.frame_syms, "fft_n_auto": True, "mimo_taps": cfg.mimo_taps,
-                   "bps_angles": cfg.bps_angles, "storage": "c64", "input": "resident in HBM, 512 MiB > L2",
+                   "bps_angles": cfg.bps_angles, "bps_search": "full" if cfg.bps_coarse_stride == 1 else
+                   f"two-stage: {cfg.bps_angles // cfg.bps_coarse_stride} coarse angles + parabolic refinement",
+                   "storage": "c64", "input": "resident in HBM, 512 MiB > L2",
                    "l2": "inputs larger than L2"},
         "decoded_gbps": round(gbps, 3),
         "ber": stats["ber"], "bits": stats["bits"], "bit_errors": stats["bit_errors"],
@@ -343,7 +350,7 @@ def workload_by_name(name):
     raise KeyError(name)
 
 
-def oracle_child(name, n_sym, reps):
+def oracle_child(name, n_sym, reps, stride=1):
     """Runs in a child process with one BLAS/OpenMP thread: simulates the
     first n_sym symbols of the named workload's link once (complex64
     samples, as the GPU forms receive them), then times the FP64 oracle on
@@ -359,6 +366,8 @@ def oracle_child(name, n_sym, reps):
     x = sim["rx"].astype(np.complex128)
     del sim
     kw = oracle_kwargs(wl["rx"])
+    if stride > 1:
+        kw["bps_coarse_stride"] = stride
     times, res = [], None
     for _ in range(reps):
         t0 = time.perf_counter()
@@ -370,7 +379,7 @@ def oracle_child(name, n_sym, reps):
                                               "evm": float(b["evm"])}}), flush=True)
 
 
-def oracle_run(n_sym, reps, name=None):
+def oracle_run(n_sym, reps, name=None, stride=1):
     """Oracle run times (and the last run's BER counters) on the host cores,
     measured in a fresh single-threaded process (fork+exec, so safe after
     CUDA initialisation)."""
@@ -378,20 +387,21 @@ def oracle_run(n_sym, reps, name=None):
     for k in ORACLE_THREAD_ENV:
         env[k] = "1"
     name = name or workload()["name"]
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", name, str(n_sym), str(reps)],
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", name, str(n_sym), str(reps),
+                          str(stride)],
                          env=env, capture_output=True, text=True, check=True, cwd=ROOT)
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def oracle_times(n_sym, reps):
-    return oracle_run(n_sym, reps)["times"]
+def oracle_times(n_sym, reps, stride=1):
+    return oracle_run(n_sym, reps, stride=stride)["times"]
 
 
 CPU_BASELINE_SYMS = 1 << 20  # one full frame, acquisition included (10-30 s of one core)
 
 
-def cpu_baseline():
-    t = oracle_times(CPU_BASELINE_SYMS, 1)[0]
+def cpu_baseline(stride=1):
+    t = oracle_times(CPU_BASELINE_SYMS, 1, stride)[0]
     v = 4 * CPU_BASELINE_SYMS / t / 1e9
     return {"value": round(v, 6), "unit": "Gsamples/s", "cores": 1, "kind": "oracle",
             "sample": f"first {CPU_BASELINE_SYMS} symbols/pol of the workload (one whole frame incl. "
@@ -764,7 +774,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--symbols", type=int, default=0, help="stream length per pol (default: the workload's 2^24)")
-    ap.add_argument("--oracle-child", nargs=3, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-child", nargs=4, help=argparse.SUPPRESS)
+    ap.add_argument("--bps-coarse-stride", type=int, default=1,
+                    help="stream workload: 4 = two-stage BPS over 16 coarse angles (default 1: all 64)")
     ap.add_argument("--workload", default="stream", choices=["stream", "qam16", "serving", "batched"],
                     help="stream: the 2^24-symbol DP-QPSK stream (default line); qam16: DP-16QAM 5,000 km "
                          "with FP16 and FP32 sample storage against the FP64 oracle; serving: 16 mixed "
@@ -772,8 +784,8 @@ def main():
                          "streams with uneven blocks, FFT sizes from the heuristic and from the autotuner")
     args = ap.parse_args()
     if args.oracle_child:
-        name, n_sym, reps = args.oracle_child
-        oracle_child(name, int(n_sym), int(reps))
+        name, n_sym, reps, stride = args.oracle_child
+        oracle_child(name, int(n_sym), int(reps), int(stride))
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -66,7 +66,12 @@ typedef struct rx_config {
   int cd_halo;             /* OLS overlap M-1 in samples (even); 0: 1.1 x CD memory */
   int mimo_taps;           /* T, odd, 3..31 */
   int bps_angles;          /* B: 32 or 64 */
-  int bps_half_window;     /* W: window is 2W+1 symbols, 1..32 */
+  int bps_half_window;     /* W: window is 2W+1 symbols, 8/12/16/24/32 */
+  int bps_coarse_stride;   /* S: 1 = search all B angles; B/16 (QPSK) or B/8
+                              (16QAM) = two-stage search: the window costs
+                              of the B/S angles b = S j, then the fine index
+                              at the vertex of the parabola through the
+                              coarse minimum and its two neighbours */
   int sub_block_syms;      /* K: symbols per tap update (64) */
   int seg_syms;            /* S: symbols per adaptive segment (multiple of K) */
   int frame_syms;          /* F: symbols per processing frame (multiple of S) */

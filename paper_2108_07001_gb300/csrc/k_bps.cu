@@ -20,14 +20,9 @@
 // stream edge take no per-step predicate.  The last block of each
 // polarisation (found with an atomic counter after a fence; nothing waits)
 // turns the runs' unwrap sums into each run's starting counter.
-#include "rx_internal.cuh"
+#include "bps_common.cuh"
 
 namespace rx {
-
-__device__ __forceinline__ int unwrap_inc(int a, int b, int B) {  // floor((2(a-b)+B)/(2B))
-  const int x = 2 * (a - b) + B;
-  return (x >= 2 * B) - (x < 0);
-}
 
 // Metric of one symbol at one test angle (scaled squared distance).
 template <bool QAM16>
@@ -89,9 +84,6 @@ __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
   extern __shared__ __align__(16) uint32_t keys_smem[];
   __shared__ uint8_t bh_s[8][kRun];
   __shared__ float2 cs_s[B];
-  __shared__ float red_s[8][3];
-  __shared__ int part[256];
-  __shared__ int am_last;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int pol = blockIdx.y;
@@ -283,87 +275,11 @@ __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
     }
   }
   __syncwarp();
-  // decisions, unwrap increments and EVM of the run
-  float evn = 0.f, evd = 0.f;
-  int inc_sum = 0;
-  uint16_t* blp = d.bl + (long long)pol * (d.F + 2 * d.W);
-  for (int ko = lane; ko < ract; ko += 32) {
-    const int bh = bh_s[warp][ko];
-    if (ko > 0) inc_sum += unwrap_inc(bh_s[warp][ko - 1], bh, B);
-    const float2 yv = PAIR ? make_float2(ys4[W + ko].x, ys4[W + ko].y) : ys2[W + ko];
-    const float2 csb = cs_s[bh];
-    const float zx = fmaf(yv.x, csb.x, yv.y * csb.y), zy = fmaf(yv.y, csb.x, -yv.x * csb.y);
-    const int lI = level_of(zx, d.nl), lQ = level_of(zy, d.nl);
-    const long long k = kr + ko;
-    blp[k - fa.k_a] = (uint16_t)(bh | (lI << 8) | (lQ << 12));
-    if (k >= d.ber_skip && k < fa.k_end) {
-      const float dx = level_val(lI, d.nl), dy = level_val(lQ, d.nl);
-      evn += (zx - dx) * (zx - dx) + (zy - dy) * (zy - dy);
-      evd += dx * dx + dy * dy;
-    }
-  }
-  const float incf = warp_sum((float)inc_sum);
-  evn = warp_sum(evn);
-  evd = warp_sum(evd);
-  const int stride = d.F / kRun + 4;
-  if (lane == 0) {
-    red_s[warp][1] = evn;
-    red_s[warp][2] = evd;
-    if (run < nruns) {
-      d.run_int[pol * stride + run] = (int)lrintf(incf);
-      d.run_edge[(pol * stride + run) * 2 + 0] = bh_s[warp][0];
-      d.run_edge[(pol * stride + run) * 2 + 1] = bh_s[warp][ract - 1];
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float a = 0.f, c = 0.f;
-    for (int w = 0; w < 8; ++w) { a += red_s[w][1]; c += red_s[w][2]; }
-    if (c > 0.f) {
-      atomicAdd(&d.st->evm_num, (double)a);
-      atomicAdd(&d.st->evm_den, (double)c);
-    }
-  }
-  // the last block of this polarisation turns run sums into run start
-  // counters (the lane-0 threads wrote the run sums and edges)
-  if (lane == 0) __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) am_last = atomicAdd(&d.bps_done[pol], 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  const int per = (nruns + 255) / 256;
-  const int r0 = threadIdx.x * per, r1 = min(r0 + per, nruns);
-  const int b_last_prev = d.st->bhat_last[pol];
-  int loc = 0;
-  for (int r = r0; r < r1; ++r) {
-    const int bf = __ldcg(&d.run_edge[(pol * stride + r) * 2 + 0]);
-    const int bp = r == 0 ? b_last_prev : __ldcg(&d.run_edge[(pol * stride + r - 1) * 2 + 1]);
-    loc += (bp >= 0 ? unwrap_inc(bp, bf, B) : 0) + __ldcg(&d.run_int[pol * stride + r]);
-  }
-  part[threadIdx.x] = loc;
-  __syncthreads();
-  for (int o = 1; o < 256; o <<= 1) {
-    const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
-  }
-  const int m_last = d.st->m_last[pol];
-  int acc = m_last + (threadIdx.x > 0 ? part[threadIdx.x - 1] : 0);
-  for (int r = r0; r < r1; ++r) {
-    const int bf = __ldcg(&d.run_edge[(pol * stride + r) * 2 + 0]);
-    const int bp = r == 0 ? b_last_prev : __ldcg(&d.run_edge[(pol * stride + r - 1) * 2 + 1]);
-    const int binc = bp >= 0 ? unwrap_inc(bp, bf, B) : 0;
-    d.run_m0[pol * stride + r] = acc + binc;
-    acc += binc + __ldcg(&d.run_int[pol * stride + r]);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    d.st->m_last[pol] = m_last + part[255];
-    d.st->bhat_last[pol] = __ldcg(&d.run_edge[(pol * stride + nruns - 1) * 2 + 1]);
-    d.bps_done[pol] = 0;
-  }
+  // decisions, unwrap increments and EVM of the run; then the block epilogue
+  float evn, evd;
+  bps_finish_run(d, fa, pol, run, nruns, kr, ract, bh_s[warp], cs_s,
+                 [&](int ko) { return PAIR ? make_float2(ys4[W + ko].x, ys4[W + ko].y) : ys2[W + ko]; }, evn, evd);
+  bps_finish_block<256>(d, pol, nruns, evn, evd);
 }
 
 // Quadrant rotation by -m (multiply by (-j)^m); one quarter turn maps
@@ -474,6 +390,9 @@ __global__ void __launch_bounds__(128) demap_kernel(RxDev d, FrameArgs fa) {
 
 // ---- launchers ------------------------------------------------------------
 
+cudaError_t bps2_set_attributes();  // k_bps2.cu
+cudaError_t launch_bps2(const RxDev& d, const FrameArgs& fa, cudaStream_t s);
+
 template <int B, int W, bool Q>
 static void launch_bps_t(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
   const long long n_dec = fa.k_b - fa.k_a;
@@ -499,11 +418,13 @@ cudaError_t bps_set_attributes() {
   RX_BA(64, 16) RX_BA(32, 16) RX_BA(64, 32) RX_BA(32, 32) RX_BA(64, 8) RX_BA(32, 8)
   RX_BA(64, 12) RX_BA(32, 12) RX_BA(64, 24) RX_BA(32, 24)
 #undef RX_BA
+  if (e == cudaSuccess) e = bps2_set_attributes();
   return e;
 }
 
 cudaError_t launch_bps(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
   if (fa.k_b <= fa.k_a) return cudaSuccess;
+  if (d.bps_stride > 1) return launch_bps2(d, fa, s);
   const bool q16 = d.bps == 4;
 #define RX_BW(b, w)                                   \
   if (d.B == b && d.W == w) {                         \

@@ -127,6 +127,7 @@ extern "C" int rx_decide_block_noalloc(const void* y, int64_t n, int modulation,
   memset(&d, 0, sizeof(d));
   d.F = (int)kF;
   d.B = bps_angles;
+  d.bps_stride = 1;
   d.W = W;
   d.bps = modulation;
   d.nl = modulation == RX_QPSK ? 2 : 4;

@@ -65,6 +65,7 @@ struct RxDev {
   // geometry
   int N, halo, h, L, c, T, K, S, F, G, B, W, bps;
   int nl;                      // levels per dimension (2 or 4)
+  int bps_stride;              // BPS coarse stride S: 1 full search, > 1 two-stage over B/S angles
   int zlen;                    // 2F + 2c
   int storage;                 // RX_C64 / RX_C16
   long long ring_cap;          // samples per polarisation

@@ -489,6 +489,8 @@ int validate(const rx_config* c, std::string& why) {
   if (c->bps_angles != 32 && c->bps_angles != 64) return why = "bps_angles must be 32 or 64", RX_EINVAL;
   const int W = c->bps_half_window;
   if (W != 8 && W != 12 && W != 16 && W != 24 && W != 32) return why = "bps_half_window must be one of 8, 12, 16, 24, 32", RX_EINVAL;
+  if (c->bps_coarse_stride != 1 && c->bps_coarse_stride * (c->modulation == RX_QAM16 ? 8 : 16) != c->bps_angles)
+    return why = "bps_coarse_stride must be 1 or bps_angles/16 (QPSK), bps_angles/8 (16QAM)", RX_EINVAL;
   if (c->sub_block_syms != 64) return why = "sub_block_syms must be 64", RX_EINVAL;
   if (c->seg_syms < 64 || c->seg_syms % 64) return why = "seg_syms must be a positive multiple of 64", RX_EINVAL;
   if (c->frame_syms < c->seg_syms || c->frame_syms % c->seg_syms || c->frame_syms % kRun)
@@ -557,6 +559,7 @@ void rx_config_default(rx_config* c) {
   c->mimo_taps = 15;
   c->bps_angles = 64;
   c->bps_half_window = 16;
+  c->bps_coarse_stride = 1;
   c->sub_block_syms = 64;
   c->seg_syms = 512;
   c->frame_syms = 1 << 16;
@@ -618,6 +621,7 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   d.G = d.F / d.S;
   d.B = cfg->bps_angles;
   d.W = cfg->bps_half_window;
+  d.bps_stride = cfg->bps_coarse_stride;
   d.bps = cfg->modulation;
   d.nl = d.bps == 2 ? 2 : 4;
   d.zlen = 2 * d.F + 2 * d.c;

@@ -51,6 +51,7 @@ class RxConfig(ctypes.Structure):
         ("mimo_taps", ctypes.c_int),
         ("bps_angles", ctypes.c_int),
         ("bps_half_window", ctypes.c_int),
+        ("bps_coarse_stride", ctypes.c_int),
         ("sub_block_syms", ctypes.c_int),
         ("seg_syms", ctypes.c_int),
         ("frame_syms", ctypes.c_int),

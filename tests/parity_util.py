@@ -5,6 +5,11 @@ Tolerances (stated where used):
   equalised symbols  rel RMS <= 1e-4 (FP32 path vs FP64 oracle);
   BPS angle          the GPU's angle is the oracle's, or a near-tie of it:
                      D_or[b_gpu] - min_b D_or <= 1e-4 * min_b D_or;
+                     two-stage search: the GPU's index is the refinement of a
+                     coarse angle that is a near-tie in the same sense, with
+                     floor(S delta + 1/2) taken anywhere within
+                     S delta +- 3 S 1e-4 max(D-, D0, D+) / c (the change of
+                     S delta when each cost moves by up to 1e-4 of itself);
   unwrapped phase    equal wherever the angles are equal;
   bits               identical except for symbols whose oracle-corrected value
                      lies within 1e-3 of a decision threshold or whose BPS
@@ -85,11 +90,37 @@ def oracle_bps_metric(y: np.ndarray, k: np.ndarray, B: int, W: int, bits_per_sym
     return out
 
 
+def two_stage_valid(y: np.ndarray, k: np.ndarray, b_gpu: np.ndarray, B: int, W: int, bits_per_sym: int,
+                    S: int) -> np.ndarray:
+    """Whether each GPU index b_gpu[i] of symbol k[i] is a valid two-stage
+    result under the oracle's own costs (see the module docstring)."""
+    C = B // S
+    phi = O.bps_angles(B)[::S]
+    ok = np.zeros(k.size, dtype=bool)
+    for i, kk in enumerate(k):
+        Dc = O.bps_costs(y, phi, W, bits_per_sym, int(kk), int(kk) + 1)[0]
+        dmin = Dc.min()
+        for j in np.nonzero(Dc - dmin <= TIE * dmin)[0]:
+            Dm, D0, Dp = Dc[(j - 1) % C], Dc[j], Dc[(j + 1) % C]
+            c = Dm - 2.0 * D0 + Dp
+            if c > 0:
+                x = S * float(np.clip((Dm - Dp) / (2.0 * c), -0.5, 0.5))
+                tol = 3.0 * S * TIE * max(Dm, D0, Dp) / c
+            else:
+                x, tol = 0.0, 0.0
+            for r in range(int(math.floor(x - tol + 0.5)), int(math.floor(x + tol + 0.5)) + 1):
+                r = min(max(r, -(S // 2)), S // 2)
+                if (S * j + r) % B == b_gpu[i]:
+                    ok[i] = True
+    return ok
+
+
 def compare(gpu: dict, ref: dict, rx_kw: dict, check_bits=True) -> dict:
     """All parity checks; returns a report (asserts on failure)."""
     B = rx_kw.get("bps_angles", 64)
     W = rx_kw.get("bps_half_window", 16)
     bps = rx_kw.get("modulation", 2)
+    S = rx_kw.get("bps_coarse_stride", 1)
     rep = {}
     y_err = rel_rms(gpu["y"], ref["y"])
     rep["y_rel_rms"] = y_err
@@ -110,7 +141,11 @@ def compare(gpu: dict, ref: dict, rx_kw: dict, check_bits=True) -> dict:
     tie = np.zeros_like(bh_o, dtype=bool)
     for p in range(2):
         diff = np.nonzero(bh_g[p] != bh_o[p])[0]
-        if diff.size:
+        if diff.size and S > 1:
+            ok = two_stage_valid(ref["y"][p], diff, bh_g[p][diff], B, W, bps, S)
+            assert ok.all(), f"pol {p}: {np.sum(~ok)} two-stage BPS indices are not near-ties"
+            tie[p, diff] = True
+        elif diff.size:
             D = oracle_bps_metric(ref["y"][p], diff, B, W, bps)
             dmin = D.min(axis=1)
             dg = D[np.arange(diff.size), bh_g[p][diff]]

@@ -54,6 +54,7 @@ def test_defaults(lib):
     c = rx.default_config()
     assert c.baud_hz == 28e9 and c.modulation == rx.RX_QPSK and c.mimo_taps == 15
     assert c.bps_angles == 64 and c.bps_half_window == 16 and c.sub_block_syms == 64
+    assert c.bps_coarse_stride == 1
     assert c.frame_syms == 65536 and c.seg_syms == 512 and c.storage_dtype == rx.RX_C64
 
 
@@ -62,6 +63,8 @@ def test_defaults(lib):
     ("mimo_taps", 33, "mimo_taps"),
     ("bps_angles", 48, "bps_angles"),
     ("bps_half_window", 5, "bps_half_window"),
+    ("bps_coarse_stride", 2, "bps_coarse_stride"),   # QPSK with 64 angles: 1 or 4
+    ("bps_coarse_stride", 8, "bps_coarse_stride"),
     ("sub_block_syms", 32, "sub_block_syms"),
     ("seg_syms", 100, "seg_syms"),
     ("frame_syms", 1000, "frame_syms"),

@@ -16,14 +16,19 @@ def link(**kw):
     return rxsim.LinkConfig(**kw)
 
 
-def test_config0_parity():
+STRIDES = pytest.mark.parametrize("stride", [1, 4], ids=["full_bps", "two_stage_bps"])
+
+
+@STRIDES
+def test_config0_parity(stride):
     """DP-QPSK 28 GBd, 2^16 symbols, complex128 input, 1,000 km, all
-    impairments at 12 dB: one frame, pushed whole."""
+    impairments at 12 dB: one frame, pushed whole (full and two-stage BPS)."""
     wl = workloads.DP_QPSK_1000KM
+    rx_kw = dict(wl["rx"], bps_coarse_stride=stride)
     sim = rxsim.simulate(link(**wl["link"]))
-    gpu, r = run_gpu(sim["rx"], wl["rx"])
-    ref = run_oracle(sim["rx"], wl["rx"])
-    rep = compare(gpu, ref, wl["rx"])
+    gpu, r = run_gpu(sim["rx"], rx_kw)
+    ref = run_oracle(sim["rx"], rx_kw)
+    rep = compare(gpu, ref, rx_kw)
     st = gpu["stats"]
     b = ref["ber"]
     assert st["synced"] == 1
@@ -39,7 +44,8 @@ def test_config0_parity():
     r.close()
 
 
-def test_multi_frame_ragged_pushes():
+@STRIDES
+def test_multi_frame_ragged_pushes(stride):
     """Four frames plus a ragged tail, pushed in irregular blocks: state
     (OLS overlap, FO phase, timing, adaptive chains, BPS window, unwrap)
     carried across pushes and frames."""
@@ -48,7 +54,7 @@ def test_multi_frame_ragged_pushes():
     sim = rxsim.simulate(link(n_sym=n_sym, snr_db=11.0, fiber_len_m=2000e3, prbs_seed=31, seed=1234,
                               out_dtype="c64"))
     rx_kw = dict(fiber_len_m=2000e3, frame_syms=F, acq_syms=F, cma_syms=4096, prbs_seed=31, seg_syms=512,
-                 ber_skip_syms=2048, sync_syms=2048)
+                 ber_skip_syms=2048, sync_syms=2048, bps_coarse_stride=stride)
     n = sim["rx"].shape[1]
     pushes = []
     rng = np.random.default_rng(3)
@@ -71,7 +77,8 @@ def test_multi_frame_ragged_pushes():
     r.close()
 
 
-def test_cycle_slips_counted_like_the_oracle():
+@STRIDES
+def test_cycle_slips_counted_like_the_oracle(stride):
     """Abrupt +-pi/2 and pi carrier steps (1 km: no dispersion to smear
     them) in a four-frame stream at 13 dB, one of them at a frame boundary:
     the GPU's slip pass (a chunk of windows run in parallel from every start
@@ -83,7 +90,7 @@ def test_cycle_slips_counted_like_the_oracle():
     sim = rxsim.simulate(link(n_sym=n_sym, snr_db=13.0, fiber_len_m=1e3, prbs_seed=9, seed=77, out_dtype="c64",
                               phase_jumps=jumps))
     rx_kw = dict(fiber_len_m=1e3, frame_syms=F, acq_syms=F, cma_syms=4096, prbs_seed=9, ber_skip_syms=2048,
-                 sync_syms=2048)
+                 sync_syms=2048, bps_coarse_stride=stride)
     gpu, r = run_gpu(sim["rx"], rx_kw)
     ref = run_oracle(sim["rx"], rx_kw)
     rep = compare(gpu, ref, rx_kw)
@@ -95,12 +102,14 @@ def test_cycle_slips_counted_like_the_oracle():
     r.close()
 
 
-def test_qam16_parity():
-    """DP-16QAM 32 GBd, T = 25, B = 32, W = 32 over 5,000 km at 18 dB."""
+@STRIDES
+def test_qam16_parity(stride):
+    """DP-16QAM 32 GBd, T = 25, B = 32, W = 32 over 5,000 km at 18 dB (full
+    search, and two-stage over 8 coarse angles)."""
     sim = rxsim.simulate(link(baud_hz=32e9, bits_per_sym=4, n_sym=1 << 15, fiber_len_m=5000e3, snr_db=18.0,
                               prbs_seed=17, seed=1002, out_dtype="c64"))
     rx_kw = dict(baud_hz=32e9, modulation=4, fiber_len_m=5000e3, mimo_taps=25, bps_angles=32,
-                 bps_half_window=32, frame_syms=1 << 15, prbs_seed=17, mu_dd=2e-3)
+                 bps_half_window=32, frame_syms=1 << 15, prbs_seed=17, mu_dd=2e-3, bps_coarse_stride=stride)
     gpu, r = run_gpu(sim["rx"], rx_kw)
     ref = run_oracle(sim["rx"], rx_kw)
     compare(gpu, ref, rx_kw)

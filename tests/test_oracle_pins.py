@@ -263,6 +263,21 @@ def test_two_stage_recovers_an_off_grid_phase_to_one_fine_step(bps_):
         assert np.mean(err) <= np.mean(full) + 0.05 * step
 
 
+def test_two_stage_parity_rule_accepts_the_oracle_and_rejects_a_coarse_step():
+    """The GPU parity rule for two-stage indices (tests/parity_util.py)
+    accepts the oracle's own result and rejects it moved by one coarse step
+    except where that step is a near-tie."""
+    from parity_util import two_stage_valid
+    rng = np.random.default_rng(23)
+    B, W, S = 64, 16, 4
+    bits = rng.integers(0, 2, 600 * 2).astype(np.uint8)
+    y = rxsim.gray_map(bits, 2) * np.exp(0.3j) + 0.2 * (rng.standard_normal(600) + 1j * rng.standard_normal(600))
+    b = O.bps_two_stage(y, B, W, 2, S)
+    k = np.arange(0, 600, 7)
+    assert two_stage_valid(y, k, b[k], B, W, 2, S).all()
+    assert two_stage_valid(y, k, (b[k] + S) % B, B, W, 2, S).mean() < 0.05
+
+
 def test_unwrap_follows_a_ramp_across_quadrants():
     rng = np.random.default_rng(10)
     n, B = 20000, 64
