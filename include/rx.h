@@ -358,6 +358,74 @@ int rx_server_stats(rx_server* s, rx_server_stats_t* out);
 /* Stops the worker, closes every stream and frees the server. */
 int rx_server_destroy(rx_server* s);
 
+/* ---- Kramers-Kronig front end (paper Sec. II) ------------------------------
+ *
+ * The paper's own receiver detects a single-polarisation minimum-phase
+ * signal (a carrier tone plus QAM on one side of it) with one photodiode
+ * and a 12-bit ADC, and recovers the optical field with the Kramers-Kronig
+ * relations.  Per sample t of the stream:
+ *
+ *   I_t = adc_gain (code_t - adc_offset)             (12-bit fixed point to float)
+ *   u_t = ln(max(I_t, adc_gain / 2)) / 2              (log amplitude)
+ *   phi = Hilbert transform of u in 100 % overlap-save blocks of N = fft_n
+ *         samples: segment b holds outputs [b N/2, (b+1) N/2) and is taken
+ *         from samples N/4 .. 3N/4 - 1 of the block over [b N/2 - N/4,
+ *         b N/2 + 3N/4) (u = 0 outside the stream), whose DFT is multiplied
+ *         by -j sgn(k) (0 at k = 0 and N/2)
+ *   E_t = exp(u_t + j phi_t) exp(-j 2 pi (f_shift_hz / fs_hz) t)   (field, downshifted)
+ *
+ * Output: complex64 field samples (re, im interleaved) in device memory, in
+ * stream order.  A segment is written once the input reaches the end of its
+ * block, so the output lags the input by N/4 to 3N/4 - 1 samples until
+ * rx_kk_end writes the rest. */
+typedef struct rx_kk_config {
+  double fs_hz;            /* ADC sample rate */
+  double f_shift_hz;       /* downshift frequency: signal centre above the carrier */
+  double adc_gain;         /* intensity per ADC code (> 0) */
+  double adc_offset;       /* ADC code of zero intensity */
+  int fft_n;               /* N: 1024 (the paper's), 2048 or 4096 */
+  size_t max_block_samples;/* largest n accepted by one rx_kk_push */
+  int device;              /* CUDA device ordinal */
+} rx_kk_config;
+
+typedef struct rx_kk rx_kk;
+
+/* Defaults: 4 GS/s, shift 0.516 GHz, gain 1, offset 0, N = 1024, 2^22-sample
+ * pushes (the paper's buffer), device 0. */
+void rx_kk_config_default(rx_kk_config* cfg);
+
+/* Validates cfg (RX_EINVAL naming the field), allocates the device state
+ * (carry of the previous block's samples, staging for host pushes, FFT
+ * twiddles) on cfg->device.  *out receives the handle; free with
+ * rx_kk_destroy. */
+int rx_kk_create(const rx_kk_config* cfg, rx_kk** out);
+
+/* Appends n ADC codes (int16, the 12-bit values).  on_device: 1 = codes is
+ * a device pointer read in stream order; 0 = host memory copied in stream
+ * order (page-locked memory is copied without a host wait and must stay
+ * unchanged until the stream passes the copy; pageable memory is staged
+ * before the call returns).  Writes the field of every newly complete
+ * segment to out (device, complex64), *n_out samples, in stream order on
+ * cuda_stream (NULL: the legacy default stream).  RX_EINVAL if n exceeds
+ * max_block_samples or out_cap (complex samples) is smaller than *n_out
+ * would be (at most n + fft_n/2 - 1); RX_ESTATE after rx_kk_end. */
+int rx_kk_push(rx_kk* h, const int16_t* codes, size_t n, int on_device, float* out, size_t out_cap,
+               size_t* n_out, void* cuda_stream);
+
+/* End of stream: writes the field of the remaining samples (at most
+ * 3 fft_n/4 - 1) to out, *n_out of them; input past the end counts as
+ * absent. */
+int rx_kk_end(rx_kk* h, float* out, size_t out_cap, size_t* n_out, void* cuda_stream);
+
+/* Starts a new stream on the same handle (stream order: call after the
+ * previous stream's work, or on the same CUDA stream). */
+int rx_kk_reset(rx_kk* h);
+
+/* Samples pushed and field samples written so far. */
+int rx_kk_position(const rx_kk* h, int64_t* samples_in, int64_t* samples_out);
+
+void rx_kk_destroy(rx_kk* h);
+
 #ifdef __cplusplus
 }
 #endif

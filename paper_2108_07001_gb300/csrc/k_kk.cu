@@ -13,9 +13,14 @@
 // segments.  The Hilbert transform has a real kernel, so the two real
 // blocks go through one complex FFT pair as u_a + j u_b: the real part of
 // the result is phi_a, the imaginary part phi_b.  u is staged once for the
-// pair's 3L-sample union; the output takes exp(u) and one sincos of
-// phi - 2 pi frac(nu t), where frac(nu t) comes from an exact 64-bit
-// fixed-point product (nu quantised to 2^-64; no drift over the stream).
+// pair's 3L-sample union (16-byte loads of 8 codes when the union lies in
+// the push), in log2 units: u2 = u / ln 2, |E| = 2^u2, and the factor
+// ln 2 / pi rides on the Hilbert multiplier so the transform returns
+// phi / pi.  The output takes one sincospi of phi / pi - 2 frac(nu t),
+// where frac(nu t) comes from an exact 64-bit fixed-point product (nu
+// quantised to 2^-64; no drift over the stream).
+#include <algorithm>
+
 #include "fft_smem.cuh"
 #include "kk_internal.h"
 
@@ -30,27 +35,58 @@ __device__ __forceinline__ bool kk_code(const KKArgs& a, long long i, float& cod
   return true;
 }
 
+// Dynamic shared memory: the FFT buffer (N float2), then u of the pair's
+// 3N/2-sample union.
+template <int N>
+constexpr size_t kk_smem_bytes() { return (size_t)N * 8 + (size_t)3 * (N / 2) * 4; }
+
 template <int N>
 __global__ void __launch_bounds__(N / 16) kk_kernel(KKArgs a) {
   constexpr int NT = N / 16, L = N / 2, U = 3 * L;
-  __shared__ __align__(16) float2 buf[N];
-  __shared__ float u_s[U];
+  static_assert(U / 8 == 3 * NT, "three 8-code vectors per thread");
+  extern __shared__ __align__(16) float2 kk_smem[];
+  float2* buf = kk_smem;
+  float* u_s = reinterpret_cast<float*>(kk_smem + N);
   __shared__ float2 tw_s[2 * kTwSplit];
   for (int i = threadIdx.x; i < 2 * kTwSplit; i += NT) tw_s[i] = a.tw2[i];
 
   const long long seg = a.seg0 + 2LL * blockIdx.x;   // first segment of the pair
   const long long lo = seg * L - N / 4;              // stream index of u_s[0]
-  for (int i = threadIdx.x; i < U; i += NT) {
-    float code;
-    const bool in = kk_code(a, lo + i, code);
-    u_s[i] = in ? 0.5f * logf(fmaxf(a.gain * (code - a.offset), a.i_min)) : 0.f;
+  auto u2_of = [&](float code) { return 0.5f * log2f(fmaxf(a.gain * (code - a.offset), a.i_min)); };
+  const long long off = lo - a.new_start;
+  if (off >= 0 && lo + U <= a.in_end && (off & 7) == 0 && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0) {
+    // the union lies in this push, 16-byte aligned: 8 codes per load
+    // U / 8 = 3 NT vectors: three per thread, all loads issued first
+    const int4* src = reinterpret_cast<const int4*>(a.in + off);
+    float4* dst = reinterpret_cast<float4*>(u_s);
+    int4 w[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) w[r] = __ldg(src + threadIdx.x + r * NT);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int v = threadIdx.x + r * NT;
+      const int c[4] = {w[r].x, w[r].y, w[r].z, w[r].w};
+      float f[8];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        f[2 * j] = u2_of((float)(short)(c[j] & 0xffff));
+        f[2 * j + 1] = u2_of((float)(c[j] >> 16));
+      }
+      dst[2 * v] = make_float4(f[0], f[1], f[2], f[3]);
+      dst[2 * v + 1] = make_float4(f[4], f[5], f[6], f[7]);
+    }
+  } else {
+    for (int i = threadIdx.x; i < U; i += NT) {
+      float code;
+      u_s[i] = kk_code(a, lo + i, code) ? u2_of(code) : 0.f;
+    }
   }
   __syncthreads();
   for (int n = threadIdx.x; n < N; n += NT) buf[swz(n)] = make_float2(u_s[n], u_s[n + L]);
   __syncthreads();
   fft_smem<N, NT, false>(buf, tw_s, 1);
-  // -j sgn(k) / N (the inverse transform is unnormalised)
-  const float s = 1.f / (float)N;
+  // -j sgn(k) ln2 / (pi N): the inverse transform is unnormalised and u is in log2 units
+  constexpr float s = 0.693147180559945309f / (3.14159265358979324f * (float)N);
   for (int k = threadIdx.x; k < N; k += NT) {
     const float2 v = buf[swz(k)];
     float2 r;
@@ -68,13 +104,12 @@ __global__ void __launch_bounds__(N / 16) kk_kernel(KKArgs a) {
       const long long t = (seg + h) * L + n;
       if (t >= a.out_end) break;
       const float2 v = buf[swz(n + N / 4)];
-      const float phi = h == 0 ? v.x : v.y;
-      const float u = u_s[h * L + n + N / 4];
+      const float phi_pi = h == 0 ? v.x : v.y;                        // phi / pi
       const unsigned long long p = a.nu_fx * (unsigned long long)t;  // frac(nu t) in 2^-64
-      const float cyc = (float)(p >> 40) * 0x1p-24f;
+      const float cyc = (float)(p >> 40) * 0x1p-23f;                 // 2 frac(nu t)
       float sn, cs;
-      sincosf(phi - 6.28318530717958648f * cyc, &sn, &cs);
-      const float m = expf(u);
+      sincospif(phi_pi - cyc, &sn, &cs);
+      const float m = exp2f(u_s[h * L + n + N / 4]);
       a.out[t - a.out_start] = make_float2(m * cs, m * sn);
     }
   }
@@ -89,16 +124,27 @@ __global__ void kk_carry_kernel(KKArgs a, int16_t* dst, long long keep_from) {
   }
 }
 
+template <int N>
+static cudaError_t launch_kk_t(const KKArgs& a, unsigned blocks, cudaStream_t s) {
+  constexpr size_t bytes = kk_smem_bytes<N>();
+  if (bytes > 48 * 1024) {  // opt in above the default (once per process)
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(kk_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (attr != cudaSuccess) return attr;
+  }
+  kk_kernel<N><<<blocks, N / 16, bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_kk(const KKArgs& a, int N, long long nseg, cudaStream_t s) {
   if (nseg <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((nseg + 1) / 2);
   switch (N) {
-    case 1024: kk_kernel<1024><<<blocks, 64, 0, s>>>(a); break;
-    case 2048: kk_kernel<2048><<<blocks, 128, 0, s>>>(a); break;
-    case 4096: kk_kernel<4096><<<blocks, 256, 0, s>>>(a); break;
+    case 1024: return launch_kk_t<1024>(a, blocks, s);
+    case 2048: return launch_kk_t<2048>(a, blocks, s);
+    case 4096: return launch_kk_t<4096>(a, blocks, s);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_kk_carry(const KKArgs& a, int16_t* dst, long long keep_from, cudaStream_t s) {

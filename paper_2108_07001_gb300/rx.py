@@ -35,7 +35,9 @@ EXPORTS = ["rx_config_default", "rx_create", "rx_push_block", "rx_pull_bits", "r
            "rx_server_config_default", "rx_server_create", "rx_server_open", "rx_server_submit",
            "rx_server_end", "rx_server_sync", "rx_server_pull_bits", "rx_server_stream_stats",
            "rx_server_handle", "rx_server_close", "rx_server_stats", "rx_server_destroy",
-           "rx_autotune_fft"]
+           "rx_autotune_fft",
+           "rx_kk_config_default", "rx_kk_create", "rx_kk_push", "rx_kk_end", "rx_kk_reset",
+           "rx_kk_position", "rx_kk_destroy"]
 
 
 class RxConfig(ctypes.Structure):
@@ -69,6 +71,19 @@ class RxConfig(ctypes.Structure):
         ("max_block_samples", ctypes.c_size_t),
         ("history_syms", ctypes.c_int64),
         ("profile", ctypes.c_int),
+        ("device", ctypes.c_int),
+    ]
+
+
+class KKConfig(ctypes.Structure):
+    """rx_kk_config: the Kramers-Kronig front end."""
+    _fields_ = [
+        ("fs_hz", ctypes.c_double),
+        ("f_shift_hz", ctypes.c_double),
+        ("adc_gain", ctypes.c_double),
+        ("adc_offset", ctypes.c_double),
+        ("fft_n", ctypes.c_int),
+        ("max_block_samples", ctypes.c_size_t),
         ("device", ctypes.c_int),
     ]
 
@@ -177,11 +192,21 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rx_server_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
     lib.rx_server_destroy.argtypes = [P]
     lib.rx_autotune_fft.argtypes = [ctypes.POINTER(RxConfig), I, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double)]
+    lib.rx_kk_config_default.argtypes = [ctypes.POINTER(KKConfig)]
+    lib.rx_kk_config_default.restype = None
+    lib.rx_kk_create.argtypes = [ctypes.POINTER(KKConfig), ctypes.POINTER(P)]
+    lib.rx_kk_push.argtypes = [P, P, SZ, I, P, SZ, ctypes.POINTER(SZ), P]
+    lib.rx_kk_end.argtypes = [P, P, SZ, ctypes.POINTER(SZ), P]
+    lib.rx_kk_reset.argtypes = [P]
+    lib.rx_kk_position.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    lib.rx_kk_destroy.argtypes = [P]
+    lib.rx_kk_destroy.restype = None
     for name in ["rx_create", "rx_push_block", "rx_pull_bits", "rx_stats", "rx_destroy", "rx_reset",
                  "rx_join", "rx_stage_times", "rx_frame_trace", "rx_get_taps", "rx_get_equalised",
                  "rx_get_phase", "rx_decide_block_noalloc", "rx_server_create", "rx_server_open",
                  "rx_server_end", "rx_server_sync", "rx_server_pull_bits", "rx_server_stream_stats",
-                 "rx_server_close", "rx_server_stats", "rx_server_destroy", "rx_autotune_fft"]:
+                 "rx_server_close", "rx_server_stats", "rx_server_destroy", "rx_autotune_fft",
+                 "rx_kk_create", "rx_kk_push", "rx_kk_end", "rx_kk_reset", "rx_kk_position"]:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -445,3 +470,88 @@ def autotune_fft(cfg: RxConfig | None = None, frames: int = 3, **overrides) -> t
     ms = ctypes.c_double()
     _check(load().rx_autotune_fft(ctypes.byref(cfg), frames, ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
+
+
+def default_kk_config(**overrides) -> KKConfig:
+    cfg = KKConfig()
+    load().rx_kk_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise KeyError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+class KKFrontEnd:
+    """Kramers-Kronig front end (rx_kk_create ... rx_kk_destroy): int16 ADC
+    codes in, the downshifted complex64 field out, both in device memory."""
+
+    def __init__(self, cfg: KKConfig | None = None, **overrides):
+        self.lib = load()
+        self.cfg = cfg if cfg is not None else default_kk_config(**overrides)
+        h = ctypes.c_void_p()
+        _check(self.lib.rx_kk_create(ctypes.byref(self.cfg), ctypes.byref(h)))
+        self.h = h
+
+    def push_device(self, codes_ptr: int, n: int, out_ptr: int, out_cap: int, stream: int = 0) -> int:
+        """Codes at a device pointer; returns the field samples written at out_ptr."""
+        n_out = ctypes.c_size_t()
+        _check(self.lib.rx_kk_push(self.h, ctypes.c_void_p(codes_ptr), n, 1, ctypes.c_void_p(out_ptr), out_cap,
+                                   ctypes.byref(n_out), ctypes.c_void_p(stream)))
+        return n_out.value
+
+    def push_host(self, codes: np.ndarray, out_ptr: int, out_cap: int, stream: int = 0) -> int:
+        """Codes from a host int16 array (copied in stream order)."""
+        codes = np.ascontiguousarray(codes, dtype=np.int16)
+        n_out = ctypes.c_size_t()
+        _check(self.lib.rx_kk_push(self.h, codes.ctypes.data_as(ctypes.c_void_p), codes.size, 0,
+                                   ctypes.c_void_p(out_ptr), out_cap, ctypes.byref(n_out), ctypes.c_void_p(stream)))
+        return n_out.value
+
+    def push_tensor(self, codes, out, stream: int | None = None) -> int:
+        """codes: int16 CUDA tensor; out: complex64 CUDA tensor with room for the
+        samples this push completes.  Returns how many were written to out[:n]."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        assert codes.is_cuda and codes.dtype == torch.int16 and codes.is_contiguous()
+        assert out.is_cuda and out.dtype == torch.complex64 and out.is_contiguous()
+        return self.push_device(codes.data_ptr(), codes.numel(), out.data_ptr(), out.numel(), stream)
+
+    def end_tensor(self, out, stream: int | None = None) -> int:
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        assert out.is_cuda and out.dtype == torch.complex64 and out.is_contiguous()
+        return self.end(out.data_ptr(), out.numel(), stream)
+
+    def end(self, out_ptr: int, out_cap: int, stream: int = 0) -> int:
+        n_out = ctypes.c_size_t()
+        _check(self.lib.rx_kk_end(self.h, ctypes.c_void_p(out_ptr), out_cap, ctypes.byref(n_out),
+                                  ctypes.c_void_p(stream)))
+        return n_out.value
+
+    def reset(self) -> None:
+        _check(self.lib.rx_kk_reset(self.h))
+
+    def position(self) -> tuple[int, int]:
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(self.lib.rx_kk_position(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.rx_kk_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

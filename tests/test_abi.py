@@ -170,3 +170,38 @@ def test_autotune_argument_checks_without_device(lib):
     far = rx.default_config(fiber_len_m=100000e3)  # halo longer than any FFT size
     assert lib.rx_autotune_fft(ctypes.byref(far), 3, ctypes.byref(n), None) == rx.RX_EINVAL
     assert b"halo" in lib.rx_last_error()
+
+
+def test_kk_struct_layout_matches_c(tmp_path, lib):
+    from paper_2108_07001_gb300 import rx
+    src = tmp_path / "klayout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "rx.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu\\n\", sizeof(rx_kk_config), offsetof(rx_kk_config, fft_n),"
+        " offsetof(rx_kk_config, max_block_samples), offsetof(rx_kk_config, device)); return 0;}\n")
+    exe = tmp_path / "klayout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals == [ctypes.sizeof(rx.KKConfig), rx.KKConfig.fft_n.offset, rx.KKConfig.max_block_samples.offset,
+                    rx.KKConfig.device.offset]
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("fft_n", 512, "fft_n"),
+    ("fft_n", 3000, "fft_n"),
+    ("fs_hz", 0.0, "fs_hz"),
+    ("adc_gain", -1.0, "adc_gain"),
+    ("max_block_samples", 0, "max_block_samples"),
+])
+def test_kk_config_checks_without_device(lib, field, value, msg):
+    from paper_2108_07001_gb300 import rx
+    c = rx.default_kk_config()
+    assert (c.fs_hz, c.f_shift_hz, c.fft_n, c.max_block_samples) == (4e9, 0.516e9, 1024, 1 << 22)
+    bad = rx.default_kk_config(**{field: value})
+    h = ctypes.c_void_p()
+    assert lib.rx_kk_create(ctypes.byref(bad), ctypes.byref(h)) == rx.RX_EINVAL
+    assert msg in lib.rx_last_error().decode()
+    assert not h.value
+    n = ctypes.c_size_t()
+    assert lib.rx_kk_push(None, None, 0, 1, None, 0, ctypes.byref(n), None) == rx.RX_EINVAL
+    assert lib.rx_kk_end(None, None, 0, ctypes.byref(n), None) == rx.RX_EINVAL
