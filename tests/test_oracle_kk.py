@@ -114,3 +114,101 @@ def test_impulse_response_follows_the_block_geometry():
                 if m % 2:
                     want[t] = 2.0 / N / math.tan(math.pi * m / N)
         assert np.max(np.abs(phi - want)) < 1e-13, p
+
+
+def test_rrc_amplitude_values():
+    f = np.array([0.0, 0.3, 0.494, 0.5, 0.506, 2.0]) * 1e9
+    h = K.rrc_amplitude(f, 1e9, 0.01)
+    assert np.allclose(h, [1.0, 1.0, 1.0, math.sqrt(0.5), 0.0, 0.0], atol=1e-12)
+
+
+def test_static_eq_with_unit_response_decimates_a_band_limited_signal():
+    """Tones on the block's bin grid inside |f| < fs/4: every interior block
+    sees whole periods, and cutting the band then halving the DFT size is
+    exact decimation, x2[m] = x4[2m]."""
+    rng = np.random.default_rng(8)
+    N4 = 1024
+    n4 = 12 * N4
+    t = np.arange(n4)
+    x4 = np.zeros(n4, dtype=np.complex128)
+    for k in rng.integers(-N4 // 4 + 1, N4 // 4, 12):
+        x4 += (rng.standard_normal() + 1j * rng.standard_normal()) * np.exp(2j * math.pi * k * t / N4)
+    x2 = K.static_eq_resample(x4, np.ones(N4 // 2, dtype=np.complex128))
+    sl = slice(N4 // 4, x2.size - N4 // 2)
+    assert np.max(np.abs(x2[sl] - x4[::2][sl])) < 1e-11
+
+
+def test_static_eq_undoes_the_simulated_dispersion():
+    """The simulator's field (dispersed with the carrier at DC) downshifted:
+    with the matched filter made all-pass (a symbol rate far above the band)
+    the equaliser is the CD compensation alone (about a sample of spread and
+    a 0.56-sample delay from the carrier offset at 2,000 km; overlap-save
+    leaves the ringing of the phase's band-edge step, ~1e-3), and it returns
+    the undispersed carrier tone plus signal at every other sample
+    (whole-array reference); no compensation, or the opposite sign, is two
+    orders of magnitude worse."""
+    d = rxsim.simulate_kk(rxsim.KKLinkConfig(n_sym=1 << 12, snr_db=None, fiber_len_m=2000e3, seed=5))
+    fs, fc = d["fs"], d["f_c"]
+    t = np.arange(d["field"].size)
+    down = np.exp(-2j * math.pi * fc / fs * t)
+    b2 = rxsim.beta2_from_dispersion(17.0, 1550e-9)
+    N4 = 1024
+    H = K.static_eq_response(N4, fs, 1e12, 0.01, b2, 2000e3, fc)
+    x2 = K.static_eq_resample(d["field"] * down, H)
+    ref = ((d["carrier"] + d["signal"] * np.exp(2j * math.pi * fc / fs * t)) * down)[::2]
+    sl = slice(N4 // 2, x2.size - N4)
+    top = np.max(np.abs(ref))
+    assert np.max(np.abs(x2[sl] - ref[sl])) < 2e-3 * top
+    x0 = K.static_eq_resample(d["field"] * down, np.ones(N4 // 2, dtype=np.complex128))
+    assert np.max(np.abs(x0[sl] - ref[sl])) > 0.1 * top
+    xm = K.static_eq_resample(d["field"] * down, K.static_eq_response(N4, fs, 1e12, 0.01, b2, -2000e3, fc))
+    assert np.max(np.abs(xm[sl] - ref[sl])) > 0.1 * top
+
+
+def ideal_2sps(n_sym, bits_per_sym, seed):
+    """Raised-cosine (RRC x RRC, roll-off 0.5) QPSK/16QAM at 2 samples per
+    symbol, symbols at the even samples; returns (signal, symbols)."""
+    rng = np.random.default_rng(seed)
+    bits = rng.integers(0, 2, n_sym * bits_per_sym).astype(np.uint8)
+    sym = rxsim.gray_map(bits, bits_per_sym)
+    up = np.zeros(2 * n_sym, dtype=np.complex128)
+    up[::2] = sym
+    f = np.fft.fftfreq(2 * n_sym, d=0.5)
+    x = np.fft.ifft(np.fft.fft(up) * K.rrc_amplitude(f, 1.0, 0.5) ** 2) * 2
+    return x, sym
+
+
+def test_widely_linear_equaliser_removes_iq_imbalance():
+    """x = s + beta conj(s) (modulator IQ imbalance): the widely-linear DD-LMS
+    drives the residual far below |beta|^2, where a strictly linear one
+    (h2 = 0) stays (the conjugate term is orthogonal to every linear
+    filter of s); a sign error in either gradient would not converge."""
+    x, sym = ideal_2sps(1 << 14, 2, 11)
+    beta = 0.12 * np.exp(0.7j)
+    xi = x + beta * np.conj(x)
+    res = {}
+    for lin in (False, True):
+        y, _ = K.wl_equalise(xi, sym.size, 2, 5e-2, 64, 512, 1 << 13, 8192, linear_only=lin)
+        res[lin] = float(np.mean(np.abs(y[8192:] - sym[8192:]) ** 2))
+    assert res[False] < 2e-4
+    assert abs(res[True] - abs(beta) ** 2) < 0.1 * abs(beta) ** 2
+
+
+def test_widely_linear_equaliser_keeps_an_ideal_input():
+    x, sym = ideal_2sps(1 << 13, 4, 12)
+    y, chains = K.wl_equalise(x, sym.size, 4, 2e-3, 64, 512, 1 << 12, 4096)
+    assert np.max(np.abs(y - sym)) < 1e-6
+    h1, h2 = chains[0]
+    assert abs(h1[K.WL_CENTRE] - 1) < 1e-6 and np.max(np.abs(h2)) < 1e-6
+
+
+def test_noiseless_kk_link_decodes_without_errors():
+    d = rxsim.simulate_kk(rxsim.KKLinkConfig(n_sym=1 << 14, snr_db=None, cspr_db=14.0, fiber_len_m=1000e3,
+                                             seed=13, prbs_seed=13))
+    b2 = rxsim.beta2_from_dispersion(17.0, 1550e-9)
+    r = K.kk_receive(d["codes"], d["gain"], d["offset"], d["fs"], d["f_c"], 1024, 1024, 1e9, 0.01, b2, 1000e3,
+                     2, 5e-3, 64, 512, 1 << 13, 4096)
+    # the first and last 64 symbols see blocks that run past the stream's
+    # ends (zero-padded log amplitude and field)
+    a, e = 2 * 64, r["bits"].size - 2 * 64
+    assert np.array_equal(r["bits"][a:e], d["bits"][a:e])
