@@ -426,6 +426,76 @@ int rx_kk_position(const rx_kk* h, int64_t* samples_in, int64_t* samples_out);
 
 void rx_kk_destroy(rx_kk* h);
 
+/* ---- KK receiver chain (paper Sec. II) -------------------------------------
+ *
+ * The rest of the paper's single-polarisation receiver after the KK front
+ * end: the downshifted field at 4 samples per symbol goes through
+ *
+ *   a static equaliser with resampling to 2 samples per symbol: 100 %
+ *     overlap-save blocks of eq_fft_n samples (N4) advancing by N4/2; each
+ *     block's DFT is cut to the 2-sps band (bins -N4/4 .. N4/4 - 1) and
+ *     multiplied by the CD compensation exp(+j beta2 L w^2 / 2), w = 2 pi
+ *     (f + f_shift) (the dispersion acted with the carrier at DC), times the
+ *     RRC matched filter; an N4/2-point inverse DFT gives 2-sps outputs
+ *     [b N4/4, (b+1) N4/4) from its samples N4/8 .. 3N4/8 - 1;
+ *   a widely-linear DD-LMS equaliser with 4 taps at 2 samples per symbol,
+ *     y_k = sum_t h1[t] x[2k+t-1] + h2[t] conj(x[2k+t-1]): block-LMS over
+ *     sub-blocks of 64 symbols (e = y - dec(y), h1 -= mu mean(e conj x),
+ *     h2 -= mu mean(e x)); one sequential acquisition chain over the first
+ *     acq_syms symbols from h1 = unit tap at offset 0, h2 = 0, then frames
+ *     of frame_syms symbols cut into segments of seg_syms, each continuing
+ *     its own taps from the previous frame;
+ *   hard decisions and Gray demapping to packed bits (symbol-major, I bits
+ *     then Q bits, MSB first; QPSK - -> 1, + -> 0; 16QAM -3, -1, 1, 3 ->
+ *     00, 01, 11, 10 at unit symbol energy). */
+typedef struct rx_kkrx_config {
+  rx_kk_config fe;         /* the front end; fe.fs_hz must be 4 x baud_hz */
+  double baud_hz;          /* symbol rate */
+  int modulation;          /* RX_QPSK or RX_QAM16 */
+  double fiber_len_m;      /* L for the CD compensation */
+  double D_ps_nm_km;       /* dispersion parameter */
+  double lambda_m;         /* carrier wavelength */
+  double rrc_rolloff;      /* matched filter roll-off (paper: 0.01) */
+  int eq_fft_n;            /* N4: 1024 or 2048 */
+  float mu;                /* DD-LMS step size */
+  int seg_syms;            /* S: multiple of 64 */
+  int frame_syms;          /* F: multiple of S, at most 2^24 */
+  int acq_syms;            /* acquisition chain length, multiple of 64, <= F */
+  int64_t history_syms;    /* keep the equalised symbols of the first history_syms
+                              symbols for rx_kkrx_equalised; 0: off */
+} rx_kkrx_config;
+
+typedef struct rx_kkrx rx_kkrx;
+
+/* Defaults: the front end's defaults, 1 GBd QPSK, no fibre, D = 17 at
+ * 1550 nm, roll-off 0.01, N4 = 1024, mu 5e-3, S = 512, F = 2^20 (one 2^22-
+ * sample ADC buffer per frame), acquisition 8192 symbols, no history. */
+void rx_kkrx_config_default(rx_kkrx_config* cfg);
+
+/* Validates cfg (RX_EINVAL naming the field) and allocates the chain on
+ * cfg->fe.device; free with rx_kkrx_destroy. */
+int rx_kkrx_create(const rx_kkrx_config* cfg, rx_kkrx** out);
+
+/* Appends n ADC codes (as rx_kk_push: on_device 1 = device pointer, 0 =
+ * host memory).  The bits of every frame this push completes are written
+ * to bits (device memory, packed) in stream order on cuda_stream, *n_bits
+ * of them (a whole number of frames).  A frame completes once the 2-sps
+ * samples reach 2(f+1)F + 1.  RX_EINVAL if bits_cap_bytes is too small. */
+int rx_kkrx_push(rx_kkrx* h, const int16_t* codes, size_t n, int on_device, uint8_t* bits,
+                 size_t bits_cap_bytes, size_t* n_bits, void* cuda_stream);
+
+/* End of stream: the remaining frames (the last one may be short; symbols
+ * = codes / 4) and their bits; samples past the end count as zero. */
+int rx_kkrx_end(rx_kkrx* h, uint8_t* bits, size_t bits_cap_bytes, size_t* n_bits, void* cuda_stream);
+
+/* Equalised symbols [first, first + n) (within history_syms) as complex
+ * float pairs, copied to host memory after the device is idle. */
+int rx_kkrx_equalised(rx_kkrx* h, int64_t first, int64_t n, float* out);
+
+int rx_kkrx_reset(rx_kkrx* h);
+
+void rx_kkrx_destroy(rx_kkrx* h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,188 @@
+// The paper's KK receiver after the field reconstruction (Sec. II):
+//
+//   static equaliser + resampling: 100 % overlap-save at 4 samples per
+//     symbol; block b (4-sps input [b N4/2 - N4/4, b N4/2 + 3N4/4), zero
+//     outside the stream) is transformed with N4 points, cut to the
+//     2-sps band (bins -N4/4 .. N4/4 - 1), multiplied by H (CD compensation
+//     x RRC matched filter, 1/N4 folded in) and transformed back with N4/2
+//     points; samples N4/8 .. 3N4/8 - 1 are the 2-sps outputs
+//     [b N4/4, (b+1) N4/4);
+//   widely-linear DD-LMS: y_k = sum_t h1[t] x[2k+t-1] + h2[t] conj(x[2k+t-1]),
+//     t < 4, block-LMS over sub-blocks of 64 symbols (taps fixed inside a
+//     sub-block, e = y - dec(y), h1 -= mu mean(e conj x), h2 -= mu mean(e x)),
+//     one chain per segment of S symbols continued from frame to frame;
+//   decisions and Gray demapping to packed bits.
+//
+// Kernel layout: the equaliser runs one N4/16-thread block per output
+// segment (the forward transform's band is compacted in place, the inverse
+// reuses the table of N4 at stride 2); the DD-LMS runs one warp per
+// segment, two symbols per lane and sub-block, the sixteen gradient sums
+// all-reduced by shuffles, decisions and bits in the same pass.
+#include "fft_smem.cuh"
+#include "kkrx_internal.h"
+
+namespace rx {
+
+__device__ __forceinline__ float2 kkrx_in(const KKEqArgs& a, long long i) {
+  if (i < 0 || i >= a.in_end) return make_float2(0.f, 0.f);
+  return i < a.new_start ? a.carry[i - a.carry_start] : a.in[i - a.new_start];
+}
+
+template <int N4>
+__global__ void __launch_bounds__(N4 / 16) kkeq_kernel(KKEqArgs a) {
+  constexpr int NT = N4 / 16, L4 = N4 / 2, L2 = N4 / 4, NB2 = N4 / 2;
+  __shared__ __align__(16) float2 buf[N4];
+  __shared__ float2 tw_s[2 * kTwSplit];
+  for (int i = threadIdx.x; i < 2 * kTwSplit; i += NT) tw_s[i] = a.tw2[i];
+  const long long b = a.seg0 + blockIdx.x;
+  const long long lo = b * L4 - N4 / 4;
+  for (int n = threadIdx.x; n < N4; n += NT) buf[swz(n)] = kkrx_in(a, lo + n);
+  __syncthreads();
+  fft_smem<N4, NT, false>(buf, tw_s, 1);
+  // the 2-sps band in the order of an N4/2-point DFT, times H
+  constexpr int PER = NB2 / NT;
+  float2 v[PER];
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int k2 = threadIdx.x + r * NT;
+    v[r] = cmul(buf[swz(k2 < N4 / 4 ? k2 : k2 + N4 / 2)], a.H2[k2]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < PER; ++r) buf[swz(threadIdx.x + r * NT)] = v[r];
+  __syncthreads();
+  fft_smem<NB2, NT, true>(buf, tw_s, 2);
+  for (int n = threadIdx.x; n < L2; n += NT) {
+    const long long t = b * L2 + n;
+    if (t < a.out_end) a.out[t - a.out_base] = buf[swz(N4 / 8 + n)];
+  }
+}
+
+template <typename T>
+__global__ void kkrx_tail_kernel(const T* carry, long long carry_start, const T* in, long long new_start,
+                                 long long keep_from, long long in_end, T* dst) {
+  const long long n = in_end - keep_from;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long k = keep_from + i;
+    dst[i] = k < new_start ? carry[k - carry_start] : in[k - new_start];
+  }
+}
+
+// Nearest level per dimension (a value on a threshold takes the larger
+// level) and its Gray label; levels +-1/sqrt2 (QPSK: - -> 1, + -> 0) or
+// {-3, -1, 1, 3}/sqrt10 (16QAM: 00, 01, 11, 10).
+template <bool Q16>
+__device__ __forceinline__ float wl_level(float x, uint32_t& bits) {
+  if (Q16) {
+    const float t = 0.632455532033675866f;  // 2 / sqrt10
+    const int l = (x >= -t) + (x >= 0.f) + (x >= t);
+    bits = (uint32_t)(l ^ (l >> 1));
+    return (float)(2 * l - 3) * 0.316227766016837933f;
+  }
+  const int l = x >= 0.f;
+  bits = (uint32_t)(1 - l);
+  return l ? 0.707106781186547524f : -0.707106781186547524f;
+}
+
+template <bool Q16>
+__global__ void __launch_bounds__(32) wl_kernel(WLArgs a) {
+  constexpr int BPS = Q16 ? 4 : 2;
+  const int lane = threadIdx.x;
+  const long long s0 = a.k_a + (long long)blockIdx.x * a.seg;
+  const long long s1 = min(s0 + a.seg, a.k_end);
+  // taps (h1[0..3], h2[0..3]) kept in every lane
+  float2 h[8];
+  const float2* tin = a.taps_in + (long long)blockIdx.x * a.taps_in_stride;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) h[i] = tin[i];
+  for (long long k0 = s0; k0 < s1; k0 += 64) {
+    const int cnt = (int)min(64LL, s1 - k0);
+    float g[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) g[i] = 0.f;
+    uint32_t lbits = 0;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int ks = 2 * lane + q;
+      if (ks < cnt) {
+        const long long k = k0 + ks;
+        float2 X[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const long long i = 2 * k + t - 1;
+          X[t] = (i < 0 || i >= a.n2) ? make_float2(0.f, 0.f) : a.x2[i - a.x2_base];
+        }
+        float yr = 0.f, yi = 0.f;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {  // h1 x + h2 conj(x)
+          yr += h[t].x * X[t].x - h[t].y * X[t].y + h[4 + t].x * X[t].x + h[4 + t].y * X[t].y;
+          yi += h[t].x * X[t].y + h[t].y * X[t].x + h[4 + t].y * X[t].x - h[4 + t].x * X[t].y;
+        }
+        uint32_t bI, bQ;
+        const float dr = wl_level<Q16>(yr, bI), di = wl_level<Q16>(yi, bQ);
+        const float er = yr - dr, ei = yi - di;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {  // e conj(x) and e x
+          g[2 * t] += er * X[t].x + ei * X[t].y;
+          g[2 * t + 1] += ei * X[t].x - er * X[t].y;
+          g[8 + 2 * t] += er * X[t].x - ei * X[t].y;
+          g[8 + 2 * t + 1] += ei * X[t].x + er * X[t].y;
+        }
+        lbits = (lbits << (2 * (BPS / 2))) | (bI << (BPS / 2)) | bQ;
+        if (a.hist && k < a.hist_syms) a.hist[k] = make_float2(yr, yi);
+      } else {
+        lbits <<= BPS;
+      }
+    }
+    // the lane's two symbols' bits: 4 (QPSK, a nibble) or 8 (16QAM, a byte)
+    if (a.bits) {
+      const long long bitpos = (k0 + 2 * lane - a.k_bits) * BPS;
+      if (Q16) {
+        if (2 * lane < cnt) a.bits[bitpos >> 3] = (uint8_t)lbits;
+      } else {
+        const uint32_t other = __shfl_down_sync(0xffffffffu, lbits, 1);
+        if ((lane & 1) == 0 && 2 * lane < cnt) a.bits[bitpos >> 3] = (uint8_t)((lbits << 4) | other);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) g[i] += __shfl_xor_sync(0xffffffffu, g[i], o);
+    }
+    const float s = a.mu / (float)cnt;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      h[i].x -= s * g[2 * i];
+      h[i].y -= s * g[2 * i + 1];
+    }
+  }
+  if (lane < 8) a.taps_out[(long long)blockIdx.x * 8 + lane] = h[lane];
+}
+
+cudaError_t launch_kkeq(const KKEqArgs& a, int N4, long long nseg, cudaStream_t s) {
+  if (nseg <= 0) return cudaSuccess;
+  switch (N4) {
+    case 1024: kkeq_kernel<1024><<<(unsigned)nseg, 64, 0, s>>>(a); break;
+    case 2048: kkeq_kernel<2048><<<(unsigned)nseg, 128, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kkeq_tail(const float2* carry, long long carry_start, const float2* in, long long new_start,
+                             long long keep_from, long long in_end, float2* dst, cudaStream_t s) {
+  const long long n = in_end - keep_from;
+  if (n <= 0) return cudaSuccess;
+  kkrx_tail_kernel<float2><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(carry, carry_start, in, new_start, keep_from,
+                                                                       in_end, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wl(const WLArgs& a, bool q16, long long nseg, cudaStream_t s) {
+  if (nseg <= 0) return cudaSuccess;
+  if (q16) wl_kernel<true><<<(unsigned)nseg, 32, 0, s>>>(a);
+  else wl_kernel<false><<<(unsigned)nseg, 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace rx

@@ -1,0 +1,376 @@
+// Host runtime of the KK receiver chain (paper Sec. II): ADC codes ->
+// field (the rx_kk front end) -> static equaliser with 4 -> 2 samples per
+// symbol -> widely-linear DD-LMS -> decisions -> packed bits.
+//
+// Each stage keeps its own stream positions:
+//   front end   codes pushed / field samples out (rx_kk);
+//   equaliser   field samples in (in4) / 2-sps samples out (out2), a whole
+//               number of segments of N4/4 until the end; segment b needs
+//               field up to b N4/2 + 3N4/4, and a carry holds the field of
+//               [2 out2 - N4/4, in4) (fewer than N4 samples);
+//   DD-LMS      frames of F symbols; frame f runs once the 2-sps samples
+//               reach 2(f+1)F + 1 (its last symbol's taps read x[2k + 2]);
+//               the first frame is preceded by the acquisition chain.
+// The 2-sps samples wait in one of two buffers from 2fF - 2 on; after the
+// frames of a push the rest moves to the other buffer's front.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/rx.h"
+#include "kkrx_internal.h"
+
+namespace rx {
+void set_last_error(const char* msg);
+}
+
+struct rx_kkrx {
+  rx_kkrx_config cfg;
+  rx_kk* fe = nullptr;
+  int N4 = 0, L4 = 0, L2 = 0, F = 0, S = 0, bps = 0;
+  bool ended = false;
+  // equaliser stage
+  long long in4 = 0, out2 = 0;
+  int cur4 = 0;
+  float2* carry4[2] = {nullptr, nullptr};
+  float2* field = nullptr;   // the front end's output of one push
+  size_t field_cap = 0;
+  float2* H2 = nullptr;
+  float2* tw4 = nullptr;
+  // DD-LMS stage
+  float2* x2buf[2] = {nullptr, nullptr};
+  int curx = 0;
+  long long x2_base = -2, x2_cap = 0;
+  long long frames = 0;      // frames done
+  float2* taps = nullptr;    // [F/S][8]
+  float2* acq_taps = nullptr;
+  float2* init_taps = nullptr;
+  float2* hist = nullptr;
+};
+
+namespace {
+
+int fail(const char* msg, int rc) {
+  rx::set_last_error(msg);
+  return rc;
+}
+
+int cuda_rc(cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return RX_OK;
+  static thread_local char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  cudaGetLastError();
+  return fail(buf, RX_EDEVICE);
+}
+
+long long kk_out_after(long long in_pos, int N) {  // the front end's output position
+  const long long q = in_pos - N / 4;
+  return q >= N / 2 ? q / (N / 2) * (N / 2) : 0;
+}
+
+long long eq_out_after(const rx_kkrx* h, long long in4) {
+  const long long q = in4 - h->N4 / 4;
+  return q >= h->L4 ? q / h->L4 * h->L2 : 0;
+}
+
+// Equaliser over the new field [in4, in4 + n) (in h->field), producing
+// 2-sps samples up to out2_new.
+int run_eq(rx_kkrx* h, long long n, long long out2_new, cudaStream_t s) {
+  rx::KKEqArgs a;
+  a.carry = h->carry4[h->cur4];
+  a.carry_start = std::max(0LL, 2 * h->out2 - h->N4 / 4);
+  a.in = h->field;
+  a.new_start = h->in4;
+  a.in_end = h->in4 + n;
+  a.seg0 = h->out2 / h->L2;
+  a.out = h->x2buf[h->curx];
+  a.out_base = h->x2_base;
+  a.out_end = out2_new;
+  a.H2 = h->H2;
+  a.tw2 = h->tw4;
+  if (out2_new - h->x2_base > h->x2_cap) return fail("rx_kkrx: internal 2-sps buffer overflow", RX_EINVAL);
+  const long long nseg = (out2_new - h->out2 + h->L2 - 1) / h->L2;
+  int rc = cuda_rc(rx::launch_kkeq(a, h->N4, nseg, s), "rx_kkrx: equaliser kernel");
+  if (rc) return rc;
+  const long long keep = std::max(0LL, 2 * out2_new - h->N4 / 4);
+  rc = cuda_rc(rx::launch_kkeq_tail(a.carry, a.carry_start, a.in, a.new_start, keep, a.in_end,
+                                    h->carry4[h->cur4 ^ 1], s),
+               "rx_kkrx: equaliser carry");
+  if (rc) return rc;
+  h->cur4 ^= 1;
+  h->in4 += n;
+  h->out2 = out2_new;
+  return RX_OK;
+}
+
+// Frames that can run with the 2-sps samples up to out2 (end: every frame
+// left of the n_sym_end symbols).
+long long frames_ready(const rx_kkrx* h, long long out2, bool end, long long n_sym_end) {
+  if (end) return (n_sym_end + h->F - 1) / h->F - h->frames;
+  long long f = h->frames;
+  while (out2 >= 2LL * (f + 1) * h->F + 1) ++f;
+  return f - h->frames;
+}
+
+// Runs `count` frames (the last may be short when end is set); bits of
+// frame frames + i go to bits + i F bps / 8.
+int run_frames(rx_kkrx* h, long long count, bool end, long long n_sym_end, uint8_t* bits, cudaStream_t s) {
+  const bool q16 = h->cfg.modulation == RX_QAM16;
+  const long long n2 = end ? h->out2 : (1LL << 62);  // before the end every sample read exists
+  for (long long i = 0; i < count; ++i) {
+    const long long f = h->frames;
+    const long long k_a = f * (long long)h->F;
+    const long long k_end = end ? std::min(k_a + h->F, n_sym_end) : k_a + h->F;
+    rx::WLArgs w;
+    std::memset(&w, 0, sizeof(w));
+    w.x2 = h->x2buf[h->curx];
+    w.x2_base = h->x2_base;
+    w.n2 = n2;
+    w.mu = h->cfg.mu;
+    if (f == 0) {  // acquisition: one sequential chain over the first symbols
+      const long long acq = std::min<long long>(h->cfg.acq_syms, end ? n_sym_end : h->cfg.acq_syms);
+      w.k_a = 0;
+      w.k_end = acq;
+      w.seg = std::max(acq, 1LL);
+      w.taps_in = h->init_taps;
+      w.taps_out = h->acq_taps;
+      int rc = cuda_rc(rx::launch_wl(w, q16, acq > 0 ? 1 : 0, s), "rx_kkrx: acquisition");
+      if (rc) return rc;
+      if (acq == 0) {
+        rc = cuda_rc(cudaMemcpyAsync(h->acq_taps, h->init_taps, 8 * sizeof(float2), cudaMemcpyDeviceToDevice, s),
+                     "rx_kkrx: taps");
+        if (rc) return rc;
+      }
+    }
+    w.k_a = k_a;
+    w.k_end = k_end;
+    w.seg = h->S;
+    w.taps_in = f == 0 ? h->acq_taps : h->taps;
+    w.taps_in_stride = f == 0 ? 0 : 8;
+    w.taps_out = h->taps;
+    w.bits = bits + i * ((long long)h->F * h->bps / 8);
+    w.k_bits = k_a;
+    w.hist = h->hist;
+    w.hist_syms = h->cfg.history_syms;
+    const int rc = cuda_rc(rx::launch_wl(w, q16, (k_end - k_a + h->S - 1) / h->S, s), "rx_kkrx: DD-LMS");
+    if (rc) return rc;
+    h->frames++;
+  }
+  if (count > 0 && !end) {  // keep the 2-sps samples from 2 frames F - 2 on
+    const long long nb = 2 * h->frames * (long long)h->F - 2;
+    const long long keep = h->out2 - nb;
+    if (keep > 0) {
+      const int rc = cuda_rc(cudaMemcpyAsync(h->x2buf[h->curx ^ 1], h->x2buf[h->curx] + (nb - h->x2_base),
+                                             keep * sizeof(float2), cudaMemcpyDeviceToDevice, s),
+                             "rx_kkrx: 2-sps carry");
+      if (rc) return rc;
+    }
+    h->curx ^= 1;
+    h->x2_base = nb;
+  }
+  return RX_OK;
+}
+
+}  // namespace
+
+extern "C" void rx_kkrx_config_default(rx_kkrx_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  rx_kk_config_default(&c->fe);
+  c->baud_hz = 1e9;
+  c->modulation = RX_QPSK;
+  c->fiber_len_m = 0.0;
+  c->D_ps_nm_km = 17.0;
+  c->lambda_m = 1550e-9;
+  c->rrc_rolloff = 0.01;
+  c->eq_fft_n = 1024;
+  c->mu = 5e-3f;
+  c->seg_syms = 512;
+  c->frame_syms = 1 << 20;
+  c->acq_syms = 8192;
+  c->history_syms = 0;
+}
+
+extern "C" int rx_kkrx_create(const rx_kkrx_config* cfg, rx_kkrx** out) {
+  if (!cfg || !out) return fail("rx_kkrx_create: null argument", RX_EINVAL);
+  *out = nullptr;
+  const rx_kkrx_config& c = *cfg;
+  if (!(c.baud_hz > 0.0) || std::fabs(c.fe.fs_hz - 4.0 * c.baud_hz) > 1e-6 * c.fe.fs_hz)
+    return fail("rx_kkrx_create: fe.fs_hz must be 4 x baud_hz (4 samples per symbol)", RX_EINVAL);
+  if (c.modulation != RX_QPSK && c.modulation != RX_QAM16)
+    return fail("rx_kkrx_create: modulation must be RX_QPSK or RX_QAM16", RX_EINVAL);
+  if (c.eq_fft_n != 1024 && c.eq_fft_n != 2048) return fail("rx_kkrx_create: eq_fft_n must be 1024 or 2048", RX_EINVAL);
+  if (!(c.rrc_rolloff > 0.0 && c.rrc_rolloff <= 1.0)) return fail("rx_kkrx_create: rrc_rolloff must be in (0, 1]", RX_EINVAL);
+  if (!(c.mu > 0.f && c.mu < 1.f)) return fail("rx_kkrx_create: mu must be in (0, 1)", RX_EINVAL);
+  if (c.seg_syms < 64 || c.seg_syms % 64) return fail("rx_kkrx_create: seg_syms must be a multiple of 64", RX_EINVAL);
+  if (c.frame_syms < c.seg_syms || c.frame_syms % c.seg_syms || c.frame_syms > (1 << 24))
+    return fail("rx_kkrx_create: frame_syms must be a multiple of seg_syms, at most 2^24", RX_EINVAL);
+  if (c.acq_syms < 0 || c.acq_syms % 64 || c.acq_syms > c.frame_syms)
+    return fail("rx_kkrx_create: acq_syms must be a multiple of 64 and at most frame_syms", RX_EINVAL);
+  if (c.history_syms < 0) return fail("rx_kkrx_create: history_syms must be >= 0", RX_EINVAL);
+  rx_kkrx* h = new rx_kkrx;
+  h->cfg = c;
+  int rc = rx_kk_create(&c.fe, &h->fe);
+  if (rc) {
+    delete h;
+    return rc;
+  }
+  h->N4 = c.eq_fft_n;
+  h->L4 = h->N4 / 2;
+  h->L2 = h->N4 / 4;
+  h->F = c.frame_syms;
+  h->S = c.seg_syms;
+  h->bps = c.modulation;
+  h->field_cap = c.fe.max_block_samples + c.fe.fft_n;
+  // 2-sps samples waiting: two frames' worth plus one push's output
+  h->x2_cap = 2LL * h->F + 16 + (long long)(c.fe.max_block_samples + c.fe.fft_n + h->N4) / 2 + h->L2;
+  bool ok = cudaMalloc(&h->field, h->field_cap * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc(&h->carry4[0], h->N4 * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc(&h->carry4[1], h->N4 * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc(&h->H2, (h->N4 / 2) * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc(&h->tw4, 256 * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc(&h->x2buf[0], h->x2_cap * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc(&h->x2buf[1], h->x2_cap * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc(&h->taps, (size_t)(h->F / h->S) * 8 * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc(&h->acq_taps, 8 * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc(&h->init_taps, 8 * sizeof(float2)) == cudaSuccess &&
+            (c.history_syms == 0 || cudaMalloc(&h->hist, c.history_syms * sizeof(float2)) == cudaSuccess);
+  if (ok) {
+    // static equaliser: exp(+j beta2 L w^2 / 2) at w = 2 pi (f + f_shift) x RRC(f), FP64, phase
+    // reduced mod 2 pi; bins 0 .. N4/4 - 1 then -N4/4 .. -1 (f = k fs / N4); 1/N4 folded in
+    const double fs = c.fe.fs_hz, Rs = c.baud_hz, rho = c.rrc_rolloff;
+    const double b2 = -(c.D_ps_nm_km * 1e-6) * c.lambda_m * c.lambda_m / (2.0 * M_PI * 299792458.0);
+    std::vector<float2> H(h->N4 / 2), tw(256), init(8, make_float2(0.f, 0.f));
+    for (int i = 0; i < h->N4 / 2; ++i) {
+      const int k = i < h->N4 / 4 ? i : i - h->N4 / 2;
+      const double f = k * fs / h->N4;
+      const double w = 2.0 * M_PI * (f + c.fe.f_shift_hz);
+      const double ph = std::fmod(b2 * c.fiber_len_m * w * w / 2.0, 2.0 * M_PI);
+      const double a = std::fabs(f) / Rs;
+      double amp = 0.0;
+      if (a <= (1 - rho) / 2) amp = 1.0;
+      else if (a <= (1 + rho) / 2) amp = std::sqrt(0.5 * (1.0 + std::cos(M_PI / rho * (a - (1 - rho) / 2))));
+      amp /= h->N4;
+      H[i] = make_float2((float)(amp * std::cos(ph)), (float)(amp * std::sin(ph)));
+    }
+    for (int i = 0; i < 128; ++i) {
+      const double ah = -2.0 * M_PI * (double)(i * 128) / h->N4, al = -2.0 * M_PI * (double)i / h->N4;
+      tw[i] = make_float2((float)std::cos(ah), (float)std::sin(ah));
+      tw[128 + i] = make_float2((float)std::cos(al), (float)std::sin(al));
+    }
+    init[1] = make_float2(1.f, 0.f);  // h1 = unit tap at offset 0, h2 = 0
+    ok = cudaMemcpy(h->H2, H.data(), H.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(h->tw4, tw.data(), 256 * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(h->init_taps, init.data(), 8 * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    rx_kkrx_destroy(h);
+    return fail("rx_kkrx_create: device allocation failed", RX_ENOMEM);
+  }
+  *out = h;
+  return RX_OK;
+}
+
+extern "C" int rx_kkrx_push(rx_kkrx* h, const int16_t* codes, size_t n, int on_device, uint8_t* bits,
+                            size_t bits_cap_bytes, size_t* n_bits, void* cuda_stream) {
+  if (!h || !n_bits || (n > 0 && !codes)) return fail("rx_kkrx_push: null argument", RX_EINVAL);
+  *n_bits = 0;
+  if (h->ended) return fail("rx_kkrx_push: stream already ended", RX_ESTATE);
+  if (n > h->cfg.fe.max_block_samples) return fail("rx_kkrx_push: n exceeds fe.max_block_samples", RX_EINVAL);
+  if (n == 0) return RX_OK;
+  int64_t fin = 0, fout = 0;
+  rx_kk_position(h->fe, &fin, &fout);
+  const long long c1 = kk_out_after(fin + (long long)n, h->cfg.fe.fft_n) - fout;
+  const long long out2_new = eq_out_after(h, h->in4 + c1);
+  const long long nf = frames_ready(h, out2_new, false, 0);
+  const size_t need = (size_t)nf * ((size_t)h->F * h->bps / 8);
+  if (need > 0 && (!bits || bits_cap_bytes < need))
+    return fail("rx_kkrx_push: bits is null or bits_cap_bytes is smaller than the frames this push completes",
+                RX_EINVAL);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  size_t got = 0;
+  int rc = rx_kk_push(h->fe, codes, n, on_device, reinterpret_cast<float*>(h->field), h->field_cap, &got, s);
+  if (rc) return rc;
+  if ((long long)got != c1) return fail("rx_kkrx_push: front-end output count mismatch", RX_EINVAL);
+  if (got > 0) {
+    rc = run_eq(h, (long long)got, out2_new, s);
+    if (rc) return rc;
+  }
+  rc = run_frames(h, nf, false, 0, bits, s);
+  if (rc) return rc;
+  *n_bits = need * 8;
+  return RX_OK;
+}
+
+extern "C" int rx_kkrx_end(rx_kkrx* h, uint8_t* bits, size_t bits_cap_bytes, size_t* n_bits, void* cuda_stream) {
+  if (!h || !n_bits) return fail("rx_kkrx_end: null argument", RX_EINVAL);
+  *n_bits = 0;
+  if (h->ended) return fail("rx_kkrx_end: stream already ended", RX_ESTATE);
+  int64_t fin = 0, fout = 0;
+  rx_kk_position(h->fe, &fin, &fout);
+  const long long n4 = fin;            // every code becomes a field sample
+  const long long n2 = n4 / 2;
+  const long long n_sym = n2 / 2;
+  const long long nf = frames_ready(h, n2, true, n_sym);
+  const long long last = n_sym - (h->frames + std::max(nf, 1LL) - 1) * (long long)h->F;
+  const size_t need = nf > 0 ? (size_t)(nf - 1) * ((size_t)h->F * h->bps / 8) + (size_t)(last * h->bps + 7) / 8 : 0;
+  if (need > 0 && (!bits || bits_cap_bytes < need))
+    return fail("rx_kkrx_end: bits is null or bits_cap_bytes is smaller than the remaining frames' bits", RX_EINVAL);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  size_t got = 0;
+  int rc = rx_kk_end(h->fe, reinterpret_cast<float*>(h->field), h->field_cap, &got, s);
+  if (rc) return rc;
+  if (n2 > h->out2) {
+    rc = run_eq(h, (long long)got, n2, s);
+    if (rc) return rc;
+  }
+  rc = run_frames(h, nf, true, n_sym, bits, s);
+  if (rc) return rc;
+  h->ended = true;
+  *n_bits = nf > 0 ? (size_t)((nf - 1) * (long long)h->F + last) * h->bps : 0;
+  return RX_OK;
+}
+
+extern "C" int rx_kkrx_equalised(rx_kkrx* h, int64_t first, int64_t n, float* out) {
+  if (!h || (n > 0 && !out)) return fail("rx_kkrx_equalised: null argument", RX_EINVAL);
+  if (first < 0 || n < 0 || first + n > h->cfg.history_syms)
+    return fail("rx_kkrx_equalised: range outside history_syms", RX_EINVAL);
+  if (n == 0) return RX_OK;
+  cudaSetDevice(h->cfg.fe.device);
+  if (cudaDeviceSynchronize() != cudaSuccess) return cuda_rc(cudaGetLastError(), "rx_kkrx_equalised");
+  return cuda_rc(cudaMemcpy(out, h->hist + first, n * sizeof(float2), cudaMemcpyDeviceToHost), "rx_kkrx_equalised");
+}
+
+extern "C" int rx_kkrx_reset(rx_kkrx* h) {
+  if (!h) return fail("rx_kkrx_reset: null handle", RX_EINVAL);
+  rx_kk_reset(h->fe);
+  h->ended = false;
+  h->in4 = h->out2 = 0;
+  h->cur4 = h->curx = 0;
+  h->x2_base = -2;
+  h->frames = 0;
+  return RX_OK;
+}
+
+extern "C" void rx_kkrx_destroy(rx_kkrx* h) {
+  if (!h) return;
+  cudaSetDevice(h->cfg.fe.device);
+  rx_kk_destroy(h->fe);
+  cudaFree(h->field);
+  cudaFree(h->carry4[0]);
+  cudaFree(h->carry4[1]);
+  cudaFree(h->H2);
+  cudaFree(h->tw4);
+  cudaFree(h->x2buf[0]);
+  cudaFree(h->x2buf[1]);
+  cudaFree(h->taps);
+  cudaFree(h->acq_taps);
+  cudaFree(h->init_taps);
+  cudaFree(h->hist);
+  delete h;
+}

@@ -37,7 +37,9 @@ EXPORTS = ["rx_config_default", "rx_create", "rx_push_block", "rx_pull_bits", "r
            "rx_server_handle", "rx_server_close", "rx_server_stats", "rx_server_destroy",
            "rx_autotune_fft",
            "rx_kk_config_default", "rx_kk_create", "rx_kk_push", "rx_kk_end", "rx_kk_reset",
-           "rx_kk_position", "rx_kk_destroy"]
+           "rx_kk_position", "rx_kk_destroy",
+           "rx_kkrx_config_default", "rx_kkrx_create", "rx_kkrx_push", "rx_kkrx_end", "rx_kkrx_equalised",
+           "rx_kkrx_reset", "rx_kkrx_destroy"]
 
 
 class RxConfig(ctypes.Structure):
@@ -85,6 +87,25 @@ class KKConfig(ctypes.Structure):
         ("fft_n", ctypes.c_int),
         ("max_block_samples", ctypes.c_size_t),
         ("device", ctypes.c_int),
+    ]
+
+
+class KKRxConfig(ctypes.Structure):
+    """rx_kkrx_config: the KK receiver chain."""
+    _fields_ = [
+        ("fe", KKConfig),
+        ("baud_hz", ctypes.c_double),
+        ("modulation", ctypes.c_int),
+        ("fiber_len_m", ctypes.c_double),
+        ("D_ps_nm_km", ctypes.c_double),
+        ("lambda_m", ctypes.c_double),
+        ("rrc_rolloff", ctypes.c_double),
+        ("eq_fft_n", ctypes.c_int),
+        ("mu", ctypes.c_float),
+        ("seg_syms", ctypes.c_int),
+        ("frame_syms", ctypes.c_int),
+        ("acq_syms", ctypes.c_int),
+        ("history_syms", ctypes.c_int64),
     ]
 
 
@@ -201,12 +222,22 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rx_kk_position.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
     lib.rx_kk_destroy.argtypes = [P]
     lib.rx_kk_destroy.restype = None
+    lib.rx_kkrx_config_default.argtypes = [ctypes.POINTER(KKRxConfig)]
+    lib.rx_kkrx_config_default.restype = None
+    lib.rx_kkrx_create.argtypes = [ctypes.POINTER(KKRxConfig), ctypes.POINTER(P)]
+    lib.rx_kkrx_push.argtypes = [P, P, SZ, I, P, SZ, ctypes.POINTER(SZ), P]
+    lib.rx_kkrx_end.argtypes = [P, P, SZ, ctypes.POINTER(SZ), P]
+    lib.rx_kkrx_equalised.argtypes = [P, I64, I64, ctypes.POINTER(ctypes.c_float)]
+    lib.rx_kkrx_reset.argtypes = [P]
+    lib.rx_kkrx_destroy.argtypes = [P]
+    lib.rx_kkrx_destroy.restype = None
     for name in ["rx_create", "rx_push_block", "rx_pull_bits", "rx_stats", "rx_destroy", "rx_reset",
                  "rx_join", "rx_stage_times", "rx_frame_trace", "rx_get_taps", "rx_get_equalised",
                  "rx_get_phase", "rx_decide_block_noalloc", "rx_server_create", "rx_server_open",
                  "rx_server_end", "rx_server_sync", "rx_server_pull_bits", "rx_server_stream_stats",
                  "rx_server_close", "rx_server_stats", "rx_server_destroy", "rx_autotune_fft",
-                 "rx_kk_create", "rx_kk_push", "rx_kk_end", "rx_kk_reset", "rx_kk_position"]:
+                 "rx_kk_create", "rx_kk_push", "rx_kk_end", "rx_kk_reset", "rx_kk_position",
+                 "rx_kkrx_create", "rx_kkrx_push", "rx_kkrx_end", "rx_kkrx_equalised", "rx_kkrx_reset"]:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -542,6 +573,78 @@ class KKFrontEnd:
     def close(self) -> None:
         if getattr(self, "h", None):
             self.lib.rx_kk_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def default_kkrx_config(fe: dict | None = None, **overrides) -> KKRxConfig:
+    """Chain defaults with overrides; fe holds front-end fields (fs_hz, ...)."""
+    cfg = KKRxConfig()
+    load().rx_kkrx_config_default(ctypes.byref(cfg))
+    for k, v in (fe or {}).items():
+        if not hasattr(cfg.fe, k):
+            raise KeyError(k)
+        setattr(cfg.fe, k, v)
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise KeyError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+class KKReceiver:
+    """The paper's KK receiver chain (rx_kkrx_*): int16 ADC codes in, packed
+    decided bits out, both in device memory."""
+
+    def __init__(self, cfg: KKRxConfig | None = None, fe: dict | None = None, **overrides):
+        self.lib = load()
+        self.cfg = cfg if cfg is not None else default_kkrx_config(fe, **overrides)
+        h = ctypes.c_void_p()
+        _check(self.lib.rx_kkrx_create(ctypes.byref(self.cfg), ctypes.byref(h)))
+        self.h = h
+
+    def push_device(self, codes_ptr: int, n: int, bits_ptr: int, bits_cap: int, stream: int = 0) -> int:
+        """Returns the number of bits written at bits_ptr."""
+        nb = ctypes.c_size_t()
+        _check(self.lib.rx_kkrx_push(self.h, ctypes.c_void_p(codes_ptr), n, 1, ctypes.c_void_p(bits_ptr), bits_cap,
+                                     ctypes.byref(nb), ctypes.c_void_p(stream)))
+        return nb.value
+
+    def push_host(self, codes: np.ndarray, bits_ptr: int, bits_cap: int, stream: int = 0) -> int:
+        codes = np.ascontiguousarray(codes, dtype=np.int16)
+        nb = ctypes.c_size_t()
+        _check(self.lib.rx_kkrx_push(self.h, codes.ctypes.data_as(ctypes.c_void_p), codes.size, 0,
+                                     ctypes.c_void_p(bits_ptr), bits_cap, ctypes.byref(nb), ctypes.c_void_p(stream)))
+        return nb.value
+
+    def end(self, bits_ptr: int, bits_cap: int, stream: int = 0) -> int:
+        nb = ctypes.c_size_t()
+        _check(self.lib.rx_kkrx_end(self.h, ctypes.c_void_p(bits_ptr), bits_cap, ctypes.byref(nb),
+                                    ctypes.c_void_p(stream)))
+        return nb.value
+
+    def equalised(self, first: int, n: int) -> np.ndarray:
+        out = np.zeros(2 * n, dtype=np.float32)
+        _check(self.lib.rx_kkrx_equalised(self.h, first, n, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out.view(np.complex64)
+
+    def reset(self) -> None:
+        _check(self.lib.rx_kkrx_reset(self.h))
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.rx_kkrx_destroy(self.h)
             self.h = None
 
     def __enter__(self):

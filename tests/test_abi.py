@@ -205,3 +205,39 @@ def test_kk_config_checks_without_device(lib, field, value, msg):
     n = ctypes.c_size_t()
     assert lib.rx_kk_push(None, None, 0, 1, None, 0, ctypes.byref(n), None) == rx.RX_EINVAL
     assert lib.rx_kk_end(None, None, 0, ctypes.byref(n), None) == rx.RX_EINVAL
+
+
+def test_kkrx_struct_layout_matches_c(tmp_path, lib):
+    from paper_2108_07001_gb300 import rx
+    src = tmp_path / "krlayout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "rx.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(rx_kkrx_config), offsetof(rx_kkrx_config, baud_hz),"
+        " offsetof(rx_kkrx_config, mu), offsetof(rx_kkrx_config, acq_syms), offsetof(rx_kkrx_config, history_syms));"
+        " return 0;}\n")
+    exe = tmp_path / "krlayout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals == [ctypes.sizeof(rx.KKRxConfig), rx.KKRxConfig.baud_hz.offset, rx.KKRxConfig.mu.offset,
+                    rx.KKRxConfig.acq_syms.offset, rx.KKRxConfig.history_syms.offset]
+
+
+@pytest.mark.parametrize("fe,kw,msg", [
+    ({"fs_hz": 3e9}, {}, "fs_hz"),
+    ({}, {"modulation": 3}, "modulation"),
+    ({}, {"eq_fft_n": 4096}, "eq_fft_n"),
+    ({}, {"seg_syms": 100}, "seg_syms"),
+    ({}, {"frame_syms": 1000}, "frame_syms"),
+    ({}, {"acq_syms": 1 << 21}, "acq_syms"),
+    ({}, {"mu": 0.0}, "mu"),
+    ({"fft_n": 512}, {}, "fft_n"),
+])
+def test_kkrx_config_checks_without_device(lib, fe, kw, msg):
+    from paper_2108_07001_gb300 import rx
+    c = rx.default_kkrx_config()
+    assert (c.baud_hz, c.fe.fs_hz, c.frame_syms, c.seg_syms, c.eq_fft_n) == (1e9, 4e9, 1 << 20, 512, 1024)
+    bad = rx.default_kkrx_config(fe, **kw)
+    h = ctypes.c_void_p()
+    assert lib.rx_kkrx_create(ctypes.byref(bad), ctypes.byref(h)) == rx.RX_EINVAL
+    assert msg in lib.rx_last_error().decode()
+    assert not h.value
