@@ -14,8 +14,9 @@
 //   decisions and Gray demapping to packed bits.
 //
 // Kernel layout: the equaliser runs one N4/16-thread block per output
-// segment (the forward transform's band is compacted in place, the inverse
-// reuses the table of N4 at stride 2); the DD-LMS runs one warp per
+// segment (16-byte loads of two field samples when the block lies in the
+// step's new field; the forward transform's band is compacted in place,
+// the inverse reuses the table of N4 at stride 2); the DD-LMS runs one warp per
 // segment, two symbols per lane and sub-block, the sixteen gradient sums
 // all-reduced by shuffles, decisions and bits in the same pass.
 #include "fft_smem.cuh"
@@ -31,12 +32,29 @@ __device__ __forceinline__ float2 kkrx_in(const KKEqArgs& a, long long i) {
 template <int N4>
 __global__ void __launch_bounds__(N4 / 16) kkeq_kernel(KKEqArgs a) {
   constexpr int NT = N4 / 16, L4 = N4 / 2, L2 = N4 / 4, NB2 = N4 / 2;
+  static_assert(N4 / 2 == 8 * NT, "eight two-sample vectors per thread");
   __shared__ __align__(16) float2 buf[N4];
   __shared__ float2 tw_s[2 * kTwSplit];
   for (int i = threadIdx.x; i < 2 * kTwSplit; i += NT) tw_s[i] = a.tw2[i];
   const long long b = a.seg0 + blockIdx.x;
   const long long lo = b * L4 - N4 / 4;
-  for (int n = threadIdx.x; n < N4; n += NT) buf[swz(n)] = kkrx_in(a, lo + n);
+  const long long off = lo - a.new_start;
+  if (off >= 0 && lo + N4 <= a.in_end && (off & 1) == 0 && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0) {
+    // the block lies in this step's field, 16-byte aligned: two samples per
+    // load, N4 / 2 = 8 NT loads issued before any is used
+    const float4* src = reinterpret_cast<const float4*>(a.in + off);
+    float4 w[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) w[r] = __ldg(src + threadIdx.x + r * NT);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int v = threadIdx.x + r * NT;
+      buf[swz(2 * v)] = make_float2(w[r].x, w[r].y);
+      buf[swz(2 * v + 1)] = make_float2(w[r].z, w[r].w);
+    }
+  } else {
+    for (int n = threadIdx.x; n < N4; n += NT) buf[swz(n)] = kkrx_in(a, lo + n);
+  }
   __syncthreads();
   fft_smem<N4, NT, false>(buf, tw_s, 1);
   // the 2-sps band in the order of an N4/2-point DFT, times H
