@@ -241,3 +241,22 @@ def test_kkrx_config_checks_without_device(lib, fe, kw, msg):
     assert lib.rx_kkrx_create(ctypes.byref(bad), ctypes.byref(h)) == rx.RX_EINVAL
     assert msg in lib.rx_last_error().decode()
     assert not h.value
+
+
+def test_smoke_configuration_is_valid(lib):
+    """The receiver settings smoke() runs pass validation (on a machine
+    without a GPU rx_create then stops at the device)."""
+    import importlib.util
+    import torch
+    from paper_2108_07001_gb300 import rx
+    spec = importlib.util.spec_from_file_location("graft_entry", os.path.join(ROOT, "__graft_entry__.py"))
+    ge = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(ge)
+    c = rx.default_config(**ge.SMOKE_RX, history_syms=1 << 14)
+    h = ctypes.c_void_p()
+    rc = lib.rx_create(ctypes.byref(c), ctypes.byref(h))
+    if torch.cuda.is_available():
+        assert rc == rx.RX_OK, lib.rx_last_error()
+        lib.rx_destroy(h)
+    else:
+        assert rc == rx.RX_EDEVICE, lib.rx_last_error()
