@@ -713,6 +713,85 @@ def run_kk(args):
             "clocks": clocks, "sim_seconds": round(gen_s, 1)}
 
 
+KKB_CHANNELS = 64
+KKB_ROUNDS = 64
+
+
+def run_kk_batch(args):
+    """Many KK front ends with small, uneven buffers (low latency): 64
+    channels, each round pushing 2^12..2^16 codes per channel (drawn per
+    channel and round), as one graph replay per round (rx_kk_batch_push)
+    and as one push per channel (rx_kk_push): throughput and host time per
+    round."""
+    import torch
+    from paper_2108_07001_gb300 import rx
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    d = kk_link(1 << 23)
+    codes = torch.from_numpy(d["codes"]).to(dev)  # every channel reads its own window of one link
+    rng = np.random.default_rng(5)
+    sizes = rng.integers(1 << 12, (1 << 16) + 1, (KKB_ROUNDS, KKB_CHANNELS))
+    total = int(sizes.sum())
+    starts = [int(s) for s in rng.integers(0, (1 << 23) - int(sizes.sum(axis=0).max()), KKB_CHANNELS)]
+    cap = int(sizes.sum(axis=0).max()) + 2048
+    out = torch.empty((KKB_CHANNELS, cap), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    fcfg = dict(fs_hz=d["fs"], f_shift_hz=d["f_c"], adc_gain=d["gain"], adc_offset=d["offset"], fft_n=1024,
+                max_block_samples=1 << 16)
+    base = codes.data_ptr()
+    obase = out.data_ptr()
+    row = cap * 8
+
+    def run(mode):
+        fes = [rx.KKFrontEnd(**fcfg) for _ in range(KKB_CHANNELS)]
+        batch = rx.KKBatch(fes) if mode == "batch" else None
+        pin = list(starts)
+        pout = [0] * KKB_CHANNELS
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        h0 = time.perf_counter()
+        for r in range(KKB_ROUNDS):
+            if batch is not None:
+                got = batch.push([base + 2 * pin[c] for c in range(KKB_CHANNELS)], [int(x) for x in sizes[r]],
+                                 [obase + c * row + 8 * pout[c] for c in range(KKB_CHANNELS)],
+                                 [cap - pout[c] for c in range(KKB_CHANNELS)], stream)
+            else:
+                got = [fes[c].push_device(base + 2 * pin[c], int(sizes[r, c]), obase + c * row + 8 * pout[c],
+                                          cap - pout[c], stream) for c in range(KKB_CHANNELS)]
+            for c in range(KKB_CHANNELS):
+                pin[c] += int(sizes[r, c])
+                pout[c] += got[c]
+        h1 = time.perf_counter()
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        res = out[:, :min(pout)].clone()
+        if batch is not None:
+            batch.close()
+        for f in fes:
+            f.close()
+        return ms, (h1 - h0) * 1e3, res
+
+    forms = {}
+    results = {}
+    for mode in ("per_channel", "batch"):
+        run(mode)  # warm-up
+        ms, host_ms, res = run(mode)
+        results[mode] = res
+        forms[mode] = {"gsamples_s": round(total / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3),
+                       "host_ms": round(host_ms, 3), "launches": KKB_ROUNDS * (1 if mode == "batch" else
+                                                                                2 * KKB_CHANNELS)}
+    same = bool(torch.equal(results["batch"], results["per_channel"]))
+    return {"metric": "gsamples_per_s", "value": forms["batch"]["gsamples_s"], "unit": "Gsamples/s", "n_gpus": 1,
+            "higher_is_better": True, "workload": "kk_batch", "dtype": "f32 (int16 codes in, c64 field out)",
+            "data": "synthetic (seeded minimum-phase link simulator)",
+            "config": {"channels": KKB_CHANNELS, "rounds": KKB_ROUNDS, "codes_per_push": "2^12..2^16 per channel",
+                       "codes_total": total, "fft_n": 1024},
+            "forms": forms, "x_per_channel": round(forms["batch"]["gsamples_s"] / forms["per_channel"]["gsamples_s"], 2),
+            "batch_equals_per_channel": same}
+
+
 def combine_replicas(line, world, reduce_max):
     """Whole-job line of N independent replicas: the step time (and the
     end-to-end step time) is the maximum over ranks (reduce_max: list of
@@ -988,12 +1067,13 @@ def main():
     ap.add_argument("--kk-oracle-child", type=int, help=argparse.SUPPRESS)
     ap.add_argument("--bps-coarse-stride", type=int, default=1,
                     help="stream workload: 4 = two-stage BPS over 16 coarse angles (default 1: all 64)")
-    ap.add_argument("--workload", default="stream", choices=["stream", "qam16", "serving", "batched", "kk"],
+    ap.add_argument("--workload", default="stream", choices=["stream", "qam16", "serving", "batched", "kk", "kk_batch"],
                     help="stream: the 2^24-symbol DP-QPSK stream (default line); qam16: DP-16QAM 5,000 km "
                          "with FP16 and FP32 sample storage against the FP64 oracle; serving: 16 mixed "
                          "channel streams through the serving layer at 80 %% of its capacity; batched: 64 "
                          "streams with uneven blocks, FFT sizes from the heuristic and from the autotuner; "
-                         "kk: the paper's Kramers-Kronig front end on 2^22-sample buffers of 12-bit codes")
+                         "kk: the paper's Kramers-Kronig receiver on 2^22-sample buffers of 12-bit codes; "
+                         "kk_batch: 64 KK front ends with small uneven pushes, one graph replay per round")
     args = ap.parse_args()
     if args.kk_oracle_child:
         kk_oracle_child(args.kk_oracle_child)
@@ -1040,6 +1120,9 @@ def main():
         return
     if args.workload == "kk":
         print(json.dumps(run_kk(args)), flush=True)
+        return
+    if args.workload == "kk_batch":
+        print(json.dumps(run_kk_batch(args)), flush=True)
         return
     print(json.dumps(run_ours(args)), flush=True)
 

@@ -426,6 +426,29 @@ int rx_kk_position(const rx_kk* h, int64_t* samples_in, int64_t* samples_out);
 
 void rx_kk_destroy(rx_kk* h);
 
+/* Many front ends in one launch: rx_kk_batch_push plans a push of every
+ * channel, writes the plans to a table and replays a CUDA graph of the
+ * table's copy, one field kernel over every channel's segment pairs
+ * (channels' pushes may differ in length; a block finds its channel from
+ * the prefix sums of their pair counts) and one carry kernel.  Each
+ * channel's results are those of rx_kk_push with the same codes.  The
+ * channels must share fft_n and device and must not be pushed otherwise
+ * while the batch is in use; rx_kk_batch_destroy does not free them. */
+typedef struct rx_kk_batch rx_kk_batch;
+
+/* n_channels in 1..256 distinct handles; builds the graphs. */
+int rx_kk_batch_create(rx_kk* const* channels, int n_channels, rx_kk_batch** out);
+
+/* For every channel c: n[c] codes at the device pointer codes[c] (0: none
+ * this time), field out to out[c] (device, capacity out_cap[c] complex
+ * samples), n_out[c] written, in stream order on cuda_stream.  Checks
+ * every channel before launching anything (RX_EINVAL / RX_ESTATE as
+ * rx_kk_push). */
+int rx_kk_batch_push(rx_kk_batch* b, const int16_t* const* codes, const size_t* n, float* const* out,
+                     const size_t* out_cap, size_t* n_out, void* cuda_stream);
+
+void rx_kk_batch_destroy(rx_kk_batch* b);
+
 /* ---- KK receiver chain (paper Sec. II) -------------------------------------
  *
  * The rest of the paper's single-polarisation receiver after the KK front

@@ -20,6 +20,7 @@
 // where frac(nu t) comes from an exact 64-bit fixed-point product (nu
 // quantised to 2^-64; no drift over the stream).
 #include <algorithm>
+#include <cstring>
 
 #include "fft_smem.cuh"
 #include "kk_internal.h"
@@ -40,8 +41,10 @@ __device__ __forceinline__ bool kk_code(const KKArgs& a, long long i, float& cod
 template <int N>
 constexpr size_t kk_smem_bytes() { return (size_t)N * 8 + (size_t)3 * (N / 2) * 4; }
 
+// The pair of segments a.seg0 + 2 pair, a.seg0 + 2 pair + 1, by one block
+// of N/16 threads (dynamic shared memory: kk_smem_bytes<N>()).
 template <int N>
-__global__ void __launch_bounds__(N / 16) kk_kernel(KKArgs a) {
+__device__ __forceinline__ void kk_pair(const KKArgs& a, long long pair) {
   constexpr int NT = N / 16, L = N / 2, U = 3 * L;
   static_assert(U / 8 == 3 * NT, "three 8-code vectors per thread");
   extern __shared__ __align__(16) float2 kk_smem[];
@@ -50,7 +53,7 @@ __global__ void __launch_bounds__(N / 16) kk_kernel(KKArgs a) {
   __shared__ float2 tw_s[2 * kTwSplit];
   for (int i = threadIdx.x; i < 2 * kTwSplit; i += NT) tw_s[i] = a.tw2[i];
 
-  const long long seg = a.seg0 + 2LL * blockIdx.x;   // first segment of the pair
+  const long long seg = a.seg0 + 2LL * pair;   // first segment of the pair
   const long long lo = seg * L - N / 4;              // stream index of u_s[0]
   auto u2_of = [&](float code) { return 0.5f * log2f(fmaxf(a.gain * (code - a.offset), a.i_min)); };
   const long long off = lo - a.new_start;
@@ -115,24 +118,67 @@ __global__ void __launch_bounds__(N / 16) kk_kernel(KKArgs a) {
   }
 }
 
+template <int N>
+__global__ void __launch_bounds__(N / 16) kk_kernel(KKArgs a) {
+  kk_pair<N>(a, blockIdx.x);
+}
+
+// Many channels in one launch: block b belongs to the channel c with
+// offs[c] <= b < offs[c + 1] (uneven pushes give uneven counts); blocks
+// past offs[nch] (the launch may be sized for more) return at once.
+template <int N>
+__global__ void __launch_bounds__(N / 16) kk_batch_kernel(const KKBatchTable* __restrict__ t) {
+  const long long b = blockIdx.x;
+  if (b >= t->offs[t->nch]) return;
+  int lo = 0, hi = t->nch;  // offs[lo] <= b < offs[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (t->offs[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  const KKArgs a = t->args[lo];
+  kk_pair<N>(a, b - t->offs[lo]);
+}
+
 // New carry: codes [keep_from, in_end) from the old carry and the push.
-__global__ void kk_carry_kernel(KKArgs a, int16_t* dst, long long keep_from) {
+__device__ __forceinline__ void kk_carry_copy(const KKArgs& a, int16_t* dst, long long keep_from, long long i0,
+                                              long long step) {
   const long long n = a.in_end - keep_from;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = i0; i < n; i += step) {
     const long long k = keep_from + i;
     dst[i] = k < a.new_start ? a.carry[k - a.carry_start] : a.in[k - a.new_start];
   }
 }
 
+__global__ void kk_carry_kernel(KKArgs a, int16_t* dst, long long keep_from) {
+  kk_carry_copy(a, dst, keep_from, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
+// One block per channel of the table (a carry is shorter than N codes).
+__global__ void kk_carry_batch_kernel(const KKBatchTable* __restrict__ t) {
+  if ((int)blockIdx.x >= t->nch) return;
+  const KKArgs a = t->args[blockIdx.x];
+  kk_carry_copy(a, t->carry_dst[blockIdx.x], t->keep_from[blockIdx.x], threadIdx.x, blockDim.x);
+}
+
+template <int N>
+static cudaError_t kk_attr() {
+  constexpr size_t bytes = kk_smem_bytes<N>();
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  static const cudaError_t attr = [] {  // opt in above the default (once per process)
+    cudaError_t e = cudaFuncSetAttribute(kk_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kk_batch_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return e;
+  }();
+  return attr;
+}
+
 template <int N>
 static cudaError_t launch_kk_t(const KKArgs& a, unsigned blocks, cudaStream_t s) {
-  constexpr size_t bytes = kk_smem_bytes<N>();
-  if (bytes > 48 * 1024) {  // opt in above the default (once per process)
-    static const cudaError_t attr =
-        cudaFuncSetAttribute(kk_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (attr != cudaSuccess) return attr;
-  }
-  kk_kernel<N><<<blocks, N / 16, bytes, s>>>(a);
+  const cudaError_t e = kk_attr<N>();
+  if (e != cudaSuccess) return e;
+  kk_kernel<N><<<blocks, N / 16, kk_smem_bytes<N>(), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -145,6 +191,23 @@ cudaError_t launch_kk(const KKArgs& a, int N, long long nseg, cudaStream_t s) {
     case 4096: return launch_kk_t<4096>(a, blocks, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t kk_batch_nodes(int N, cudaKernelNodeParams* field, cudaKernelNodeParams* carry) {
+  std::memset(field, 0, sizeof(*field));
+  std::memset(carry, 0, sizeof(*carry));
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (N) {
+    case 1024: e = kk_attr<1024>(); field->func = (void*)kk_batch_kernel<1024>; break;
+    case 2048: e = kk_attr<2048>(); field->func = (void*)kk_batch_kernel<2048>; break;
+    case 4096: e = kk_attr<4096>(); field->func = (void*)kk_batch_kernel<4096>; break;
+    default: return cudaErrorInvalidValue;
+  }
+  field->blockDim = dim3(N / 16);
+  field->sharedMemBytes = (unsigned)(N * 8 + 3 * (N / 2) * 4);
+  carry->func = (void*)kk_carry_batch_kernel;
+  carry->blockDim = dim3(256);
+  return e;
 }
 
 cudaError_t launch_kk_carry(const KKArgs& a, int16_t* dst, long long keep_from, cudaStream_t s) {

@@ -19,7 +19,22 @@ struct KKArgs {
   unsigned long long nu_fx;      // downshift frequency / sample rate, fixed point 2^-64
 };
 
+// Arguments of many channels' pushes in one launch (rx_kk_batch_push):
+// channel c's blocks are [offs[c], offs[c + 1]).
+constexpr int kKKBatchMax = 256;
+struct KKBatchTable {
+  int nch;
+  int pad;
+  long long offs[kKKBatchMax + 1];
+  KKArgs args[kKKBatchMax];
+  int16_t* carry_dst[kKKBatchMax];
+  long long keep_from[kKKBatchMax];
+};
+
 cudaError_t launch_kk(const KKArgs& a, int N, long long nseg, cudaStream_t s);
+// Kernel-node templates (function, block, shared memory) of the batched
+// field and carry kernels for a graph; grid and arguments are the caller's.
+cudaError_t kk_batch_nodes(int N, cudaKernelNodeParams* field, cudaKernelNodeParams* carry);
 cudaError_t launch_kk_carry(const KKArgs& a, int16_t* dst, long long keep_from, cudaStream_t s);
 
 }  // namespace rx

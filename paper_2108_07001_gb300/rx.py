@@ -37,7 +37,7 @@ EXPORTS = ["rx_config_default", "rx_create", "rx_push_block", "rx_pull_bits", "r
            "rx_server_handle", "rx_server_close", "rx_server_stats", "rx_server_destroy",
            "rx_autotune_fft",
            "rx_kk_config_default", "rx_kk_create", "rx_kk_push", "rx_kk_end", "rx_kk_reset",
-           "rx_kk_position", "rx_kk_destroy",
+           "rx_kk_position", "rx_kk_destroy", "rx_kk_batch_create", "rx_kk_batch_push", "rx_kk_batch_destroy",
            "rx_kkrx_config_default", "rx_kkrx_create", "rx_kkrx_push", "rx_kkrx_end", "rx_kkrx_equalised",
            "rx_kkrx_reset", "rx_kkrx_destroy"]
 
@@ -222,6 +222,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rx_kk_position.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
     lib.rx_kk_destroy.argtypes = [P]
     lib.rx_kk_destroy.restype = None
+    lib.rx_kk_batch_create.argtypes = [ctypes.POINTER(P), I, ctypes.POINTER(P)]
+    lib.rx_kk_batch_push.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(SZ), ctypes.POINTER(P), ctypes.POINTER(SZ),
+                                     ctypes.POINTER(SZ), P]
+    lib.rx_kk_batch_destroy.argtypes = [P]
+    lib.rx_kk_batch_destroy.restype = None
     lib.rx_kkrx_config_default.argtypes = [ctypes.POINTER(KKRxConfig)]
     lib.rx_kkrx_config_default.restype = None
     lib.rx_kkrx_create.argtypes = [ctypes.POINTER(KKRxConfig), ctypes.POINTER(P)]
@@ -237,6 +242,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                  "rx_server_end", "rx_server_sync", "rx_server_pull_bits", "rx_server_stream_stats",
                  "rx_server_close", "rx_server_stats", "rx_server_destroy", "rx_autotune_fft",
                  "rx_kk_create", "rx_kk_push", "rx_kk_end", "rx_kk_reset", "rx_kk_position",
+                 "rx_kk_batch_create", "rx_kk_batch_push",
                  "rx_kkrx_create", "rx_kkrx_push", "rx_kkrx_end", "rx_kkrx_equalised", "rx_kkrx_reset"]:
         getattr(lib, name).restype = I
     _lib = lib
@@ -574,6 +580,54 @@ class KKFrontEnd:
         if getattr(self, "h", None):
             self.lib.rx_kk_destroy(self.h)
             self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class KKBatch:
+    """Several KK front ends pushed together (rx_kk_batch_*): one graph
+    replay per batch push, whatever the channels' push lengths."""
+
+    def __init__(self, channels: list):
+        self.lib = load()
+        self.channels = list(channels)
+        n = len(self.channels)
+        arr = (ctypes.c_void_p * n)(*[c.h.value for c in self.channels])
+        b = ctypes.c_void_p()
+        _check(self.lib.rx_kk_batch_create(arr, n, ctypes.byref(b)))
+        self.b = b
+        self._codes = (ctypes.c_void_p * n)()
+        self._n = (ctypes.c_size_t * n)()
+        self._out = (ctypes.c_void_p * n)()
+        self._cap = (ctypes.c_size_t * n)()
+        self._nout = (ctypes.c_size_t * n)()
+
+    def push(self, codes_ptrs, ns, out_ptrs, out_caps, stream: int = 0) -> list[int]:
+        """Device pointers and lengths per channel (n = 0: nothing for that
+        channel); returns the field samples written per channel."""
+        for i in range(len(self.channels)):
+            self._codes[i] = codes_ptrs[i]
+            self._n[i] = ns[i]
+            self._out[i] = out_ptrs[i]
+            self._cap[i] = out_caps[i]
+        _check(self.lib.rx_kk_batch_push(self.b, self._codes, self._n, self._out, self._cap, self._nout,
+                                         ctypes.c_void_p(stream)))
+        return list(self._nout)
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            self.lib.rx_kk_batch_destroy(self.b)
+            self.b = None
 
     def __enter__(self):
         return self

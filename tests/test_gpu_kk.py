@@ -163,3 +163,50 @@ def test_edge_cases():
         assert np.array_equal(out[:200].cpu().numpy(), first)
     want = K.kk_field(d["codes"][:200], d["gain"], d["offset"], 1024, d["f_c"] / d["fs"])
     check(first, want)
+
+
+def test_batch_push_equals_single_pushes():
+    """Six channels (different links) pushed together through one graph
+    replay per round, with uneven lengths per channel and round (empty,
+    below a quarter block, several blocks), give bit for bit the field of
+    the same pushes one channel at a time; the streams then end alike."""
+    import torch
+    rng = np.random.default_rng(77)
+    links = [link(4096 + 500 * c, seed=80 + c) for c in range(6)]
+    n = [d["codes"].size for d in links]
+    dev = torch.device("cuda:0")
+    codes = [torch.from_numpy(d["codes"]).to(dev) for d in links]
+    outs = {k: [torch.zeros(m, dtype=torch.complex64, device=dev) for m in n] for k in ("batch", "single")}
+    fes = {k: [frontend(d, 1024, block=20000) for d in links] for k in ("batch", "single")}
+    pos_in = [0] * 6
+    pos_out = {k: [0] * 6 for k in outs}
+    stream = torch.cuda.current_stream().cuda_stream
+    with rx.KKBatch(fes["batch"]) as batch:
+        for r in range(8):
+            sizes = [int(min(n[c] - pos_in[c], rng.choice([0, 3, 200, 1500, 9000, 20000]))) for c in range(6)]
+            got = batch.push([codes[c][pos_in[c]:].data_ptr() for c in range(6)], sizes,
+                             [outs["batch"][c][pos_out["batch"][c]:].data_ptr() for c in range(6)],
+                             [n[c] - pos_out["batch"][c] for c in range(6)], stream)
+            for c in range(6):
+                k = fes["single"][c].push_tensor(codes[c][pos_in[c]:pos_in[c] + sizes[c]],
+                                                 outs["single"][c][pos_out["single"][c]:])
+                assert got[c] == k
+                pos_out["batch"][c] += got[c]
+                pos_out["single"][c] += k
+                pos_in[c] += sizes[c]
+    for key in outs:
+        for c in range(6):
+            fe = fes[key][c]
+            rest = torch.from_numpy(links[c]["codes"][pos_in[c]:]).to(dev)
+            p = pos_out[key][c]
+            p += fe.push_tensor(rest, outs[key][c][p:]) if rest.numel() else 0
+            p += fe.end_tensor(outs[key][c][p:])
+            assert p == n[c]
+            fe.close()
+    torch.cuda.synchronize()
+    for c in range(6):
+        a, b = outs["batch"][c].cpu().numpy(), outs["single"][c].cpu().numpy()
+        assert np.array_equal(a, b), c
+    want = K.kk_field(links[0]["codes"], links[0]["gain"], links[0]["offset"], 1024,
+                      links[0]["f_c"] / links[0]["fs"])
+    check(outs["batch"][0].cpu().numpy(), want)
