@@ -122,16 +122,30 @@ __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
   float2* ys2 = reinterpret_cast<float2*>(ybase) + warp * SM::YSP;
   // the paired form stages whole super-steps (zeros past the run) and so
   // runs every super-step, the partial last one included, without predicates
-  const int staged = PAIR ? SM::NSUP * WIN : total;
-  for (int i = lane; i < staged; i += 32) {
-    const bool in = i >= sv_lo && i < sv_hi;
-    const float2 v = in ? yf[kr - W - fbase + i] : make_float2(0.f, 0.f);
-    if (PAIR) {
-      const float h = in ? fmaf(v.x, v.x, fmaf(v.y, v.y, 1.f)) * (1.f + 0x1p-17f) : 0.f;
-      ys4[i] = make_float4(v.x, v.y, v.y, v.x);
-      hs2[i] = make_float2(h, h);
-    } else {
-      ys2[i] = v;
+  if constexpr (PAIR) {
+    // a fixed count per lane: every lane's loads are in flight before the
+    // first store
+    constexpr int PER = (SM::NSUP * WIN + 31) / 32;
+    float2 v[PER];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int i = lane + 32 * r;
+      v[r] = (i < SM::NSUP * WIN && i >= sv_lo && i < sv_hi) ? yf[kr - W - fbase + i] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int i = lane + 32 * r;
+      if (i < SM::NSUP * WIN) {
+        const bool in = i >= sv_lo && i < sv_hi;
+        const float h = in ? fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, 1.f)) * (1.f + 0x1p-17f) : 0.f;
+        ys4[i] = make_float4(v[r].x, v[r].y, v[r].y, v[r].x);
+        hs2[i] = make_float2(h, h);
+      }
+    }
+  } else {
+    for (int i = lane; i < total; i += 32) {
+      const bool in = i >= sv_lo && i < sv_hi;
+      ys2[i] = in ? yf[kr - W - fbase + i] : make_float2(0.f, 0.f);
     }
   }
   const bool edge = sv_lo > 0 || sv_hi < total;

@@ -119,13 +119,26 @@ __global__ void __launch_bounds__(128, Bps2Smem<W, QAM16>::MIN_BLOCKS) bps2_kern
   const long long fbase = fa.f * (long long)d.F;
   const float2* yf = d.y + ((long long)(fa.f & 1) * 2 + pol) * (kYHist + d.F) + kYHist;
   const long long ylim = min(fa.n_sym, fbase + fa.Ff);  // symbols beyond do not exist (yet)
-  for (int e = lane; e < G * SM::STEPS; e += 32) {
-    const int g = e / SM::STEPS, i = e - g * SM::STEPS;
-    const long long k = kw0 + (long long)g * kRun - W + i;
-    const bool in = k >= 0 && k < ylim;
-    const float2 v = in ? yf[k - fbase] : make_float2(0.f, 0.f);
-    if (QAM16) ys4[g * SM::GS + i] = make_float4(v.x, v.y, in ? 1.f : 0.f, 0.f);
-    else ys2[g * SM::GS + i] = v;
+  // eight loads per lane in flight before their stores
+  for (int e0 = 0; e0 < G * SM::STEPS; e0 += 8 * 32) {
+    float2 v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int e = e0 + lane + 32 * r;
+      const int g = e / SM::STEPS, i = e - g * SM::STEPS;
+      const long long k = kw0 + (long long)g * kRun - W + i;
+      v[r] = (e < G * SM::STEPS && k >= 0 && k < ylim) ? yf[k - fbase] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int e = e0 + lane + 32 * r;
+      if (e < G * SM::STEPS) {
+        const int g = e / SM::STEPS, i = e - g * SM::STEPS;
+        const long long k = kw0 + (long long)g * kRun - W + i;
+        if (QAM16) ys4[g * SM::GS + i] = make_float4(v[r].x, v[r].y, (k >= 0 && k < ylim) ? 1.f : 0.f, 0.f);
+        else ys2[g * SM::GS + i] = v[r];
+      }
+    }
   }
   __syncthreads();  // cs_s, staged symbols
 
