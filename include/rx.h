@@ -500,21 +500,28 @@ void rx_kkrx_config_default(rx_kkrx_config* cfg);
 int rx_kkrx_create(const rx_kkrx_config* cfg, rx_kkrx** out);
 
 /* Appends n ADC codes (as rx_kk_push: on_device 1 = device pointer, 0 =
- * host memory).  The bits of every frame this push completes are written
- * to bits (device memory, packed) in stream order on cuda_stream, *n_bits
- * of them (a whole number of frames).  A frame completes once the 2-sps
- * samples reach 2(f+1)F + 1.  RX_EINVAL if bits_cap_bytes is too small. */
+ * host memory).  The bits of every frame this push completes, *n_bits of
+ * them (a whole number of frames), are written to bits (device memory,
+ * packed); a frame completes once the 2-sps samples reach 2(f+1)F + 1.
+ * The front end runs in stream order on cuda_stream, the equaliser and the
+ * DD-LMS on the handle's own stream, so successive pushes overlap: the bits
+ * are in place (and the codes' device memory free) in cuda_stream's order
+ * after rx_kkrx_end, or after cudaDeviceSynchronize.  RX_EINVAL if
+ * bits_cap_bytes is too small. */
 int rx_kkrx_push(rx_kkrx* h, const int16_t* codes, size_t n, int on_device, uint8_t* bits,
                  size_t bits_cap_bytes, size_t* n_bits, void* cuda_stream);
 
 /* End of stream: the remaining frames (the last one may be short; symbols
- * = codes / 4) and their bits; samples past the end count as zero. */
+ * = codes / 4) and their bits; samples past the end count as zero.  Joins
+ * the handle's stream onto cuda_stream: all of the stream's bits are in
+ * place in cuda_stream's order. */
 int rx_kkrx_end(rx_kkrx* h, uint8_t* bits, size_t bits_cap_bytes, size_t* n_bits, void* cuda_stream);
 
 /* Equalised symbols [first, first + n) (within history_syms) as complex
  * float pairs, copied to host memory after the device is idle. */
 int rx_kkrx_equalised(rx_kkrx* h, int64_t first, int64_t n, float* out);
 
+/* Starts a new stream (waits for the handle's own stream first). */
 int rx_kkrx_reset(rx_kkrx* h);
 
 void rx_kkrx_destroy(rx_kkrx* h);

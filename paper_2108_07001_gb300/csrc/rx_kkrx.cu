@@ -13,6 +13,14 @@
 //               the first frame is preceded by the acquisition chain.
 // The 2-sps samples wait in one of two buffers from 2fF - 2 on; after the
 // frames of a push the rest moves to the other buffer's front.
+//
+// Streams: the front end runs on the caller's stream, the equaliser, the
+// DD-LMS and the decisions on the handle's own (non-blocking) stream, so
+// the front end of push k + 1 overlaps the equaliser and DD-LMS of push k.
+// The front end writes its field into one of two buffers (push k: buffer
+// k mod 2); an event per buffer hands it to the equaliser, another hands it
+// back once the equaliser has read it.  rx_kkrx_end joins the handle's
+// stream back onto the caller's.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,8 +45,11 @@ struct rx_kkrx {
   long long in4 = 0, out2 = 0;
   int cur4 = 0;
   float2* carry4[2] = {nullptr, nullptr};
-  float2* field = nullptr;   // the front end's output of one push
+  float2* field[2] = {nullptr, nullptr};  // the front end's output of push k in field[k & 1]
   size_t field_cap = 0;
+  long long npush = 0;       // pushes (and the end) that ran the front end
+  cudaStream_t s2 = nullptr; // equaliser + DD-LMS stream
+  cudaEvent_t ev_field[2] = {nullptr, nullptr}, ev_read[2] = {nullptr, nullptr}, ev_join = nullptr;
   float2* H2 = nullptr;
   float2* tw4 = nullptr;
   // DD-LMS stage
@@ -77,13 +88,13 @@ long long eq_out_after(const rx_kkrx* h, long long in4) {
   return q >= h->L4 ? q / h->L4 * h->L2 : 0;
 }
 
-// Equaliser over the new field [in4, in4 + n) (in h->field), producing
+// Equaliser over the new field [in4, in4 + n) (in field), producing
 // 2-sps samples up to out2_new.
-int run_eq(rx_kkrx* h, long long n, long long out2_new, cudaStream_t s) {
+int run_eq(rx_kkrx* h, const float2* field, long long n, long long out2_new, cudaStream_t s) {
   rx::KKEqArgs a;
   a.carry = h->carry4[h->cur4];
   a.carry_start = std::max(0LL, 2 * h->out2 - h->N4 / 4);
-  a.in = h->field;
+  a.in = field;
   a.new_start = h->in4;
   a.in_end = h->in4 + n;
   a.seg0 = h->out2 / h->L2;
@@ -228,7 +239,14 @@ extern "C" int rx_kkrx_create(const rx_kkrx_config* cfg, rx_kkrx** out) {
   h->field_cap = c.fe.max_block_samples + c.fe.fft_n;
   // 2-sps samples waiting: two frames' worth plus one push's output
   h->x2_cap = 2LL * h->F + 16 + (long long)(c.fe.max_block_samples + c.fe.fft_n + h->N4) / 2 + h->L2;
-  bool ok = cudaMalloc(&h->field, h->field_cap * sizeof(float2)) == cudaSuccess &&
+  bool ok = cudaMalloc(&h->field[0], h->field_cap * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc(&h->field[1], h->field_cap * sizeof(float2)) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&h->ev_field[0], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&h->ev_field[1], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&h->ev_read[0], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&h->ev_read[1], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess &&
             cudaMalloc(&h->carry4[0], h->N4 * sizeof(float2)) == cudaSuccess &&
             cudaMalloc(&h->carry4[1], h->N4 * sizeof(float2)) == cudaSuccess &&
             cudaMalloc(&h->H2, (h->N4 / 2) * sizeof(float2)) == cudaSuccess &&
@@ -293,15 +311,20 @@ extern "C" int rx_kkrx_push(rx_kkrx* h, const int16_t* codes, size_t n, int on_d
     return fail("rx_kkrx_push: bits is null or bits_cap_bytes is smaller than the frames this push completes",
                 RX_EINVAL);
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int fb = (int)(h->npush & 1);
+  int rc = RX_OK;
+  if (h->npush >= 2) rc = cuda_rc(cudaStreamWaitEvent(s, h->ev_read[fb], 0), "rx_kkrx_push: field buffer");
+  if (rc) return rc;
   size_t got = 0;
-  int rc = rx_kk_push(h->fe, codes, n, on_device, reinterpret_cast<float*>(h->field), h->field_cap, &got, s);
+  rc = rx_kk_push(h->fe, codes, n, on_device, reinterpret_cast<float*>(h->field[fb]), h->field_cap, &got, s);
   if (rc) return rc;
   if ((long long)got != c1) return fail("rx_kkrx_push: front-end output count mismatch", RX_EINVAL);
-  if (got > 0) {
-    rc = run_eq(h, (long long)got, out2_new, s);
-    if (rc) return rc;
-  }
-  rc = run_frames(h, nf, false, 0, bits, s);
+  h->npush++;
+  rc = cuda_rc(cudaEventRecord(h->ev_field[fb], s), "rx_kkrx_push: event");
+  if (!rc) rc = cuda_rc(cudaStreamWaitEvent(h->s2, h->ev_field[fb], 0), "rx_kkrx_push: event");
+  if (!rc && got > 0) rc = run_eq(h, h->field[fb], (long long)got, out2_new, h->s2);
+  if (!rc) rc = cuda_rc(cudaEventRecord(h->ev_read[fb], h->s2), "rx_kkrx_push: event");
+  if (!rc) rc = run_frames(h, nf, false, 0, bits, h->s2);
   if (rc) return rc;
   *n_bits = need * 8;
   return RX_OK;
@@ -322,14 +345,22 @@ extern "C" int rx_kkrx_end(rx_kkrx* h, uint8_t* bits, size_t bits_cap_bytes, siz
   if (need > 0 && (!bits || bits_cap_bytes < need))
     return fail("rx_kkrx_end: bits is null or bits_cap_bytes is smaller than the remaining frames' bits", RX_EINVAL);
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  size_t got = 0;
-  int rc = rx_kk_end(h->fe, reinterpret_cast<float*>(h->field), h->field_cap, &got, s);
+  const int fb = (int)(h->npush & 1);
+  int rc = RX_OK;
+  if (h->npush >= 2) rc = cuda_rc(cudaStreamWaitEvent(s, h->ev_read[fb], 0), "rx_kkrx_end: field buffer");
   if (rc) return rc;
-  if (n2 > h->out2) {
-    rc = run_eq(h, (long long)got, n2, s);
-    if (rc) return rc;
-  }
-  rc = run_frames(h, nf, true, n_sym, bits, s);
+  size_t got = 0;
+  rc = rx_kk_end(h->fe, reinterpret_cast<float*>(h->field[fb]), h->field_cap, &got, s);
+  if (rc) return rc;
+  h->npush++;
+  rc = cuda_rc(cudaEventRecord(h->ev_field[fb], s), "rx_kkrx_end: event");
+  if (!rc) rc = cuda_rc(cudaStreamWaitEvent(h->s2, h->ev_field[fb], 0), "rx_kkrx_end: event");
+  if (!rc && n2 > h->out2) rc = run_eq(h, h->field[fb], (long long)got, n2, h->s2);
+  if (!rc) rc = cuda_rc(cudaEventRecord(h->ev_read[fb], h->s2), "rx_kkrx_end: event");
+  if (!rc) rc = run_frames(h, nf, true, n_sym, bits, h->s2);
+  // the bits and the handle's state are complete in the caller's stream order from here
+  if (!rc) rc = cuda_rc(cudaEventRecord(h->ev_join, h->s2), "rx_kkrx_end: join");
+  if (!rc) rc = cuda_rc(cudaStreamWaitEvent(s, h->ev_join, 0), "rx_kkrx_end: join");
   if (rc) return rc;
   h->ended = true;
   *n_bits = nf > 0 ? (size_t)((nf - 1) * (long long)h->F + last) * h->bps : 0;
@@ -348,6 +379,9 @@ extern "C" int rx_kkrx_equalised(rx_kkrx* h, int64_t first, int64_t n, float* ou
 
 extern "C" int rx_kkrx_reset(rx_kkrx* h) {
   if (!h) return fail("rx_kkrx_reset: null handle", RX_EINVAL);
+  const int rc = cuda_rc(cudaStreamSynchronize(h->s2), "rx_kkrx_reset");  // no work of the old stream in flight
+  if (rc) return rc;
+  h->npush = 0;
   rx_kk_reset(h->fe);
   h->ended = false;
   h->in4 = h->out2 = 0;
@@ -361,7 +395,15 @@ extern "C" void rx_kkrx_destroy(rx_kkrx* h) {
   if (!h) return;
   cudaSetDevice(h->cfg.fe.device);
   rx_kk_destroy(h->fe);
-  cudaFree(h->field);
+  if (h->s2) cudaStreamSynchronize(h->s2);
+  cudaFree(h->field[0]);
+  cudaFree(h->field[1]);
+  for (int i = 0; i < 2; ++i) {
+    if (h->ev_field[i]) cudaEventDestroy(h->ev_field[i]);
+    if (h->ev_read[i]) cudaEventDestroy(h->ev_read[i]);
+  }
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->s2) cudaStreamDestroy(h->s2);
   cudaFree(h->carry4[0]);
   cudaFree(h->carry4[1]);
   cudaFree(h->H2);

@@ -149,3 +149,31 @@ def test_short_streams():
         bits, y = run_chain(d, cfg, [d["codes"].size])
         ref = oracle(d, cfg)
         compare(bits, y, ref, 2)
+
+
+def test_reset_reproduces_the_stream():
+    """A second stream on the same handle after rx_kkrx_reset gives the same
+    bits as the first (every stage's positions, carries and taps restart)."""
+    import torch
+    F = 1 << 12
+    d = case(4, 2 * F + 99, 77, 16.0, 14.0)
+    cfg = chain_cfg(d, 4, F, acq=2048, mu=2e-3)
+    codes = torch.from_numpy(d["codes"]).cuda()
+    n = codes.numel()
+    nbytes = (n // 4 * 4 + 7) // 8
+    outs = []
+    stream = torch.cuda.current_stream().cuda_stream
+    with rx.KKReceiver(cfg) as r:
+        for _ in range(2):
+            bits = torch.zeros(nbytes + 64, dtype=torch.uint8, device="cuda")
+            nb = 0
+            for a in range(0, n, 7000):
+                m = min(7000, n - a)
+                nb += r.push_device(codes.data_ptr() + 2 * a, m, bits.data_ptr() + nb // 8, bits.numel() - nb // 8,
+                                    stream)
+            nb += r.end(bits.data_ptr() + nb // 8, bits.numel() - nb // 8, stream)
+            torch.cuda.synchronize()
+            outs.append((nb, bits.cpu().numpy()))
+            r.reset()
+    assert outs[0][0] == outs[1][0] == (n // 4) * 4
+    assert np.array_equal(outs[0][1], outs[1][1])

@@ -117,12 +117,13 @@ def test_qam16_parity(stride):
     r.close()
 
 
-def test_fp16_storage_parity():
+@STRIDES
+def test_fp16_storage_parity(stride):
     """Complex-half storage: the oracle runs on the same half-precision
-    samples, so only the arithmetic differs."""
+    samples, so only the arithmetic differs (full and two-stage BPS)."""
     sim = rxsim.simulate(link(n_sym=1 << 15, snr_db=12.0, fiber_len_m=1000e3, prbs_seed=5, seed=55,
                               out_dtype="c16"))
-    rx_kw = dict(fiber_len_m=1000e3, frame_syms=1 << 15, prbs_seed=5, storage_dtype=2)
+    rx_kw = dict(fiber_len_m=1000e3, frame_syms=1 << 15, prbs_seed=5, storage_dtype=2, bps_coarse_stride=stride)
     gpu, r = run_gpu(sim["rx"], rx_kw)
     ref = run_oracle(sim["rx"], rx_kw)
     compare(gpu, ref, rx_kw)
