@@ -792,6 +792,88 @@ def run_kk_batch(args):
             "batch_equals_per_channel": same}
 
 
+def run_kkrx_batch(args):
+    """Many whole KK receivers with small, uneven buffers: 64 receivers
+    (frames of 2^16 symbols = 65 us of signal, acquisition 4096), each round pushing
+    2^12..2^16 codes per receiver, as one batch push per round
+    (rx_kkrx_batch_push: a front-end graph, an equaliser graph, the DD-LMS
+    of completed frames) and as one push per receiver (rx_kkrx_push), all
+    streams ended; throughput, host time, and the bits of both forms."""
+    import torch
+    from paper_2108_07001_gb300 import rx
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    d = kk_link(1 << 23)
+    codes = torch.from_numpy(d["codes"]).to(dev)
+    rng = np.random.default_rng(6)
+    sizes = rng.integers(1 << 12, (1 << 16) + 1, (KKB_ROUNDS, KKB_CHANNELS))
+    per = sizes.sum(axis=0)
+    total = int(per.sum())
+    starts = [4 * (int(s) // 4) for s in rng.integers(0, (1 << 23) - int(per.max()), KKB_CHANNELS)]  # whole symbols
+    nbytes = int(per.max()) // 4 * 2 // 8 + 4096
+    bits = torch.zeros((KKB_CHANNELS, nbytes), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    base, bbase = codes.data_ptr(), bits.data_ptr()
+    fe = dict(fs_hz=d["fs"], f_shift_hz=d["f_c"], adc_gain=d["gain"], adc_offset=d["offset"], fft_n=1024,
+              max_block_samples=1 << 16)
+    rcfg = dict(baud_hz=1e9, modulation=2, fiber_len_m=1000e3, rrc_rolloff=0.01, eq_fft_n=1024, mu=5e-3, seg_syms=512,
+                frame_syms=1 << 16, acq_syms=4096)
+
+    def run(mode):
+        rcvs = [rx.KKReceiver(fe=fe, **rcfg) for _ in range(KKB_CHANNELS)]
+        batch = rx.KKReceiverBatch(rcvs) if mode == "batch" else None
+        pin = list(starts)
+        nb = [0] * KKB_CHANNELS
+        bits.zero_()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        h0 = time.perf_counter()
+        for r in range(KKB_ROUNDS):
+            if batch is not None:
+                got = batch.push([base + 2 * pin[c] for c in range(KKB_CHANNELS)], [int(x) for x in sizes[r]],
+                                 [bbase + c * nbytes + nb[c] // 8 for c in range(KKB_CHANNELS)],
+                                 [nbytes - nb[c] // 8 for c in range(KKB_CHANNELS)], stream)
+            else:
+                got = [rcvs[c].push_device(base + 2 * pin[c], int(sizes[r, c]), bbase + c * nbytes + nb[c] // 8,
+                                           nbytes - nb[c] // 8, stream) for c in range(KKB_CHANNELS)]
+            for c in range(KKB_CHANNELS):
+                pin[c] += int(sizes[r, c])
+                nb[c] += got[c]
+        if batch is not None:
+            batch.close()
+        for c in range(KKB_CHANNELS):
+            nb[c] += rcvs[c].end(bbase + c * nbytes + nb[c] // 8, nbytes - nb[c] // 8, stream)
+        h1 = time.perf_counter()
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        for r_ in rcvs:
+            r_.close()
+        return ms, (h1 - h0) * 1e3, bits.clone(), nb
+
+    forms, out = {}, {}
+    for mode in ("per_channel", "batch"):
+        run(mode)  # warm-up
+        ms, host_ms, b, nb = run(mode)
+        out[mode] = (b, nb)
+        forms[mode] = {"gsamples_s": round(total / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3),
+                       "host_ms": round(host_ms, 3)}
+    same = bool(torch.equal(out["batch"][0], out["per_channel"][0])) and out["batch"][1] == out["per_channel"][1]
+    # BER of channel 0 against the transmitted bits of its window
+    sym0 = starts[0] // 4
+    tx = np.tile(d["bits"], 2)[2 * sym0:2 * sym0 + out["batch"][1][0]]
+    got0 = np.unpackbits(out["batch"][0][0].cpu().numpy())[:out["batch"][1][0]]
+    ber0 = float(np.mean(got0[2 * 4096:-256] != tx[2 * 4096:-256]))
+    return {"metric": "gsamples_per_s", "value": forms["batch"]["gsamples_s"], "unit": "Gsamples/s", "n_gpus": 1,
+            "higher_is_better": True, "workload": "kkrx_batch", "dtype": "f32 (int16 codes in, packed bits out)",
+            "data": "synthetic (seeded minimum-phase link simulator)",
+            "config": {"receivers": KKB_CHANNELS, "rounds": KKB_ROUNDS, "codes_per_push": "2^12..2^16 per receiver",
+                       "codes_total": total, "frame_syms": 1 << 16, "fft_n": 1024, "eq_fft_n": 1024},
+            "forms": forms, "x_per_channel": round(forms["batch"]["gsamples_s"] / forms["per_channel"]["gsamples_s"], 2),
+            "batch_equals_per_channel": same, "ber_receiver0": ber0}
+
+
 def combine_replicas(line, world, reduce_max):
     """Whole-job line of N independent replicas: the step time (and the
     end-to-end step time) is the maximum over ranks (reduce_max: list of
@@ -1067,13 +1149,14 @@ def main():
     ap.add_argument("--kk-oracle-child", type=int, help=argparse.SUPPRESS)
     ap.add_argument("--bps-coarse-stride", type=int, default=1,
                     help="stream workload: 4 = two-stage BPS over 16 coarse angles (default 1: all 64)")
-    ap.add_argument("--workload", default="stream", choices=["stream", "qam16", "serving", "batched", "kk", "kk_batch"],
+    ap.add_argument("--workload", default="stream", choices=["stream", "qam16", "serving", "batched", "kk", "kk_batch", "kkrx_batch"],
                     help="stream: the 2^24-symbol DP-QPSK stream (default line); qam16: DP-16QAM 5,000 km "
                          "with FP16 and FP32 sample storage against the FP64 oracle; serving: 16 mixed "
                          "channel streams through the serving layer at 80 %% of its capacity; batched: 64 "
                          "streams with uneven blocks, FFT sizes from the heuristic and from the autotuner; "
                          "kk: the paper's Kramers-Kronig receiver on 2^22-sample buffers of 12-bit codes; "
-                         "kk_batch: 64 KK front ends with small uneven pushes, one graph replay per round")
+                         "kk_batch: 64 KK front ends with small uneven pushes, one graph replay per round; "
+                         "kkrx_batch: 64 whole KK receivers the same way")
     args = ap.parse_args()
     if args.kk_oracle_child:
         kk_oracle_child(args.kk_oracle_child)
@@ -1123,6 +1206,9 @@ def main():
         return
     if args.workload == "kk_batch":
         print(json.dumps(run_kk_batch(args)), flush=True)
+        return
+    if args.workload == "kkrx_batch":
+        print(json.dumps(run_kkrx_batch(args)), flush=True)
         return
     print(json.dumps(run_ours(args)), flush=True)
 

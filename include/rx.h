@@ -524,6 +524,29 @@ int rx_kkrx_equalised(rx_kkrx* h, int64_t first, int64_t n, float* out);
 /* Starts a new stream (waits for the handle's own stream first). */
 int rx_kkrx_reset(rx_kkrx* h);
 
+/* Many receivers in one launch per stage: rx_kkrx_batch_push runs every
+ * channel's front end in one rx_kk_batch graph replay, every channel's
+ * new equaliser segments in one more graph replay (uneven counts; a block
+ * finds its channel from their prefix sums) and the DD-LMS of each frame
+ * that completed, all in stream order on cuda_stream.  Each channel's bits
+ * are those of rx_kkrx_push with the same codes.  The channels must share
+ * fe.fft_n, eq_fft_n, frame_syms, seg_syms, acq_syms, modulation and device,
+ * and are not pushed otherwise while the batch is in use; their streams
+ * end with rx_kkrx_end.  rx_kkrx_batch_destroy does not free them. */
+typedef struct rx_kkrx_batch rx_kkrx_batch;
+
+/* n_channels in 1..256 distinct handles (waits for their own streams). */
+int rx_kkrx_batch_create(rx_kkrx* const* channels, int n_channels, rx_kkrx_batch** out);
+
+/* For every channel c: n[c] codes at the device pointer codes[c] (0: none),
+ * the bits of the frames it completes to bits[c] (device, capacity
+ * bits_cap_bytes[c]), n_bits[c] of them.  Checks every channel before
+ * launching anything. */
+int rx_kkrx_batch_push(rx_kkrx_batch* b, const int16_t* const* codes, const size_t* n, uint8_t* const* bits,
+                       const size_t* bits_cap_bytes, size_t* n_bits, void* cuda_stream);
+
+void rx_kkrx_batch_destroy(rx_kkrx_batch* b);
+
 void rx_kkrx_destroy(rx_kkrx* h);
 
 #ifdef __cplusplus

@@ -19,6 +19,8 @@
 // the inverse reuses the table of N4 at stride 2); the DD-LMS runs one warp per
 // segment, two symbols per lane and sub-block, the sixteen gradient sums
 // all-reduced by shuffles, decisions and bits in the same pass.
+#include <cstring>
+
 #include "fft_smem.cuh"
 #include "kkrx_internal.h"
 
@@ -29,14 +31,15 @@ __device__ __forceinline__ float2 kkrx_in(const KKEqArgs& a, long long i) {
   return i < a.new_start ? a.carry[i - a.carry_start] : a.in[i - a.new_start];
 }
 
+// Output segment a.seg0 + seg by one block of N4/16 threads.
 template <int N4>
-__global__ void __launch_bounds__(N4 / 16) kkeq_kernel(KKEqArgs a) {
+__device__ __forceinline__ void kkeq_segment(const KKEqArgs& a, long long seg) {
   constexpr int NT = N4 / 16, L4 = N4 / 2, L2 = N4 / 4, NB2 = N4 / 2;
   static_assert(N4 / 2 == 8 * NT, "eight two-sample vectors per thread");
   __shared__ __align__(16) float2 buf[N4];
   __shared__ float2 tw_s[2 * kTwSplit];
   for (int i = threadIdx.x; i < 2 * kTwSplit; i += NT) tw_s[i] = a.tw2[i];
-  const long long b = a.seg0 + blockIdx.x;
+  const long long b = a.seg0 + seg;
   const long long lo = b * L4 - N4 / 4;
   const long long off = lo - a.new_start;
   if (off >= 0 && lo + N4 <= a.in_end && (off & 1) == 0 && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0) {
@@ -76,14 +79,51 @@ __global__ void __launch_bounds__(N4 / 16) kkeq_kernel(KKEqArgs a) {
   }
 }
 
+template <int N4>
+__global__ void __launch_bounds__(N4 / 16) kkeq_kernel(KKEqArgs a) {
+  kkeq_segment<N4>(a, blockIdx.x);
+}
+
+// Many channels in one launch: block b belongs to the channel c with
+// offs[c] <= b < offs[c + 1]; blocks past offs[nch] return at once.
+template <int N4>
+__global__ void __launch_bounds__(N4 / 16) kkeq_batch_kernel(const KKEqBatchTable* __restrict__ t) {
+  const long long b = blockIdx.x;
+  if (b >= t->offs[t->nch]) return;
+  int lo = 0, hi = t->nch;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (t->offs[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  const KKEqArgs a = t->args[lo];
+  kkeq_segment<N4>(a, b - t->offs[lo]);
+}
+
 template <typename T>
-__global__ void kkrx_tail_kernel(const T* carry, long long carry_start, const T* in, long long new_start,
-                                 long long keep_from, long long in_end, T* dst) {
+__device__ __forceinline__ void kkrx_tail_copy(const T* carry, long long carry_start, const T* in, long long new_start,
+                                               long long keep_from, long long in_end, T* dst, long long i0,
+                                               long long step) {
   const long long n = in_end - keep_from;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = i0; i < n; i += step) {
     const long long k = keep_from + i;
     dst[i] = k < new_start ? carry[k - carry_start] : in[k - new_start];
   }
+}
+
+template <typename T>
+__global__ void kkrx_tail_kernel(const T* carry, long long carry_start, const T* in, long long new_start,
+                                 long long keep_from, long long in_end, T* dst) {
+  kkrx_tail_copy(carry, carry_start, in, new_start, keep_from, in_end, dst,
+                 blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
+// The equaliser carries of a batch, one block per channel (fewer than N4 samples each).
+__global__ void kkeq_tail_batch_kernel(const KKEqBatchTable* __restrict__ t) {
+  if ((int)blockIdx.x >= t->nch) return;
+  const KKEqArgs& a = t->args[blockIdx.x];
+  kkrx_tail_copy(a.carry, a.carry_start, a.in, a.new_start, t->keep_from[blockIdx.x], a.in_end,
+                 t->carry_dst[blockIdx.x], threadIdx.x, blockDim.x);
 }
 
 // Nearest level per dimension (a value on a threshold takes the larger
@@ -102,15 +142,16 @@ __device__ __forceinline__ float wl_level(float x, uint32_t& bits) {
   return l ? 0.707106781186547524f : -0.707106781186547524f;
 }
 
+// Segment seg of a DD-LMS launch by one warp.
 template <bool Q16>
-__global__ void __launch_bounds__(32) wl_kernel(WLArgs a) {
+__device__ __forceinline__ void wl_segment(const WLArgs& a, long long seg) {
   constexpr int BPS = Q16 ? 4 : 2;
   const int lane = threadIdx.x;
-  const long long s0 = a.k_a + (long long)blockIdx.x * a.seg;
+  const long long s0 = a.k_a + seg * a.seg;
   const long long s1 = min(s0 + a.seg, a.k_end);
   // taps (h1[0..3], h2[0..3]) kept in every lane
   float2 h[8];
-  const float2* tin = a.taps_in + (long long)blockIdx.x * a.taps_in_stride;
+  const float2* tin = a.taps_in + seg * a.taps_in_stride;
 #pragma unroll
   for (int i = 0; i < 8; ++i) h[i] = tin[i];
   for (long long k0 = s0; k0 < s1; k0 += 64) {
@@ -174,7 +215,37 @@ __global__ void __launch_bounds__(32) wl_kernel(WLArgs a) {
       h[i].y -= s * g[2 * i + 1];
     }
   }
-  if (lane < 8) a.taps_out[(long long)blockIdx.x * 8 + lane] = h[lane];
+  if (lane < 8) a.taps_out[seg * 8 + lane] = h[lane];
+}
+
+template <bool Q16>
+__global__ void __launch_bounds__(32) wl_kernel(WLArgs a) {
+  wl_segment<Q16>(a, blockIdx.x);
+}
+
+// One DD-LMS step (acquisitions, or the i-th completed frame) of many
+// channels: block b belongs to the entry e with offs[e] <= b < offs[e + 1].
+template <bool Q16>
+__global__ void __launch_bounds__(32) wl_batch_kernel(const WLBatchTable* __restrict__ t, int node) {
+  const int ne = t->n[node];
+  const long long b = blockIdx.x;
+  if (b >= t->offs[node][ne]) return;
+  int lo = 0, hi = ne;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (t->offs[node][mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  const WLArgs& a = t->args[node][lo];
+  wl_segment<Q16>(a, b - t->offs[node][lo]);
+}
+
+// The moves of the remaining 2-sps samples to the other buffer, a block per channel.
+__global__ void x2_shift_batch_kernel(const WLBatchTable* __restrict__ t) {
+  if ((int)blockIdx.x >= t->nshift) return;
+  const float2* src = t->shift_src[blockIdx.x];
+  float2* dst = t->shift_dst[blockIdx.x];
+  for (long long i = threadIdx.x; i < t->shift_n[blockIdx.x]; i += blockDim.x) dst[i] = src[i];
 }
 
 cudaError_t launch_kkeq(const KKEqArgs& a, int N4, long long nseg, cudaStream_t s) {
@@ -187,12 +258,39 @@ cudaError_t launch_kkeq(const KKEqArgs& a, int N4, long long nseg, cudaStream_t 
   return cudaGetLastError();
 }
 
+cudaError_t kkeq_batch_nodes(int N4, cudaKernelNodeParams* eq, cudaKernelNodeParams* tail) {
+  std::memset(eq, 0, sizeof(*eq));
+  std::memset(tail, 0, sizeof(*tail));
+  switch (N4) {
+    case 1024: eq->func = (void*)kkeq_batch_kernel<1024>; break;
+    case 2048: eq->func = (void*)kkeq_batch_kernel<2048>; break;
+    default: return cudaErrorInvalidValue;
+  }
+  eq->blockDim = dim3(N4 / 16);
+  tail->func = (void*)kkeq_tail_batch_kernel;
+  tail->blockDim = dim3(256);
+  return cudaSuccess;
+}
+
 cudaError_t launch_kkeq_tail(const float2* carry, long long carry_start, const float2* in, long long new_start,
                              long long keep_from, long long in_end, float2* dst, cudaStream_t s) {
   const long long n = in_end - keep_from;
   if (n <= 0) return cudaSuccess;
   kkrx_tail_kernel<float2><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(carry, carry_start, in, new_start, keep_from,
                                                                        in_end, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wl_batch(const WLBatchTable* t, int node, bool q16, long long blocks, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  if (q16) wl_batch_kernel<true><<<(unsigned)blocks, 32, 0, s>>>(t, node);
+  else wl_batch_kernel<false><<<(unsigned)blocks, 32, 0, s>>>(t, node);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_x2_shift_batch(const WLBatchTable* t, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  x2_shift_batch_kernel<<<(unsigned)n, 256, 0, s>>>(t);
   return cudaGetLastError();
 }
 

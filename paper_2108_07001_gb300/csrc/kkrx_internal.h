@@ -33,7 +33,41 @@ struct WLArgs {
   long long hist_syms;
 };
 
+// Equaliser arguments of many channels in one launch: channel c's blocks
+// are [offs[c], offs[c + 1]); its carry goes to carry_dst[c] from keep_from[c].
+constexpr int kKKEqBatchMax = 256;
+struct KKEqBatchTable {
+  int nch;
+  int pad;
+  long long offs[kKKEqBatchMax + 1];
+  KKEqArgs args[kKKEqBatchMax];
+  float2* carry_dst[kKKEqBatchMax];
+  long long keep_from[kKKEqBatchMax];
+};
+
+// DD-LMS work of many channels: node 0 holds the acquisitions, node 1 + i
+// the i-th frame each channel completed (a channel's frames run in order,
+// one node after the other); entry e of a node has blocks
+// [offs[node][e], offs[node][e + 1]).  Then the moves of the channels'
+// remaining 2-sps samples.
+constexpr int kWLNodes = 5;
+struct WLBatchTable {
+  int n[kWLNodes];
+  int nshift;
+  long long offs[kWLNodes][kKKEqBatchMax + 1];
+  WLArgs args[kWLNodes][kKKEqBatchMax];
+  const float2* shift_src[kKKEqBatchMax];
+  float2* shift_dst[kKKEqBatchMax];
+  long long shift_n[kKKEqBatchMax];
+};
+
+cudaError_t launch_wl_batch(const WLBatchTable* t, int node, bool q16, long long blocks, cudaStream_t s);
+cudaError_t launch_x2_shift_batch(const WLBatchTable* t, int n, cudaStream_t s);
+
 cudaError_t launch_kkeq(const KKEqArgs& a, int N4, long long nseg, cudaStream_t s);
+// Kernel-node templates of the batched equaliser and its carries (grid and
+// arguments are the caller's).
+cudaError_t kkeq_batch_nodes(int N4, cudaKernelNodeParams* eq, cudaKernelNodeParams* tail);
 cudaError_t launch_kkeq_tail(const float2* carry, long long carry_start, const float2* in, long long new_start,
                              long long keep_from, long long in_end, float2* dst, cudaStream_t s);
 cudaError_t launch_wl(const WLArgs& a, bool q16, long long nseg, cudaStream_t s);

@@ -88,10 +88,17 @@ long long eq_out_after(const rx_kkrx* h, long long in4) {
   return q >= h->L4 ? q / h->L4 * h->L2 : 0;
 }
 
-// Equaliser over the new field [in4, in4 + n) (in field), producing
-// 2-sps samples up to out2_new.
-int run_eq(rx_kkrx* h, const float2* field, long long n, long long out2_new, cudaStream_t s) {
+// The equaliser step over the new field [in4, in4 + n) (in field) that
+// produces 2-sps samples up to out2_new, without launching: its arguments,
+// segments and carry start.
+struct EqPlan {
   rx::KKEqArgs a;
+  long long nseg, keep;
+  long long n, out2_new;
+};
+
+int eq_plan(const rx_kkrx* h, const float2* field, long long n, long long out2_new, EqPlan* p) {
+  rx::KKEqArgs& a = p->a;
   a.carry = h->carry4[h->cur4];
   a.carry_start = std::max(0LL, 2 * h->out2 - h->N4 / 4);
   a.in = field;
@@ -104,17 +111,30 @@ int run_eq(rx_kkrx* h, const float2* field, long long n, long long out2_new, cud
   a.H2 = h->H2;
   a.tw2 = h->tw4;
   if (out2_new - h->x2_base > h->x2_cap) return fail("rx_kkrx: internal 2-sps buffer overflow", RX_EINVAL);
-  const long long nseg = (out2_new - h->out2 + h->L2 - 1) / h->L2;
-  int rc = cuda_rc(rx::launch_kkeq(a, h->N4, nseg, s), "rx_kkrx: equaliser kernel");
+  p->nseg = (out2_new - h->out2 + h->L2 - 1) / h->L2;
+  p->keep = std::max(0LL, 2 * out2_new - h->N4 / 4);
+  p->n = n;
+  p->out2_new = out2_new;
+  return RX_OK;
+}
+
+void eq_commit(rx_kkrx* h, const EqPlan& p) {
+  h->cur4 ^= 1;
+  h->in4 += p.n;
+  h->out2 = p.out2_new;
+}
+
+int run_eq(rx_kkrx* h, const float2* field, long long n, long long out2_new, cudaStream_t s) {
+  EqPlan p;
+  int rc = eq_plan(h, field, n, out2_new, &p);
   if (rc) return rc;
-  const long long keep = std::max(0LL, 2 * out2_new - h->N4 / 4);
-  rc = cuda_rc(rx::launch_kkeq_tail(a.carry, a.carry_start, a.in, a.new_start, keep, a.in_end,
+  rc = cuda_rc(rx::launch_kkeq(p.a, h->N4, p.nseg, s), "rx_kkrx: equaliser kernel");
+  if (rc) return rc;
+  rc = cuda_rc(rx::launch_kkeq_tail(p.a.carry, p.a.carry_start, p.a.in, p.a.new_start, p.keep, p.a.in_end,
                                     h->carry4[h->cur4 ^ 1], s),
                "rx_kkrx: equaliser carry");
   if (rc) return rc;
-  h->cur4 ^= 1;
-  h->in4 += n;
-  h->out2 = out2_new;
+  eq_commit(h, p);
   return RX_OK;
 }
 
@@ -127,62 +147,100 @@ long long frames_ready(const rx_kkrx* h, long long out2, bool end, long long n_s
   return f - h->frames;
 }
 
-// Runs `count` frames (the last may be short when end is set); bits of
-// frame frames + i go to bits + i F bps / 8.
-int run_frames(rx_kkrx* h, long long count, bool end, long long n_sym_end, uint8_t* bits, cudaStream_t s) {
-  const bool q16 = h->cfg.modulation == RX_QAM16;
+// The DD-LMS work of `count` frames (the last may be short when end is
+// set), without launching: the acquisition before the first frame, each
+// frame's arguments and segment count in order (bits of frame frames + i
+// go to bits + i F bps / 8), the move of the remaining 2-sps samples to the
+// other buffer, and the state after it.
+struct FramePlan {
+  bool has_acq = false;
+  rx::WLArgs acq;
+  std::vector<rx::WLArgs> frames;
+  std::vector<long long> segs;
+  long long shift_n = 0;  // samples moved (0: none)
+  const float2* shift_src = nullptr;
+  float2* shift_dst = nullptr;
+  long long frames_after = 0, x2_base_after = 0;
+  int curx_after = 0;
+};
+
+FramePlan plan_frames(const rx_kkrx* h, long long count, bool end, long long n_sym_end, uint8_t* bits) {
+  FramePlan p;
   const long long n2 = end ? h->out2 : (1LL << 62);  // before the end every sample read exists
+  rx::WLArgs base;
+  std::memset(&base, 0, sizeof(base));
+  base.x2 = h->x2buf[h->curx];
+  base.x2_base = h->x2_base;
+  base.n2 = n2;
+  base.mu = h->cfg.mu;
+  const float2* first_taps = h->acq_taps;
   for (long long i = 0; i < count; ++i) {
-    const long long f = h->frames;
+    const long long f = h->frames + i;
     const long long k_a = f * (long long)h->F;
     const long long k_end = end ? std::min(k_a + h->F, n_sym_end) : k_a + h->F;
-    rx::WLArgs w;
-    std::memset(&w, 0, sizeof(w));
-    w.x2 = h->x2buf[h->curx];
-    w.x2_base = h->x2_base;
-    w.n2 = n2;
-    w.mu = h->cfg.mu;
     if (f == 0) {  // acquisition: one sequential chain over the first symbols
       const long long acq = std::min<long long>(h->cfg.acq_syms, end ? n_sym_end : h->cfg.acq_syms);
-      w.k_a = 0;
-      w.k_end = acq;
-      w.seg = std::max(acq, 1LL);
-      w.taps_in = h->init_taps;
-      w.taps_out = h->acq_taps;
-      int rc = cuda_rc(rx::launch_wl(w, q16, acq > 0 ? 1 : 0, s), "rx_kkrx: acquisition");
-      if (rc) return rc;
-      if (acq == 0) {
-        rc = cuda_rc(cudaMemcpyAsync(h->acq_taps, h->init_taps, 8 * sizeof(float2), cudaMemcpyDeviceToDevice, s),
-                     "rx_kkrx: taps");
-        if (rc) return rc;
+      if (acq > 0) {
+        p.has_acq = true;
+        p.acq = base;
+        p.acq.k_a = 0;
+        p.acq.k_end = acq;
+        p.acq.seg = acq;
+        p.acq.taps_in = h->init_taps;
+        p.acq.taps_out = h->acq_taps;
+      } else {
+        first_taps = h->init_taps;  // nothing to acquire on: frame 0 starts from the initial taps
       }
     }
+    rx::WLArgs w = base;
     w.k_a = k_a;
     w.k_end = k_end;
     w.seg = h->S;
-    w.taps_in = f == 0 ? h->acq_taps : h->taps;
+    w.taps_in = f == 0 ? first_taps : h->taps;
     w.taps_in_stride = f == 0 ? 0 : 8;
     w.taps_out = h->taps;
     w.bits = bits + i * ((long long)h->F * h->bps / 8);
     w.k_bits = k_a;
     w.hist = h->hist;
     w.hist_syms = h->cfg.history_syms;
-    const int rc = cuda_rc(rx::launch_wl(w, q16, (k_end - k_a + h->S - 1) / h->S, s), "rx_kkrx: DD-LMS");
-    if (rc) return rc;
-    h->frames++;
+    p.frames.push_back(w);
+    p.segs.push_back((k_end - k_a + h->S - 1) / h->S);
   }
+  p.frames_after = h->frames + count;
+  p.curx_after = h->curx;
+  p.x2_base_after = h->x2_base;
   if (count > 0 && !end) {  // keep the 2-sps samples from 2 frames F - 2 on
-    const long long nb = 2 * h->frames * (long long)h->F - 2;
+    const long long nb = 2 * p.frames_after * (long long)h->F - 2;
     const long long keep = h->out2 - nb;
     if (keep > 0) {
-      const int rc = cuda_rc(cudaMemcpyAsync(h->x2buf[h->curx ^ 1], h->x2buf[h->curx] + (nb - h->x2_base),
-                                             keep * sizeof(float2), cudaMemcpyDeviceToDevice, s),
-                             "rx_kkrx: 2-sps carry");
-      if (rc) return rc;
+      p.shift_n = keep;
+      p.shift_src = h->x2buf[h->curx] + (nb - h->x2_base);
+      p.shift_dst = h->x2buf[h->curx ^ 1];
     }
-    h->curx ^= 1;
-    h->x2_base = nb;
+    p.curx_after = h->curx ^ 1;
+    p.x2_base_after = nb;
   }
+  return p;
+}
+
+void commit_frames(rx_kkrx* h, const FramePlan& p) {
+  h->frames = p.frames_after;
+  h->curx = p.curx_after;
+  h->x2_base = p.x2_base_after;
+}
+
+int run_frames(rx_kkrx* h, long long count, bool end, long long n_sym_end, uint8_t* bits, cudaStream_t s) {
+  const bool q16 = h->cfg.modulation == RX_QAM16;
+  const FramePlan p = plan_frames(h, count, end, n_sym_end, bits);
+  int rc = RX_OK;
+  if (p.has_acq) rc = cuda_rc(rx::launch_wl(p.acq, q16, 1, s), "rx_kkrx: acquisition");
+  for (size_t i = 0; i < p.frames.size() && !rc; ++i)
+    rc = cuda_rc(rx::launch_wl(p.frames[i], q16, p.segs[i], s), "rx_kkrx: DD-LMS");
+  if (!rc && p.shift_n > 0)
+    rc = cuda_rc(cudaMemcpyAsync(p.shift_dst, p.shift_src, p.shift_n * sizeof(float2), cudaMemcpyDeviceToDevice, s),
+                 "rx_kkrx: 2-sps carry");
+  if (rc) return rc;
+  commit_frames(h, p);
   return RX_OK;
 }
 
@@ -294,6 +352,24 @@ extern "C" int rx_kkrx_create(const rx_kkrx_config* cfg, rx_kkrx** out) {
   return RX_OK;
 }
 
+// What a push of n codes will complete: the front end's new field
+// samples, the equaliser's output position, the frames and their bytes.
+struct PushForecast {
+  long long c1, out2_new, nf;
+  size_t need;
+};
+
+PushForecast forecast(const rx_kkrx* h, size_t n) {
+  int64_t fin = 0, fout = 0;
+  rx_kk_position(h->fe, &fin, &fout);
+  PushForecast f;
+  f.c1 = kk_out_after(fin + (long long)n, h->cfg.fe.fft_n) - fout;
+  f.out2_new = eq_out_after(h, h->in4 + f.c1);
+  f.nf = frames_ready(h, f.out2_new, false, 0);
+  f.need = (size_t)f.nf * ((size_t)h->F * h->bps / 8);
+  return f;
+}
+
 extern "C" int rx_kkrx_push(rx_kkrx* h, const int16_t* codes, size_t n, int on_device, uint8_t* bits,
                             size_t bits_cap_bytes, size_t* n_bits, void* cuda_stream) {
   if (!h || !n_bits || (n > 0 && !codes)) return fail("rx_kkrx_push: null argument", RX_EINVAL);
@@ -301,12 +377,9 @@ extern "C" int rx_kkrx_push(rx_kkrx* h, const int16_t* codes, size_t n, int on_d
   if (h->ended) return fail("rx_kkrx_push: stream already ended", RX_ESTATE);
   if (n > h->cfg.fe.max_block_samples) return fail("rx_kkrx_push: n exceeds fe.max_block_samples", RX_EINVAL);
   if (n == 0) return RX_OK;
-  int64_t fin = 0, fout = 0;
-  rx_kk_position(h->fe, &fin, &fout);
-  const long long c1 = kk_out_after(fin + (long long)n, h->cfg.fe.fft_n) - fout;
-  const long long out2_new = eq_out_after(h, h->in4 + c1);
-  const long long nf = frames_ready(h, out2_new, false, 0);
-  const size_t need = (size_t)nf * ((size_t)h->F * h->bps / 8);
+  const PushForecast fc = forecast(h, n);
+  const long long c1 = fc.c1, out2_new = fc.out2_new, nf = fc.nf;
+  const size_t need = fc.need;
   if (need > 0 && (!bits || bits_cap_bytes < need))
     return fail("rx_kkrx_push: bits is null or bits_cap_bytes is smaller than the frames this push completes",
                 RX_EINVAL);
@@ -415,4 +488,231 @@ extern "C" void rx_kkrx_destroy(rx_kkrx* h) {
   cudaFree(h->init_taps);
   cudaFree(h->hist);
   delete h;
+}
+
+// ---- many receivers in one launch per stage -------------------------------
+//
+// A batch push runs every channel's front end through one rx_kk_batch graph
+// replay, then one replay of a graph of the equaliser (a block per output
+// segment of any channel, found from the prefix sums of the channels'
+// uneven segment counts) and its carries, then the DD-LMS of the frames
+// that completed: one launch for every channel's acquisition, one for the
+// first frame each channel completed, one for the second, ... (a channel's
+// frames stay in order), and one for the moves of the 2-sps samples.  All
+// on the caller's stream.  Two table slots (with a graph each) alternate,
+// as in rx_kk_batch.
+
+struct rx_kkrx_batch {
+  std::vector<rx_kkrx*> ch;
+  rx_kk_batch* fe = nullptr;
+  int N4 = 0, device = 0, slot = 0;
+  rx::KKEqBatchTable* host_tab[2] = {nullptr, nullptr};
+  rx::KKEqBatchTable* dev_tab[2] = {nullptr, nullptr};
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaGraphNode_t eq_node[2] = {nullptr, nullptr};
+  cudaKernelNodeParams eq_params[2];
+  cudaEvent_t done[2] = {nullptr, nullptr};
+  bool used[2] = {false, false};
+  rx::WLBatchTable* host_wl[2] = {nullptr, nullptr};
+  rx::WLBatchTable* dev_wl[2] = {nullptr, nullptr};
+};
+
+extern "C" int rx_kkrx_batch_create(rx_kkrx* const* channels, int n_channels, rx_kkrx_batch** out) {
+  if (!channels || !out || n_channels < 1) return fail("rx_kkrx_batch_create: null argument or no channels", RX_EINVAL);
+  *out = nullptr;
+  if (n_channels > rx::kKKEqBatchMax) return fail("rx_kkrx_batch_create: at most 256 channels", RX_EINVAL);
+  for (int c = 0; c < n_channels; ++c) {
+    const rx_kkrx* h = channels[c];
+    if (!h) return fail("rx_kkrx_batch_create: null channel", RX_EINVAL);
+    const rx_kkrx* h0 = channels[0];
+    if (h->N4 != h0->N4 || h->F != h0->F || h->S != h0->S || h->bps != h0->bps ||
+        h->cfg.acq_syms != h0->cfg.acq_syms || h->cfg.fe.fft_n != h0->cfg.fe.fft_n ||
+        h->cfg.fe.device != h0->cfg.fe.device)
+      return fail("rx_kkrx_batch_create: channels must share fft_n, eq_fft_n, frame, segment and acquisition "
+                  "lengths, modulation and device", RX_EINVAL);
+    for (int d = 0; d < c; ++d)
+      if (channels[d] == channels[c]) return fail("rx_kkrx_batch_create: a channel appears twice", RX_EINVAL);
+  }
+  rx_kkrx_batch* b = new rx_kkrx_batch;
+  b->ch.assign(channels, channels + n_channels);
+  b->N4 = channels[0]->N4;
+  b->device = channels[0]->cfg.fe.device;
+  int rc = cuda_rc(cudaSetDevice(b->device), "rx_kkrx_batch_create");
+  for (int c = 0; c < n_channels && !rc; ++c)  // no single-push work of a channel still in flight
+    rc = cuda_rc(cudaStreamSynchronize(channels[c]->s2), "rx_kkrx_batch_create");
+  std::vector<rx_kk*> fes(n_channels);
+  for (int c = 0; c < n_channels; ++c) fes[c] = channels[c]->fe;
+  if (!rc) rc = rx_kk_batch_create(fes.data(), n_channels, &b->fe);
+  for (int k = 0; k < 2 && !rc; ++k) {
+    rc = cuda_rc(cudaHostAlloc(&b->host_tab[k], sizeof(rx::KKEqBatchTable), cudaHostAllocDefault), "table");
+    if (!rc) rc = cuda_rc(cudaMalloc(&b->dev_tab[k], sizeof(rx::KKEqBatchTable)), "table");
+    if (!rc) rc = cuda_rc(cudaEventCreateWithFlags(&b->done[k], cudaEventDisableTiming), "event");
+    if (!rc) rc = cuda_rc(cudaHostAlloc(&b->host_wl[k], sizeof(rx::WLBatchTable), cudaHostAllocDefault), "table");
+    if (!rc) rc = cuda_rc(cudaMalloc(&b->dev_wl[k], sizeof(rx::WLBatchTable)), "table");
+    if (rc) break;
+    std::memset(b->host_tab[k], 0, sizeof(rx::KKEqBatchTable));
+    cudaKernelNodeParams eq, tail;
+    rc = cuda_rc(rx::kkeq_batch_nodes(b->N4, &eq, &tail), "rx_kkrx_batch_create: kernels");
+    if (!rc) rc = cuda_rc(cudaGraphCreate(&b->graph[k], 0), "graph");
+    cudaGraphNode_t copy = nullptr, tnode = nullptr;
+    if (!rc)
+      rc = cuda_rc(cudaGraphAddMemcpyNode1D(&copy, b->graph[k], nullptr, 0, b->dev_tab[k], b->host_tab[k],
+                                            sizeof(rx::KKEqBatchTable), cudaMemcpyHostToDevice),
+                   "graph copy node");
+    void* arg[1] = {&b->dev_tab[k]};
+    eq.gridDim = dim3(1);
+    eq.kernelParams = arg;
+    tail.gridDim = dim3((unsigned)n_channels);
+    tail.kernelParams = arg;
+    if (!rc) rc = cuda_rc(cudaGraphAddKernelNode(&b->eq_node[k], b->graph[k], &copy, 1, &eq), "equaliser node");
+    if (!rc) rc = cuda_rc(cudaGraphAddKernelNode(&tnode, b->graph[k], &b->eq_node[k], 1, &tail), "carry node");
+    if (!rc) rc = cuda_rc(cudaGraphInstantiate(&b->exec[k], b->graph[k], 0), "graph instantiate");
+    b->eq_params[k] = eq;
+  }
+  if (rc) {
+    rx_kkrx_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return RX_OK;
+}
+
+extern "C" int rx_kkrx_batch_push(rx_kkrx_batch* b, const int16_t* const* codes, const size_t* n,
+                                  uint8_t* const* bits, const size_t* bits_cap_bytes, size_t* n_bits,
+                                  void* cuda_stream) {
+  if (!b || !codes || !n || !bits || !bits_cap_bytes || !n_bits)
+    return fail("rx_kkrx_batch_push: null argument", RX_EINVAL);
+  const int nch = (int)b->ch.size();
+  std::vector<PushForecast> fc(nch);
+  for (int c = 0; c < nch; ++c) {  // all or nothing: check every channel first
+    rx_kkrx* h = b->ch[c];
+    n_bits[c] = 0;
+    if (h->ended) return fail("rx_kkrx_batch_push: a channel's stream already ended", RX_ESTATE);
+    if (n[c] > h->cfg.fe.max_block_samples) return fail("rx_kkrx_batch_push: n exceeds fe.max_block_samples", RX_EINVAL);
+    if (n[c] > 0 && !codes[c]) return fail("rx_kkrx_batch_push: null codes", RX_EINVAL);
+    fc[c] = forecast(h, n[c]);
+    if (fc[c].need > 0 && (!bits[c] || bits_cap_bytes[c] < fc[c].need))
+      return fail("rx_kkrx_batch_push: a channel's bits capacity is smaller than the frames the push completes",
+                  RX_EINVAL);
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int rc = cuda_rc(cudaSetDevice(b->device), "rx_kkrx_batch_push");
+  if (rc) return rc;
+  // front ends: one graph replay
+  std::vector<float*> fout(nch);
+  std::vector<size_t> fcap(nch), got(nch);
+  for (int c = 0; c < nch; ++c) {
+    fout[c] = reinterpret_cast<float*>(b->ch[c]->field[b->ch[c]->npush & 1]);
+    fcap[c] = b->ch[c]->field_cap;
+  }
+  rc = rx_kk_batch_push(b->fe, codes, n, fout.data(), fcap.data(), got.data(), cuda_stream);
+  if (rc) return rc;
+  // equalisers: one graph replay over every channel's new segments
+  const int k = b->slot;
+  if (b->used[k]) {
+    rc = cuda_rc(cudaEventSynchronize(b->done[k]), "rx_kkrx_batch_push: table slot");
+    if (rc) return rc;
+  }
+  rx::KKEqBatchTable* t = b->host_tab[k];
+  std::vector<EqPlan> plans(nch);
+  t->nch = nch;
+  t->offs[0] = 0;
+  for (int c = 0; c < nch; ++c) {
+    rx_kkrx* h = b->ch[c];
+    if ((long long)got[c] != fc[c].c1) return fail("rx_kkrx_batch_push: front-end output count mismatch", RX_EINVAL);
+    if (got[c] > 0) {
+      rc = eq_plan(h, h->field[h->npush & 1], (long long)got[c], fc[c].out2_new, &plans[c]);
+      if (rc) return rc;
+    } else {  // no new field: no segments and an empty carry copy
+      plans[c].a.in_end = h->in4;
+      plans[c].nseg = 0;
+      plans[c].keep = h->in4;
+    }
+    t->args[c] = plans[c].a;
+    t->offs[c + 1] = t->offs[c] + plans[c].nseg;
+    t->carry_dst[c] = h->carry4[h->cur4 ^ 1];
+    t->keep_from[c] = plans[c].keep;
+  }
+  if (t->offs[nch] > 0x7fffffffLL) return fail("rx_kkrx_batch_push: too many segments in one batch", RX_EINVAL);
+  cudaKernelNodeParams ep = b->eq_params[k];
+  void* arg[1] = {&b->dev_tab[k]};
+  ep.kernelParams = arg;
+  ep.gridDim = dim3((unsigned)std::max(1LL, t->offs[nch]));
+  rc = cuda_rc(cudaGraphExecKernelNodeSetParams(b->exec[k], b->eq_node[k], &ep), "rx_kkrx_batch_push: grid");
+  if (!rc) rc = cuda_rc(cudaGraphLaunch(b->exec[k], s), "rx_kkrx_batch_push: graph");
+  if (rc) return rc;
+  for (int c = 0; c < nch; ++c) {
+    rx_kkrx* h = b->ch[c];
+    if (n[c] > 0) h->npush++;
+    if (got[c] > 0) eq_commit(h, plans[c]);
+  }
+  // DD-LMS of the frames that completed: one launch for every acquisition,
+  // one per frame ordinal, one for the moves of the 2-sps samples (a channel
+  // with more frames than ordinals runs them on its own, in order)
+  const bool q16 = b->ch[0]->cfg.modulation == RX_QAM16;
+  rx::WLBatchTable* w = b->host_wl[k];
+  for (int node = 0; node < rx::kWLNodes; ++node) {
+    w->n[node] = 0;
+    w->offs[node][0] = 0;
+  }
+  w->nshift = 0;
+  for (int c = 0; c < nch; ++c) {
+    rx_kkrx* h = b->ch[c];
+    n_bits[c] = fc[c].need * 8;
+    if (fc[c].nf == 0) continue;
+    if (fc[c].nf > rx::kWLNodes - 1) {
+      rc = run_frames(h, fc[c].nf, false, 0, bits[c], s);
+      if (rc) return rc;
+      continue;
+    }
+    const FramePlan fp = plan_frames(h, fc[c].nf, false, 0, bits[c]);
+    auto add = [&](int node, const rx::WLArgs& a, long long segs) {
+      const int e = w->n[node]++;
+      w->args[node][e] = a;
+      w->offs[node][e + 1] = w->offs[node][e] + segs;
+    };
+    if (fp.has_acq) add(0, fp.acq, 1);
+    for (size_t i = 0; i < fp.frames.size(); ++i) add(1 + (int)i, fp.frames[i], fp.segs[i]);
+    if (fp.shift_n > 0) {
+      w->shift_src[w->nshift] = fp.shift_src;
+      w->shift_dst[w->nshift] = fp.shift_dst;
+      w->shift_n[w->nshift] = fp.shift_n;
+      w->nshift++;
+    }
+    commit_frames(h, fp);
+  }
+  bool any = w->nshift > 0;
+  for (int node = 0; node < rx::kWLNodes; ++node) any = any || w->n[node] > 0;
+  if (any) {
+    rc = cuda_rc(cudaMemcpyAsync(b->dev_wl[k], w, sizeof(rx::WLBatchTable), cudaMemcpyHostToDevice, s),
+                 "rx_kkrx_batch_push: DD-LMS table");
+    for (int node = 0; node < rx::kWLNodes && !rc; ++node)
+      rc = cuda_rc(rx::launch_wl_batch(b->dev_wl[k], node, q16, w->offs[node][w->n[node]], s),
+                   "rx_kkrx_batch_push: DD-LMS");
+    if (!rc) rc = cuda_rc(rx::launch_x2_shift_batch(b->dev_wl[k], w->nshift, s), "rx_kkrx_batch_push: 2-sps carry");
+    if (rc) return rc;
+  }
+  rc = cuda_rc(cudaEventRecord(b->done[k], s), "rx_kkrx_batch_push: event");
+  if (rc) return rc;
+  b->used[k] = true;
+  b->slot ^= 1;
+  return RX_OK;
+}
+
+extern "C" void rx_kkrx_batch_destroy(rx_kkrx_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  for (int k = 0; k < 2; ++k) {
+    if (b->done[k]) cudaEventSynchronize(b->done[k]);
+    if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+    if (b->graph[k]) cudaGraphDestroy(b->graph[k]);
+    if (b->done[k]) cudaEventDestroy(b->done[k]);
+    cudaFreeHost(b->host_tab[k]);
+    cudaFree(b->dev_tab[k]);
+    cudaFreeHost(b->host_wl[k]);
+    cudaFree(b->dev_wl[k]);
+  }
+  rx_kk_batch_destroy(b->fe);
+  delete b;
 }

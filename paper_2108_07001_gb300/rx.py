@@ -39,7 +39,8 @@ EXPORTS = ["rx_config_default", "rx_create", "rx_push_block", "rx_pull_bits", "r
            "rx_kk_config_default", "rx_kk_create", "rx_kk_push", "rx_kk_end", "rx_kk_reset",
            "rx_kk_position", "rx_kk_destroy", "rx_kk_batch_create", "rx_kk_batch_push", "rx_kk_batch_destroy",
            "rx_kkrx_config_default", "rx_kkrx_create", "rx_kkrx_push", "rx_kkrx_end", "rx_kkrx_equalised",
-           "rx_kkrx_reset", "rx_kkrx_destroy"]
+           "rx_kkrx_reset", "rx_kkrx_destroy", "rx_kkrx_batch_create", "rx_kkrx_batch_push",
+           "rx_kkrx_batch_destroy"]
 
 
 class RxConfig(ctypes.Structure):
@@ -236,6 +237,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rx_kkrx_reset.argtypes = [P]
     lib.rx_kkrx_destroy.argtypes = [P]
     lib.rx_kkrx_destroy.restype = None
+    lib.rx_kkrx_batch_create.argtypes = [ctypes.POINTER(P), I, ctypes.POINTER(P)]
+    lib.rx_kkrx_batch_push.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(SZ), ctypes.POINTER(P), ctypes.POINTER(SZ),
+                                       ctypes.POINTER(SZ), P]
+    lib.rx_kkrx_batch_destroy.argtypes = [P]
+    lib.rx_kkrx_batch_destroy.restype = None
     for name in ["rx_create", "rx_push_block", "rx_pull_bits", "rx_stats", "rx_destroy", "rx_reset",
                  "rx_join", "rx_stage_times", "rx_frame_trace", "rx_get_taps", "rx_get_equalised",
                  "rx_get_phase", "rx_decide_block_noalloc", "rx_server_create", "rx_server_open",
@@ -243,7 +249,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                  "rx_server_close", "rx_server_stats", "rx_server_destroy", "rx_autotune_fft",
                  "rx_kk_create", "rx_kk_push", "rx_kk_end", "rx_kk_reset", "rx_kk_position",
                  "rx_kk_batch_create", "rx_kk_batch_push",
-                 "rx_kkrx_create", "rx_kkrx_push", "rx_kkrx_end", "rx_kkrx_equalised", "rx_kkrx_reset"]:
+                 "rx_kkrx_create", "rx_kkrx_push", "rx_kkrx_end", "rx_kkrx_equalised", "rx_kkrx_reset",
+                 "rx_kkrx_batch_create", "rx_kkrx_batch_push"]:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -700,6 +707,53 @@ class KKReceiver:
         if getattr(self, "h", None):
             self.lib.rx_kkrx_destroy(self.h)
             self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class KKReceiverBatch:
+    """Several KK receivers pushed together (rx_kkrx_batch_*); their streams
+    end with each receiver's own end()."""
+
+    def __init__(self, receivers: list):
+        self.lib = load()
+        self.receivers = list(receivers)
+        n = len(self.receivers)
+        arr = (ctypes.c_void_p * n)(*[r.h.value for r in self.receivers])
+        b = ctypes.c_void_p()
+        _check(self.lib.rx_kkrx_batch_create(arr, n, ctypes.byref(b)))
+        self.b = b
+        self._codes = (ctypes.c_void_p * n)()
+        self._n = (ctypes.c_size_t * n)()
+        self._bits = (ctypes.c_void_p * n)()
+        self._cap = (ctypes.c_size_t * n)()
+        self._nb = (ctypes.c_size_t * n)()
+
+    def push(self, codes_ptrs, ns, bits_ptrs, bits_caps, stream: int = 0) -> list[int]:
+        """Device pointers and lengths per channel; returns the bits written per channel."""
+        for i in range(len(self.receivers)):
+            self._codes[i] = codes_ptrs[i]
+            self._n[i] = ns[i]
+            self._bits[i] = bits_ptrs[i]
+            self._cap[i] = bits_caps[i]
+        _check(self.lib.rx_kkrx_batch_push(self.b, self._codes, self._n, self._bits, self._cap, self._nb,
+                                           ctypes.c_void_p(stream)))
+        return list(self._nb)
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            self.lib.rx_kkrx_batch_destroy(self.b)
+            self.b = None
 
     def __enter__(self):
         return self

@@ -177,3 +177,51 @@ def test_reset_reproduces_the_stream():
             r.reset()
     assert outs[0][0] == outs[1][0] == (n // 4) * 4
     assert np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_batch_push_equals_single_pushes():
+    """Five receivers (different links, QPSK) pushed together, one front-end
+    graph and one equaliser graph per round, uneven lengths per channel and
+    round (including none), 4096-symbol frames completing at different
+    rounds: bit for bit the bits of the same pushes one receiver at a time,
+    the streams' ends included."""
+    import torch
+    F = 1 << 12
+    rng = np.random.default_rng(91)
+    links = [case(2, 3 * F + 200 * c, 90 + c, 12.0, 9.0) for c in range(5)]
+    n = [d["codes"].size for d in links]
+    dev = torch.device("cuda:0")
+    codes = [torch.from_numpy(d["codes"]).to(dev) for d in links]
+    nbytes = [(m // 4 * 2 + 7) // 8 + 64 for m in n]
+    out = {k: [torch.zeros(nbytes[c], dtype=torch.uint8, device=dev) for c in range(5)] for k in ("batch", "single")}
+    rxs = {k: [rx.KKReceiver(chain_cfg(d, 2, F, acq=2048, block=20000)) for d in links] for k in out}
+    pos = [0] * 5
+    nb = {k: [0] * 5 for k in out}
+    stream = torch.cuda.current_stream().cuda_stream
+    with rx.KKReceiverBatch(rxs["batch"]) as batch:
+        for r in range(12):
+            sizes = [int(min(n[c] - pos[c], rng.choice([0, 5, 700, 3000, 12000, 20000]))) for c in range(5)]
+            got = batch.push([codes[c].data_ptr() + 2 * pos[c] for c in range(5)], sizes,
+                             [out["batch"][c].data_ptr() + nb["batch"][c] // 8 for c in range(5)],
+                             [nbytes[c] - nb["batch"][c] // 8 for c in range(5)], stream)
+            for c in range(5):
+                k = rxs["single"][c].push_device(codes[c].data_ptr() + 2 * pos[c], sizes[c],
+                                                 out["single"][c].data_ptr() + nb["single"][c] // 8,
+                                                 nbytes[c] - nb["single"][c] // 8, stream)
+                assert got[c] == k
+                nb["batch"][c] += got[c]
+                nb["single"][c] += k
+                pos[c] += sizes[c]
+    for key in out:
+        for c in range(5):
+            r = rxs[key][c]
+            if n[c] > pos[c]:
+                nb[key][c] += r.push_device(codes[c].data_ptr() + 2 * pos[c], n[c] - pos[c],
+                                            out[key][c].data_ptr() + nb[key][c] // 8, nbytes[c] - nb[key][c] // 8,
+                                            stream)
+            nb[key][c] += r.end(out[key][c].data_ptr() + nb[key][c] // 8, nbytes[c] - nb[key][c] // 8, stream)
+            r.close()
+    torch.cuda.synchronize()
+    for c in range(5):
+        assert nb["batch"][c] == nb["single"][c] == (n[c] // 4) * 2
+        assert torch.equal(out["batch"][c], out["single"][c]), c
