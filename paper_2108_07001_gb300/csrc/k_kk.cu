@@ -9,10 +9,11 @@
 //         samples N/4 .. 3N/4 - 1
 //   E_t = exp(u_t + j phi_t) exp(-j 2 pi nu t),  nu = f_shift / f_s
 //
-// Kernel layout: one thread block (N/16 threads) per pair of adjacent
-// segments.  The Hilbert transform has a real kernel, so the two real
-// blocks go through one complex FFT pair as u_a + j u_b: the real part of
-// the result is phi_a, the imaginary part phi_b.  u is staged once for the
+// Kernel layout: one thread block per pair of adjacent segments (one warp
+// with the one-warp FFT of fft_warp.cuh for N = 1024; N/16 threads with the
+// shared-memory FFT otherwise).  The Hilbert transform has a real kernel, so
+// the two real blocks go through one complex FFT pair as u_a + j u_b: the
+// real part of the result is phi_a, the imaginary part phi_b.  u is staged once for the
 // pair's 3L-sample union (16-byte loads of 8 codes when the union lies in
 // the push), in log2 units: u2 = u / ln 2, |E| = 2^u2, and the factor
 // ln 2 / pi rides on the Hilbert multiplier so the transform returns
@@ -23,6 +24,7 @@
 #include <cstring>
 
 #include "fft_smem.cuh"
+#include "fft_warp.cuh"
 #include "kk_internal.h"
 
 namespace rx {
@@ -36,37 +38,36 @@ __device__ __forceinline__ bool kk_code(const KKArgs& a, long long i, float& cod
   return true;
 }
 
-// Dynamic shared memory: the FFT buffer (N float2), then u of the pair's
-// 3N/2-sample union.
+// Threads per block: one warp for N = 1024 (the one-warp FFT), N/16 otherwise;
+// the one-warp blocks are held to 128 registers so that 16 fit on an SM.
 template <int N>
-constexpr size_t kk_smem_bytes() { return (size_t)N * 8 + (size_t)3 * (N / 2) * 4; }
-
-// The pair of segments a.seg0 + 2 pair, a.seg0 + 2 pair + 1, by one block
-// of N/16 threads (dynamic shared memory: kk_smem_bytes<N>()).
+constexpr int kk_threads() { return N == 1024 ? 32 : N / 16; }
 template <int N>
-__device__ __forceinline__ void kk_pair(const KKArgs& a, long long pair) {
-  constexpr int NT = N / 16, L = N / 2, U = 3 * L;
-  static_assert(U / 8 == 3 * NT, "three 8-code vectors per thread");
-  extern __shared__ __align__(16) float2 kk_smem[];
-  float2* buf = kk_smem;
-  float* u_s = reinterpret_cast<float*>(kk_smem + N);
-  __shared__ float2 tw_s[2 * kTwSplit];
-  for (int i = threadIdx.x; i < 2 * kTwSplit; i += NT) tw_s[i] = a.tw2[i];
+constexpr int kk_min_blocks() { return N == 1024 ? 16 : 1; }
 
-  const long long seg = a.seg0 + 2LL * pair;   // first segment of the pair
-  const long long lo = seg * L - N / 4;              // stream index of u_s[0]
+// Dynamic shared memory: the FFT buffer (N float2; for N = 1024 the warp's
+// 32 x 33 transpose buffer), then u of the pair's 3N/2-sample union.
+template <int N>
+constexpr size_t kk_smem_bytes() {
+  return (N == 1024 ? (size_t)32 * kWarpT * 8 : (size_t)N * 8) + (size_t)3 * (N / 2) * 4;
+}
+
+// u2 = u / ln 2 of the codes of [lo, lo + U) into u_s by NT threads (16-byte
+// loads of 8 codes when the union lies in the push).
+template <int U, int NT>
+__device__ __forceinline__ void kk_stage_u(const KKArgs& a, long long lo, float* u_s) {
+  static_assert(U % (8 * NT) == 0, "whole 8-code vectors per thread");
+  constexpr int PER = U / (8 * NT);
   auto u2_of = [&](float code) { return 0.5f * log2f(fmaxf(a.gain * (code - a.offset), a.i_min)); };
   const long long off = lo - a.new_start;
   if (off >= 0 && lo + U <= a.in_end && (off & 7) == 0 && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0) {
-    // the union lies in this push, 16-byte aligned: 8 codes per load
-    // U / 8 = 3 NT vectors: three per thread, all loads issued first
     const int4* src = reinterpret_cast<const int4*>(a.in + off);
     float4* dst = reinterpret_cast<float4*>(u_s);
-    int4 w[3];
+    int4 w[PER];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) w[r] = __ldg(src + threadIdx.x + r * NT);
+    for (int r = 0; r < PER; ++r) w[r] = __ldg(src + threadIdx.x + r * NT);
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
+    for (int r = 0; r < PER; ++r) {
       const int v = threadIdx.x + r * NT;
       const int c[4] = {w[r].x, w[r].y, w[r].z, w[r].w};
       float f[8];
@@ -84,6 +85,80 @@ __device__ __forceinline__ void kk_pair(const KKArgs& a, long long pair) {
       u_s[i] = kk_code(a, lo + i, code) ? u2_of(code) : 0.f;
     }
   }
+}
+
+// The field of output sample t from phi / pi and u2.
+__device__ __forceinline__ void kk_store(const KKArgs& a, long long t, float phi_pi, float u2) {
+  const unsigned long long p = a.nu_fx * (unsigned long long)t;  // frac(nu t) in 2^-64
+  const float cyc = (float)(p >> 40) * 0x1p-23f;                 // 2 frac(nu t)
+  float sn, cs;
+  sincospif(phi_pi - cyc, &sn, &cs);
+  const float m = exp2f(u2);
+  a.out[t - a.out_start] = make_float2(m * cs, m * sn);
+}
+
+// The pair of segments a.seg0 + 2 pair (+1) with N = 1024 by one warp: the
+// two blocks' u as one complex input, the one-warp forward FFT, the Hilbert
+// multiplier on the lane-k1 layout in registers, the inverse as the
+// conjugate of the forward transform of the conjugate.
+__device__ __forceinline__ void kk_pair_1024w(const KKArgs& a, long long pair) {
+  constexpr int N = 1024, L = 512, U = 3 * L;
+  extern __shared__ __align__(16) float2 kk_smem[];
+  float2* t = kk_smem;
+  float* u_s = reinterpret_cast<float*>(kk_smem + 32 * kWarpT);
+  const int lane = threadIdx.x & 31;
+  const long long seg = a.seg0 + 2LL * pair;
+  const long long lo = seg * L - N / 4;
+  kk_stage_u<U, 32>(a, lo, u_s);
+  __syncwarp();
+  float2 v[32];
+#pragma unroll
+  for (int n1 = 0; n1 < 32; ++n1) v[n1] = make_float2(u_s[32 * n1 + lane], u_s[32 * n1 + lane + L]);
+  // pass 0: the forward transform, then -j sgn(k) ln2 / (pi N) on bin
+  // k = lane + 32 k2 and the conjugate; pass 1: the forward transform again,
+  // whose conjugate is the inverse (one copy of the transform's code)
+  constexpr float s = 0.693147180559945309f / (3.14159265358979324f * (float)N);
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    fft1024_warp_fwd(v, t);
+    if (pass == 0) {
+#pragma unroll
+      for (int k2 = 0; k2 < 32; ++k2) {
+        const int k = lane + 32 * k2;
+        const float2 x = v[k2];
+        // conj(-j x) = (x.y, x.x), conj(+j x) = (-x.y, -x.x)
+        v[k2] = (k == 0 || k == N / 2) ? make_float2(0.f, 0.f)
+                : k < N / 2           ? make_float2(x.y * s, x.x * s)
+                                      : make_float2(-x.y * s, -x.x * s);
+      }
+    }
+  }
+  // lane holds conj(x[lane + 32 n_b]); block samples N/4 .. 3N/4 - 1 are n_b = 8 .. 23:
+  // phi_a = Re x = v.x, phi_b = Im x = -v.y
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+#pragma unroll
+    for (int nb = 8; nb < 24; ++nb) {
+      const int n = lane + 32 * nb;
+      const long long tt = (seg + h) * L + (n - N / 4);
+      if (tt < a.out_end) kk_store(a, tt, h == 0 ? v[nb].x : -v[nb].y, u_s[h * L + n]);
+    }
+  }
+}
+
+// The pair of segments a.seg0 + 2 pair, a.seg0 + 2 pair + 1 by one block of
+// N/16 threads with the shared-memory FFT (N = 2048, 4096).
+template <int N>
+__device__ __forceinline__ void kk_pair_smem(const KKArgs& a, long long pair) {
+  constexpr int NT = N / 16, L = N / 2, U = 3 * L;
+  extern __shared__ __align__(16) float2 kk_smem[];
+  float2* buf = kk_smem;
+  float* u_s = reinterpret_cast<float*>(kk_smem + N);
+  __shared__ float2 tw_s[2 * kTwSplit];
+  for (int i = threadIdx.x; i < 2 * kTwSplit; i += NT) tw_s[i] = a.tw2[i];
+  const long long seg = a.seg0 + 2LL * pair;   // first segment of the pair
+  const long long lo = seg * L - N / 4;        // stream index of u_s[0]
+  kk_stage_u<U, NT>(a, lo, u_s);
   __syncthreads();
   for (int n = threadIdx.x; n < N; n += NT) buf[swz(n)] = make_float2(u_s[n], u_s[n + L]);
   __syncthreads();
@@ -107,19 +182,19 @@ __device__ __forceinline__ void kk_pair(const KKArgs& a, long long pair) {
       const long long t = (seg + h) * L + n;
       if (t >= a.out_end) break;
       const float2 v = buf[swz(n + N / 4)];
-      const float phi_pi = h == 0 ? v.x : v.y;                        // phi / pi
-      const unsigned long long p = a.nu_fx * (unsigned long long)t;  // frac(nu t) in 2^-64
-      const float cyc = (float)(p >> 40) * 0x1p-23f;                 // 2 frac(nu t)
-      float sn, cs;
-      sincospif(phi_pi - cyc, &sn, &cs);
-      const float m = exp2f(u_s[h * L + n + N / 4]);
-      a.out[t - a.out_start] = make_float2(m * cs, m * sn);
+      kk_store(a, t, h == 0 ? v.x : v.y, u_s[h * L + n + N / 4]);
     }
   }
 }
 
 template <int N>
-__global__ void __launch_bounds__(N / 16) kk_kernel(KKArgs a) {
+__device__ __forceinline__ void kk_pair(const KKArgs& a, long long pair) {
+  if constexpr (N == 1024) kk_pair_1024w(a, pair);
+  else kk_pair_smem<N>(a, pair);
+}
+
+template <int N>
+__global__ void __launch_bounds__(kk_threads<N>(), kk_min_blocks<N>()) kk_kernel(KKArgs a) {
   kk_pair<N>(a, blockIdx.x);
 }
 
@@ -127,7 +202,7 @@ __global__ void __launch_bounds__(N / 16) kk_kernel(KKArgs a) {
 // offs[c] <= b < offs[c + 1] (uneven pushes give uneven counts); blocks
 // past offs[nch] (the launch may be sized for more) return at once.
 template <int N>
-__global__ void __launch_bounds__(N / 16) kk_batch_kernel(const KKBatchTable* __restrict__ t) {
+__global__ void __launch_bounds__(kk_threads<N>(), kk_min_blocks<N>()) kk_batch_kernel(const KKBatchTable* __restrict__ t) {
   const long long b = blockIdx.x;
   if (b >= t->offs[t->nch]) return;
   int lo = 0, hi = t->nch;  // offs[lo] <= b < offs[hi]
@@ -136,8 +211,7 @@ __global__ void __launch_bounds__(N / 16) kk_batch_kernel(const KKBatchTable* __
     if (t->offs[mid] <= b) lo = mid;
     else hi = mid;
   }
-  const KKArgs a = t->args[lo];
-  kk_pair<N>(a, b - t->offs[lo]);
+  kk_pair<N>(t->args[lo], b - t->offs[lo]);
 }
 
 // New carry: codes [keep_from, in_end) from the old carry and the push.
@@ -178,7 +252,7 @@ template <int N>
 static cudaError_t launch_kk_t(const KKArgs& a, unsigned blocks, cudaStream_t s) {
   const cudaError_t e = kk_attr<N>();
   if (e != cudaSuccess) return e;
-  kk_kernel<N><<<blocks, N / 16, kk_smem_bytes<N>(), s>>>(a);
+  kk_kernel<N><<<blocks, kk_threads<N>(), kk_smem_bytes<N>(), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -203,8 +277,9 @@ cudaError_t kk_batch_nodes(int N, cudaKernelNodeParams* field, cudaKernelNodePar
     case 4096: e = kk_attr<4096>(); field->func = (void*)kk_batch_kernel<4096>; break;
     default: return cudaErrorInvalidValue;
   }
-  field->blockDim = dim3(N / 16);
-  field->sharedMemBytes = (unsigned)(N * 8 + 3 * (N / 2) * 4);
+  field->blockDim = dim3(N == 1024 ? kk_threads<1024>() : N / 16);
+  field->sharedMemBytes = (unsigned)(N == 1024 ? kk_smem_bytes<1024>() : N == 2048 ? kk_smem_bytes<2048>()
+                                                                                    : kk_smem_bytes<4096>());
   carry->func = (void*)kk_carry_batch_kernel;
   carry->blockDim = dim3(256);
   return e;
