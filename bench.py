@@ -809,7 +809,9 @@ def run_kkrx_batch(args):
     sizes = rng.integers(1 << 12, (1 << 16) + 1, (KKB_ROUNDS, KKB_CHANNELS))
     per = sizes.sum(axis=0)
     total = int(per.sum())
-    starts = [4 * (int(s) // 4) for s in rng.integers(0, (1 << 23) - int(per.max()), KKB_CHANNELS)]  # whole symbols
+    # windows start on multiples of 256 samples: whole symbols, and whole turns of the tone offset
+    # (33/256 of a turn per sample), so each receiver's downshift matches the link's phase
+    starts = [256 * (int(s) // 256) for s in rng.integers(0, (1 << 23) - int(per.max()), KKB_CHANNELS)]
     nbytes = int(per.max()) // 4 * 2 // 8 + 4096
     bits = torch.zeros((KKB_CHANNELS, nbytes), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream().cuda_stream
