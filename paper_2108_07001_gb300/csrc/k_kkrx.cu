@@ -13,15 +13,19 @@
 //     one chain per segment of S symbols continued from frame to frame;
 //   decisions and Gray demapping to packed bits.
 //
-// Kernel layout: the equaliser runs one N4/16-thread block per output
-// segment (16-byte loads of two field samples when the block lies in the
-// step's new field; the forward transform's band is compacted in place,
-// the inverse reuses the table of N4 at stride 2); the DD-LMS runs one warp per
+// Kernel layout: the equaliser runs one block per output segment.  For
+// N4 = 1024 the block is one warp: the field straight into registers, the
+// one-warp four-step forward FFT, the band times H through shared memory
+// into the 512-point inverse.  Otherwise N4/16 threads: 16-byte loads of
+// two field samples when the block lies in the step's new field, the
+// forward transform's band compacted in place; the inverse reuses the
+// table of N4 at stride 2 in both forms.  The DD-LMS runs one warp per
 // segment, two symbols per lane and sub-block, the sixteen gradient sums
 // all-reduced by shuffles, decisions and bits in the same pass.
 #include <cstring>
 
 #include "fft_smem.cuh"
+#include "fft_warp.cuh"
 #include "kkrx_internal.h"
 
 namespace rx {
@@ -31,9 +35,46 @@ __device__ __forceinline__ float2 kkrx_in(const KKEqArgs& a, long long i) {
   return i < a.new_start ? a.carry[i - a.carry_start] : a.in[i - a.new_start];
 }
 
+// Output segment a.seg0 + seg with N4 = 1024 by one warp: the block's 1024
+// field samples straight into registers (lane n2 holds samples 32 n1 + n2),
+// the one-warp forward FFT, the 2-sps band times H written in the order of
+// a 512-point DFT into the freed transpose buffer, the shared-memory
+// inverse transform.
+__device__ __forceinline__ void kkeq_segment_1024w(const KKEqArgs& a, long long seg) {
+  constexpr int N4 = 1024, L4 = 512, L2 = 256;
+  __shared__ __align__(16) float2 t[32 * kWarpT];
+  __shared__ float2 tw_s[2 * kTwSplit];
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < 2 * kTwSplit; i += 32) tw_s[i] = a.tw2[i];
+  const long long b = a.seg0 + seg;
+  const long long lo = b * L4 - N4 / 4;
+  const long long off = lo - a.new_start;
+  float2 v[32];
+  if (off >= 0 && lo + N4 <= a.in_end) {
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) v[n1] = __ldg(a.in + off + 32 * n1 + lane);
+  } else {
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) v[n1] = kkrx_in(a, lo + 32 * n1 + lane);
+  }
+  fft1024_warp_fwd(v, t);
+  // lane k1 holds X[k1 + 32 k2]; the band is k2 < 8 (bins k1 + 32 k2) and
+  // k2 >= 24 (bins k1 + 32 (k2 - 16) of the 512-point transform)
+#pragma unroll
+  for (int k2 = 0; k2 < 8; ++k2) t[swz(lane + 32 * k2)] = cmul(v[k2], a.H2[lane + 32 * k2]);
+#pragma unroll
+  for (int k2 = 24; k2 < 32; ++k2) t[swz(lane + 32 * (k2 - 16))] = cmul(v[k2], a.H2[lane + 32 * (k2 - 16)]);
+  __syncthreads();
+  fft_smem<N4 / 2, 32, true>(t, tw_s, 2);
+  for (int n = lane; n < L2; n += 32) {
+    const long long tt = b * L2 + n;
+    if (tt < a.out_end) a.out[tt - a.out_base] = t[swz(N4 / 8 + n)];
+  }
+}
+
 // Output segment a.seg0 + seg by one block of N4/16 threads.
 template <int N4>
-__device__ __forceinline__ void kkeq_segment(const KKEqArgs& a, long long seg) {
+__device__ __forceinline__ void kkeq_segment_smem(const KKEqArgs& a, long long seg) {
   constexpr int NT = N4 / 16, L4 = N4 / 2, L2 = N4 / 4, NB2 = N4 / 2;
   static_assert(N4 / 2 == 8 * NT, "eight two-sample vectors per thread");
   __shared__ __align__(16) float2 buf[N4];
@@ -79,15 +120,31 @@ __device__ __forceinline__ void kkeq_segment(const KKEqArgs& a, long long seg) {
   }
 }
 
+// Threads per equaliser block: one warp for N4 = 1024, else N4/16.
 template <int N4>
-__global__ void __launch_bounds__(N4 / 16) kkeq_kernel(KKEqArgs a) {
+constexpr int kkeq_threads() {
+  return N4 == 1024 ? 32 : N4 / 16;
+}
+
+template <int N4>
+__device__ __forceinline__ void kkeq_segment(const KKEqArgs& a, long long seg) {
+  if constexpr (N4 == 1024) {
+    kkeq_segment_1024w(a, seg);
+  } else {
+    kkeq_segment_smem<N4>(a, seg);
+  }
+}
+
+// The one-warp form is capped at 128 registers (16 blocks per SM).
+template <int N4>
+__global__ void __launch_bounds__(kkeq_threads<N4>(), N4 == 1024 ? 16 : 1) kkeq_kernel(KKEqArgs a) {
   kkeq_segment<N4>(a, blockIdx.x);
 }
 
 // Many channels in one launch: block b belongs to the channel c with
 // offs[c] <= b < offs[c + 1]; blocks past offs[nch] return at once.
 template <int N4>
-__global__ void __launch_bounds__(N4 / 16) kkeq_batch_kernel(const KKEqBatchTable* __restrict__ t) {
+__global__ void __launch_bounds__(kkeq_threads<N4>(), N4 == 1024 ? 16 : 1) kkeq_batch_kernel(const KKEqBatchTable* __restrict__ t) {
   const long long b = blockIdx.x;
   if (b >= t->offs[t->nch]) return;
   int lo = 0, hi = t->nch;
@@ -251,8 +308,8 @@ __global__ void x2_shift_batch_kernel(const WLBatchTable* __restrict__ t) {
 cudaError_t launch_kkeq(const KKEqArgs& a, int N4, long long nseg, cudaStream_t s) {
   if (nseg <= 0) return cudaSuccess;
   switch (N4) {
-    case 1024: kkeq_kernel<1024><<<(unsigned)nseg, 64, 0, s>>>(a); break;
-    case 2048: kkeq_kernel<2048><<<(unsigned)nseg, 128, 0, s>>>(a); break;
+    case 1024: kkeq_kernel<1024><<<(unsigned)nseg, kkeq_threads<1024>(), 0, s>>>(a); break;
+    case 2048: kkeq_kernel<2048><<<(unsigned)nseg, kkeq_threads<2048>(), 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -262,11 +319,16 @@ cudaError_t kkeq_batch_nodes(int N4, cudaKernelNodeParams* eq, cudaKernelNodePar
   std::memset(eq, 0, sizeof(*eq));
   std::memset(tail, 0, sizeof(*tail));
   switch (N4) {
-    case 1024: eq->func = (void*)kkeq_batch_kernel<1024>; break;
-    case 2048: eq->func = (void*)kkeq_batch_kernel<2048>; break;
+    case 1024:
+      eq->func = (void*)kkeq_batch_kernel<1024>;
+      eq->blockDim = dim3(kkeq_threads<1024>());
+      break;
+    case 2048:
+      eq->func = (void*)kkeq_batch_kernel<2048>;
+      eq->blockDim = dim3(kkeq_threads<2048>());
+      break;
     default: return cudaErrorInvalidValue;
   }
-  eq->blockDim = dim3(N4 / 16);
   tail->func = (void*)kkeq_tail_batch_kernel;
   tail->blockDim = dim3(256);
   return cudaSuccess;
