@@ -1041,11 +1041,14 @@ def batched_streams(n_streams, n_sym):
 
 
 def run_batched(args):
-    """64 independent streams with uneven capture blocks through the serving
-    layer, every block submitted at once: throughput and frame latency with
-    the FFT size of the default rule (N >= 4 halo), with the size the
-    autotuner picks per stream, and the latter with FP16 sample storage;
-    beside them the plain per-stream chain (one stream at a time)."""
+    """64 independent streams with uneven capture blocks, every block
+    submitted at once: through the serving layer (throughput and frame
+    latency with the FFT size of the default rule (N >= 4 halo), with the
+    size the autotuner picks per stream, and the latter with FP16 sample
+    storage) and through one rx_batch (round j pushes every stream's j-th
+    block in one call: one launch per stage and frame ordinal, pipelined
+    over the batch's four streams); beside them the plain per-stream chain
+    (one stream at a time).  The value is the fastest form."""
     import torch
     import rxsim
     from paper_2108_07001_gb300 import rx
@@ -1065,7 +1068,9 @@ def run_batched(args):
     torch.cuda.synchronize()
     gen_s = time.time() - t0
     t0 = time.time()
-    tuned = [rx.autotune_fft(rx.default_config(**rxc), frames=8)[0] for _, rxc, _ in streams]
+    only_batch = args.batched_forms == "batch"
+    tuned = [0] * len(streams) if only_batch else \
+        [rx.autotune_fft(rx.default_config(**rxc), frames=8)[0] for _, rxc, _ in streams]
     tune_s = time.time() - t0
     total_samples = 4 * n_sym * len(streams)
     order = [(i, j) for j in range(max(len(b) for b in data)) for i in range(len(streams)) if j < len(data[i])]
@@ -1106,7 +1111,39 @@ def run_batched(args):
             r.close()
         return wall, per
 
+    def batch_pass(fft, storage):
+        """All streams through one rx_batch: round j pushes every stream's
+        j-th block in one call (one launch per stage and frame ordinal),
+        the last call ends every stream."""
+        cur = torch.cuda.current_stream()
+        recs = [rx.Receiver(**dict(rxc, fft_n=fft[i], storage_dtype=storage)) for i, (_, rxc, _) in enumerate(streams)]
+        dummy = torch.zeros(16, dtype=torch.complex64, device=dev)
+        n_rounds = max(len(b) for b in data)
+        with rx.Batch(recs) as batch:
+            torch.cuda.synchronize()
+            t_start = time.perf_counter()
+            for j in range(n_rounds):
+                ptrs = [data[i][j].data_ptr() if j < len(data[i]) else dummy.data_ptr() for i in range(len(streams))]
+                ns = [data[i][j].shape[1] if j < len(data[i]) else 0 for i in range(len(streams))]
+                batch.push(ptrs, ns, rx.RX_C64, cur.cuda_stream)
+            batch.end(cur.cuda_stream)
+            host = time.perf_counter() - t_start
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t_start
+            info = batch.info()
+        per = [r.stats() for r in recs]
+        for r in recs:
+            r.close()
+        return wall, host, info, per
+
     forms = {}
+    if only_batch:  # the batched launch alone (for launch lists)
+        batch_pass([0] * len(streams), rx.RX_C64)
+        wall, host, info, per = batch_pass([0] * len(streams), rx.RX_C64)
+        return {"workload": "batched", "form": "batch_default_fft", "gsamples_s": round(total_samples / wall / 1e9, 3),
+                "wall_ms": round(wall * 1e3, 1), "host_ms": round(host * 1e3, 1), "calls": info["calls"],
+                "launches": info["launches"], "synced_streams": int(sum(p["synced"] for p in per)),
+                "ber_max": max(p["ber"] for p in per)}
     plain_per_stream()
     wall, per = plain_per_stream()
     forms["plain_per_stream"] = {"gsamples_s": round(total_samples / wall / 1e9, 3), "wall_ms": round(wall * 1e3, 1),
@@ -1123,10 +1160,21 @@ def run_batched(args):
                        "synced_streams": int(sum(p["synced"] for p in per)),
                        "ber_max": max(p["ber"] for p in per), "cycle_slips": int(sum(p["cycle_slips"] for p in per)),
                        "mem_gib": round(st["mem_in_use_bytes"] / 2 ** 30, 2) if st["mem_in_use_bytes"] else None}
+    for form, fft, storage in (("batch_default_fft", [0] * len(streams), rx.RX_C64),
+                               ("batch_autotuned_fft_fp16_storage", tuned, rx.RX_C16)):
+        batch_pass(fft, storage)
+        wall, host, info, per = batch_pass(fft, storage)
+        forms[form] = {"gsamples_s": round(total_samples / wall / 1e9, 3), "wall_ms": round(wall * 1e3, 1),
+                       "host_ms": round(host * 1e3, 1), "calls": info["calls"], "launches": info["launches"],
+                       "fft_groups": len(set(fft)) if fft[0] else None,
+                       "synced_streams": int(sum(p["synced"] for p in per)),
+                       "ber_max": max(p["ber"] for p in per), "cycle_slips": int(sum(p["cycle_slips"] for p in per))}
     base = forms["plain_per_stream"]["gsamples_s"]
-    for form in ("default_fft", "autotuned_fft", "autotuned_fft_fp16_storage"):
+    for form in ("default_fft", "autotuned_fft", "autotuned_fft_fp16_storage", "batch_default_fft",
+                 "batch_autotuned_fft_fp16_storage"):
         forms[form]["x_plain_per_stream"] = round(forms[form]["gsamples_s"] / base, 2) if base else None
-    return {"metric": "gsamples_per_s", "value": forms["autotuned_fft_fp16_storage"]["gsamples_s"],
+    best = max((f for f in forms if f != "plain_per_stream"), key=lambda f: forms[f]["gsamples_s"])
+    return {"metric": "gsamples_per_s", "value": forms[best]["gsamples_s"], "value_form": best,
             "unit": "Gsamples/s",
             "n_gpus": 1, "higher_is_better": True, "workload": "batched", "dtype": "f16 storage, f32 arithmetic",
             "data": "synthetic (seeded link simulator)",
@@ -1149,6 +1197,8 @@ def main():
     ap.add_argument("--symbols", type=int, default=0, help="stream length per pol (default: the workload's 2^24)")
     ap.add_argument("--oracle-child", nargs=4, help=argparse.SUPPRESS)
     ap.add_argument("--kk-oracle-child", type=int, help=argparse.SUPPRESS)
+    ap.add_argument("--batched-forms", default="all", choices=["all", "batch"],
+                    help="batched workload: all forms, or the batched launch alone")
     ap.add_argument("--bps-coarse-stride", type=int, default=1,
                     help="stream workload: 4 = two-stage BPS over 16 coarse angles (default 1: all 64)")
     ap.add_argument("--workload", default="stream", choices=["stream", "qam16", "serving", "batched", "kk", "kk_batch", "kkrx_batch"],

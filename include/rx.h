@@ -170,6 +170,50 @@ int rx_pull_bits(rx_handle* h, uint8_t* out, size_t cap_bytes, size_t* n_bits, i
 /* Waits for all queued work, then fills *out.  RX_EDEVICE on CUDA error. */
 int rx_stats(rx_handle* h, rx_stats_t* out);
 
+/* Many streams pushed in one call, one launch per stage (Sec. II: large
+ * buffers keep many threads busy and cut per-launch overhead; here the
+ * blocks of many streams fill each launch instead).  rx_batch_push
+ * ingests every stream's block with one launch and then runs the frames
+ * the blocks complete by ordinal: the i-th frame of every stream that
+ * completes at least i + 1 frames goes through each stage (CD + timing/FO
+ * statistics, estimators, acquisition, MIMO, BPS, demap, BER) in one
+ * launch; streams whose FFT size and storage type, tap count or BPS form
+ * differ get a launch of their own for that stage.
+ * The ingest runs on cuda_stream; the stages run on the batch's own four
+ * streams (front: CD and estimators, mid: acquisition and MIMO, back: BPS
+ * and demap, BER), pipelined over ordinals and calls with the buffer-reuse
+ * waits of the plain path, so every stream's bits and counters are those
+ * of the same blocks pushed with rx_push_block (soft values agree to FP32
+ * rounding).  The arguments of a call are one page-locked table copied to
+ * the device once (four tables rotate: a call waits on the host for the
+ * call four back to finish).
+ *
+ * rx_batch_create: n_streams (1..RX_BATCH_MAX) distinct handles of one
+ * device; the batch keeps the pointers (the caller keeps the handles alive
+ * and destroys the batch first).  RX_EINVAL, RX_EDEVICE.
+ * rx_batch_push: samples[c], n_per_pol[c] as rx_push_block for stream c
+ * (n_per_pol[c] = 0 with samples[c] != NULL: nothing for c; samples[c] =
+ * NULL with n_per_pol[c] = 0: end of stream c); on_device 1 (device
+ * pointers) or 2 (page-locked host memory mapped for the device, read by
+ * the ingest kernel in stream order: the caller keeps it unchanged until
+ * the work on cuda_stream has passed it).  A refused call changes nothing:
+ * RX_EINVAL (bad argument, size > max_block_samples), RX_ESTATE (a stream
+ * has ended), RX_EAGAIN (a stream's output ring is full: pull its bits),
+ * RX_EDEVICE.  Streams of a batch may also be pushed, pulled, reset and
+ * ended through their own calls; work is ordered across the two paths.
+ * Bits and statistics are read per stream (rx_pull_bits, rx_stats).
+ * rx_batch_info: calls, kernel launches and frames of the batch so far
+ * (NULL pointers skipped).
+ * rx_batch_destroy: waits for the batch's streams, frees the batch (not
+ * the streams). */
+#define RX_BATCH_MAX 256
+typedef struct rx_batch rx_batch;
+int rx_batch_create(rx_handle* const* streams, int n_streams, rx_batch** out);
+int rx_batch_push(rx_batch* b, const void* const* samples, const size_t* n_per_pol, int dtype, int on_device,
+                  void* cuda_stream);
+int rx_batch_info(const rx_batch* b, int64_t* calls, int64_t* launches, int64_t* frames);
+void rx_batch_destroy(rx_batch* b);
+
 /* Waits for queued work and frees everything the handle owns. */
 int rx_destroy(rx_handle* h);
 

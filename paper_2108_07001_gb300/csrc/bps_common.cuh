@@ -62,7 +62,8 @@ __device__ __forceinline__ void bps_finish_run(const RxDev& d, const FrameArgs& 
 // counter and carries the last angle and counter to the next frame.
 // evn / evd: the calling warp's sums (read on lane 0).
 template <int NT>
-__device__ __forceinline__ void bps_finish_block(const RxDev& d, int pol, int nruns, float evn, float evd) {
+__device__ __forceinline__ void bps_finish_block(const RxDev& d, int pol, int nruns, float evn, float evd,
+                                                 int nblk) {
   constexpr int NW = NT / 32;
   __shared__ float red_s[NW][2];
   __shared__ int part[NT];
@@ -88,7 +89,7 @@ __device__ __forceinline__ void bps_finish_block(const RxDev& d, int pol, int nr
   // the lane-0 threads wrote the run sums and edges
   if (lane == 0) __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) am_last = atomicAdd(&d.bps_done[pol], 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) am_last = atomicAdd(&d.bps_done[pol], 1u) == (unsigned)nblk - 1;
   __syncthreads();
   if (!am_last) return;
   __threadfence();

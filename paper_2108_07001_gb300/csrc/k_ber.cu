@@ -44,13 +44,13 @@ __device__ uint32_t prbs_window_at(const uint32_t* jump, uint32_t s, long long P
 // is kRefChunk bits.
 constexpr int kRefChunk = 256;
 
-__global__ void __launch_bounds__(128) ref_gen_kernel(RxDev d, long long sym0, int nbits, int use_delay) {
+__device__ __forceinline__ void ref_gen_body(const RxDev& d, long long sym0, int nbits, int use_delay, VBlock vb) {
   __shared__ uint32_t jump_s[48 * 31];
   __shared__ uint32_t base_s;
   for (int i = threadIdx.x; i < 48 * 31; i += blockDim.x) jump_s[i] = d.prbs_jump[i];
   __syncthreads();
-  const int pol = blockIdx.y;
-  const int chunk0 = blockIdx.x * blockDim.x;
+  const int pol = vb.y;
+  const int chunk0 = vb.x * blockDim.x;
   if ((long long)chunk0 * kRefChunk >= nbits) return;  // whole block past the end (uniform)
   const long long delay = use_delay ? d.st->sync_delay : 0;
   const long long B0 = (sym0 - delay) * d.bps;
@@ -90,6 +90,19 @@ __global__ void __launch_bounds__(128) ref_gen_kernel(RxDev d, long long sym0, i
   }
 }
 
+__global__ void __launch_bounds__(128) ref_gen_kernel(RxDev d, long long sym0, int nbits, int use_delay) {
+  ref_gen_body(d, sym0, nbits, use_delay, own_block());
+}
+
+// Batched: use_delay 0 generates the sync window, 1 the counted range.
+__global__ void __launch_bounds__(128) ref_gen_batch_kernel(BView v, int use_delay) {
+  int fi;
+  VBlock vb;
+  if (!batch_block(v, fi, vb)) return;
+  const BFrame& f = v.frames[fi];
+  ref_gen_body(f.d, use_delay ? f.ref_sym0 : f.sync_sym0, use_delay ? f.ref_nbits : f.sync_nbits, use_delay, vb);
+}
+
 __device__ __forceinline__ uint32_t ref_bits(const uint32_t* ref, long long off, int n) {
   const long long w = off >> 5;
   const int sh = (int)(off & 31);
@@ -113,9 +126,9 @@ __device__ __forceinline__ uint32_t rx_sym_bits(int lI, int lQ, int q, int nl) {
 
 // One block per (delay, order) candidate over the sync window; the
 // reference holds tx symbols [k_s - Dmax, k_s + n_sync + Dmax).
-__global__ void __launch_bounds__(256) sync_kernel(RxDev d) {
+__device__ __forceinline__ void sync_body(const RxDev& d, VBlock vb) {
   __shared__ unsigned red[8][8];
-  const int cand = blockIdx.x;
+  const int cand = vb.x;
   const int delay = cand / 2 - d.sync_dmax, perm = cand & 1;
   const long long ks = d.ber_skip;
   unsigned err[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
@@ -152,7 +165,7 @@ __global__ void __launch_bounds__(256) sync_kernel(RxDev d) {
   __shared__ int am_last;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) am_last = atomicAdd(&d.ber_done[0], 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) am_last = atomicAdd(&d.ber_done[0], 1u) == vb.nx - 1;
   __syncthreads();
   if (!am_last || threadIdx.x >= 32) return;
   __threadfence();
@@ -193,6 +206,17 @@ __global__ void __launch_bounds__(256) sync_kernel(RxDev d) {
   }
 }
 
+__global__ void __launch_bounds__(256) sync_kernel(RxDev d) {
+  sync_body(d, own_block());
+}
+
+__global__ void __launch_bounds__(256) sync_batch_kernel(BView v) {
+  int fi;
+  VBlock vb;
+  if (!batch_block(v, fi, vb)) return;
+  sync_body(v.frames[fi].d, vb);
+}
+
 // Errors of symbols [ka, kb) under the four quadrants, per slip window.
 // The symbols are cut into pieces of at most kBerPiece symbols that never
 // cross a window; one warp counts one piece (lane l takes symbols k0 + l of
@@ -213,8 +237,8 @@ __host__ __device__ inline long long ber_items(long long ka, long long kb, long 
   return (wb - wa + 1) * ((sw + kBerPiece - 1) / kBerPiece);
 }
 
-__global__ void __launch_bounds__(256) ber_count_kernel(RxDev d, long long ka, long long kb, long long w_from,
-                                                        long long w_to, long long k_lim, int n_win_ring) {
+__device__ __forceinline__ void ber_count_body(const RxDev& d, long long ka, long long kb, long long w_from,
+                                               long long w_to, long long k_lim, int n_win_ring, VBlock vb) {
   __shared__ uint8_t lut[4][16];  // bits of level code (lI | lQ << 2) rotated by q
   __shared__ int am_last;
   if (threadIdx.x < 64) {
@@ -226,7 +250,7 @@ __global__ void __launch_bounds__(256) ber_count_kernel(RxDev d, long long ka, l
   const long long ppw = (sw + kBerPiece - 1) / kBerPiece;  // pieces per window
   const long long k_lo = ka > ks ? ka : ks;
   const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const long long item = (long long)blockIdx.x * 8 + warp;
+  const long long item = (long long)vb.x * 8 + warp;
   bool wrote = false;
   if (item < ber_items(ka, kb, ks, sw)) {  // warp-uniform
     const long long w = (k_lo - ks) / sw + item / ppw;
@@ -268,13 +292,26 @@ __global__ void __launch_bounds__(256) ber_count_kernel(RxDev d, long long ka, l
   // block takes its ticket
   if (wrote) __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) am_last = atomicAdd(&d.ber_done[1], 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) am_last = atomicAdd(&d.ber_done[1], 1u) == vb.nx - 1;
   __syncthreads();
   if (!am_last) return;
   __threadfence();
   extern __shared__ unsigned win_s[];
   slip_pass(d, w_from, w_to, k_lim, n_win_ring, win_s);
   if (threadIdx.x == 0) d.ber_done[1] = 0;
+}
+
+__global__ void __launch_bounds__(256) ber_count_kernel(RxDev d, long long ka, long long kb, long long w_from,
+                                                        long long w_to, long long k_lim, int n_win_ring) {
+  ber_count_body(d, ka, kb, w_from, w_to, k_lim, n_win_ring, own_block());
+}
+
+__global__ void __launch_bounds__(256) ber_count_batch_kernel(BView v) {
+  int fi;
+  VBlock vb;
+  if (!batch_block(v, fi, vb)) return;
+  const BFrame& f = v.frames[fi];
+  ber_count_body(f.d, f.ka, f.kb, f.w_from, f.w_to, f.k_lim, f.n_win_ring, vb);
 }
 
 // Slip pass over windows [w_from, w_to); window w covers symbols
@@ -407,9 +444,10 @@ __device__ void slip_pass(const RxDev& d, long long w_from, long long w_to, long
 }
 
 // Push conversion: src planar [2][n] of dtype (0 c128, 1 c64, 2 c16) into
-// the ring at absolute sample offset w0 (index mod cap), storage dtype.
-__global__ void ingest_kernel(RxDev d, const void* __restrict__ src, int dtype, long long n, long long j0) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// the ring at absolute sample offset w0 (index mod cap), storage dtype;
+// element i of the push.
+__device__ __forceinline__ void ingest_one(void* ring, long long ring_cap, int storage, const void* __restrict__ src,
+                                           int dtype, long long n, long long j0, long long i) {
   if (i >= 2 * n) return;
   const int pol = i >= n;
   const long long j = i - pol * n;
@@ -423,10 +461,14 @@ __global__ void ingest_kernel(RxDev d, const void* __restrict__ src, int dtype, 
     v = __half22float2(reinterpret_cast<const __half2*>(src)[i]);
   }
   long long slot = j0 + j;  // j0 = w0 mod cap, n <= cap
-  if (slot >= d.ring_cap) slot -= d.ring_cap;
-  const long long dst = (long long)pol * d.ring_cap + slot;
-  if (d.storage == 2) reinterpret_cast<__half2*>(d.ring)[dst] = __float22half2_rn(v);
-  else reinterpret_cast<float2*>(d.ring)[dst] = v;
+  if (slot >= ring_cap) slot -= ring_cap;
+  const long long dst = (long long)pol * ring_cap + slot;
+  if (storage == 2) reinterpret_cast<__half2*>(ring)[dst] = __float22half2_rn(v);
+  else reinterpret_cast<float2*>(ring)[dst] = v;
+}
+
+__global__ void ingest_kernel(RxDev d, const void* __restrict__ src, int dtype, long long n, long long j0) {
+  ingest_one(d.ring, d.ring_cap, d.storage, src, dtype, n, j0, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // c64 input into a c64 ring, two samples (16 bytes) per access: pair j of
@@ -434,13 +476,13 @@ __global__ void ingest_kernel(RxDev d, const void* __restrict__ src, int dtype, 
 // n, j0 and cap even and a 16-byte aligned source, so a pair never
 // straddles the polarisations or the ring's wrap.  Each thread moves four
 // pairs, all four loads issued before the stores.
-__global__ void __launch_bounds__(256) ingest_pairs_kernel(RxDev d, const float4* __restrict__ src, long long n2,
-                                                            long long j0) {
-  float4* ring4 = reinterpret_cast<float4*>(d.ring);
-  const long long cap2 = d.ring_cap / 2;
+__device__ __forceinline__ void ingest_pairs_body(void* ring, long long ring_cap, const float4* __restrict__ src,
+                                                  long long n2, long long j0, VBlock vb) {
+  float4* ring4 = reinterpret_cast<float4*>(ring);
+  const long long cap2 = ring_cap / 2;
   const long long s0 = j0 / 2;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)vb.nx * blockDim.x;
+  const long long i0 = (long long)vb.x * blockDim.x + threadIdx.x;
   float4 v[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -460,6 +502,26 @@ __global__ void __launch_bounds__(256) ingest_pairs_kernel(RxDev d, const float4
   }
 }
 
+__global__ void __launch_bounds__(256) ingest_pairs_kernel(RxDev d, const float4* __restrict__ src, long long n2,
+                                                            long long j0) {
+  ingest_pairs_body(d.ring, d.ring_cap, src, n2, j0, own_block());
+}
+
+// The pushes of many streams in one launch: entry e of the list (frames
+// unused) is ingest e, its nx[e] blocks of 256 threads as in the plain
+// launches (pairs: four pairs per thread; else one element).
+__global__ void __launch_bounds__(256) ingest_batch_kernel(const BIngest* __restrict__ ing, BView v) {
+  int e;
+  VBlock vb;
+  if (!batch_block(v, e, vb)) return;
+  const BIngest& g = ing[e];
+  if (g.pairs) {
+    ingest_pairs_body(g.ring, g.ring_cap, static_cast<const float4*>(g.src), g.n / 2, g.j0, vb);
+  } else {
+    ingest_one(g.ring, g.ring_cap, g.storage, g.src, g.dtype, g.n, g.j0, (long long)vb.x * blockDim.x + threadIdx.x);
+  }
+}
+
 // ---- launchers ------------------------------------------------------------
 
 cudaError_t launch_ref_gen(const RxDev& d, long long sym0, int nbits, int use_delay, cudaStream_t s) {
@@ -475,8 +537,12 @@ cudaError_t launch_sync(const RxDev& d, cudaStream_t s) {
 }
 
 cudaError_t ber_set_attributes() {
-  return cudaFuncSetAttribute(ber_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(kSlipChunk * 8 * sizeof(unsigned)));
+  cudaError_t e = cudaFuncSetAttribute(ber_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(kSlipChunk * 8 * sizeof(unsigned)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ber_count_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSlipChunk * 8 * sizeof(unsigned)));
+  return e;
 }
 
 cudaError_t launch_ber(const RxDev& d, long long ka, long long kb, long long w_from, long long w_to,
@@ -501,6 +567,45 @@ cudaError_t launch_ingest(const RxDev& d, const void* src, int dtype, long long 
     return cudaGetLastError();
   }
   ingest_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d, src, dtype, n, j0);
+  return cudaGetLastError();
+}
+
+// ---- batched launchers (grids as above) -------------------------------------
+
+int ref_grid_x(int nbits) { return ((nbits + kRefChunk - 1) / kRefChunk + 127) / 128; }
+int sync_grid_x(const RxDev& d) { return (2 * d.sync_dmax + 1) * 2; }
+int ber_grid_x(const RxDev& d, long long ka, long long kb) {
+  return (int)std::max(1LL, (ber_items(ka, kb, d.ber_skip, d.slip_win) + 7) / 8);
+}
+int ingest_grid_x(long long n, bool pairs) { return (int)(pairs ? (n + 1023) / 1024 : (2 * n + 255) / 256); }
+// The 16-byte pair path of launch_ingest applies.
+bool ingest_pairs_ok(const RxDev& d, const void* src, int dtype, long long n, long long w0) {
+  const long long j0 = w0 % d.ring_cap;
+  return dtype == 1 && d.storage == 1 && (n & 1) == 0 && (j0 & 1) == 0 && (d.ring_cap & 1) == 0 &&
+         (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+}
+
+cudaError_t launch_ref_gen_batch(const BView& v, int blocks, int use_delay, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  ref_gen_batch_kernel<<<blocks, 128, 0, s>>>(v, use_delay);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sync_batch(const BView& v, int blocks, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  sync_batch_kernel<<<blocks, 256, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ber_batch(const BView& v, int blocks, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  ber_count_batch_kernel<<<blocks, 256, kSlipChunk * 8 * sizeof(unsigned), s>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ingest_batch(const BIngest* ing, const BView& v, int blocks, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  ingest_batch_kernel<<<blocks, 256, 0, s>>>(ing, v);
   return cudaGetLastError();
 }
 

@@ -75,7 +75,7 @@ struct BpsSmem {
 // d) that keeps every metric positive under rounding; symbols outside the
 // stream are staged as y = 0, h = 0 and contribute exactly 0.
 template <int B, int W, bool QAM16>
-__global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
+__device__ __forceinline__ void bps_body(const RxDev& d, const FrameArgs& fa, VBlock vb) {
   using SM = BpsSmem<B, W, QAM16>;
   constexpr bool PAIR = SM::PAIR;
   constexpr int APL = B / 32;            // angles per lane
@@ -86,10 +86,10 @@ __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
   __shared__ float2 cs_s[B];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int pol = blockIdx.y;
+  const int pol = vb.y;
   const long long n_dec = fa.k_b - fa.k_a;
   const int nruns = (int)((n_dec + kRun - 1) / kRun);
-  const int run = blockIdx.x * 8 + warp;
+  const int run = vb.x * 8 + warp;
   const long long kr = fa.k_a + (long long)run * kRun;
   const int ract = run < nruns ? (int)min((long long)kRun, fa.k_b - kr) : 0;
 
@@ -293,7 +293,21 @@ __global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
   float evn, evd;
   bps_finish_run(d, fa, pol, run, nruns, kr, ract, bh_s[warp], cs_s,
                  [&](int ko) { return PAIR ? make_float2(ys4[W + ko].x, ys4[W + ko].y) : ys2[W + ko]; }, evn, evd);
-  bps_finish_block<256>(d, pol, nruns, evn, evd);
+  bps_finish_block<256>(d, pol, nruns, evn, evd, vb.nx);
+}
+
+template <int B, int W, bool QAM16>
+__global__ void __launch_bounds__(256, 2) bps_kernel(RxDev d, FrameArgs fa) {
+  bps_body<B, W, QAM16>(d, fa, own_block());
+}
+
+template <int B, int W, bool QAM16>
+__global__ void __launch_bounds__(256, 2) bps_batch_kernel(BView v) {
+  int fi;
+  VBlock vb;
+  if (!batch_block(v, fi, vb)) return;
+  const BFrame& f = v.frames[fi];
+  bps_body<B, W, QAM16>(f.d, f.fa, vb);
 }
 
 // Quadrant rotation by -m (multiply by (-j)^m); one quarter turn maps
@@ -312,9 +326,9 @@ __device__ __forceinline__ uint32_t gray_bits(int l, int nl) {  // MSB first
 // Demap: one block per run, thread t handles symbols k_r + 2t, k_r + 2t + 1
 // of both polarisations.  Writes the output bits, the decision ring and
 // the inspection history.
-__global__ void __launch_bounds__(128) demap_kernel(RxDev d, FrameArgs fa) {
+__device__ __forceinline__ void demap_body(const RxDev& d, const FrameArgs& fa, VBlock vb) {
   __shared__ int wt[2][4];
-  const int r = blockIdx.x;
+  const int r = vb.x;
   const long long kr = fa.k_a + (long long)r * kRun;
   const int t = threadIdx.x;
   const int stride = d.F / kRun + 4;
@@ -402,6 +416,18 @@ __global__ void __launch_bounds__(128) demap_kernel(RxDev d, FrameArgs fa) {
   (void)n_dec;
 }
 
+__global__ void __launch_bounds__(128) demap_kernel(RxDev d, FrameArgs fa) {
+  demap_body(d, fa, own_block());
+}
+
+__global__ void __launch_bounds__(128) demap_batch_kernel(BView v) {
+  int fi;
+  VBlock vb;
+  if (!batch_block(v, fi, vb)) return;
+  const BFrame& f = v.frames[fi];
+  demap_body(f.d, f.fa, vb);
+}
+
 // ---- launchers ------------------------------------------------------------
 
 cudaError_t bps2_set_attributes();  // k_bps2.cu
@@ -421,6 +447,12 @@ static cudaError_t bps_attr_t() {
                                        (int)BpsSmem<B, W, true>::BYTES);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(bps_kernel<B, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BpsSmem<B, W, false>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(bps_batch_kernel<B, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BpsSmem<B, W, true>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(bps_batch_kernel<B, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)BpsSmem<B, W, false>::BYTES);
   return e;
 }
@@ -450,6 +482,40 @@ cudaError_t launch_bps(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
   RX_BW(64, 12) RX_BW(32, 12) RX_BW(64, 24) RX_BW(32, 24)
 #undef RX_BW
   return cudaErrorInvalidValue;
+}
+
+// ---- batched launchers (every frame of v has d's B, W, modulation and stride)
+
+int launch_bps2_batch(const RxDev& d, const BView& v, int blocks, cudaStream_t s);  // k_bps2.cu
+
+int bps_grid_x(const RxDev& d, const FrameArgs& fa) {
+  const long long n_dec = fa.k_b - fa.k_a;
+  const int nruns = (int)((n_dec + kRun - 1) / kRun);
+  return d.bps_stride > 1 ? (nruns + 15) / 16 : (nruns + 7) / 8;
+}
+
+int demap_grid_x(const FrameArgs& fa) { return (int)((fa.k_b - fa.k_a + kRun - 1) / kRun); }
+
+cudaError_t launch_bps_batch(const RxDev& d, const BView& v, int blocks, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  if (d.bps_stride > 1) return (cudaError_t)launch_bps2_batch(d, v, blocks, s);
+  const bool q16 = d.bps == 4;
+#define RX_BW(b, w)                                                                                 \
+  if (d.B == b && d.W == w) {                                                                       \
+    if (q16) bps_batch_kernel<b, w, true><<<blocks, 256, BpsSmem<b, w, true>::BYTES, s>>>(v);       \
+    else bps_batch_kernel<b, w, false><<<blocks, 256, BpsSmem<b, w, false>::BYTES, s>>>(v);         \
+    return cudaGetLastError();                                                                      \
+  }
+  RX_BW(64, 16) RX_BW(32, 16) RX_BW(64, 32) RX_BW(32, 32) RX_BW(64, 8) RX_BW(32, 8)
+  RX_BW(64, 12) RX_BW(32, 12) RX_BW(64, 24) RX_BW(32, 24)
+#undef RX_BW
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_demap_batch(const BView& v, int blocks, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  demap_batch_kernel<<<blocks, 128, 0, s>>>(v);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_unwrap_demap(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {

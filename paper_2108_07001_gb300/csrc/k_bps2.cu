@@ -77,7 +77,7 @@ struct Bps2Smem {
 __device__ __forceinline__ int qpsk_word(int j) { return 2 * (j & 7) + (j >> 3); }
 
 template <int W, bool QAM16>
-__global__ void __launch_bounds__(128, Bps2Smem<W, QAM16>::MIN_BLOCKS) bps2_kernel(RxDev d, FrameArgs fa) {
+__device__ __forceinline__ void bps2_body(const RxDev& d, const FrameArgs& fa, VBlock vb) {
   using SM = Bps2Smem<W, QAM16>;
   constexpr int C = SM::C, G = SM::G, WIN = SM::WIN, R = SM::R, ROWW = SM::ROWW;
   extern __shared__ __align__(16) unsigned char bps2_smem[];
@@ -85,11 +85,11 @@ __global__ void __launch_bounds__(128, Bps2Smem<W, QAM16>::MIN_BLOCKS) bps2_kern
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane >> 3, q = lane & 7;
-  const int pol = blockIdx.y;
+  const int pol = vb.y;
   const int B = d.B, S = d.bps_stride;
   const long long n_dec = fa.k_b - fa.k_a;
   const int nruns = (int)((n_dec + kRun - 1) / kRun);
-  const int run0 = (blockIdx.x * 4 + warp) * G;
+  const int run0 = (vb.x * 4 + warp) * G;
   const long long kw0 = fa.k_a + (long long)run0 * kRun;
   // symbols left from the warp's first run on (runs are consecutive; only
   // the last run of the frame can be short)
@@ -260,7 +260,21 @@ __global__ void __launch_bounds__(128, Bps2Smem<W, QAM16>::MIN_BLOCKS) bps2_kern
     evn += en;
     evd += ed;
   }
-  bps_finish_block<128>(d, pol, nruns, evn, evd);
+  bps_finish_block<128>(d, pol, nruns, evn, evd, vb.nx);
+}
+
+template <int W, bool QAM16>
+__global__ void __launch_bounds__(128, Bps2Smem<W, QAM16>::MIN_BLOCKS) bps2_kernel(RxDev d, FrameArgs fa) {
+  bps2_body<W, QAM16>(d, fa, own_block());
+}
+
+template <int W, bool QAM16>
+__global__ void __launch_bounds__(128, Bps2Smem<W, QAM16>::MIN_BLOCKS) bps2_batch_kernel(BView v) {
+  int fi;
+  VBlock vb;
+  if (!batch_block(v, fi, vb)) return;
+  const BFrame& f = v.frames[fi];
+  bps2_body<W, QAM16>(f.d, f.fa, vb);
 }
 
 template <int W, bool Q>
@@ -277,6 +291,12 @@ static cudaError_t bps2_attr_t() {
                                        (int)Bps2Smem<W, true>::BYTES);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(bps2_kernel<W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Bps2Smem<W, false>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(bps2_batch_kernel<W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Bps2Smem<W, true>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(bps2_batch_kernel<W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Bps2Smem<W, false>::BYTES);
   return e;
 }
@@ -300,6 +320,22 @@ cudaError_t launch_bps2(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
     if (q16) launch_bps2_t<w, true>(d, fa, s);    \
     else launch_bps2_t<w, false>(d, fa, s);       \
     return cudaGetLastError();                    \
+  }
+  RX_W(16) RX_W(32) RX_W(8) RX_W(12) RX_W(24)
+#undef RX_W
+  return cudaErrorInvalidValue;
+}
+
+// Batched two-stage search (a cudaError_t value); every frame of v has d's W and modulation.
+int launch_bps2_batch(const RxDev& d, const BView& v, int blocks, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  const bool q16 = d.bps == 4;
+  if (d.bps_stride * (q16 ? 8 : 16) != d.B) return cudaErrorInvalidValue;
+#define RX_W(w)                                                                                 \
+  if (d.W == w) {                                                                               \
+    if (q16) bps2_batch_kernel<w, true><<<blocks, 128, Bps2Smem<w, true>::BYTES, s>>>(v);       \
+    else bps2_batch_kernel<w, false><<<blocks, 128, Bps2Smem<w, false>::BYTES, s>>>(v);         \
+    return cudaGetLastError();                                                                  \
   }
   RX_W(16) RX_W(32) RX_W(8) RX_W(12) RX_W(24)
 #undef RX_W

@@ -43,13 +43,13 @@ __device__ __forceinline__ float block_sum(float v, float* scratch) {
 }
 
 template <int N, int NT, int STOR>
-__global__ void __launch_bounds__(NT) cd_ols_kernel(RxDev d, FrameArgs fa) {
+__device__ __forceinline__ void cd_ols_body(const RxDev& d, const FrameArgs& fa, VBlock vb) {
   extern __shared__ float2 buf[];
   __shared__ float scratch[NT / 32];
   __shared__ float2 tw_s[2 * kTwSplit];  // [hi | lo] two-level twiddle table
   for (int i = threadIdx.x; i < 2 * kTwSplit; i += NT) tw_s[i] = d.tw2[i];
-  const int pol = blockIdx.y;
-  const long long a = fa.s0 + (long long)blockIdx.x * d.L;
+  const int pol = vb.y;
+  const long long a = fa.s0 + (long long)vb.x * d.L;
   const long long zlen_f = 2LL * fa.Ff + 2 * d.c;
   const int keep = (int)min((long long)d.L, fa.s0 + zlen_f - a);
   const long long lo = a - d.h;
@@ -215,6 +215,21 @@ __global__ void __launch_bounds__(NT) cd_ols_kernel(RxDev d, FrameArgs fa) {
   }
 }
 
+template <int N, int NT, int STOR>
+__global__ void __launch_bounds__(NT) cd_ols_kernel(RxDev d, FrameArgs fa) {
+  cd_ols_body<N, NT, STOR>(d, fa, own_block());
+}
+
+// Batched: pass 0 runs the timing-acquisition pass (fe), pass 1 the frame.
+template <int N, int NT, int STOR>
+__global__ void __launch_bounds__(NT) cd_ols_batch_kernel(BView v, int pass) {
+  int fi;
+  VBlock vb;
+  if (!batch_block(v, fi, vb)) return;
+  const BFrame& f = v.frames[fi];
+  cd_ols_body<N, NT, STOR>(f.d, pass ? f.fa : f.fe, vb);
+}
+
 // x reduced to [-pi, pi] in FP64 (x - 2 pi rint(x / 2 pi)).
 __device__ __forceinline__ double wrap_pi(double x) {
   constexpr double kTwoPi = 6.283185307179586477, kInvTwoPi = 0.15915494309189533577;
@@ -234,7 +249,7 @@ __device__ __forceinline__ double wrap_pi(double x) {
 // Accumulators and estimator state are double-buffered by frame parity:
 // frame f reads acc/psd slot fa.acc_slot and state es[f & 1], clears the
 // other accumulator slot and writes es[(f + 1) & 1].
-__global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mode) {
+__device__ __forceinline__ void est_body(const RxDev& d, const FrameArgs& fa, int mode, VBlock vb) {
   __shared__ long long sv[32];
   __shared__ int si[32];
   __shared__ double sh[4];
@@ -296,7 +311,7 @@ __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mo
       sh[0] = om;
       sh[1] = gain;
       sh[2] = es.tau + (double)d.timing_gain * resid;
-      if (blockIdx.x == 0) {
+      if (vb.x == 0) {
         if (fa.f < kMaxTrace) {
           FrameRec r;
           r.tau = es.tau;
@@ -317,13 +332,13 @@ __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mo
     const double om = sh[0], gain = sh[1], theta = es.theta;
     tau_next = sh[2];
     const float omf = (float)om;  // |w l| < 1024 |w|: FP32 phase is exact to ~1e-6 rad
-    for (int l = blockIdx.x * 1024 + tid; l < kRotLo; l += gridDim.x * 1024) {
+    for (int l = vb.x * 1024 + tid; l < kRotLo; l += vb.nx * 1024) {
       float s, c;
       sincosf(omf * (float)l, &s, &c);
       d.rot_lo[l] = make_float2(c, -s);
     }
     const int nhi = (d.zlen + kRotLo - 1) / kRotLo;
-    for (int hh = blockIdx.x * 1024 + tid; hh < nhi; hh += gridDim.x * 1024) {
+    for (int hh = vb.x * 1024 + tid; hh < nhi; hh += vb.nx * 1024) {
       const double ph = wrap_pi(theta + om * (double)(hh * kRotLo - d.c));
       float s, c;
       sincosf((float)ph, &s, &c);
@@ -331,14 +346,14 @@ __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mo
     }
     // clear the other accumulator slot for the next frame's CD pass
     double* psd_n = d.psd + (long long)((fa.f + 1) & 1) * (d.N / 2);
-    for (int k = blockIdx.x * 1024 + tid; k < n2; k += gridDim.x * 1024) psd_n[k] = 0.0;
-    if (blockIdx.x == 0 && tid == 0) {
+    for (int k = vb.x * 1024 + tid; k < n2; k += vb.nx * 1024) psd_n[k] = 0.0;
+    if (vb.x == 0 && tid == 0) {
       FrameAcc* an = d.acc + ((fa.f + 1) & 1);
       an->C[0] = an->C[1] = an->P = 0.0;
     }
   } else {
     tau_next = resid;
-    if (blockIdx.x == 0 && tid == 0) {
+    if (vb.x == 0 && tid == 0) {
       EstState nx;
       nx.tau = resid;
       nx.theta = 0.0;
@@ -350,12 +365,25 @@ __global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mo
   // exp(+j 2 pi f_k tau) = sincospi(2 (k'/N) fs tau), k' = k or k - N: the
   // scalar fs tau is formed in FP64, the per-bin product (k'/N exact) in FP32
   const float u2 = (float)(2.0 * d.fs * tau_next) / (float)d.N;
-  for (int k = blockIdx.x * 1024 + tid; k < d.N; k += gridDim.x * 1024) {
+  for (int k = vb.x * 1024 + tid; k < d.N; k += vb.nx * 1024) {
     const int kk = k < d.N / 2 ? k : k - d.N;
     float s, c;
     sincospif((float)kk * u2, &s, &c);
     d.Hf[k] = cmul(d.Hs[k], make_float2(c, s));
   }
+}
+
+__global__ void __launch_bounds__(1024) est_kernel(RxDev d, FrameArgs fa, int mode) {
+  est_body(d, fa, mode, own_block());
+}
+
+// Batched: mode 0 on the timing-acquisition pass (fe), mode 1 on the frame.
+__global__ void __launch_bounds__(1024) est_batch_kernel(BView v, int mode) {
+  int fi;
+  VBlock vb;
+  if (!batch_block(v, fi, vb)) return;
+  const BFrame& f = v.frames[fi];
+  est_body(f.d, mode ? f.fa : f.fe, mode, vb);
 }
 
 // ---- host-side launchers -------------------------------------------------
@@ -380,6 +408,10 @@ static cudaError_t cd_attr_n() {
   cudaError_t e = cudaFuncSetAttribute(cd_ols_kernel<N, NT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(cd_ols_kernel<N, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(cd_ols_batch_kernel<N, NT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(cd_ols_batch_kernel<N, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return e;
 }
 
@@ -404,9 +436,44 @@ cudaError_t launch_cd(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
   }
 }
 
+int est_grid_x(const RxDev& d) { return max(1, min(16, (d.N + 1023) / 1024)); }
+
 cudaError_t launch_est(const RxDev& d, const FrameArgs& fa, int mode, cudaStream_t s) {
-  const int nb = max(1, min(16, (d.N + 1023) / 1024));
-  est_kernel<<<nb, 1024, 0, s>>>(d, fa, mode);
+  est_kernel<<<est_grid_x(d), 1024, 0, s>>>(d, fa, mode);
+  return cudaGetLastError();
+}
+
+// ---- batched launchers (grids as above, one row per polarisation) ---------
+
+int cd_grid_x(const RxDev& d, const FrameArgs& fa) {
+  const long long zlen_f = 2LL * fa.Ff + 2 * d.c;
+  return (int)((zlen_f + d.L - 1) / d.L);
+}
+
+template <int N, int NT>
+static cudaError_t launch_cd_batch_n(const RxDev& d, const BView& v, int blocks, int pass, cudaStream_t s) {
+  const size_t smem = sizeof(float2) * N;
+  if (d.storage == 2) cd_ols_batch_kernel<N, NT, 2><<<blocks, NT, smem, s>>>(v, pass);
+  else cd_ols_batch_kernel<N, NT, 1><<<blocks, NT, smem, s>>>(v, pass);
+  return cudaGetLastError();
+}
+
+// Every frame of v has d's FFT size and storage type.
+cudaError_t launch_cd_batch(const RxDev& d, const BView& v, int blocks, int pass, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  switch (d.N) {
+    case 1024: return launch_cd_batch_n<1024, 256>(d, v, blocks, pass, s);
+    case 2048: return launch_cd_batch_n<2048, 256>(d, v, blocks, pass, s);
+    case 4096: return launch_cd_batch_n<4096, 256>(d, v, blocks, pass, s);
+    case 8192: return launch_cd_batch_n<8192, 512>(d, v, blocks, pass, s);
+    case 16384: return launch_cd_batch_n<16384, 1024>(d, v, blocks, pass, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_est_batch(const BView& v, int blocks, int mode, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  est_batch_kernel<<<blocks, 1024, 0, s>>>(v, mode);
   return cudaGetLastError();
 }
 

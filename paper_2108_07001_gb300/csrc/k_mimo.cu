@@ -176,7 +176,7 @@ __device__ __forceinline__ void store_taps(const ChainSmem<T>& sm, float2* dst) 
 // over the sub-block's symbols k = quarter mod 4; the quarters are added
 // with shuffles and the quarter-0 thread updates the tap.
 template <int T>
-__global__ void __launch_bounds__(256) acq_kernel(RxDev d, FrameArgs fa) {
+__device__ __forceinline__ void acq_body(const RxDev& d, const FrameArgs& fa) {
   constexpr int PL = 344;   // plane stride (float2): 256 + 80 mirror, = 64 B mod 128 B
   __shared__ float2 r_s[4 * PL + 8];
   __shared__ float2 w_s[2][2][T];         // [p][q][t]
@@ -362,12 +362,26 @@ __global__ void __launch_bounds__(256) acq_kernel(RxDev d, FrameArgs fa) {
   }
 }
 
+template <int T>
+__global__ void __launch_bounds__(256) acq_kernel(RxDev d, FrameArgs fa) {
+  acq_body<T>(d, fa);
+}
+
+template <int T>
+__global__ void __launch_bounds__(256) acq_batch_kernel(BView v) {
+  int fi;
+  VBlock vb;
+  if (!batch_block(v, fi, vb)) return;
+  const BFrame& f = v.frames[fi];
+  acq_body<T>(f.d, f.fa);
+}
+
 // All segments of one frame, one warp per segment.
 template <int T>
-__global__ void __launch_bounds__(128) mimo_kernel(RxDev d, FrameArgs fa, long long hist_base) {
+__device__ __forceinline__ void mimo_body(const RxDev& d, const FrameArgs& fa, long long hist_base, VBlock vb) {
   __shared__ ChainSmem<T> sms[4];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = blockIdx.x * 4 + wib;
+  const int j = vb.x * 4 + wib;
   const int nseg = (fa.Ff + d.S - 1) / d.S;
   if (j >= nseg) return;
   ChainSmem<T>& sm = sms[wib];
@@ -377,7 +391,7 @@ __global__ void __launch_bounds__(128) mimo_kernel(RxDev d, FrameArgs fa, long l
   // frame f's equalised symbols go to buffer f % 2 after a copy of the last
   // kYHist symbols of frame f-1 (zeros for the first frame)
   float2* yb = d.y + (long long)(fa.f & 1) * 2 * (kYHist + d.F);
-  if (blockIdx.x == 0 && wib == 0) {
+  if (vb.x == 0 && wib == 0) {
     const float2* yp = d.y + (long long)((fa.f + 1) & 1) * 2 * (kYHist + d.F);
     for (int i = lane; i < 2 * kYHist; i += 32) {
       const int p = i / kYHist, t = i % kYHist;
@@ -444,6 +458,20 @@ __global__ void __launch_bounds__(128) mimo_kernel(RxDev d, FrameArgs fa, long l
   store_taps<T>(sm, chain);
 }
 
+template <int T>
+__global__ void __launch_bounds__(128) mimo_kernel(RxDev d, FrameArgs fa, long long hist_base) {
+  mimo_body<T>(d, fa, hist_base, own_block());
+}
+
+template <int T>
+__global__ void __launch_bounds__(128) mimo_batch_kernel(BView v) {
+  int fi;
+  VBlock vb;
+  if (!batch_block(v, fi, vb)) return;
+  const BFrame& f = v.frames[fi];
+  mimo_body<T>(f.d, f.fa, f.hist_base, vb);
+}
+
 // ---- launchers ------------------------------------------------------------
 
 template <int T>
@@ -477,6 +505,35 @@ cudaError_t launch_mimo(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
 #undef RX_T
     default: return cudaErrorInvalidValue;
   }
+}
+
+// ---- batched launchers (every frame of v has d's tap count) ----------------
+
+int mimo_grid_x(const RxDev& d, const FrameArgs& fa) {
+  const int nseg = (fa.Ff + d.S - 1) / d.S;
+  return (nseg + 3) / 4;
+}
+
+cudaError_t launch_acquire_batch(const RxDev& d, const BView& v, int blocks, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  switch (d.T) {
+#define RX_T(t) case t: acq_batch_kernel<t><<<blocks, 256, 0, s>>>(v); break;
+    RX_TAPS(RX_T)
+#undef RX_T
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mimo_batch(const RxDev& d, const BView& v, int blocks, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  switch (d.T) {
+#define RX_T(t) case t: mimo_batch_kernel<t><<<blocks, 128, 0, s>>>(v); break;
+    RX_TAPS(RX_T)
+#undef RX_T
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace rx

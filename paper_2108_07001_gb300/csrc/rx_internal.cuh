@@ -197,4 +197,73 @@ __device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsign
   return r;
 }
 
+
+// ---- batched launches (rx_batch_push) -------------------------------------
+//
+// Every kernel of the chain is a body over block coordinates (x, y) of a
+// grid nx blocks wide.  A plain launch passes its own blockIdx / gridDim.x;
+// a batched launch runs the grids of many streams' frames one after the
+// other in one flat grid, and each block finds its frame and coordinates
+// from the launch's prefix sums.
+
+struct VBlock {
+  int x, y, nx;
+};
+
+__device__ __forceinline__ VBlock own_block() { return VBlock{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x}; }
+
+// One frame of one stream in a batched launch: the stream's device state
+// with the frame's slot applied and every stage's arguments.
+struct BFrame {
+  RxDev d;
+  FrameArgs fa;                  // the frame (or the decide-only pass at the stream end)
+  FrameArgs fe;                  // the timing-acquisition pass of the first frame
+  long long hist_base;           // first symbol of the frame (inspection history)
+  long long sync_sym0, ref_sym0; // reference bits: the sync window, the counted range
+  int sync_nbits, ref_nbits;
+  long long ka, kb, w_from, w_to, k_lim;  // BER count
+  int n_win_ring, pad;
+};
+
+// Ingest of one stream's push in a batched launch.
+struct BIngest {
+  void* ring;
+  long long ring_cap;
+  const void* src;
+  long long n, j0;
+  int storage, dtype, pairs, pad;
+};
+
+// A batched launch: list = [n, idx[nmax], nx[nmax], offs[nmax + 1]]; entry
+// e runs frame idx[e]'s grid (nx[e] blocks wide) as the launch's blocks
+// [offs[e], offs[e + 1]).
+struct BView {
+  const BFrame* frames;
+  const int* list;
+  int nmax;
+};
+
+// The frame and block coordinates of this block; false for the blocks past
+// the last entry (the whole block returns).
+__device__ __forceinline__ bool batch_block(const BView& v, int& frame, VBlock& vb) {
+  const int n = v.list[0];
+  const int* idx = v.list + 1;
+  const int* nx = idx + v.nmax;
+  const int* offs = nx + v.nmax;
+  const int b = (int)blockIdx.x;
+  if (n <= 0 || b >= offs[n]) return false;
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (offs[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  const int r = b - offs[lo];
+  vb.nx = nx[lo];
+  vb.x = r % vb.nx;
+  vb.y = r / vb.nx;
+  frame = idx[lo];
+  return true;
+}
+
 }  // namespace rx

@@ -31,7 +31,7 @@ STAGES = ["ingest", "cd", "est", "acquire", "mimo", "bps", "demap", "ber"]
 EXPORTS = ["rx_config_default", "rx_create", "rx_push_block", "rx_pull_bits", "rx_stats",
            "rx_destroy", "rx_reset", "rx_join", "rx_stage_times", "rx_last_error",
            "rx_frame_trace", "rx_get_taps", "rx_get_equalised", "rx_get_phase",
-           "rx_decide_block_noalloc",
+           "rx_decide_block_noalloc", "rx_batch_create", "rx_batch_push", "rx_batch_info", "rx_batch_destroy",
            "rx_server_config_default", "rx_server_create", "rx_server_open", "rx_server_submit",
            "rx_server_end", "rx_server_sync", "rx_server_pull_bits", "rx_server_stream_stats",
            "rx_server_handle", "rx_server_close", "rx_server_stats", "rx_server_destroy",
@@ -242,6 +242,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                        ctypes.POINTER(SZ), P]
     lib.rx_kkrx_batch_destroy.argtypes = [P]
     lib.rx_kkrx_batch_destroy.restype = None
+    lib.rx_batch_create.argtypes = [ctypes.POINTER(P), I, ctypes.POINTER(P)]
+    lib.rx_batch_push.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(SZ), I, I, P]
+    lib.rx_batch_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    lib.rx_batch_destroy.argtypes = [P]
+    lib.rx_batch_destroy.restype = None
     for name in ["rx_create", "rx_push_block", "rx_pull_bits", "rx_stats", "rx_destroy", "rx_reset",
                  "rx_join", "rx_stage_times", "rx_frame_trace", "rx_get_taps", "rx_get_equalised",
                  "rx_get_phase", "rx_decide_block_noalloc", "rx_server_create", "rx_server_open",
@@ -250,7 +255,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                  "rx_kk_create", "rx_kk_push", "rx_kk_end", "rx_kk_reset", "rx_kk_position",
                  "rx_kk_batch_create", "rx_kk_batch_push",
                  "rx_kkrx_create", "rx_kkrx_push", "rx_kkrx_end", "rx_kkrx_equalised", "rx_kkrx_reset",
-                 "rx_kkrx_batch_create", "rx_kkrx_batch_push"]:
+                 "rx_kkrx_batch_create", "rx_kkrx_batch_push", "rx_batch_create", "rx_batch_push",
+                 "rx_batch_info"]:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -425,6 +431,57 @@ class _Borrowed(Receiver):
 
     def close(self) -> None:
         self.h = None
+
+
+class Batch:
+    """Several receiver streams pushed together (rx_batch_*): one launch per
+    stage and frame ordinal over every stream's frames."""
+
+    def __init__(self, receivers: list):
+        self.lib = load()
+        self.receivers = list(receivers)
+        n = len(self.receivers)
+        arr = (ctypes.c_void_p * n)(*[r.h.value for r in self.receivers])
+        b = ctypes.c_void_p()
+        _check(self.lib.rx_batch_create(arr, n, ctypes.byref(b)))
+        self.b = b
+        self._ptr = (ctypes.c_void_p * n)()
+        self._n = (ctypes.c_size_t * n)()
+
+    def push(self, ptrs, ns, dtype: int, stream: int = 0, on_device: int = 1) -> None:
+        """Pointers (planar [2][n] each) and samples per polarisation per
+        stream; n = 0 pushes nothing to that stream, ptr None with n = 0
+        ends it."""
+        for i in range(len(self.receivers)):
+            self._ptr[i] = ptrs[i]
+            self._n[i] = ns[i]
+        _check(self.lib.rx_batch_push(self.b, self._ptr, self._n, dtype, on_device, ctypes.c_void_p(stream)))
+
+    def end(self, stream: int = 0) -> None:
+        """Ends every stream of the batch in one call."""
+        self.push([None] * len(self.receivers), [0] * len(self.receivers), RX_C64, stream)
+
+    def info(self) -> dict:
+        c, l, f = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(self.lib.rx_batch_info(self.b, ctypes.byref(c), ctypes.byref(l), ctypes.byref(f)))
+        return {"calls": c.value, "launches": l.value, "frames": f.value}
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            self.lib.rx_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -282,3 +282,16 @@ def test_kkrx_batch_argument_checks_without_device(lib):
     assert lib.rx_kkrx_batch_create(arr, 1, ctypes.byref(b)) == rx.RX_EINVAL
     assert lib.rx_kkrx_batch_create(arr, 257, ctypes.byref(b)) == rx.RX_EINVAL
     assert lib.rx_kkrx_batch_push(None, None, None, None, None, None, None) == rx.RX_EINVAL
+
+
+def test_batch_argument_checks_without_device(lib):
+    from paper_2108_07001_gb300 import rx
+    b = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.rx_batch_create(None, 1, ctypes.byref(b)) == rx.RX_EINVAL
+    assert lib.rx_batch_create(arr, 0, ctypes.byref(b)) == rx.RX_EINVAL
+    assert lib.rx_batch_create(arr, 1, ctypes.byref(b)) == rx.RX_EINVAL  # null stream
+    assert lib.rx_batch_create(arr, 257, ctypes.byref(b)) == rx.RX_EINVAL
+    assert lib.rx_batch_push(None, None, None, rx.RX_C64, 1, None) == rx.RX_EINVAL
+    assert lib.rx_batch_info(None, None, None, None) == rx.RX_EINVAL
+    lib.rx_batch_destroy(None)  # no-op

@@ -1,0 +1,161 @@
+"""Batched pushes of many dual-polarisation streams (rx_batch_*): one
+launch per stage and frame ordinal over every stream's frames gives the
+bits and counters of the same blocks pushed stream by stream, exactly.
+
+The batched kernels inline the same stage bodies into other kernels, and
+the compiler may fuse a different multiply into an FMA there, so soft
+values (equalised symbols, EVM) agree to FP32 rounding rather than bit for
+bit: both paths are deterministic, and 1-ulp differences in the CD output
+show up downstream as differences of order 1e-6 of the unit-power
+symbols.  The bound used, 1e-4, leaves room for the adaptive equaliser to
+carry such differences over a few frames."""
+import numpy as np
+import pytest
+
+import rxsim
+from paper_2108_07001_gb300 import rx
+
+pytestmark = pytest.mark.gpu
+
+F = 1 << 13
+
+
+def stream_case(kind, seed):
+    """A short stream and its receiver configuration; the kinds differ in
+    FFT size, tap count, BPS form, modulation and storage type, so the
+    batch runs several launch groups per stage."""
+    if kind == "qpsk1000":
+        link = dict(baud_hz=28e9, bits_per_sym=2, n_sym=4 * F + 999, fiber_len_m=1000e3, snr_db=12.0)
+        cfg = dict(baud_hz=28e9, modulation=2, fiber_len_m=1000e3)
+    elif kind == "qpsk3000_fft8192":
+        link = dict(baud_hz=32e9, bits_per_sym=2, n_sym=3 * F + 77, fiber_len_m=3000e3, snr_db=11.0)
+        cfg = dict(baud_hz=32e9, modulation=2, fiber_len_m=3000e3, fft_n=8192)
+    elif kind == "qpsk_two_stage_fp16":
+        link = dict(baud_hz=28e9, bits_per_sym=2, n_sym=5 * F, fiber_len_m=1500e3, snr_db=12.0)
+        cfg = dict(baud_hz=28e9, modulation=2, fiber_len_m=1500e3, bps_coarse_stride=4,
+                   storage_dtype=rx.RX_C16)
+    else:
+        link = dict(baud_hz=32e9, bits_per_sym=4, n_sym=3 * F + 500, fiber_len_m=500e3, snr_db=18.0)
+        cfg = dict(baud_hz=32e9, modulation=4, fiber_len_m=500e3, mimo_taps=25, bps_angles=32, bps_half_window=32,
+                   mu_dd=2e-3)
+    sim = rxsim.simulate(rxsim.LinkConfig(**link, prbs_seed=seed, seed=seed, out_dtype="c64"))
+    n_sym = link["n_sym"]
+    cfg.update(frame_syms=F, acq_syms=F, cma_syms=4096, prbs_seed=seed, ber_skip_syms=2048, sync_syms=2048,
+               history_syms=n_sym, max_block_samples=1 << 15)
+    x = sim["rx"]
+    rng = np.random.default_rng(seed)
+    cuts, left = [], x.shape[1]
+    while left:
+        m = int(min(left, rng.choice([0, 1000, 5000, 1 << 14, 1 << 15, int(rng.integers(1, 1 << 15))])))
+        cuts.append(m)
+        left -= m
+    blocks, a = [], 0
+    for m in cuts:
+        blocks.append(np.ascontiguousarray(x[:, a:a + m]))
+        a += m
+    return cfg, blocks, n_sym
+
+
+KINDS = ("qpsk1000", "qpsk3000_fft8192", "qpsk_two_stage_fp16", "qam16")
+
+
+@pytest.fixture(scope="module")
+def cases():
+    return [stream_case(k, 900 + i) for i, k in enumerate(KINDS)]
+
+
+def results(r, n_sym):
+    buf = np.empty(1 << 22, dtype=np.uint8)
+    nb = r.pull_bytes(buf, timeout_ms=-1)
+    return buf[:(nb + 7) // 8].copy(), nb, r.equalised(0, n_sym), r.stats()
+
+
+def plain(cases):
+    import torch
+    out = []
+    s = torch.cuda.current_stream().cuda_stream
+    for cfg, blocks, n_sym in cases:
+        r = rx.Receiver(**cfg)
+        for b in blocks:
+            if b.shape[1]:
+                t = torch.from_numpy(b).cuda()
+                r.push_device(t.data_ptr(), b.shape[1], rx.RX_C64, s)
+                torch.cuda.current_stream().synchronize()
+        r.end()
+        out.append(results(r, n_sym))
+        r.close()
+    return out
+
+
+def test_batch_equals_plain_pushes(cases):
+    """Uneven rounds (some streams idle in a round), one stream's block of
+    round 2 pushed through its own call in the middle of the batch's
+    rounds, one stream ended through its own call, the others by the
+    batch: bits, equalised symbols and counters equal the plain pushes'."""
+    import torch
+    want = plain(cases)
+    s = torch.cuda.current_stream().cuda_stream
+    recs = [rx.Receiver(**cfg) for cfg, _, _ in cases]
+    dev = [[torch.from_numpy(b).cuda() for b in blocks] for _, blocks, _ in cases]
+    dummy = torch.zeros(16, dtype=torch.complex64, device="cuda")  # a non-null pointer for "nothing"
+    n_rounds = max(len(b) for b in dev)
+    with rx.Batch(recs) as batch:
+        for j in range(n_rounds):
+            ptrs, ns = [], []
+            for c, blocks in enumerate(dev):
+                if j < len(blocks) and blocks[j].shape[1] and not (c == 1 and j == 2):
+                    ptrs.append(blocks[j].data_ptr())
+                    ns.append(blocks[j].shape[1])
+                else:
+                    ptrs.append(dummy.data_ptr())
+                    ns.append(0)
+            if n_rounds > 2 and j == 2 and len(dev[1]) > 2 and dev[1][2].shape[1]:
+                recs[1].push_device(dev[1][2].data_ptr(), dev[1][2].shape[1], rx.RX_C64, s)
+            batch.push(ptrs, ns, rx.RX_C64, s)
+        recs[0].end()
+        with pytest.raises(rx.RxError) as e:  # stream 0 has ended: the whole call is refused
+            batch.end(s)
+        assert e.value.code == rx.RX_ESTATE
+        ptrs = [dummy.data_ptr()] + [None] * (len(recs) - 1)
+        batch.push(ptrs, [0] * len(recs), rx.RX_C64, s)
+        info = batch.info()
+    got = [results(r, n_sym) for r, (_, _, n_sym) in zip(recs, cases)]
+    for r in recs:
+        r.close()
+    frames = 0
+    for k, (a, b) in enumerate(zip(want, got)):
+        bits0, n0, y0, s0 = a
+        bits1, n1, y1, s1 = b
+        assert n0 == n1 > 0, KINDS[k]
+        assert np.array_equal(bits0, bits1), KINDS[k]
+        assert np.abs(y0 - y1).max() <= 1e-4, KINDS[k]
+        for f in ("bits", "bit_errors", "cycle_slips", "synced", "frames"):
+            assert s0[f] == s1[f], (KINDS[k], f)
+        assert s1["synced"] == 1 and s1["ber"] < 1e-2, KINDS[k]
+        assert s1["evm"] == pytest.approx(s0["evm"], rel=1e-4)
+        frames += s1["frames"]
+    assert 0 < info["frames"] <= frames
+    assert info["calls"] == n_rounds + 1
+    assert info["launches"] > 0
+
+
+def test_refused_batch_push_changes_nothing(cases):
+    import torch
+    cfg, blocks, _ = cases[0]
+    s = torch.cuda.current_stream().cuda_stream
+    r0, r1 = rx.Receiver(**cfg), rx.Receiver(**cfg)
+    t = torch.from_numpy(next(b for b in blocks if b.shape[1])).cuda()
+    big = torch.zeros((2, (1 << 15) + 1), dtype=torch.complex64, device="cuda")
+    with rx.Batch([r0, r1]) as batch:
+        with pytest.raises(rx.RxError) as e:  # stream 1's block exceeds max_block_samples
+            batch.push([t.data_ptr(), big.data_ptr()], [t.shape[1], big.shape[1]], rx.RX_C64, s)
+        assert e.value.code == rx.RX_EINVAL
+        assert batch.info()["calls"] == 0
+        with pytest.raises(rx.RxError):
+            batch.push([t.data_ptr(), t.data_ptr()], [t.shape[1], t.shape[1]], rx.RX_C64, s, on_device=0)
+        batch.push([t.data_ptr(), t.data_ptr()], [t.shape[1], t.shape[1]], rx.RX_C64, s)
+        batch.end(s)
+    a, b = results(r0, 1000), results(r1, 1000)
+    assert a[1] == b[1] and np.array_equal(a[0], b[0])
+    r0.close()
+    r1.close()
