@@ -1141,7 +1141,8 @@ def run_batched(args):
         batch_pass([0] * len(streams), rx.RX_C64)
         wall, host, info, per = batch_pass([0] * len(streams), rx.RX_C64)
         return {"workload": "batched", "form": "batch_default_fft", "gsamples_s": round(total_samples / wall / 1e9, 3),
-                "wall_ms": round(wall * 1e3, 1), "host_ms": round(host * 1e3, 1), "calls": info["calls"],
+                "wall_ms": round(wall * 1e3, 1), "host_ms": round(host * 1e3, 1),
+                "host_wait_ms": round(info["wait_ms"], 1), "calls": info["calls"],
                 "launches": info["launches"], "synced_streams": int(sum(p["synced"] for p in per)),
                 "ber_max": max(p["ber"] for p in per)}
     plain_per_stream()
@@ -1165,7 +1166,8 @@ def run_batched(args):
         batch_pass(fft, storage)
         wall, host, info, per = batch_pass(fft, storage)
         forms[form] = {"gsamples_s": round(total_samples / wall / 1e9, 3), "wall_ms": round(wall * 1e3, 1),
-                       "host_ms": round(host * 1e3, 1), "calls": info["calls"], "launches": info["launches"],
+                       "host_ms": round(host * 1e3, 1), "host_wait_ms": round(info["wait_ms"], 1),
+                       "calls": info["calls"], "launches": info["launches"],
                        "fft_groups": len(set(fft)) if fft[0] else None,
                        "synced_streams": int(sum(p["synced"] for p in per)),
                        "ber_max": max(p["ber"] for p in per), "cycle_slips": int(sum(p["cycle_slips"] for p in per))}

@@ -202,8 +202,9 @@ int rx_stats(rx_handle* h, rx_stats_t* out);
  * RX_EDEVICE.  Streams of a batch may also be pushed, pulled, reset and
  * ended through their own calls; work is ordered across the two paths.
  * Bits and statistics are read per stream (rx_pull_bits, rx_stats).
- * rx_batch_info: calls, kernel launches and frames of the batch so far
- * (NULL pointers skipped).
+ * rx_batch_info: calls, kernel launches and frames of the batch so far, and
+ * the host time its calls spent waiting for a table (ms; NULL pointers
+ * skipped).
  * rx_batch_destroy: waits for the batch's streams, frees the batch (not
  * the streams). */
 #define RX_BATCH_MAX 256
@@ -211,7 +212,7 @@ typedef struct rx_batch rx_batch;
 int rx_batch_create(rx_handle* const* streams, int n_streams, rx_batch** out);
 int rx_batch_push(rx_batch* b, const void* const* samples, const size_t* n_per_pol, int dtype, int on_device,
                   void* cuda_stream);
-int rx_batch_info(const rx_batch* b, int64_t* calls, int64_t* launches, int64_t* frames);
+int rx_batch_info(const rx_batch* b, int64_t* calls, int64_t* launches, int64_t* frames, double* wait_ms);
 void rx_batch_destroy(rx_batch* b);
 
 /* Waits for queued work and frees everything the handle owns. */

@@ -1279,6 +1279,7 @@ struct rx_batch {
   std::vector<cudaEvent_t> ev_ring;   // call start / end events (round robin)
   size_t ev_i = 0;
   long long calls = 0, launches = 0, frames = 0;
+  double wait_s = 0.0;                // host time spent waiting for table slots
 };
 
 namespace {
@@ -1600,7 +1601,11 @@ int rx_batch_push(rx_batch* b, const void* const* samples, const size_t* n_per_p
   // the ingest overwrites ring slots the earlier calls' CD passes read
   if (b->ev_front_last) RX_CK(cudaStreamWaitEvent(cs, b->ev_front_last, 0));
   const int sl = (int)(b->calls % rx_batch::kSlots);
-  RX_CK(cudaEventSynchronize(b->ev_slot[sl]));  // the call kSlots back is done with both copies of the table
+  {
+    const auto t0 = std::chrono::steady_clock::now();
+    RX_CK(cudaEventSynchronize(b->ev_slot[sl]));  // the call kSlots back is done with both copies of the table
+    b->wait_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
   char* hb = static_cast<char*>(b->host[sl]);
   char* db = static_cast<char*>(b->dev[sl]);
   // ingests
@@ -1735,11 +1740,12 @@ int rx_batch_push(rx_batch* b, const void* const* samples, const size_t* n_per_p
   return RX_OK;
 }
 
-int rx_batch_info(const rx_batch* b, int64_t* calls, int64_t* launches, int64_t* frames) {
+int rx_batch_info(const rx_batch* b, int64_t* calls, int64_t* launches, int64_t* frames, double* wait_ms) {
   if (!b) return fail(RX_EINVAL, "null batch");
   if (calls) *calls = b->calls;
   if (launches) *launches = b->launches;
   if (frames) *frames = b->frames;
+  if (wait_ms) *wait_ms = 1e3 * b->wait_s;
   return RX_OK;
 }
 

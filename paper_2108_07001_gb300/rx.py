@@ -244,7 +244,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rx_kkrx_batch_destroy.restype = None
     lib.rx_batch_create.argtypes = [ctypes.POINTER(P), I, ctypes.POINTER(P)]
     lib.rx_batch_push.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(SZ), I, I, P]
-    lib.rx_batch_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    lib.rx_batch_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                  ctypes.POINTER(ctypes.c_double)]
     lib.rx_batch_destroy.argtypes = [P]
     lib.rx_batch_destroy.restype = None
     for name in ["rx_create", "rx_push_block", "rx_pull_bits", "rx_stats", "rx_destroy", "rx_reset",
@@ -462,9 +463,9 @@ class Batch:
         self.push([None] * len(self.receivers), [0] * len(self.receivers), RX_C64, stream)
 
     def info(self) -> dict:
-        c, l, f = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-        _check(self.lib.rx_batch_info(self.b, ctypes.byref(c), ctypes.byref(l), ctypes.byref(f)))
-        return {"calls": c.value, "launches": l.value, "frames": f.value}
+        c, l, f, w = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        _check(self.lib.rx_batch_info(self.b, ctypes.byref(c), ctypes.byref(l), ctypes.byref(f), ctypes.byref(w)))
+        return {"calls": c.value, "launches": l.value, "frames": f.value, "wait_ms": w.value}
 
     def close(self) -> None:
         if getattr(self, "b", None):

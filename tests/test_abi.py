@@ -293,5 +293,5 @@ def test_batch_argument_checks_without_device(lib):
     assert lib.rx_batch_create(arr, 1, ctypes.byref(b)) == rx.RX_EINVAL  # null stream
     assert lib.rx_batch_create(arr, 257, ctypes.byref(b)) == rx.RX_EINVAL
     assert lib.rx_batch_push(None, None, None, rx.RX_C64, 1, None) == rx.RX_EINVAL
-    assert lib.rx_batch_info(None, None, None, None) == rx.RX_EINVAL
+    assert lib.rx_batch_info(None, None, None, None, None) == rx.RX_EINVAL
     lib.rx_batch_destroy(None)  # no-op
