@@ -260,8 +260,8 @@ def run_ours(args):
                            else "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz")
     gpu_launches = int(sum(v[1] for v in stage_tot.values()))
 
-    # e2e: the same stream from pinned host memory (copied to the device in
-    # stream order without a host wait, on_device = 2), bits read back
+    # e2e: the same stream from pinned host memory (taken in stream order
+    # without a host wait, on_device = 2 or 3), bits read back
     if not args.e2e:
         return finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, other_ms,
                       gpu_launches, clocks, host0, host1, gen_s, None)
@@ -274,10 +274,11 @@ def run_ours(args):
     r2 = rx.Receiver(cfg)
     outbufs = [np.empty_like(outbuf), np.empty_like(outbuf)]
 
-    def push_host_step(rr):
+    def push_host_step(rr, mode):
         rr.reset()
         for b in range(nb):
-            rc = lib.rx_push_block(rr.h, ctypes.c_void_p(hbase + b * bbytes), m, rx.RX_C64, 2, ctypes.c_void_p(stream))
+            rc = lib.rx_push_block(rr.h, ctypes.c_void_p(hbase + b * bbytes), m, rx.RX_C64, mode,
+                                   ctypes.c_void_p(stream))
             if rc:
                 raise rx.RxError(rc, lib.rx_last_error().decode())
         rr.end()
@@ -286,27 +287,37 @@ def run_ours(args):
         rr.pull_bytes(outbufs[k % 2], timeout_ms=-1)
         rr.stats()
 
-    push_host_step(r)
-    read_back(r, 0)
-    torch.cuda.synchronize()
-    ke = args.steps
-    e0 = time.perf_counter()
-    prev = None
-    for k in range(ke):
-        rr = (r, r2)[k % 2]
-        push_host_step(rr)
-        if prev is not None:
-            read_back(prev, k - 1)
-        prev = rr
-    read_back(prev, ke - 1)
-    torch.cuda.synchronize()
-    e_s = (time.perf_counter() - e0) / ke
+    def e2e_run(mode):
+        push_host_step(r, mode)
+        read_back(r, 0)
+        torch.cuda.synchronize()
+        ke = args.steps
+        e0 = time.perf_counter()
+        prev = None
+        for k in range(ke):
+            rr = (r, r2)[k % 2]
+            push_host_step(rr, mode)
+            if prev is not None:
+                read_back(prev, k - 1)
+            prev = rr
+        read_back(prev, ke - 1)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - e0) / ke
+
+    # on_device = 2: a copy engine moves each block into a staging slot;
+    # on_device = 3: the ingest kernel reads the pinned block itself
+    e_times = {mode: e2e_run(mode) for mode in (2, 3)}
+    best = min(e_times, key=e_times.get)
+    e_s = e_times[best]
     r2.close()
+    how = {2: "copied by a copy engine into staging slots in stream order (on_device=2)",
+           3: "read by the ingest kernel through the device mapping in stream order (on_device=3)"}
     e2e = {"value": round(samples_step / e_s / 1e9, 3), "unit": "Gsamples/s",
            "h2d_bytes_per_step": int(blocks.nbytes), "d2h_bytes_per_step": int(out_bytes),
            "ms_per_step": round(e_s * 1e3, 2),
-           "protocol": "pinned host blocks copied in stream order (on_device=2); bits and stats read back "
-                       "every step, overlapped with the next step on a second receiver"}
+           "protocol": "pinned host blocks " + how[best] + "; bits and stats read back every step, overlapped "
+                       "with the next step on a second receiver",
+           "forms": {f"on_device={mode}": round(samples_step / t / 1e9, 3) for mode, t in e_times.items()}}
 
     return finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, other_ms,
                   gpu_launches, clocks, host0, host1, gen_s, e2e)

@@ -139,9 +139,12 @@ int rx_create(const rx_config* cfg, rx_handle** out);
  * (RX_C128 / RX_C64 / RX_C16).  on_device: 1 = samples is a device
  * pointer; 0 = a host pointer, copied before the call returns; 2 = a
  * pointer to page-locked host memory, copied to the device by a copy
- * engine in stream order without a host wait: the caller keeps the buffer
- * unchanged until the work on cuda_stream has passed it (RX_EINVAL if the
- * memory is not page-locked).  The call is asynchronous: the copy into the
+ * engine in stream order without a host wait; 3 = a pointer to
+ * page-locked host memory that the ingest kernel reads itself through the
+ * device mapping (no copy engine, no staging buffer).  With 2 and 3 the
+ * caller keeps the buffer unchanged until the work on cuda_stream has
+ * passed it (RX_EINVAL if the memory is not page-locked and mapped).  The
+ * call is asynchronous: the copy into the
  * library's ring is a kernel launched on cuda_stream (a cudaStream_t, NULL =
  * legacy default stream), so it follows the work already queued there and
  * later work on cuda_stream follows it; the caller may reuse a device
@@ -194,9 +197,9 @@ int rx_stats(rx_handle* h, rx_stats_t* out);
  * rx_batch_push: samples[c], n_per_pol[c] as rx_push_block for stream c
  * (n_per_pol[c] = 0 with samples[c] != NULL: nothing for c; samples[c] =
  * NULL with n_per_pol[c] = 0: end of stream c); on_device 1 (device
- * pointers) or 2 (page-locked host memory mapped for the device, read by
- * the ingest kernel in stream order: the caller keeps it unchanged until
- * the work on cuda_stream has passed it).  A refused call changes nothing:
+ * pointers) or 2 and 3 alike (page-locked host memory mapped for the
+ * device, read by the ingest kernel in stream order: the caller keeps it
+ * unchanged until the work on cuda_stream has passed it).  A refused call changes nothing:
  * RX_EINVAL (bad argument, size > max_block_samples), RX_ESTATE (a stream
  * has ended), RX_EAGAIN (a stream's output ring is full: pull its bits),
  * RX_EDEVICE.  Streams of a batch may also be pushed, pulled, reset and

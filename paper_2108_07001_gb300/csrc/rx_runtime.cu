@@ -905,21 +905,27 @@ int rx_push_block(rx_handle* h, const void* samples, size_t n_per_pol, int dtype
   if (samples == nullptr) return fail(RX_EINVAL, "samples is NULL");
   if (dtype < RX_C128 || dtype > RX_C16) return fail(RX_EINVAL, "bad dtype");
   if (n_per_pol > h->cfg.max_block_samples) return fail(RX_EINVAL, "n_per_pol exceeds max_block_samples");
-  if (on_device < 0 || on_device > 2) return fail(RX_EINVAL, "on_device must be 0, 1 or 2");
+  if (on_device < 0 || on_device > 3) return fail(RX_EINVAL, "on_device must be 0, 1, 2 or 3");
   if (n_per_pol == 0) return RX_OK;
   bool async_host = false;
-  if (on_device == 2) {
-    // page-locked host memory: copied by a copy engine into a staging slot
-    // in stream order, without a host wait (the caller keeps the buffer
-    // until the stream has passed it)
+  if (on_device >= 2) {
+    // page-locked host memory, without a host wait (the caller keeps the
+    // buffer until the stream has passed it): 2 = copied by a copy engine
+    // into a staging slot in stream order; 3 = read by the ingest kernel
+    // itself through the device mapping (no staging copy)
     cudaPointerAttributes pa;
     if (cudaPointerGetAttributes(&pa, samples) != cudaSuccess || pa.type != cudaMemoryTypeHost ||
         pa.devicePointer == nullptr) {
       cudaGetLastError();
-      return fail(RX_EINVAL, "on_device = 2 needs page-locked host memory mapped for the device");
+      return fail(RX_EINVAL, "on_device = 2 or 3 needs page-locked host memory mapped for the device");
     }
-    async_host = true;
-    on_device = 0;
+    if (on_device == 3) {
+      samples = pa.devicePointer;
+      on_device = 1;
+    } else {
+      async_host = true;
+      on_device = 0;
+    }
   }
   const long long n = (long long)n_per_pol;
   // output ring room for the frames this push completes
@@ -1555,8 +1561,8 @@ int rx_batch_push(rx_batch* b, const void* const* samples, const size_t* n_per_p
                   void* cuda_stream) {
   if (!b || !samples || !n_per_pol) return fail(RX_EINVAL, "null argument");
   if (dtype < RX_C128 || dtype > RX_C16) return fail(RX_EINVAL, "bad dtype");
-  if (on_device != 1 && on_device != 2)
-    return fail(RX_EINVAL, "batched pushes take device memory (on_device = 1) or mapped page-locked host memory (2)");
+  if (on_device < 1 || on_device > 3)
+    return fail(RX_EINVAL, "batched pushes take device memory (on_device = 1) or mapped page-locked host memory (2, 3)");
   RX_CK(cudaSetDevice(b->device));
   const int nh = b->nh;
   std::vector<const void*> src(nh, nullptr);
@@ -1575,12 +1581,12 @@ int rx_batch_push(rx_batch* b, const void* const* samples, const size_t* n_per_p
     if (!samples[c]) return fail(RX_EINVAL, "samples is NULL");
     if (n > h->cfg.max_block_samples) return fail(RX_EINVAL, "n_per_pol exceeds max_block_samples");
     src[c] = samples[c];
-    if (on_device == 2) {
+    if (on_device >= 2) {
       cudaPointerAttributes pa;
       if (cudaPointerGetAttributes(&pa, samples[c]) != cudaSuccess || pa.type != cudaMemoryTypeHost ||
           pa.devicePointer == nullptr) {
         cudaGetLastError();
-        return fail(RX_EINVAL, "on_device = 2 needs page-locked host memory mapped for the device");
+        return fail(RX_EINVAL, "on_device = 2 or 3 needs page-locked host memory mapped for the device");
       }
       src[c] = pa.devicePointer;
     }

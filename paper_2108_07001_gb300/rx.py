@@ -309,6 +309,12 @@ class Receiver:
         has passed it)."""
         _check(self.lib.rx_push_block(self.h, ctypes.c_void_p(ptr), n_per_pol, dtype, 2, ctypes.c_void_p(stream)))
 
+    def push_mapped(self, ptr: int, n_per_pol: int, dtype: int, stream: int = 0) -> None:
+        """Push from page-locked host memory at ptr, read by the ingest
+        kernel through the device mapping in stream order (no copy engine;
+        keep it unchanged until the stream has passed it)."""
+        _check(self.lib.rx_push_block(self.h, ctypes.c_void_p(ptr), n_per_pol, dtype, 3, ctypes.c_void_p(stream)))
+
     def push_host(self, x: np.ndarray, stream: int = 0) -> None:
         """Push a host array: complex [2, n] (c128/c64) or float16 [2, n, 2] (c16)."""
         if x.dtype == np.float16:

@@ -252,8 +252,10 @@ def test_autotuned_fft_size_is_admissible_and_keeps_parity():
 
 
 def test_pinned_host_push_equals_device_push():
-    """Page-locked host blocks read by the device in stream order (on_device
-    = 2) give exactly the device-push result; unpinned memory is refused."""
+    """Page-locked host blocks taken in stream order, copied by a copy
+    engine (on_device = 2) or read by the ingest kernel through the device
+    mapping (on_device = 3), give exactly the device-push result; unpinned
+    memory is refused."""
     import torch
     from paper_2108_07001_gb300 import rx
     sim = rxsim.simulate(link(n_sym=1 << 15, snr_db=12.0, fiber_len_m=600e3, seed=88, out_dtype="c64"))
@@ -261,7 +263,7 @@ def test_pinned_host_push_equals_device_push():
     x = np.ascontiguousarray(sim["rx"])
     blocks = [np.ascontiguousarray(x[:, a:a + (1 << 14)]) for a in range(0, x.shape[1], 1 << 14)]
     out = []
-    for mode in ("device", "pinned"):
+    for mode in ("device", "pinned", "mapped"):
         r = rx.Receiver(**rx_kw)
         stream = torch.cuda.current_stream().cuda_stream
         keep = []
@@ -273,18 +275,23 @@ def test_pinned_host_push_equals_device_push():
             else:
                 t = torch.from_numpy(b).pin_memory()
                 keep.append(t)
-                r.push_pinned(t.data_ptr(), b.shape[1], rx.RX_C64, stream)
+                if mode == "pinned":
+                    r.push_pinned(t.data_ptr(), b.shape[1], rx.RX_C64, stream)
+                else:
+                    r.push_mapped(t.data_ptr(), b.shape[1], rx.RX_C64, stream)
         r.end()
         buf = np.empty(1 << 20, dtype=np.uint8)
         nb = r.pull_bytes(buf, timeout_ms=-1)
         out.append((buf[:(nb + 7) // 8].copy(), r.equalised(0, 1 << 15)))
-        if mode == "pinned":
+        if mode != "device":
             with pytest.raises(rx.RxError):
                 r2 = rx.Receiver(**rx_kw)
                 try:
-                    r2.push_pinned(blocks[0].ctypes.data, blocks[0].shape[1], rx.RX_C64, stream)
+                    push = r2.push_pinned if mode == "pinned" else r2.push_mapped
+                    push(blocks[0].ctypes.data, blocks[0].shape[1], rx.RX_C64, stream)
                 finally:
                     r2.close()
         r.close()
-    assert np.array_equal(out[0][0], out[1][0])
-    assert np.array_equal(out[0][1], out[1][1])
+    for k in (1, 2):
+        assert np.array_equal(out[0][0], out[k][0])
+        assert np.array_equal(out[0][1], out[k][1])
