@@ -907,6 +907,39 @@ def combine_replicas(line, world, reduce_max):
     return out
 
 
+def shard_streams(costs, world):
+    """Streams to ranks, greedy by cost (e.g. Gsamples): the costliest
+    stream first, each to the rank with the least cost so far (the lowest
+    rank on a tie).  Returns every rank's stream indices, ascending."""
+    load = [0.0] * world
+    out = [[] for _ in range(world)]
+    for i in sorted(range(len(costs)), key=lambda i: (-costs[i], i)):
+        r = min(range(world), key=lambda r: (load[r], r))
+        out[r].append(i)
+        load[r] += costs[i]
+    return [sorted(o) for o in out]
+
+
+def combine_shards(part, world, reduce_max, reduce_sum):
+    """Whole-job line of a stream-sharded run (every rank ran its own
+    streams on its own GPU, no collective on the data path): the wall time
+    is the slowest rank's, samples, streams, synced streams, slips and
+    launches add up, the BER is the worst stream's.  reduce_max /
+    reduce_sum: list of floats -> element-wise max / sum over ranks, a
+    collective every rank calls."""
+    wall_ms, ber_max = reduce_max([float(part["wall_ms"]), float(part["ber_max"])])
+    samples, streams, synced, slips, launches = reduce_sum(
+        [float(part["samples"]), float(part["streams"]), float(part["synced_streams"]),
+         float(part["cycle_slips"]), float(part["launches"])])
+    return {"metric": "gsamples_per_s", "value": round(samples / (wall_ms * 1e-3) / 1e9, 3), "unit": "Gsamples/s",
+            "n_gpus": world, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "workload": "batched", "form": part["form"], "dtype": part.get("dtype", "f32"),
+            "data": "synthetic (seeded link simulator)", "wall_ms": round(wall_ms, 3),
+            "config": {"streams": int(streams), "parallelism": f"streams sharded x{world} (greedy by Gsamples)",
+                       "symbols_per_pol_per_stream": part["symbols_per_pol_per_stream"]},
+            "synced_streams": int(synced), "cycle_slips": int(slips), "ber_max": ber_max, "launches": int(launches)}
+
+
 SERVING_STREAMS = 16
 SERVING_SYMS = 1 << 21       # symbols per polarisation per stream
 SERVING_FRAME = 1 << 18
@@ -1051,7 +1084,7 @@ def batched_streams(n_streams, n_sym):
     return out
 
 
-def run_batched(args):
+def run_batched(args, rank=0, world=1, barrier=None):
     """64 independent streams with uneven capture blocks, every block
     submitted at once: through the serving layer (throughput and frame
     latency with the FFT size of the default rule (N >= 4 halo), with the
@@ -1067,6 +1100,10 @@ def run_batched(args):
     torch.cuda.set_device(dev)
     n_sym = args.symbols or BATCH_SYMS
     streams = batched_streams(BATCH_STREAMS, n_sym)
+    if world > 1:  # this rank's shard of the streams (the batched launch alone)
+        shard = shard_streams([4.0 * n_sym] * len(streams), world)[rank]
+        streams = [streams[i] for i in shard]
+        args.batched_forms = "batch"
     data = []
     t0 = time.time()
     for link, rxc, sizes in streams:
@@ -1132,6 +1169,8 @@ def run_batched(args):
         n_rounds = max(len(b) for b in data)
         with rx.Batch(recs) as batch:
             torch.cuda.synchronize()
+            if barrier:
+                barrier()
             t_start = time.perf_counter()
             for j in range(n_rounds):
                 ptrs = [data[i][j].data_ptr() if j < len(data[i]) else dummy.data_ptr() for i in range(len(streams))]
@@ -1141,6 +1180,8 @@ def run_batched(args):
             host = time.perf_counter() - t_start
             torch.cuda.synchronize()
             wall = time.perf_counter() - t_start
+            if barrier:
+                barrier()
             info = batch.info()
         per = [r.stats() for r in recs]
         for r in recs:
@@ -1152,6 +1193,8 @@ def run_batched(args):
         batch_pass([0] * len(streams), rx.RX_C64)
         wall, host, info, per = batch_pass([0] * len(streams), rx.RX_C64)
         return {"workload": "batched", "form": "batch_default_fft", "gsamples_s": round(total_samples / wall / 1e9, 3),
+                "samples": total_samples, "streams": len(streams), "symbols_per_pol_per_stream": n_sym,
+                "cycle_slips": int(sum(p["cycle_slips"] for p in per)),
                 "wall_ms": round(wall * 1e3, 1), "host_ms": round(host * 1e3, 1),
                 "host_wait_ms": round(info["wait_ms"], 1), "calls": info["calls"],
                 "launches": info["launches"], "synced_streams": int(sum(p["synced"] for p in per)),
@@ -1237,7 +1280,8 @@ def main():
             print(json.dumps(run_reference(args)), flush=True)
         return
     if world > 1:
-        # replicas only: every rank runs its own stream on its own GPU
+        # one stream: replicas, every rank runs its own stream on its own
+        # GPU; the 64-stream workload: the streams shard over the ranks
         import torch
         import torch.distributed as dist
         local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -1245,14 +1289,20 @@ def main():
         dist.init_process_group("nccl")
         dist.barrier()
         args.cpu_baseline = False  # the CPU baseline is taken on one rank at N=1 only
-        line = run_ours(args)
 
-        def reduce_max(vals):
-            t = torch.tensor(vals, device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return t.tolist()
+        def reduce_op(op):
+            def f(vals):
+                t = torch.tensor(vals, device="cuda", dtype=torch.float64)
+                dist.all_reduce(t, op=op)
+                return t.tolist()
+            return f
 
-        line = combine_replicas(line, world, reduce_max)
+        reduce_max = reduce_op(dist.ReduceOp.MAX)
+        if args.workload == "batched":
+            part = run_batched(args, rank, world, barrier=dist.barrier)
+            line = combine_shards(part, world, reduce_max, reduce_op(dist.ReduceOp.SUM))
+        else:
+            line = combine_replicas(run_ours(args), world, reduce_max)
         if rank == 0:
             print(json.dumps(line), flush=True)
         dist.destroy_process_group()
