@@ -1216,10 +1216,15 @@ def run_batched(args, rank=0, world=1, barrier=None):
                        "ber_max": max(p["ber"] for p in per), "cycle_slips": int(sum(p["cycle_slips"] for p in per)),
                        "mem_gib": round(st["mem_in_use_bytes"] / 2 ** 30, 2) if st["mem_in_use_bytes"] else None}
     for form, fft, storage in (("batch_default_fft", [0] * len(streams), rx.RX_C64),
+                               ("batch_default_fft_fp16_storage", [0] * len(streams), rx.RX_C16),
                                ("batch_autotuned_fft_fp16_storage", tuned, rx.RX_C16)):
         batch_pass(fft, storage)
         wall, host, info, per = batch_pass(fft, storage)
+        # block latency of a call (its start on the stream to its bits), the
+        # same for every stream the call carried
         forms[form] = {"gsamples_s": round(total_samples / wall / 1e9, 3), "wall_ms": round(wall * 1e3, 1),
+                       "latency_p50_ms": round(float(np.median([p["latency_p50_ms"] for p in per])), 3),
+                       "latency_p99_ms": round(max(p["latency_p99_ms"] for p in per), 3),
                        "host_ms": round(host * 1e3, 1), "host_wait_ms": round(info["wait_ms"], 1),
                        "calls": info["calls"], "launches": info["launches"],
                        "fft_groups": len(set(fft)) if fft[0] else None,
@@ -1227,7 +1232,7 @@ def run_batched(args, rank=0, world=1, barrier=None):
                        "ber_max": max(p["ber"] for p in per), "cycle_slips": int(sum(p["cycle_slips"] for p in per))}
     base = forms["plain_per_stream"]["gsamples_s"]
     for form in ("default_fft", "autotuned_fft", "autotuned_fft_fp16_storage", "batch_default_fft",
-                 "batch_autotuned_fft_fp16_storage"):
+                 "batch_default_fft_fp16_storage", "batch_autotuned_fft_fp16_storage"):
         forms[form]["x_plain_per_stream"] = round(forms[form]["gsamples_s"] / base, 2) if base else None
     best = max((f for f in forms if f != "plain_per_stream"), key=lambda f: forms[f]["gsamples_s"])
     return {"metric": "gsamples_per_s", "value": forms[best]["gsamples_s"], "value_form": best,
