@@ -159,6 +159,9 @@ def run_ours(args):
     wl = workload(args.bps_coarse_stride)
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
+    if args.fft_n:  # an FFT size, or -1: the one rx_autotune_fft picks on this GPU
+        n = args.fft_n if args.fft_n > 0 else rx.autotune_fft(rx.default_config(**wl["rx"]), frames=4)[0]
+        wl = dict(wl, rx=dict(wl["rx"], fft_n=n))
     import rxsim
     t0 = time.time()
     lk = dict(wl["link"])
@@ -332,7 +335,10 @@ def finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, o
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded link simulator)",
         "config": {"workload": wl["name"], "symbols_per_pol": n_sym, "push_syms": wl["push_syms"],
-                   "frame_syms": cfg.frame_syms, "fft_n_auto": True, "mimo_taps": cfg.mimo_taps,
+                   "frame_syms": cfg.frame_syms,
+                   "fft_n": cfg.fft_n if cfg.fft_n else "default rule (smallest power of 2 >= 4 x halo)",
+                   "fft_n_from": "autotuner" if args.fft_n < 0 else ("given" if args.fft_n else "default rule"),
+                   "mimo_taps": cfg.mimo_taps,
                    "bps_angles": cfg.bps_angles, "bps_search": "full" if cfg.bps_coarse_stride == 1 else
                    f"two-stage: {cfg.bps_angles // cfg.bps_coarse_stride} coarse angles + parabolic refinement",
                    "storage": "c64", "input": "resident in HBM, 512 MiB > L2",
@@ -1258,6 +1264,8 @@ def main():
     ap.add_argument("--symbols", type=int, default=0, help="stream length per pol (default: the workload's 2^24)")
     ap.add_argument("--oracle-child", nargs=4, help=argparse.SUPPRESS)
     ap.add_argument("--kk-oracle-child", type=int, help=argparse.SUPPRESS)
+    ap.add_argument("--fft-n", type=int, default=0,
+                    help="stream workload: overlap-save FFT size (0: the default rule, -1: the autotuner's pick)")
     ap.add_argument("--batched-forms", default="all", choices=["all", "batch"],
                     help="batched workload: all forms, or the batched launch alone")
     ap.add_argument("--bps-coarse-stride", type=int, default=1,
