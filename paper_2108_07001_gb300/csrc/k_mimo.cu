@@ -122,15 +122,24 @@ __device__ __forceinline__ void sub_block(ChainSmem<T>& sm, int nk, int mode, fl
   for (int pr = lane; pr < 2 * T; pr += 32) {
     const int q = pr / T, t = pr - q * T;
     float g0x = 0.f, g0y = 0.f, g1x = 0.f, g1y = 0.f;
-    for (int k = 0; k < nk; ++k) {
-      const float4 ee = sm.e[k];
-      const float2 x = sm_r(sm, q, 2 * k + t);
-      // e * conj(x)
+    // e * conj(x) summed over k in order; r_q[2k + t] sits in plane
+    // (2k + t) mod 4 at (2k + t) / 4, so even k read one plane and odd k
+    // another, each at consecutive entries
+    auto acc = [&](const float4& ee, const float2& x) {
       g0x = fmaf(ee.x, x.x, fmaf(ee.y, x.y, g0x));
       g0y = fmaf(ee.y, x.x, fmaf(-ee.x, x.y, g0y));
       g1x = fmaf(ee.z, x.x, fmaf(ee.w, x.y, g1x));
       g1y = fmaf(ee.w, x.x, fmaf(-ee.z, x.y, g1y));
+    };
+    const float2* xe = &sm.r[q * ChainSmem<T>::QS + (t & 3) * ChainSmem<T>::P4 + (t >> 2)];
+    const float2* xo = &sm.r[q * ChainSmem<T>::QS + ((t + 2) & 3) * ChainSmem<T>::P4 + ((t + 2) >> 2)];
+    const int npair = nk >> 1;
+#pragma unroll 4
+    for (int m = 0; m < npair; ++m) {
+      acc(sm.e[2 * m], xe[m]);
+      acc(sm.e[2 * m + 1], xo[m]);
     }
+    if (nk & 1) acc(sm.e[nk - 1], xe[npair]);
     float4 w = sm.w[q][t];
     w.x -= step * g0x;
     w.y -= step * g0y;
