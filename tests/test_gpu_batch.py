@@ -1,19 +1,23 @@
 """Batched pushes of many dual-polarisation streams (rx_batch_*): one
-launch per stage and frame ordinal over every stream's frames gives the
-bits and counters of the same blocks pushed stream by stream, exactly.
+launch per stage and frame ordinal over every stream's frames gives what
+the same blocks pushed stream by stream give.
 
 The batched kernels inline the same stage bodies into other kernels, and
 the compiler may fuse a different multiply into an FMA there, so soft
-values (equalised symbols, EVM) agree to FP32 rounding rather than bit for
-bit: both paths are deterministic, and 1-ulp differences in the CD output
-show up downstream as differences of order 1e-6 of the unit-power
-symbols.  The bound used, 1e-4, leaves room for the adaptive equaliser to
-carry such differences over a few frames."""
+values agree to FP32 rounding rather than bit for bit: both paths are
+deterministic, and 1-ulp differences in the CD output show up downstream as
+differences of order 1e-6 of the unit-power symbols (bound used: 1e-4,
+room for the adaptive equaliser to carry them over a few frames).  A
+decision within rounding of a threshold (or a BPS near-tie) can then come
+out differently, so the bits of both runs are held to the oracle parity
+rules on the same samples (identical except near a threshold or at a
+near-tie); frame, sync and slip counters must be equal."""
 import numpy as np
 import pytest
 
 import rxsim
 from paper_2108_07001_gb300 import rx
+from parity_util import compare, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -67,7 +71,17 @@ def cases():
 def results(r, n_sym):
     buf = np.empty(1 << 22, dtype=np.uint8)
     nb = r.pull_bytes(buf, timeout_ms=-1)
-    return buf[:(nb + 7) // 8].copy(), nb, r.equalised(0, n_sym), r.stats()
+    bhat, m = r.phase(0, n_sym)
+    return buf[:(nb + 7) // 8].copy(), nb, r.equalised(0, n_sym), r.stats(), \
+        {"bhat": bhat, "m": m, "trace": r.frame_trace()}
+
+
+def oracle_input(x, cfg):
+    """The samples as the receiver stores them (FP16 storage: rounded to
+    half precision, as the parity tests feed the oracle)."""
+    if cfg.get("storage_dtype") == rx.RX_C16:
+        return np.stack([x.real, x.imag], axis=-1).astype(np.float16)
+    return x
 
 
 def plain(cases):
@@ -124,16 +138,23 @@ def test_batch_equals_plain_pushes(cases):
         r.close()
     frames = 0
     for k, (a, b) in enumerate(zip(want, got)):
-        bits0, n0, y0, s0 = a
-        bits1, n1, y1, s1 = b
+        bits0, n0, y0, s0, _ = a
+        bits1, n1, y1, s1, _ = b
         assert n0 == n1 > 0, KINDS[k]
-        assert np.array_equal(bits0, bits1), KINDS[k]
         assert np.abs(y0 - y1).max() <= 1e-4, KINDS[k]
-        for f in ("bits", "bit_errors", "cycle_slips", "synced", "frames"):
+        for f in ("bits", "cycle_slips", "synced", "frames", "sync_delay", "sync_perm"):
             assert s0[f] == s1[f], (KINDS[k], f)
+        nd = int(np.count_nonzero(np.unpackbits(bits0) != np.unpackbits(bits1)))
+        assert abs(s0["bit_errors"] - s1["bit_errors"]) <= nd, KINDS[k]
         assert s1["synced"] == 1 and s1["ber"] < 1e-2, KINDS[k]
         assert s1["evm"] == pytest.approx(s0["evm"], rel=1e-4)
         frames += s1["frames"]
+        if nd:  # every differing decision is explained under the oracle's rules, in both runs
+            cfg, blocks, n_sym = cases[k]
+            ocfg = {key: v for key, v in cfg.items() if key != "history_syms"}
+            ref = run_oracle(oracle_input(np.concatenate(blocks, axis=1), cfg), ocfg)
+            for bits, nb, y, _, ph in (a, b):
+                compare(dict(ph, y=y, bits=np.unpackbits(bits)[:nb]), ref, ocfg)
     assert 0 < info["frames"] <= frames
     assert info["calls"] == n_rounds + 1
     assert info["launches"] > 0
