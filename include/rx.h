@@ -185,9 +185,11 @@ int rx_stats(rx_handle* h, rx_stats_t* out);
  * The ingest runs on cuda_stream; the stages run on the batch's own four
  * streams (front: CD and estimators, mid: acquisition and MIMO, back: BPS
  * and demap, BER), pipelined over ordinals and calls with the buffer-reuse
- * waits of the plain path, so every stream's bits and counters are those
- * of the same blocks pushed with rx_push_block (soft values agree to FP32
- * rounding).  The arguments of a call are one page-locked table copied to
+ * waits of the plain path, so every stream gets what the same blocks
+ * pushed with rx_push_block give: the same frames, sync and slips, soft
+ * values equal to FP32 rounding (the batched kernels are compiled
+ * separately), and so the same bits except where a decision lies within
+ * that rounding of a threshold.  The arguments of a call are one page-locked table copied to
  * the device once (four tables rotate: a call waits on the host for the
  * call four back to finish).
  *
