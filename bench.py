@@ -231,9 +231,12 @@ def run_ours(args):
     value = samples_step / (ms_step * 1e-3) / 1e9
     gbps = bits_step / (ms_step * 1e-3) / 1e9
 
-    # roofline of the dominant stage (live stage timings of the timed steps)
+    # roofline of the dominant stage (live stage timings of the timed steps);
+    # the FP32 peak is measured on this GPU (scalar and packed-pair FMA)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
+    fma_tf, fma2_tf = rx.fp32_peak(0)
+    alu_peak = max(fma_tf, fma2_tf) or FP32_PEAK_TFLOPS
     work = stage_work(wl, n_sym)
     stages = {}
     for k in ("cd", "mimo", "bps"):
@@ -246,7 +249,7 @@ def run_ours(args):
             unit = "GB/s"
         else:
             ach = w / sec / 1e12
-            peak = FP32_PEAK_TFLOPS
+            peak = alu_peak
             unit = "TFLOP/s"
         stages[k] = {"bound": bound, "achieved": round(ach, 2), "peak": round(peak, 1), "unit": unit,
                      "frac": round(ach / peak, 4), "ms_per_step": round(ms / args.steps, 3),
@@ -260,7 +263,14 @@ def run_ours(args):
         roof["traffic_unit"] = "bytes per launch (ncu dram read+write, profiles/traffic.txt)"
     roof.pop("launches_per_step", None)
     roof["peak_source"] = ("measured MEASURED_PEAKS.json hbm_gbs" if roof["bound"] == "hbm" and hbm_peak
-                           else "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz")
+                           else f"measured on this GPU by rx_fp32_peak: {fma_tf:.1f} TFLOP/s fma.rn.f32, "
+                                f"{fma2_tf:.1f} fma.rn.f32x2 (the larger is the peak; derived nominal "
+                                f"{FP32_PEAK_TFLOPS:.1f}: 152 SMs x 128 lanes x 2 flops x 2070 MHz)")
+    if roof["traffic"] is not None:  # DRAM bytes of one launch over its live duration
+        launch_s = roof["ms_per_step"] * 1e-3 / stages[dom]["launches_per_step"]
+        roof["dram_gbs"] = round(roof["traffic"] / launch_s / 1e9, 1)
+        if hbm_peak:
+            roof["dram_frac_of_hbm"] = round(roof["dram_gbs"] / hbm_peak, 4)
     gpu_launches = int(sum(v[1] for v in stage_tot.values()))
 
     # e2e: the same stream from pinned host memory (taken in stream order

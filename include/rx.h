@@ -309,6 +309,14 @@ int rx_decide_block_noalloc(const void* y, int64_t n, int modulation, int bps_an
  * or when no N is admissible. */
 int rx_autotune_fft(const rx_config* cfg, int frames, int* fft_n, double* ms_per_msample);
 
+/* FP32 arithmetic peak of device, measured (the denominator of the ALU
+ * rooflines): every SM filled with 2048 threads running eight independent
+ * FMA chains, best of six timed launches, in TFLOP/s for the scalar form
+ * (fma.rn.f32) in *tflops_fma and the packed-pair form (fma.rn.f32x2, two
+ * FMAs per instruction) in *tflops_fma2.  RX_EINVAL (null pointer),
+ * RX_EDEVICE. */
+int rx_fp32_peak(int device, double* tflops_fma, double* tflops_fma2);
+
 /* ---- serving: many channel streams on one GPU ---------------------------
  * The paper runs several CUDA streams so that buffers are processed
  * concurrently (Sec. II); a server extends this to many independent channel

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librx.so")
-SOURCES = ["k_cd.cu", "k_mimo.cu", "k_bps.cu", "k_bps2.cu", "k_ber.cu", "k_noalloc.cu", "rx_runtime.cu", "rx_batch.cu",
+SOURCES = ["k_peak.cu", "k_cd.cu", "k_mimo.cu", "k_bps.cu", "k_bps2.cu", "k_ber.cu", "k_noalloc.cu", "rx_runtime.cu", "rx_batch.cu",
            "rx_server.cu", "rx_tune.cu", "k_kk.cu", "rx_kk.cu", "k_kkrx.cu", "rx_kkrx.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

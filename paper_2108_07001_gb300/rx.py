@@ -35,7 +35,7 @@ EXPORTS = ["rx_config_default", "rx_create", "rx_push_block", "rx_pull_bits", "r
            "rx_server_config_default", "rx_server_create", "rx_server_open", "rx_server_submit",
            "rx_server_end", "rx_server_sync", "rx_server_pull_bits", "rx_server_stream_stats",
            "rx_server_handle", "rx_server_close", "rx_server_stats", "rx_server_destroy",
-           "rx_autotune_fft",
+           "rx_autotune_fft", "rx_fp32_peak",
            "rx_kk_config_default", "rx_kk_create", "rx_kk_push", "rx_kk_end", "rx_kk_reset",
            "rx_kk_position", "rx_kk_destroy", "rx_kk_batch_create", "rx_kk_batch_push", "rx_kk_batch_destroy",
            "rx_kkrx_config_default", "rx_kkrx_create", "rx_kkrx_push", "rx_kkrx_end", "rx_kkrx_equalised",
@@ -242,6 +242,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                        ctypes.POINTER(SZ), P]
     lib.rx_kkrx_batch_destroy.argtypes = [P]
     lib.rx_kkrx_batch_destroy.restype = None
+    lib.rx_fp32_peak.argtypes = [I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.rx_batch_create.argtypes = [ctypes.POINTER(P), I, ctypes.POINTER(P)]
     lib.rx_batch_push.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(SZ), I, I, P]
     lib.rx_batch_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64),
@@ -257,7 +258,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                  "rx_kk_batch_create", "rx_kk_batch_push",
                  "rx_kkrx_create", "rx_kkrx_push", "rx_kkrx_end", "rx_kkrx_equalised", "rx_kkrx_reset",
                  "rx_kkrx_batch_create", "rx_kkrx_batch_push", "rx_batch_create", "rx_batch_push",
-                 "rx_batch_info"]:
+                 "rx_batch_info", "rx_fp32_peak"]:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -568,6 +569,14 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def fp32_peak(device: int = 0) -> tuple[float, float]:
+    """Measured FP32 peak of the device in TFLOP/s: (fma.rn.f32 form,
+    fma.rn.f32x2 form)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().rx_fp32_peak(device, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def autotune_fft(cfg: RxConfig | None = None, frames: int = 3, **overrides) -> tuple[int, float]:

@@ -22,7 +22,7 @@ def lib():
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(rx_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(rx_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -295,3 +295,8 @@ def test_batch_argument_checks_without_device(lib):
     assert lib.rx_batch_push(None, None, None, rx.RX_C64, 1, None) == rx.RX_EINVAL
     assert lib.rx_batch_info(None, None, None, None, None) == rx.RX_EINVAL
     lib.rx_batch_destroy(None)  # no-op
+
+
+def test_fp32_peak_argument_checks_without_device(lib):
+    from paper_2108_07001_gb300 import rx
+    assert lib.rx_fp32_peak(0, None, None) == rx.RX_EINVAL
