@@ -180,3 +180,31 @@ def test_refused_batch_push_changes_nothing(cases):
     assert a[1] == b[1] and np.array_equal(a[0], b[0])
     r0.close()
     r1.close()
+
+
+def test_batch_from_page_locked_host_memory_equals_device_memory(cases):
+    """Blocks in page-locked host memory, read by the batched ingest
+    through the device mapping (on_device = 2), give bit for bit what the
+    same blocks in device memory give (the same batched kernels)."""
+    import torch
+    s = torch.cuda.current_stream().cuda_stream
+    sel = [cases[0], cases[2]]
+    out = []
+    for mode in ("device", "pinned"):
+        recs = [rx.Receiver(**cfg) for cfg, _, _ in sel]
+        keep = [[torch.from_numpy(b).cuda() if mode == "device" else torch.from_numpy(b).pin_memory()
+                 for b in blocks if b.shape[1]] for _, blocks, _ in sel]
+        dummy = keep[0][0]
+        with rx.Batch(recs) as batch:
+            for j in range(max(len(k) for k in keep)):
+                ptrs = [k[j].data_ptr() if j < len(k) else dummy.data_ptr() for k in keep]
+                ns = [k[j].shape[1] if j < len(k) else 0 for k in keep]
+                batch.push(ptrs, ns, rx.RX_C64, s, on_device=1 if mode == "device" else 2)
+            batch.end(s)
+        out.append([results(r, n_sym)[:3] for r, (_, _, n_sym) in zip(recs, sel)])
+        for r in recs:
+            r.close()
+    for (b0, n0, y0), (b1, n1, y1) in zip(out[0], out[1]):
+        assert n0 == n1 > 0
+        assert np.array_equal(b0, b1)
+        assert np.array_equal(y0, y1)
