@@ -554,6 +554,12 @@ void rx_batch_destroy(rx_batch* b) {
     bool mine = false;
     for (cudaEvent_t e : b->ev_ring) mine |= h->batch_done == e;
     if (mine) h->batch_done = nullptr;
+    // the batch's streams go away: the stream's work is complete, so its
+    // next plain push starts from the legacy stream with nothing to join
+    if (h->last_cs == b->s_stage[3]) {
+      h->last_cs = nullptr;
+      h->copy_dirty = false;
+    }
   }
   batch_free(b);
   delete b;

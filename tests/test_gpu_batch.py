@@ -208,3 +208,29 @@ def test_batch_from_page_locked_host_memory_equals_device_memory(cases):
         assert n0 == n1 > 0
         assert np.array_equal(b0, b1)
         assert np.array_equal(y0, y1)
+
+
+def test_plain_pushes_after_the_batch_is_destroyed(cases):
+    """Streams pushed through a batch, then (after rx_batch_destroy) through
+    their own calls, give what plain pushes throughout give: the plain path
+    no longer refers to the batch's streams."""
+    import torch
+    s = torch.cuda.current_stream().cuda_stream
+    sel = [cases[0], cases[3]]
+    want = plain(sel)
+    recs = [rx.Receiver(**cfg) for cfg, _, _ in sel]
+    dev = [[torch.from_numpy(b).cuda() for b in blocks if b.shape[1]] for _, blocks, _ in sel]
+    with rx.Batch(recs) as batch:
+        batch.push([d[0].data_ptr() for d in dev], [d[0].shape[1] for d in dev], rx.RX_C64, s)
+    for r, d in zip(recs, dev):  # the batch is gone
+        for t in d[1:]:
+            r.push_device(t.data_ptr(), t.shape[1], rx.RX_C64, s)
+        r.end()
+    got = [results(r, n_sym) for r, (_, _, n_sym) in zip(recs, sel)]
+    for r in recs:
+        r.close()
+    for (b0, n0, y0, s0, _), (b1, n1, y1, s1, _) in zip(want, got):
+        assert n0 == n1 > 0
+        assert np.abs(y0 - y1).max() <= 1e-4
+        for f in ("frames", "synced", "cycle_slips"):
+            assert s0[f] == s1[f], f
