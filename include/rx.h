@@ -284,6 +284,7 @@ int rx_get_phase(rx_handle* h, int64_t first, int64_t n, uint8_t* bhat, int32_t*
  * all working memory is one static device array of about 1.4 MB that every
  * device which loads the library holds until the process exits.
  *   n                 1 .. RX_NOALLOC_MAX_SYMS, else RX_EINVAL
+ *   y                 8-byte aligned (a complex float), else RX_EINVAL
  *   modulation        RX_QPSK or RX_QAM16; bps_angles 32 or 64;
  *   bps_half_window   8, 12, 16, 24 or 32
  * The first call on a device (the device current at the call) looks up

@@ -14,8 +14,9 @@ time-domain equaliser followed by decisions and demapping (Sec. II), and
 BER-derived Q-factor (Sec. III).  It is silent on polarisation
 demultiplexing, CMA, frequency-offset and timing recovery and blind phase
 search; for those the oracle writes out the textbook definition of each
-estimator and the schedule fixed for this receiver, and the readings are
-listed in the design notes.
+estimator and the schedule fixed for this receiver; where the paper is
+silent, the reading taken is stated in the docstring of the function that
+takes it.
 
 Parity status per function is given in ``rx_oracle.PIN_STATUS``.
 """

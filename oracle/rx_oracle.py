@@ -60,7 +60,12 @@ PIN_STATUS = {
     "unwrap_increments": "pinned: phase ramp across quadrants tracked without slips",
     "decide/demap": "pinned: exhaustive constellation round trip, Gray neighbour property",
     "prbs31_bits": "pinned: independent generator agreement, recurrence, balance",
-    "ber_count": "pinned: AWGN BER inside the 99% Clopper-Pearson interval of the Q-function",
+    "ber_count": "pinned: AWGN BER inside the 99% Clopper-Pearson interval of the Q-function; "
+                 "quarter-turn carrier steps counted as slips with hand-counted errors",
+    "cma_radius": "pinned: QPSK 1 and 16QAM 1.32 from the constellation's moduli by hand",
+    "acquire": "pinned: CMA inverts a known unitary (QPSK and 16QAM, < -30 dB) with unit output power",
+    "dd_phase": "pinned: constant phase of the whole constellation recovered to 1e-12, quarter turns ignored",
+    "q_factor_db": "pinned: BER = Q(x) of a Gaussian tail gives 20 log10(x) to 1e-9",
 }
 
 

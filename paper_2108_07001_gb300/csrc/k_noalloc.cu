@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 
@@ -80,6 +81,10 @@ extern "C" int rx_decide_block_noalloc(const void* y, int64_t n, int modulation,
                                        int bps_half_window, uint8_t* bits, void* cuda_stream) {
   if (!y || !bits || n < 1) {
     set_last_error("rx_decide_block_noalloc: null buffer or empty block");
+    return RX_EINVAL;
+  }
+  if (reinterpret_cast<uintptr_t>(y) % alignof(float2) != 0) {
+    set_last_error("rx_decide_block_noalloc: y must be aligned to 8 bytes (complex float)");
     return RX_EINVAL;
   }
   if (n > kMaxSyms) {

@@ -37,6 +37,8 @@ def test_config0_parity(stride):
     assert abs(int(st["bit_errors"]) - b["errors"]) <= 2 * rep.get("bit_mismatch_syms", 0) * 2 + 2
     assert st["cycle_slips"] == b["slips"]
     assert abs(st["evm"] - b["evm"]) <= 1e-3 * b["evm"] + 1e-6
+    from oracle import rx_oracle as O
+    assert abs(st["q_db"] - O.q_factor_db(st["ber"])) < 1e-9
     tr = gpu["trace"]
     assert abs(tr[0, 0] - ref["trace"]["tau"][0]) * 28e9 < 1e-4
     assert abs(tr[0, 1] - ref["trace"]["dfo"][0]) < 1e3
@@ -295,3 +297,56 @@ def test_pinned_host_push_equals_device_push():
     for k in (1, 2):
         assert np.array_equal(out[0][0], out[k][0])
         assert np.array_equal(out[0][1], out[k][1])
+
+
+# ------------------------------------------------- the bench's own workload ---
+
+def test_headline_stream_parity_two_frames():
+    """The bench workload's receiver exactly as the bench runs it (28 GBd,
+    10,000 km: N = 16384 by the default rule, frames of 2^20 symbols,
+    512-symbol segment chains, complex64 pushes of 2^16 symbols) on the
+    first 2^21 symbols per polarisation of the bench's own samples: two
+    frames, so the second frame's segment chains, overlap, FO phase and
+    timing continue from the first.  Equalised symbols, BPS angles and bits
+    follow the parity rules; the BER counters, sync and slips equal the
+    oracle's on the same samples."""
+    from oracle import rx_oracle as O
+    wl = workloads.DP_QPSK_10000KM_STREAM
+    n_sym = 1 << 21
+    x = rxsim.simulate(link(**wl["link"]))["rx"][:, :2 * n_sym]
+    rx_kw = dict(wl["rx"])
+    assert O.geometry(O.RxConfig(**workloads.oracle_kwargs(rx_kw))).N == 16384
+    m = 2 * wl["push_syms"]
+    gpu, r = run_gpu(x, rx_kw, pushes=[m] * (2 * n_sym // m))
+    ref = run_oracle(x, rx_kw)
+    rep = compare(gpu, ref, rx_kw)
+    st, b = gpu["stats"], ref["ber"]
+    assert st["frames"] == 2 and len(ref["trace"]["tau"]) == 2
+    assert st["synced"] == 1
+    assert (st["sync_delay"], st["sync_perm"]) == (b["sync"]["delay"], b["sync"]["perm"])
+    assert [st["sync_quadrant_x"], st["sync_quadrant_y"]] == [int(q) for q in b["sync"]["quadrant"]]
+    assert st["bits"] == b["bits"]
+    assert abs(int(st["bit_errors"]) - b["errors"]) <= 2 * rep.get("bit_mismatch_syms", 0)
+    assert st["cycle_slips"] == b["slips"]
+    assert abs(st["q_db"] - O.q_factor_db(st["ber"])) < 1e-9
+    tr = gpu["trace"]
+    assert np.allclose(tr[:, 0], ref["trace"]["tau"], atol=1e-4 / 28e9)
+    assert np.allclose(tr[:, 2], ref["trace"]["gain"], rtol=1e-5)
+    r.close()
+
+
+def test_64gbd_10000km_parity():
+    """64 GBd over 10,000 km: a CD halo of ~12k samples in a 16384-point
+    block, the largest halo fraction the overlap-save kernel meets; two
+    frames of 2^17 symbols pushed in 2^16-symbol blocks."""
+    n_sym = 1 << 18
+    sim = rxsim.simulate(link(baud_hz=64e9, n_sym=n_sym, fiber_len_m=10000e3, snr_db=12.0, prbs_seed=64,
+                              seed=6400, out_dtype="c64"))
+    rx_kw = dict(baud_hz=64e9, fiber_len_m=10000e3, frame_syms=1 << 17, prbs_seed=64)
+    gpu, r = run_gpu(sim["rx"], rx_kw, pushes=[1 << 17] * (2 * n_sym >> 17))
+    ref = run_oracle(sim["rx"], rx_kw)
+    rep = compare(gpu, ref, rx_kw)
+    st, b = gpu["stats"], ref["ber"]
+    assert st["bits"] == b["bits"] and st["cycle_slips"] == b["slips"]
+    assert abs(int(st["bit_errors"]) - b["errors"]) <= 2 * rep.get("bit_mismatch_syms", 0)
+    r.close()

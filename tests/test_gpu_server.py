@@ -6,6 +6,7 @@ import pytest
 
 import rxsim
 from paper_2108_07001_gb300 import rx
+from parity_util import compare, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -63,8 +64,10 @@ def serve(cases, interleave=True):
             srv.sync(sids[k], timeout_ms=120000)
         for k, (cfg, _, n_sym) in cases.items():
             bits, nb = srv.pull_bytes(sids[k])
-            y = srv.receiver(sids[k]).equalised(0, n_sym)
-            out[k] = (bits, nb, y, srv.stream_stats(sids[k]))
+            rcv = srv.receiver(sids[k])
+            y = rcv.equalised(0, n_sym)
+            bhat, m = rcv.phase(0, n_sym)
+            out[k] = (bits, nb, y, srv.stream_stats(sids[k]), {"bhat": bhat, "m": m, "trace": rcv.frame_trace()})
         sst = srv.stats()
     return out, sst
 
@@ -86,8 +89,8 @@ def test_each_stream_alone_equals_the_mix(cases, mixed):
     mix, _ = mixed
     for k in CASES:
         alone, _ = serve({k: cases[k]})
-        b0, n0, y0, s0 = alone[k]
-        b1, n1, y1, s1 = mix[k]
+        b0, n0, y0, s0, _ = alone[k]
+        b1, n1, y1, s1, _ = mix[k]
         assert n0 == n1 > 0
         assert np.array_equal(b0, b1), k
         assert np.array_equal(y0, y1), k
@@ -109,11 +112,26 @@ def test_served_stream_equals_a_plain_receiver(cases, mixed):
     y = r.equalised(0, n_sym)
     st = r.stats()
     r.close()
-    b1, n1, y1, s1 = mix[k]
+    b1, n1, y1, s1, _ = mix[k]
     assert nb == n1
     assert np.array_equal(bits, b1)
     assert np.array_equal(y, y1)
     assert st["bit_errors"] == s1["bit_errors"] and st["bits"] == s1["bits"]
+
+
+def test_served_streams_match_the_oracle(cases, mixed):
+    """Every stream served in the mix against the FP64 oracle on the same
+    samples, under the parity rules of the single-stream tests (equalised
+    symbols, BPS angles, bits, BER counters)."""
+    mix, _ = mixed
+    for k in CASES:
+        cfg, blocks, n_sym = cases[k]
+        ocfg = {key: v for key, v in cfg.items() if key != "history_syms"}
+        ref = run_oracle(np.concatenate(blocks, axis=1), ocfg)
+        bits, nb, y, st, ph = mix[k]
+        rep = compare(dict(ph, y=y, bits=np.unpackbits(bits)[:nb]), ref, ocfg)
+        assert st["bits"] == ref["ber"]["bits"] and st["cycle_slips"] == ref["ber"]["slips"], k
+        assert abs(int(st["bit_errors"]) - ref["ber"]["errors"]) <= 2 * rep.get("bit_mismatch_syms", 0), k
 
 
 def test_server_statistics(cases, mixed):

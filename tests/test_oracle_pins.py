@@ -188,6 +188,63 @@ def test_cma_converges_to_inverse_rotation():
         assert 10 * math.log10(ratio) < -30
 
 
+def test_cma_radius_values():
+    """R2 = E|s|^4 / E|s|^2 at unit power, evaluated by hand: QPSK points all
+    have |s|^2 = 1, so R2 = 1; 16QAM has |s|^2 = 2/10, 10/10, 18/10 on 4, 8
+    and 4 points, E|s|^4 = (4*0.04 + 8*1 + 4*3.24)/16 = 1.32."""
+    assert O.cma_radius(2) == pytest.approx(1.0, abs=1e-15)
+    assert O.cma_radius(4) == pytest.approx(1.32, abs=1e-14)
+
+
+def test_cma_converges_to_inverse_rotation_16qam():
+    """Noiseless DP-16QAM, no CD or offsets: CMA with R2 = 1.32 over 2^16
+    symbols turns the FIR's DC response times a Haar unitary into a diagonal
+    or anti-diagonal matrix (cross terms below -30 dB), and the converged
+    outputs have unit power (E|y|^4 = R2 E|y|^2 holds at unit scale only for
+    the right radius)."""
+    n = 1 << 16
+    for seed in (11, 12, 13):
+        sim = rxsim.simulate(quiet_link(fiber_len_m=0.0, rotate=True, seed=seed, n_sym=n, bits_per_sym=4,
+                                        baud_hz=32e9))
+        cfg = O.RxConfig(fiber_len_m=0.0, frame_syms=n, bits_per_sym=4, baud_hz=32e9, mimo_taps=25,
+                         bps_angles=32, bps_half_window=32, mu_cma=5e-3, cma_syms=n, acq_syms=n)
+        rx = O.Receiver(cfg)
+        g = rx.g
+        x = sim["rx"]
+        ns = x.shape[1]
+        z, acc = rx._cd_frame(x, ns, -g.c, ns + g.c, 0.0, 0, ns, True)
+        r = z / math.sqrt(acc["P"] / (2.0 * ns))
+        w, _ = O.acquire(r, n, cfg)
+        M = w.sum(axis=2) @ sim["U"]
+        p = np.abs(M) ** 2
+        ratio = min((p[0, 1] + p[1, 0]) / (p[0, 0] + p[1, 1]), (p[0, 0] + p[1, 1]) / (p[0, 1] + p[1, 0]))
+        assert 10 * math.log10(ratio) < -30, (seed, 10 * math.log10(ratio))
+        y, _ = O.mimo_fir(w, r, n - 4096, n - 64)
+        assert abs(np.mean(np.abs(y) ** 2) - 1.0) < 0.05
+
+
+@pytest.mark.parametrize("bps_", [2, 4])
+def test_dd_phase_recovers_a_constant_phase(bps_):
+    """The 4th-power block phase of the whole constellation (every point
+    once, so the odd terms of s^4 cancel) turned by theta in (-pi/4, pi/4)
+    is theta; a further quarter turn of the symbols gives theta again."""
+    n = 1 << bps_
+    bits = np.array([[(v >> (bps_ - 1 - i)) & 1 for i in range(bps_)] for v in range(n)],
+                    dtype=np.uint8).ravel()
+    s = rxsim.gray_map(bits, bps_)
+    for theta in (-0.78, -0.3, 0.0, 0.1234, 0.5, 0.78):
+        for quarter in (0, 1, -1, 2):
+            y = s * np.exp(1j * (theta + quarter * math.pi / 2))
+            assert abs(O.dd_phase(y) - theta) < 1e-12, (theta, quarter)
+
+
+@pytest.mark.parametrize("x", [2.0, 3.0, 4.5])
+def test_q_factor_of_a_gaussian_tail(x):
+    """For BER = Q(x) = erfc(x / sqrt 2) / 2 (the Gaussian tail), the
+    Q-factor is x itself: 20 log10(x) dB."""
+    assert abs(O.q_factor_db(Q(x)) - 20.0 * math.log10(x)) < 1e-9
+
+
 # ------------------------------------------------------- a6 BPS, a7 ---
 
 @pytest.mark.parametrize("bps_", [2, 4])
