@@ -63,7 +63,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -80,17 +80,24 @@ class ClockSampler:
             time.sleep(0.01)
 
     def stop(self, t0=None, t1=None):
-        """Summary of the samples taken in [t0, t1] (host perf_counter
-        times); when the window is shorter than the sampling period, the
-        samples within one period of it."""
+        """Stops sampling after a short grace period; summary of [t0, t1]."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = [(t, r) for t, r in self.rows if len(r) >= 7]
+        return self.summary(t0, t1)
+
+    def summary(self, t0=None, t1=None):
+        """Summary of the samples taken in [t0, t1] (host perf_counter
+        times); when the window is shorter than the sampling period, the
+        samples within one period of it."""
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = [(t, r) for t, r in list(self.rows) if len(r) >= 7]
         if t0 is not None:
             inside = [r for t, r in rows if t0 <= t <= t1]
             rows = inside or [r for t, r in rows if t0 - 0.15 <= t <= t1 + 0.15]
@@ -147,8 +154,10 @@ def stage_work(wl, n_sym):
         "cd": ("hbm", samples * 16.0),
         # FIR (2 outputs x 2 inputs x T complex MACs) + gradient (same), 8 flops per CMAC
         "mimo": ("alu", n_sym * 2 * (4 * T) * 8.0),
-        # per symbol, polarisation and searched angle: rotation 6, |Re|+|Im| 1, window add/sub 2
-        "bps": ("alu", n_sym * 2 * B * 9.0),
+        # per symbol, polarisation and searched angle: 7.5 flops (the count of the
+        # blind phase search's arithmetic: rotation, distance to the nearest
+        # point, sliding-window update)
+        "bps": ("alu", n_sym * 2 * B * 7.5),
     }
 
 
@@ -225,11 +234,15 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk.wait_first()
     total_ms, host0, host1 = timed(r, args.steps)
-    clocks = clk.stop(host0, time.perf_counter())
+    host_t1 = time.perf_counter()
     stats = r.stats()
     before = rp.stage_times()
     prof_ms, _, _ = timed(rp, args.steps)
     after = rp.stage_times()
+    # the timed region, and (more samples) the timed and the profiled passes
+    # of the same steps together
+    clocks = clk.stop(host0, host_t1)
+    clocks["both_passes"] = clk.summary(host0, time.perf_counter())
     stage_tot = {k: [after[k][0] - before[k][0], after[k][1] - before[k][1]] for k in rx.STAGES}
     rp.close()
     ms_step = total_ms / args.steps
@@ -348,6 +361,7 @@ def run_ours(args):
 def finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, other_ms,
            gpu_launches, clocks, host0, host1, gen_s, e2e):
     cpu = cpu_baseline(args.bps_coarse_stride) if args.cpu_baseline else None
+    batched = batched_fp16_summary(measured_peaks().get("hbm_gbs")) if args.batched else None
     line = {
         "metric": "gsamples_per_s", "value": round(value, 3), "unit": "Gsamples/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
@@ -369,6 +383,7 @@ def finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, o
         "roofline": roof, "stages": stages, "other_stage_ms": other_ms,
         "stage_timing": "per-stage CUDA events on a second, profiled handle over the same timed protocol",
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
+        "batched_fp16": batched,
         "host_launch_s_per_step": round((host1 - host0) / args.steps, 4), "sim_seconds": round(gen_s, 1),
     }
     r.close()
@@ -439,9 +454,10 @@ CPU_BASELINE_SYMS = 1 << 20  # one full frame, acquisition included (10-30 s of 
 def cpu_baseline(stride=1):
     t = oracle_times(CPU_BASELINE_SYMS, 1, stride)[0]
     v = 4 * CPU_BASELINE_SYMS / t / 1e9
-    return {"value": round(v, 6), "unit": "Gsamples/s", "cores": 1, "kind": "oracle",
+    return {"value": round(v, 6), "unit": "Gsamples/s", "cores": 1, "host_cores": os.cpu_count(),
+            "kind": "oracle",
             "sample": f"first {CPU_BASELINE_SYMS} symbols/pol of the workload (one whole frame incl. "
-                      f"acquisition), FP64 numpy oracle, one thread, {t:.1f} s"}
+                      f"acquisition), FP64 numpy oracle, one thread of the host's {os.cpu_count()}, {t:.1f} s"}
 
 
 REFERENCE_STEP_SYMS = 1 << 18
@@ -458,8 +474,10 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded link simulator)",
             "config": {"workload": wl["name"], "sample_symbols_per_pol": n_sym},
-            "cpu_baseline": {"value": round(v, 6), "unit": "Gsamples/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {n_sym} symbols/pol of the workload per step, one thread"},
+            "cpu_baseline": {"value": round(v, 6), "unit": "Gsamples/s", "cores": 1, "host_cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"first {n_sym} symbols/pol of the workload per step, one thread of the "
+                                       f"host's {os.cpu_count()}"},
             "e2e": {"value": round(v, 6), "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -1026,8 +1044,8 @@ def run_serving(args):
     bits_per_pass = sum(2 * rxc["modulation"] * n_sym for _, rxc, _ in streams)
     order = [(i, j) for j in range(max(len(b) for b in data)) for i in range(len(streams)) if j < len(data[i])]
 
-    def one_pass(storage, arrivals):
-        with rx.Server(max_streams=64) as srv:
+    def one_pass(storage, arrivals, batch=0):
+        with rx.Server(max_streams=64, batch=batch) as srv:
             sids = [srv.open(**dict(rxc, storage_dtype=storage)) for _, rxc, _ in streams]
             t_start = time.perf_counter()
             for k, (i, j) in enumerate(order):
@@ -1046,16 +1064,17 @@ def run_serving(args):
         return wall, st, ber
 
     forms = {}
-    for form, storage in (("fp32_storage", rx.RX_C64), ("fp16_storage", rx.RX_C16)):
-        one_pass(storage, None)  # warm-up
-        wall, st, ber = one_pass(storage, None)
+    for form, storage, batch in (("fp32_storage", rx.RX_C64, 0), ("fp16_storage", rx.RX_C16, 0),
+                                 ("batched_fp32_storage", rx.RX_C64, 1), ("batched_fp16_storage", rx.RX_C16, 1)):
+        one_pass(storage, None, batch)  # warm-up
+        wall, st, ber = one_pass(storage, None, batch)
         cap = total_samples / wall / 1e9
         rate = 0.8 * cap * 1e9  # samples/s offered
         rng = np.random.default_rng(7)
         sizes = [4 * streams[i][2][j] for i, j in order]
         gaps = rng.exponential(np.asarray(sizes, dtype=np.float64) / rate)
         arrivals = np.cumsum(gaps) - gaps[0]
-        wall_l, st_l, ber_l = one_pass(storage, arrivals)
+        wall_l, st_l, ber_l = one_pass(storage, arrivals, batch)
         forms[form] = {
             "capacity_gsamples_s": round(cap, 3),
             "offered_gsamples_s": round(0.8 * cap, 3),
@@ -1068,8 +1087,10 @@ def run_serving(args):
             "ber_max": max(b["ber"] for b in ber_l), "cycle_slips": int(sum(b["cycle_slips"] for b in ber_l)),
             "synced_streams": int(sum(b["synced"] for b in ber_l)),
             "mem_gib": round(st_l["mem_in_use_bytes"] / 2 ** 30, 2) if st_l["mem_in_use_bytes"] else None,
+            "batch_calls": st_l["batch_calls"],
         }
-    return {"metric": "gsamples_per_s", "value": forms["fp16_storage"]["sustained_gsamples_s"], "unit": "Gsamples/s",
+    return {"metric": "gsamples_per_s", "value": forms["batched_fp16_storage"]["sustained_gsamples_s"],
+            "value_form": "batched_fp16_storage", "unit": "Gsamples/s",
             "n_gpus": 1, "higher_is_better": True, "workload": "serving", "dtype": "f32 arithmetic",
             "data": "synthetic (seeded link simulator)",
             "config": {"streams": len(streams), "symbols_per_pol_per_stream": n_sym,
@@ -1109,28 +1130,15 @@ def batched_streams(n_streams, n_sym):
     return out
 
 
-def run_batched(args, rank=0, world=1, barrier=None):
-    """64 independent streams with uneven capture blocks, every block
-    submitted at once: through the serving layer (throughput and frame
-    latency with the FFT size of the default rule (N >= 4 halo), with the
-    size the autotuner picks per stream, and the latter with FP16 sample
-    storage) and through one rx_batch (round j pushes every stream's j-th
-    block in one call: one launch per stage and frame ordinal, pipelined
-    over the batch's four streams); beside them the plain per-stream chain
-    (one stream at a time).  The value is the fastest form."""
+def load_batched_streams(n_sym, dev, subset=None):
+    """The 64 streams of batched_streams (or the listed subset) simulated
+    and split into their capture blocks, resident on the device."""
     import torch
     import rxsim
-    from paper_2108_07001_gb300 import rx
-    dev = torch.device("cuda:0")
-    torch.cuda.set_device(dev)
-    n_sym = args.symbols or BATCH_SYMS
     streams = batched_streams(BATCH_STREAMS, n_sym)
-    if world > 1:  # this rank's shard of the streams (the batched launch alone)
-        shard = shard_streams([4.0 * n_sym] * len(streams), world)[rank]
-        streams = [streams[i] for i in shard]
-        args.batched_forms = "batch"
+    if subset is not None:
+        streams = [streams[i] for i in subset]
     data = []
-    t0 = time.time()
     for link, rxc, sizes in streams:
         x = rxsim.simulate(rxsim.LinkConfig(**link))["rx"]
         blocks, a = [], 0
@@ -1139,6 +1147,113 @@ def run_batched(args, rank=0, world=1, barrier=None):
             a += m
         data.append(blocks)
     torch.cuda.synchronize()
+    return streams, data
+
+
+def serve_pass(streams, data, fft, storage, batch=0):
+    """Every block of every stream submitted at once to one server (batch =
+    1: batched rounds); wall time from the first submission to the last
+    stream's end, server and per-stream statistics."""
+    from paper_2108_07001_gb300 import rx
+    order = [(i, j) for j in range(max(len(b) for b in data)) for i in range(len(streams)) if j < len(data[i])]
+    with rx.Server(max_streams=128, batch=batch) as srv:
+        sids = [srv.open(**dict(rxc, fft_n=fft[i], storage_dtype=storage)) for i, (_, rxc, _) in enumerate(streams)]
+        t_start = time.perf_counter()
+        for i, j in order:
+            b = data[i][j]
+            srv.submit_device(sids[i], b.data_ptr(), b.shape[1], rx.RX_C64)
+        for sid in sids:
+            srv.end(sid)
+        for sid in sids:
+            srv.sync(sid, timeout_ms=600000)
+        wall = time.perf_counter() - t_start
+        st = srv.stats()
+        per = [srv.stream_stats(sid) for sid in sids]
+    return wall, st, per
+
+
+def plain_pass(streams, data):
+    """The same streams one after another, each through its own plain
+    receiver (FP32 storage, default FFT size) from its first block to its
+    last frame, before the next stream starts."""
+    import torch
+    from paper_2108_07001_gb300 import rx
+    cur = torch.cuda.current_stream()
+    wall, per = 0.0, []
+    for i, (_, rxc, _) in enumerate(streams):
+        r = rx.Receiver(**rxc)
+        torch.cuda.synchronize()
+        t_start = time.perf_counter()
+        for b in data[i]:
+            r.push_device(b.data_ptr(), b.shape[1], rx.RX_C64, cur.cuda_stream)
+        r.end()
+        r.join(cur.cuda_stream)
+        torch.cuda.synchronize()
+        wall += time.perf_counter() - t_start
+        per.append(r.stats())
+        r.close()
+    return wall, per
+
+
+def batch_pass(streams, data, fft, storage, barrier=None):
+    """All streams through one rx_batch: round j pushes every stream's j-th
+    block in one call (one launch per stage and frame ordinal), the last
+    call ends every stream."""
+    import torch
+    from paper_2108_07001_gb300 import rx
+    cur = torch.cuda.current_stream()
+    dev = data[0][0].device
+    recs = [rx.Receiver(**dict(rxc, fft_n=fft[i], storage_dtype=storage)) for i, (_, rxc, _) in enumerate(streams)]
+    dummy = torch.zeros(16, dtype=torch.complex64, device=dev)
+    n_rounds = max(len(b) for b in data)
+    with rx.Batch(recs) as batch:
+        torch.cuda.synchronize()
+        if barrier:
+            barrier()
+        t_start = time.perf_counter()
+        for j in range(n_rounds):
+            ptrs = [data[i][j].data_ptr() if j < len(data[i]) else dummy.data_ptr() for i in range(len(streams))]
+            ns = [data[i][j].shape[1] if j < len(data[i]) else 0 for i in range(len(streams))]
+            batch.push(ptrs, ns, rx.RX_C64, cur.cuda_stream)
+        batch.end(cur.cuda_stream)
+        host = time.perf_counter() - t_start
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_start
+        if barrier:
+            barrier()
+        info = batch.info()
+    per = [r.stats() for r in recs]
+    for r in recs:
+        r.close()
+    return wall, host, info, per
+
+
+def stream_summary(per):
+    return {"synced_streams": int(sum(p["synced"] for p in per)), "ber_max": max(p["ber"] for p in per),
+            "cycle_slips": int(sum(p["cycle_slips"] for p in per))}
+
+
+def run_batched(args, rank=0, world=1, barrier=None):
+    """64 independent streams with uneven capture blocks, every block
+    submitted at once: through the serving layer with per-stream pushes
+    (FFT size of the default rule (N >= 4 halo), the size the autotuner picks
+    per stream, and the latter with FP16 sample storage), through the
+    serving layer in batched rounds (FP32 and FP16 storage), and through one
+    rx_batch (round j pushes every stream's j-th block in one call: one
+    launch per stage and frame ordinal, pipelined over the batch's four
+    streams); beside them the plain per-stream chain (one stream at a time).
+    The value is the fastest form."""
+    import torch
+    from paper_2108_07001_gb300 import rx
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    n_sym = args.symbols or BATCH_SYMS
+    subset = None
+    if world > 1:  # this rank's shard of the streams (the batched launch alone)
+        subset = shard_streams([4.0 * n_sym] * BATCH_STREAMS, world)[rank]
+        args.batched_forms = "batch"
+    t0 = time.time()
+    streams, data = load_batched_streams(n_sym, dev, subset)
     gen_s = time.time() - t0
     t0 = time.time()
     only_batch = args.batched_forms == "batch"
@@ -1146,130 +1261,108 @@ def run_batched(args, rank=0, world=1, barrier=None):
         [rx.autotune_fft(rx.default_config(**rxc), frames=8)[0] for _, rxc, _ in streams]
     tune_s = time.time() - t0
     total_samples = 4 * n_sym * len(streams)
-    order = [(i, j) for j in range(max(len(b) for b in data)) for i in range(len(streams)) if j < len(data[i])]
-
-    def one_pass(fft, storage=rx.RX_C64):
-        with rx.Server(max_streams=128) as srv:
-            sids = [srv.open(**dict(rxc, fft_n=fft[i], storage_dtype=storage)) for i, (_, rxc, _) in enumerate(streams)]
-            t_start = time.perf_counter()
-            for i, j in order:
-                b = data[i][j]
-                srv.submit_device(sids[i], b.data_ptr(), b.shape[1], rx.RX_C64)
-            for sid in sids:
-                srv.end(sid)
-            for sid in sids:
-                srv.sync(sid, timeout_ms=600000)
-            wall = time.perf_counter() - t_start
-            st = srv.stats()
-            per = [srv.stream_stats(sid) for sid in sids]
-        return wall, st, per
-
-    def plain_per_stream():
-        """The same streams one after another, each through its own plain
-        receiver (FP32 storage, default FFT size) from its first block to its
-        last frame, before the next stream starts."""
-        cur = torch.cuda.current_stream()
-        wall, per = 0.0, []
-        for i, (_, rxc, _) in enumerate(streams):
-            r = rx.Receiver(**rxc)
-            torch.cuda.synchronize()
-            t_start = time.perf_counter()
-            for b in data[i]:
-                r.push_device(b.data_ptr(), b.shape[1], rx.RX_C64, cur.cuda_stream)
-            r.end()
-            r.join(cur.cuda_stream)
-            torch.cuda.synchronize()
-            wall += time.perf_counter() - t_start
-            per.append(r.stats())
-            r.close()
-        return wall, per
-
-    def batch_pass(fft, storage):
-        """All streams through one rx_batch: round j pushes every stream's
-        j-th block in one call (one launch per stage and frame ordinal),
-        the last call ends every stream."""
-        cur = torch.cuda.current_stream()
-        recs = [rx.Receiver(**dict(rxc, fft_n=fft[i], storage_dtype=storage)) for i, (_, rxc, _) in enumerate(streams)]
-        dummy = torch.zeros(16, dtype=torch.complex64, device=dev)
-        n_rounds = max(len(b) for b in data)
-        with rx.Batch(recs) as batch:
-            torch.cuda.synchronize()
-            if barrier:
-                barrier()
-            t_start = time.perf_counter()
-            for j in range(n_rounds):
-                ptrs = [data[i][j].data_ptr() if j < len(data[i]) else dummy.data_ptr() for i in range(len(streams))]
-                ns = [data[i][j].shape[1] if j < len(data[i]) else 0 for i in range(len(streams))]
-                batch.push(ptrs, ns, rx.RX_C64, cur.cuda_stream)
-            batch.end(cur.cuda_stream)
-            host = time.perf_counter() - t_start
-            torch.cuda.synchronize()
-            wall = time.perf_counter() - t_start
-            if barrier:
-                barrier()
-            info = batch.info()
-        per = [r.stats() for r in recs]
-        for r in recs:
-            r.close()
-        return wall, host, info, per
+    n_blocks = sum(len(b) for b in data)
+    deflt = [0] * len(streams)
 
     forms = {}
     if only_batch:  # the batched launch alone (for launch lists)
-        batch_pass([0] * len(streams), rx.RX_C64)
-        wall, host, info, per = batch_pass([0] * len(streams), rx.RX_C64)
-        return {"workload": "batched", "form": "batch_default_fft", "gsamples_s": round(total_samples / wall / 1e9, 3),
-                "samples": total_samples, "streams": len(streams), "symbols_per_pol_per_stream": n_sym,
-                "cycle_slips": int(sum(p["cycle_slips"] for p in per)),
-                "wall_ms": round(wall * 1e3, 1), "host_ms": round(host * 1e3, 1),
-                "host_wait_ms": round(info["wait_ms"], 1), "calls": info["calls"],
-                "launches": info["launches"], "synced_streams": int(sum(p["synced"] for p in per)),
-                "ber_max": max(p["ber"] for p in per)}
-    plain_per_stream()
-    wall, per = plain_per_stream()
-    forms["plain_per_stream"] = {"gsamples_s": round(total_samples / wall / 1e9, 3), "wall_ms": round(wall * 1e3, 1),
-                                 "synced_streams": int(sum(p["synced"] for p in per)),
-                                 "ber_max": max(p["ber"] for p in per),
-                                 "cycle_slips": int(sum(p["cycle_slips"] for p in per))}
-    for form, fft, storage in (("default_fft", [0] * len(streams), rx.RX_C64), ("autotuned_fft", tuned, rx.RX_C64),
-                               ("autotuned_fft_fp16_storage", tuned, rx.RX_C16)):
-        one_pass(fft, storage)
-        wall, st, per = one_pass(fft, storage)
-        forms[form] = {"gsamples_s": round(total_samples / wall / 1e9, 3), "wall_ms": round(wall * 1e3, 1),
-                       "latency_p50_ms": round(st["latency_p50_ms"], 3),
-                       "latency_p99_ms": round(st["latency_p99_ms"], 3),
-                       "synced_streams": int(sum(p["synced"] for p in per)),
-                       "ber_max": max(p["ber"] for p in per), "cycle_slips": int(sum(p["cycle_slips"] for p in per)),
-                       "mem_gib": round(st["mem_in_use_bytes"] / 2 ** 30, 2) if st["mem_in_use_bytes"] else None}
-    for form, fft, storage in (("batch_default_fft", [0] * len(streams), rx.RX_C64),
-                               ("batch_default_fft_fp16_storage", [0] * len(streams), rx.RX_C16),
+        batch_pass(streams, data, deflt, rx.RX_C64)
+        wall, host, info, per = batch_pass(streams, data, deflt, rx.RX_C64, barrier)
+        return dict({"workload": "batched", "form": "batch_default_fft",
+                     "gsamples_s": round(total_samples / wall / 1e9, 3),
+                     "samples": total_samples, "streams": len(streams), "symbols_per_pol_per_stream": n_sym,
+                     "wall_ms": round(wall * 1e3, 1), "host_ms": round(host * 1e3, 1),
+                     "host_wait_ms": round(info["wait_ms"], 1), "calls": info["calls"],
+                     "launches": info["launches"]}, **stream_summary(per))
+    plain_pass(streams, data)
+    wall, per = plain_pass(streams, data)
+    forms["plain_per_stream"] = dict({"gsamples_s": round(total_samples / wall / 1e9, 3),
+                                      "wall_ms": round(wall * 1e3, 1)}, **stream_summary(per))
+    for form, fft, storage, batch in (("default_fft", deflt, rx.RX_C64, 0), ("autotuned_fft", tuned, rx.RX_C64, 0),
+                                      ("autotuned_fft_fp16_storage", tuned, rx.RX_C16, 0),
+                                      ("served_batched_default_fft", deflt, rx.RX_C64, 1),
+                                      ("served_batched_default_fft_fp16_storage", deflt, rx.RX_C16, 1)):
+        serve_pass(streams, data, fft, storage, batch)
+        wall, st, per = serve_pass(streams, data, fft, storage, batch)
+        forms[form] = dict({"gsamples_s": round(total_samples / wall / 1e9, 3), "wall_ms": round(wall * 1e3, 1),
+                            "latency_p50_ms": round(st["latency_p50_ms"], 3),
+                            "latency_p99_ms": round(st["latency_p99_ms"], 3),
+                            "mem_gib": round(st["mem_in_use_bytes"] / 2 ** 30, 2) if st["mem_in_use_bytes"] else None,
+                            "batch_calls": st["batch_calls"]}, **stream_summary(per))
+    for form, fft, storage in (("batch_default_fft", deflt, rx.RX_C64),
+                               ("batch_default_fft_fp16_storage", deflt, rx.RX_C16),
                                ("batch_autotuned_fft_fp16_storage", tuned, rx.RX_C16)):
-        batch_pass(fft, storage)
-        wall, host, info, per = batch_pass(fft, storage)
+        batch_pass(streams, data, fft, storage)
+        wall, host, info, per = batch_pass(streams, data, fft, storage)
         # block latency of a call (its start on the stream to its bits), the
         # same for every stream the call carried
-        forms[form] = {"gsamples_s": round(total_samples / wall / 1e9, 3), "wall_ms": round(wall * 1e3, 1),
-                       "latency_p50_ms": round(float(np.median([p["latency_p50_ms"] for p in per])), 3),
-                       "latency_p99_ms": round(max(p["latency_p99_ms"] for p in per), 3),
-                       "host_ms": round(host * 1e3, 1), "host_wait_ms": round(info["wait_ms"], 1),
-                       "calls": info["calls"], "launches": info["launches"],
-                       "fft_groups": len(set(fft)) if fft[0] else None,
-                       "synced_streams": int(sum(p["synced"] for p in per)),
-                       "ber_max": max(p["ber"] for p in per), "cycle_slips": int(sum(p["cycle_slips"] for p in per))}
+        forms[form] = dict({"gsamples_s": round(total_samples / wall / 1e9, 3), "wall_ms": round(wall * 1e3, 1),
+                            "latency_p50_ms": round(float(np.median([p["latency_p50_ms"] for p in per])), 3),
+                            "latency_p99_ms": round(max(p["latency_p99_ms"] for p in per), 3),
+                            "host_ms": round(host * 1e3, 1), "host_wait_ms": round(info["wait_ms"], 1),
+                            "calls": info["calls"], "launches": info["launches"],
+                            "fft_groups": len(set(fft)) if fft[0] else None}, **stream_summary(per))
     base = forms["plain_per_stream"]["gsamples_s"]
-    for form in ("default_fft", "autotuned_fft", "autotuned_fft_fp16_storage", "batch_default_fft",
-                 "batch_default_fft_fp16_storage", "batch_autotuned_fft_fp16_storage"):
-        forms[form]["x_plain_per_stream"] = round(forms[form]["gsamples_s"] / base, 2) if base else None
+    strong = forms["default_fft"]["gsamples_s"]
+    for form in forms:
+        if form != "plain_per_stream":
+            forms[form]["x_plain_per_stream"] = round(forms[form]["gsamples_s"] / base, 2) if base else None
+            forms[form]["x_served_per_stream"] = round(forms[form]["gsamples_s"] / strong, 2) if strong else None
     best = max((f for f in forms if f != "plain_per_stream"), key=lambda f: forms[f]["gsamples_s"])
     return {"metric": "gsamples_per_s", "value": forms[best]["gsamples_s"], "value_form": best,
             "unit": "Gsamples/s",
             "n_gpus": 1, "higher_is_better": True, "workload": "batched", "dtype": "f16 storage, f32 arithmetic",
             "data": "synthetic (seeded link simulator)",
-            "config": {"streams": len(streams), "symbols_per_pol_per_stream": n_sym, "blocks": len(order),
+            "config": {"streams": len(streams), "symbols_per_pol_per_stream": n_sym, "blocks": n_blocks,
                        "block_syms": "2^12..2^18", "frame_syms": BATCH_FRAME,
                        "baud_gbd": [s[0]["baud_hz"] / 1e9 for s in streams],
                        "fiber_km": [round(s[0]["fiber_len_m"] / 1e3) for s in streams],
                        "autotuned_fft": tuned, "submission": "every block at once"},
             "forms": forms, "autotune_seconds": round(tune_s, 1), "sim_seconds": round(gen_s, 1)}
+
+
+def batched_fp16_summary(hbm_peak):
+    """The 64-stream workload (batched_streams) through the batched
+    FP16-storage serving path (the serving layer in batched rounds), beside
+    the plain per-stream FP32 chain (one stream at a time) and the same
+    streams served concurrently through plain receivers (per-stream
+    pushes, FP32): throughput, ratios, frame latency, worst BER, and the
+    chain's algorithmic HBM bytes (complex64 input read once, decided bits
+    written once) over the measured HBM bandwidth."""
+    import torch
+    from paper_2108_07001_gb300 import rx
+    t0 = time.time()
+    streams, data = load_batched_streams(BATCH_SYMS, torch.device("cuda:0"))
+    gen_s = time.time() - t0
+    total = 4 * BATCH_SYMS * len(streams)
+    deflt = [0] * len(streams)
+    plain_pass(streams, data)
+    w_plain, per_plain = plain_pass(streams, data)
+    serve_pass(streams, data, deflt, rx.RX_C64, 0)
+    w_serv, _, per_serv = serve_pass(streams, data, deflt, rx.RX_C64, 0)
+    serve_pass(streams, data, deflt, rx.RX_C16, 1)
+    w_b, st_b, per_b = serve_pass(streams, data, deflt, rx.RX_C16, 1)
+    del data
+    torch.cuda.empty_cache()
+    v = total / w_b / 1e9
+    bytes_per_sample = 8.0 + 2.0 / 8.0 / 2.0  # c64 in; 2 bits per QPSK symbol and polarisation out (1 bit per sample)
+    out = {"path": "serving layer, batched rounds (rx_server batch = 1), FP16 sample storage, FP32 arithmetic",
+           "streams": len(streams), "symbols_per_pol_per_stream": BATCH_SYMS, "block_syms": "2^12..2^18",
+           "gsamples_s": round(v, 3), "decoded_gbps": round(v, 3),
+           "latency_p50_ms": round(st_b["latency_p50_ms"], 3), "latency_p99_ms": round(st_b["latency_p99_ms"], 3),
+           "batch_calls": st_b["batch_calls"],
+           "plain_per_stream_fp32_gsamples_s": round(total / w_plain / 1e9, 3),
+           "x_plain_per_stream_fp32": round(w_plain / w_b, 2),
+           "served_per_stream_fp32_gsamples_s": round(total / w_serv / 1e9, 3),
+           "x_served_per_stream_fp32": round(w_serv / w_b, 2),
+           "ber_max": max(p["ber"] for p in per_b), "ber_max_plain_fp32": max(p["ber"] for p in per_plain),
+           "synced_streams": int(sum(p["synced"] for p in per_b)),
+           "cycle_slips": int(sum(p["cycle_slips"] for p in per_b)),
+           "hbm_algorithmic_gbs": round(v * bytes_per_sample, 1),
+           "sim_seconds": round(gen_s, 1)}
+    if hbm_peak:
+        out["hbm_frac"] = round(v * bytes_per_sample / hbm_peak, 4)
+    return out
 
 
 def main():
@@ -1279,6 +1372,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="stream workload: leave out the batched_fp16 sub-record (64 streams, batched serving)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--symbols", type=int, default=0, help="stream length per pol (default: the workload's 2^24)")
     ap.add_argument("--oracle-child", nargs=4, help=argparse.SUPPRESS)
@@ -1321,6 +1416,7 @@ def main():
         dist.init_process_group("nccl")
         dist.barrier()
         args.cpu_baseline = False  # the CPU baseline is taken on one rank at N=1 only
+        args.batched = False       # as is the 64-stream sub-record
 
         def reduce_op(op):
             def f(vals):

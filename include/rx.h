@@ -338,6 +338,20 @@ int rx_fp32_peak(int device, double* tflops_fma, double* tflops_fma2);
  * completed the frame's input (its look-ahead included) to the frame's
  * bits being ready, host clock, queueing inside the server included.
  *
+ * Batched rounds (batch = 1; max_streams <= RX_BATCH_MAX, one worker): the
+ * worker keeps one rx_batch over the open streams and, each round, takes
+ * the first queued block of every stream and pushes the device blocks of
+ * one input type (dtype and on_device of the first such block) and the
+ * ends of stream in one rx_batch_push, so each stage of every stream's
+ * completed frames runs in one launch; the other blocks of the round
+ * (pageable host blocks, other input types, or all of them when a
+ * stream's output ring is full) go through their stream's rx_push_block.
+ * A stream's results are the same alone and in any mix, and equal to the
+ * same blocks pushed through an rx_batch of its own.  When streams open
+ * or close, the worker replaces the batch at its next round, waiting for
+ * the old batch's work (rx_server_close returns once the stream is out of
+ * the batch and freed).
+ *
  * Each receiver runs four CUDA streams; set CUDA_DEVICE_MAX_CONNECTIONS=32
  * in the environment before the process creates its CUDA context, or the
  * default 8 hardware queues serialise the streams' kernels (64 streams:
@@ -352,6 +366,7 @@ typedef struct rx_server_config {
   int64_t bits_cap_bytes;   /* per-stream host buffer of decided bits not yet pulled (>= 4096);
                                when full the stream's blocks wait (backpressure) */
   int workers;              /* worker threads, 1..64; worker k serves the streams with id % workers == k */
+  int batch;                /* 0: every block through its stream's rx_push_block; 1: batched rounds (below) */
 } rx_server_config;
 
 typedef struct rx_server_stats_t {
@@ -363,6 +378,10 @@ typedef struct rx_server_stats_t {
   int64_t mem_in_use_bytes, mem_budget_bytes;
   int streams_open;
   int worker_error;          /* first error of the worker (RX_* code), 0 if none */
+  int64_t batch_calls;       /* batched mode: rx_batch_push calls made so far */
+  double worker_round_ms;    /* host time the workers spent in passes / rounds */
+  double worker_push_ms;     /* of which in rx_push_block / rx_batch_push calls */
+  double worker_poll_ms;     /* of which polling frame completion and moving bits to the host */
 } rx_server_stats_t;
 
 void rx_server_config_default(rx_server_config* cfg);

@@ -72,6 +72,7 @@ struct rx_batch {
   std::vector<cudaEvent_t> ev_ring;   // call start / end events (round robin)
   size_t ev_i = 0;
   long long calls = 0, launches = 0, frames = 0;
+  long long calls_done = 0;          // calls seen complete (batch_calls_done)
   double wait_s = 0.0;                // host time spent waiting for table slots
 };
 
@@ -262,6 +263,51 @@ void batch_free(rx_batch* b) {
 }
 
 }  // namespace
+
+namespace rx {
+// Calls of the batch whose device work is complete (polled, nothing waits):
+// at most kSlots calls are in flight, so the slot events of the calls not
+// yet seen complete are all distinct.
+long long batch_calls_done(rx_batch* b) {
+  while (b->calls_done < b->calls &&
+         cudaEventQuery(b->ev_slot[b->calls_done % rx_batch::kSlots]) == cudaSuccess)
+    ++b->calls_done;
+  cudaGetLastError();
+  return b->calls_done;
+}
+
+// Frees the batch without waiting when its device work is complete: true
+// when freed, false while some of it still runs (try again later).  The
+// handles may meanwhile carry work of another batch or of plain pushes;
+// the caller holds no other call on them.
+bool batch_try_free(rx_batch* b) {
+  cudaSetDevice(b->device);
+  if (batch_calls_done(b) < b->calls) return false;
+  for (int p = 0; p < 4; ++p)
+    if (cudaStreamQuery(b->s_stage[p]) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+  for (rx_handle* h : b->h) {
+    harvest(h);  // the batch's entries are complete, so they leave the queue
+    for (const PendingFrame& pf : h->pend)
+      for (cudaEvent_t e : b->ev_ring)
+        if (pf.ev_done == e || pf.ev_in == e) return false;
+  }
+  for (rx_handle* h : b->h) {
+    bool mine = false;
+    for (cudaEvent_t e : b->ev_ring) mine |= h->batch_done == e;
+    if (mine) h->batch_done = nullptr;
+    if (h->last_cs == b->s_stage[3]) {  // its work is complete: nothing to join
+      h->last_cs = nullptr;
+      h->copy_dirty = false;
+    }
+  }
+  batch_free(b);
+  delete b;
+  return true;
+}
+}  // namespace rx
 
 extern "C" {
 

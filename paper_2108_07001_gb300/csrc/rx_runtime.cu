@@ -160,14 +160,42 @@ void free_all(rx_handle* h) {
 }
 
 // Harvest completed frames (in order): latency, device time, bits.
+// Elapsed time between two recorded, complete events.  A batched call's
+// events are shared by every stream it carried, and the streams are polled
+// one after another: the last pair's result is reused.
+float elapsed_ms(cudaEvent_t a, cudaEvent_t b, bool* ok) {
+  thread_local cudaEvent_t la = nullptr, lb = nullptr;
+  thread_local float lms = 0.f;
+  thread_local bool lok = false;
+  if (a == b) {
+    *ok = true;
+    return 0.f;
+  }
+  if (a != la || b != lb) {
+    lok = cudaEventElapsedTime(&lms, a, b) == cudaSuccess;
+    la = a;
+    lb = b;
+  }
+  *ok = lok;
+  return lms;
+}
+
 void harvest(rx_handle* h) {
   while (!h->pend.empty()) {
     PendingFrame& pf = h->pend.front();
     if (cudaEventQuery(pf.ev_done) != cudaSuccess) break;
     float a = 0.f, b = 0.f;
     if (pf.gen == h->gen) {
-      if (cudaEventElapsedTime(&a, pf.ev_in, pf.ev_done) == cudaSuccess) h->lat_ms.push_back(a);
-      if (cudaEventElapsedTime(&b, pf.ev_start, pf.ev_done) == cudaSuccess) h->gpu_ms += b;
+      bool ok = false;
+      if (pf.shared) {  // a batched call: events recorded once, shared by its streams
+        a = elapsed_ms(pf.ev_in, pf.ev_done, &ok);
+        if (ok) h->lat_ms.push_back(a);
+        b = elapsed_ms(pf.ev_start, pf.ev_done, &ok);
+        if (ok) h->gpu_ms += b;
+      } else {
+        if (cudaEventElapsedTime(&a, pf.ev_in, pf.ev_done) == cudaSuccess) h->lat_ms.push_back(a);
+        if (cudaEventElapsedTime(&b, pf.ev_start, pf.ev_done) == cudaSuccess) h->gpu_ms += b;
+      }
       h->bits_done = pf.bits_after;
       h->dec_done = pf.dec_after;
       h->frames_done += pf.nframes;
@@ -502,6 +530,40 @@ void handle_progress(rx_handle* h, long long* launched, long long* done, long lo
   *done = h->frames_done;
   *pending = (long long)h->pend.size();
 }
+
+// Frames launched so far (no polling).
+long long handle_launched(const rx_handle* h) { return h->f_next; }
+
+// Decided bits of completed frames not yet pulled, and the output ring's
+// capacity in bits (as of the last poll).
+void handle_bits(const rx_handle* h, long long* ready, long long* ring_bits) {
+  *ready = h->bits_done - h->bits_pulled;
+  *ring_bits = 8LL * h->d.out_cap_bytes;
+}
+
+// Queues on cs the copy of the bits rx_pull_bits(h, out, cap_bytes, n_bits,
+// 0) would return into out (page-locked host memory) without marking them
+// pulled: pull_bits_commit(h, *n_bits) does that once the copy is complete.
+// Until then the output ring keeps those bits (pushes see them unpulled),
+// and no other pull of h may come in between.
+int pull_bits_begin(rx_handle* h, uint8_t* out, size_t cap_bytes, size_t* n_bits, cudaStream_t cs) {
+  *n_bits = 0;
+  harvest(h);
+  const bool all_done = h->ended && h->pend.empty() && h->decided >= h->n_total / 2;
+  const long long avail = h->bits_done - h->bits_pulled;
+  long long nbytes = all_done ? (avail + 7) / 8 : avail / 8;
+  nbytes = std::min<long long>(nbytes, (long long)cap_bytes);
+  if (nbytes <= 0) return RX_OK;
+  const long long cap = h->d.out_cap_bytes;
+  const long long o = (h->bits_pulled / 8) % cap;
+  const long long first = std::min(nbytes, cap - o);
+  RX_CK(cudaMemcpyAsync(out, h->d.out + o, first, cudaMemcpyDeviceToHost, cs));
+  if (nbytes > first) RX_CK(cudaMemcpyAsync(out + first, h->d.out, nbytes - first, cudaMemcpyDeviceToHost, cs));
+  *n_bits = (size_t)std::min(nbytes * 8, avail);
+  return RX_OK;
+}
+
+void pull_bits_commit(rx_handle* h, size_t n_bits) { h->bits_pulled += (long long)n_bits; }
 }  // namespace rx
 
 extern "C" {

@@ -145,6 +145,7 @@ class ServerConfig(ctypes.Structure):
         ("device", ctypes.c_int),
         ("bits_cap_bytes", ctypes.c_int64),
         ("workers", ctypes.c_int),
+        ("batch", ctypes.c_int),
     ]
 
 
@@ -163,6 +164,10 @@ class ServerStats(ctypes.Structure):
         ("mem_budget_bytes", ctypes.c_int64),
         ("streams_open", ctypes.c_int),
         ("worker_error", ctypes.c_int),
+        ("batch_calls", ctypes.c_int64),
+        ("worker_round_ms", ctypes.c_double),
+        ("worker_push_ms", ctypes.c_double),
+        ("worker_poll_ms", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:

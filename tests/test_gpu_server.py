@@ -42,22 +42,36 @@ def stream_case(kind, seed):
     return cfg, blocks, n_sym
 
 
-def serve(cases, interleave=True):
-    """Runs the given streams through one server; returns per-stream
-    (bits, n_bits, y, stats) and the server statistics."""
+def submit(srv, sid, block, device):
+    """A host block, or (device) a device copy kept alive by the caller."""
+    if not device:
+        srv.submit_host(sid, block)
+        return None
+    import torch
+    t = torch.from_numpy(block).cuda()
+    torch.cuda.synchronize()
+    srv.submit_device(sid, t.data_ptr(), block.shape[1], rx.RX_C64)
+    return t
+
+
+def serve(cases, interleave=True, batch=0, device=False):
+    """Runs the given streams through one server (batch = 1: batched rounds,
+    device: blocks submitted from device memory); returns per-stream (bits,
+    n_bits, y, stats, BPS angles/unwrap/trace) and the server statistics."""
     out = {}
-    with rx.Server(max_streams=16) as srv:
+    keep = []
+    with rx.Server(max_streams=16, batch=batch) as srv:
         sids = {k: srv.open(**cfg) for k, (cfg, _, _) in cases.items()}
         queues = {k: list(blocks) for k, (_, blocks, _) in cases.items()}
         if interleave:
             while any(queues.values()):
                 for k in cases:
                     if queues[k]:
-                        srv.submit_host(sids[k], queues[k].pop(0))
+                        keep.append(submit(srv, sids[k], queues[k].pop(0), device))
         else:
             for k in cases:
                 for b in queues[k]:
-                    srv.submit_host(sids[k], b)
+                    keep.append(submit(srv, sids[k], b, device))
         for k in cases:
             srv.end(sids[k])
         for k in cases:
@@ -80,15 +94,26 @@ def cases():
     return {k: stream_case(k, 700 + i) for i, k in enumerate(CASES)}
 
 
+MODES = {"per_stream": dict(batch=0, device=False), "batched": dict(batch=1, device=True)}
+
+
+@pytest.fixture(scope="module", params=list(MODES))
+def mode(request):
+    return request.param
+
+
 @pytest.fixture(scope="module")
-def mixed(cases):
-    return serve(cases, interleave=True)
+def mixed(cases, mode):
+    return serve(cases, interleave=True, **MODES[mode])
 
 
-def test_each_stream_alone_equals_the_mix(cases, mixed):
+def test_each_stream_alone_equals_the_mix(cases, mixed, mode):
+    """Bit for bit: decided bits, equalised symbols and counters of each
+    stream served alone and served in the mix (per-stream pushes, and
+    batched rounds where the mix shares every launch)."""
     mix, _ = mixed
     for k in CASES:
-        alone, _ = serve({k: cases[k]})
+        alone, _ = serve({k: cases[k]}, **MODES[mode])
         b0, n0, y0, s0, _ = alone[k]
         b1, n1, y1, s1, _ = mix[k]
         assert n0 == n1 > 0
@@ -98,7 +123,9 @@ def test_each_stream_alone_equals_the_mix(cases, mixed):
             assert s0[f] == s1[f], (k, f)
 
 
-def test_served_stream_equals_a_plain_receiver(cases, mixed):
+def test_served_stream_equals_a_plain_receiver(cases, mixed, mode):
+    if mode != "per_stream":
+        pytest.skip("batched rounds: compared with an rx_batch of the same blocks below")
     mix, _ = mixed
     k = "qpsk1000"
     cfg, blocks, n_sym = cases[k]
@@ -119,6 +146,32 @@ def test_served_stream_equals_a_plain_receiver(cases, mixed):
     assert st["bit_errors"] == s1["bit_errors"] and st["bits"] == s1["bits"]
 
 
+def test_batched_rounds_equal_a_batch_of_the_stream_alone(cases, mixed, mode):
+    """A stream served in batched rounds gives bit for bit what its blocks
+    pushed through an rx_batch of its own give (the same batched kernels)."""
+    if mode != "batched":
+        pytest.skip("per-stream pushes: compared with a plain receiver above")
+    import torch
+    mix, sst = mixed
+    assert sst["batch_calls"] > 0
+    k = "qam16"
+    cfg, blocks, n_sym = cases[k]
+    r = rx.Receiver(**cfg)
+    s = torch.cuda.current_stream().cuda_stream
+    dev = [torch.from_numpy(b).cuda() for b in blocks]
+    with rx.Batch([r]) as batch:
+        for t in dev:
+            batch.push([t.data_ptr()], [t.shape[1]], rx.RX_C64, s)
+        batch.end(s)
+    buf = np.empty(1 << 22, dtype=np.uint8)
+    nb = r.pull_bytes(buf, timeout_ms=-1)
+    y = r.equalised(0, n_sym)
+    r.close()
+    b1, n1, y1, s1, _ = mix[k]
+    assert nb == n1 and np.array_equal(buf[:(nb + 7) // 8], b1)
+    assert np.array_equal(y, y1)
+
+
 def test_served_streams_match_the_oracle(cases, mixed):
     """Every stream served in the mix against the FP64 oracle on the same
     samples, under the parity rules of the single-stream tests (equalised
@@ -134,8 +187,9 @@ def test_served_streams_match_the_oracle(cases, mixed):
         assert abs(int(st["bit_errors"]) - ref["ber"]["errors"]) <= 2 * rep.get("bit_mismatch_syms", 0), k
 
 
-def test_server_statistics(cases, mixed):
+def test_server_statistics(cases, mixed, mode):
     mix, sst = mixed
+    assert (sst["batch_calls"] > 0) == (mode == "batched")
     n_blocks = sum(len(cases[k][1]) for k in CASES)
     assert sst["blocks_submitted"] == sst["blocks_pushed"] == n_blocks
     assert sst["blocks_queued"] == 0 and sst["worker_error"] == 0
@@ -164,3 +218,45 @@ def test_streams_are_admitted_by_device_memory(cases):
         srv.close_stream(a)
         srv.open(**cfg)  # room again
         assert srv.stats()["mem_in_use_bytes"] == 2 * one
+
+
+def test_batched_server_admits_and_retires_streams_continuously(cases):
+    """Batched rounds with streams opening and closing while others are on
+    the GPU: a stream opened after the others have been running, and a
+    stream closed (and its receiver freed) in the middle, each give what
+    they give served alone."""
+    import torch
+    keep = []
+    got = {}
+    with rx.Server(max_streams=16, batch=1) as srv:
+        a = srv.open(**cases["qpsk1000"][0])
+        b = srv.open(**cases["qam16"][0])
+        qa, qb = list(cases["qpsk1000"][1]), list(cases["qam16"][1])
+        for _ in range(3):
+            keep.append(submit(srv, a, qa.pop(0), True))
+            keep.append(submit(srv, b, qb.pop(0), True))
+        c = srv.open(**cases["qpsk2000"][0])  # joins while a and b are running
+        qc = list(cases["qpsk2000"][1])
+        while qb:
+            keep.append(submit(srv, b, qb.pop(0), True))
+            if qc:
+                keep.append(submit(srv, c, qc.pop(0), True))
+        srv.end(b)
+        srv.sync(b, timeout_ms=120000)
+        got["qam16"] = srv.pull_bytes(b)
+        srv.close_stream(b)  # leaves while a and c keep going
+        while qa or qc:
+            if qa:
+                keep.append(submit(srv, a, qa.pop(0), True))
+            if qc:
+                keep.append(submit(srv, c, qc.pop(0), True))
+        for sid, k in ((a, "qpsk1000"), (c, "qpsk2000")):
+            srv.end(sid)
+            srv.sync(sid, timeout_ms=120000)
+            got[k] = srv.pull_bytes(sid)
+        assert srv.stats()["batch_calls"] > 0
+    for k in ("qpsk1000", "qam16", "qpsk2000"):
+        alone, _ = serve({k: cases[k]}, batch=1, device=True)
+        bits, nb = got[k]
+        assert nb == alone[k][1] > 0, k
+        assert np.array_equal(bits, alone[k][0]), k
