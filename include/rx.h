@@ -183,8 +183,8 @@ int rx_stats(rx_handle* h, rx_stats_t* out);
  * launch; streams whose FFT size and storage type, tap count or BPS form
  * differ get a launch of their own for that stage.
  * The ingest runs on cuda_stream; the stages run on the batch's own four
- * streams (front: CD and estimators, mid: acquisition and MIMO, back: BPS
- * and demap, BER), pipelined over ordinals and calls with the buffer-reuse
+ * streams (front: CD and estimators, mid: acquisition and MIMO, back: BPS,
+ * then demap and BER), pipelined over ordinals and calls with the buffer-reuse
  * waits of the plain path, so every stream gets what the same blocks
  * pushed with rx_push_block give: the same frames, sync and slips, soft
  * values equal to FP32 rounding (the batched kernels are compiled

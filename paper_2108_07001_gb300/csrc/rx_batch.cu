@@ -20,11 +20,11 @@ using namespace rxrt;
 // each stage in one launch (streams with another FFT size, tap count or
 // BPS form in a launch of their own).  The stages are pipelined over four
 // streams of the batch like the plain path's: front (CD + estimators), mid
-// (acquisition + MIMO), back (BPS + demap) and BER; ordinal q's stage waits
+// (acquisition + MIMO), back (BPS) and demap + BER; ordinal q's stage waits
 // for the same ordinal's previous stage and for the ordinals whose buffers
 // it reuses (front: the MIMO of q - kZSlots, whose CD output slot it
 // overwrites; mid: the BPS of q - 2, whose equalised-symbol buffer it
-// overwrites; back: the BER of q - 2, whose decision-ring slots it
+// overwrites; back: the demap of q - 2, whose decision buffers it
 // overwrites), and the ingest of the next call waits for this call's
 // front work (ring slots).  The arguments of a call (ingest list,
 // per-ordinal launch lists and frames) are written to a page-locked table
@@ -125,7 +125,7 @@ int count_work(const rx_handle* h, long long n) {
 BPlan plan_frame(rx_handle* h, long long f, bool final_) {
   BPlan p;
   p.fa = frame_args(h, f, final_);
-  p.d = slot_dev(h, f);
+  p.d = decide_dev(slot_dev(h, f), h->n_decide);
   p.frame = true;
   p.final_ = final_;
   h->n_decide++;
@@ -209,7 +209,9 @@ int join_stream(rx_handle* h, cudaStream_t cs, cudaStream_t batch_end) {
 
 // Pipeline stage of each launch.
 int stage_of(int st) {
-  return st <= BS_EST1 ? 0 : (st <= BS_MIMO ? 1 : (st <= BS_DEMAP ? 2 : 3));
+  // demap with the BER work: the next ordinal's BPS overlaps it (the two
+  // use the decision buffers of different decide passes)
+  return st <= BS_EST1 ? 0 : (st <= BS_MIMO ? 1 : (st <= BS_BPS ? 2 : 3));
 }
 
 // The launches of one ordinal's lists that belong to pipeline stage ps.
@@ -501,7 +503,7 @@ int rx_batch_push(rx_batch* b, const void* const* samples, const size_t* n_per_p
       if (!h->tail_launched && h->f_next != 0 && h->decided < n_sym) {
         BPlan p;
         p.fa = tail_args(h);
-        p.d = h->d;
+        p.d = decide_dev(h->d, h->n_decide);
         p.frame = false;
         p.final_ = true;
         h->n_decide++;

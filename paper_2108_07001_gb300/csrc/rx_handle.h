@@ -67,6 +67,8 @@ int cuda_fail(cudaError_t e, const char* where);
 
 constexpr double kC = 299792458.0;
 constexpr int kZSlots = 6;      // frames in flight between the front and back streams
+constexpr int kRingFrames = 3;  // frames of input the ring holds (plus look-ahead and one push): the
+                                // pushes of the next frames land while the CD reads the current one
 constexpr int kStageSlots = 8;  // device staging buffers of host pushes
 
 struct StageEv {
@@ -93,13 +95,14 @@ struct rx_handle {
   cudaStream_t s_copy = nullptr;
   cudaStream_t s_front = nullptr;  // CD + estimator of each frame
   cudaStream_t s_mid = nullptr;    // acquisition and MIMO
-  cudaStream_t s_comp = nullptr;   // BPS and demap ("back")
+  cudaStream_t s_comp = nullptr;   // BPS ("back")
   cudaEvent_t ev_mid[2] = {};      // MIMO of a frame done (its y buffer written), by frame parity
   cudaEvent_t ev_bpsd[2] = {};     // BPS of a frame done (its y buffer free again), by frame parity
+  cudaEvent_t ev_bpsp[2] = {};     // BPS of a decide pass done (its decision buffers written), by pass parity
   cudaEvent_t ev_front[rxrt::kZSlots] = {};  // front work of the frame in slot done
   cudaEvent_t ev_mimo[rxrt::kZSlots] = {};   // MIMO of the frame in slot done (slot reusable)
-  cudaStream_t s_ber = nullptr;        // BER counting (metrics), off the decision path
-  cudaEvent_t ev_dem[2] = {};          // demap of a frame done (decisions in the ring)
+  cudaStream_t s_ber = nullptr;        // unwrap/demap and BER counting, after the BPS
+  cudaEvent_t ev_dem[2] = {};          // demap of a decide pass done (its decision buffers free), by pass parity
   cudaEvent_t ev_berd[2] = {};         // BER work of a frame done (its ring slots reusable)
   long long n_decide = 0;              // decision passes launched in this stream
   cudaEvent_t ev_copy = nullptr;   // last ingest (recorded on the pushing stream)
@@ -174,6 +177,7 @@ FrameArgs frame_args(const rx_handle* h, long long f, bool final_);
 FrameArgs est_pass_args(const FrameArgs& fa);
 // Device state with frame f's slot.
 RxDev slot_dev(const rx_handle* h, long long f);
+RxDev decide_dev(const RxDev& base, long long pass);
 // The decide-only pass at the stream end.
 FrameArgs tail_args(const rx_handle* h);
 

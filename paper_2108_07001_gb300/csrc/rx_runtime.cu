@@ -146,6 +146,7 @@ void free_all(rx_handle* h) {
   for (int i = 0; i < 2; ++i) {
     if (h->ev_mid[i]) cudaEventDestroy(h->ev_mid[i]);
     if (h->ev_bpsd[i]) cudaEventDestroy(h->ev_bpsd[i]);
+    if (h->ev_bpsp[i]) cudaEventDestroy(h->ev_bpsp[i]);
   }
   if (h->s_front) cudaStreamDestroy(h->s_front);
   if (h->s_ber) cudaStreamDestroy(h->s_ber);
@@ -305,20 +306,30 @@ BerPlan plan_ber(rx_handle* h, const FrameArgs& fa, bool final_) {
   return p;
 }
 
-// Launch the decision stages (BPS .. BER) for decided range [k_a, k_b).
+// Launch the decision stages (BPS .. BER) for decided range [k_a, k_b):
+// BPS on the back stream, then unwrap/demap and the BER work on the BER
+// stream, so the next pass's BPS overlaps this pass's demap.  pf.ev_done
+// is recorded after the demap (the bits are out).
 int launch_decide(rx_handle* h, PendingFrame& pf, const FrameArgs& fa, bool final_) {
-  const RxDev& d = h->d;
+  const long long pass = h->n_decide;
+  const int par = (int)(pass & 1);
+  const RxDev d = decide_dev(h->d, pass);
+  // this pass's decision buffers were read by the demap of pass n - 2
+  if (pass >= 2) RX_CK(cudaStreamWaitEvent(h->s_comp, h->ev_dem[par], 0));
   RX_STAGE(RX_STAGE_BPS, 1, h->s_comp, launch_bps(d, fa, h->s_comp));
   if (fa.f >= 0) RX_CK(cudaEventRecord(h->ev_bpsd[fa.f & 1], h->s_comp));
-  // the decision ring slots of pass n were read by the BER work of pass n-2
-  const int par = (int)(h->n_decide & 1);
-  if (d.ber_on && h->n_decide >= 2) RX_CK(cudaStreamWaitEvent(h->s_comp, h->ev_berd[par], 0));
-  RX_STAGE(RX_STAGE_DEMAP, 1, h->s_comp, launch_unwrap_demap(d, fa, h->s_comp));
+  RX_CK(cudaEventRecord(h->ev_bpsp[par], h->s_comp));
+  cudaStream_t sb = h->s_ber;
+  RX_CK(cudaStreamWaitEvent(sb, h->ev_bpsp[par], 0));
+  // (the decision ring slots it writes were read by the BER work of pass
+  // n - 2, earlier on the same stream)
+  RX_STAGE(RX_STAGE_DEMAP, 1, sb, launch_unwrap_demap(d, fa, sb));
+  RX_CK(cudaEventRecord(h->ev_dem[par], sb));
+  // the bits are out; with per-stage timing, the pass ends after its BER
+  // work too, so every stage event of the pass is complete at ev_done
+  if (!h->cfg.profile) RX_CK(cudaEventRecord(pf.ev_done, sb));
   h->n_decide++;
   if (d.ber_on) {
-    RX_CK(cudaEventRecord(h->ev_dem[par], h->s_comp));
-    RX_CK(cudaStreamWaitEvent(h->s_ber, h->ev_dem[par], 0));
-    cudaStream_t sb = h->s_ber;
     int rcb = staged(h, pf, RX_STAGE_BER, sb, [&]() -> int {
       const BerPlan p = plan_ber(h, fa, final_);
       if (p.sync) {
@@ -333,6 +344,7 @@ int launch_decide(rx_handle* h, PendingFrame& pf, const FrameArgs& fa, bool fina
     if (rcb != RX_OK) return rcb;
     RX_CK(cudaEventRecord(h->ev_berd[par], sb));
   }
+  if (h->cfg.profile) RX_CK(cudaEventRecord(pf.ev_done, sb));
   return RX_OK;
 }
 
@@ -374,6 +386,22 @@ RxDev slot_dev(const rx_handle* h, long long f) {
   df.rot_hi = d.rot_hi + (long long)slot * (d.zlen / kRotLo + 2);
   df.rot_lo = d.rot_lo + (long long)slot * kRotLo;
   return df;
+}
+
+// Device state of decide pass `pass`: the BPS angles / levels and run sums
+// of passes n and n + 1 live in separate buffers, so the demap of pass n
+// (on the BER stream) overlaps the BPS of pass n + 1 (on the back stream);
+// the BPS of pass n + 2 waits for the demap of pass n.
+RxDev decide_dev(const RxDev& base, long long pass) {
+  RxDev dd = base;
+  if (pass & 1) {
+    const long long nruns = base.F / kRun + 4;
+    dd.bl += 2LL * (base.F + 2 * base.W);
+    dd.run_int += 2 * nruns;
+    dd.run_m0 += 2 * nruns;
+    dd.run_edge += 4 * nruns;
+  }
+  return dd;
 }
 
 // The decide-only pass at the stream end (the last W symbols, when the
@@ -434,7 +462,6 @@ int launch_frame(rx_handle* h, long long f, bool final_) {
   RX_CK(cudaStreamWaitEvent(h->s_comp, h->ev_mid[f & 1], 0));
   int rc = launch_decide(h, pf, fa, final_);
   if (rc != RX_OK) return rc;
-  RX_CK(cudaEventRecord(pf.ev_done, h->s_comp));
   h->decided = fa.k_b;
   pf.dec_after = fa.k_b;
   pf.bits_after = 2LL * d.bps * fa.k_b;
@@ -463,7 +490,6 @@ int launch_tail(rx_handle* h) {
   RX_CK(cudaEventRecord(pf.ev_start, h->s_comp));
   int rc = launch_decide(h, pf, fa, true);
   if (rc != RX_OK) return rc;
-  RX_CK(cudaEventRecord(pf.ev_done, h->s_comp));
   h->decided = n_sym;
   pf.dec_after = n_sym;
   pf.bits_after = 2LL * d.bps * n_sym;
@@ -670,7 +696,7 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   // samples beyond the frame end; the BER end rule needs tail + W symbols
   h->la = std::max(d.L + d.h + d.c + 2, 2 * (h->tail + d.W + 2));
   const long long mb = (long long)cfg->max_block_samples;
-  d.ring_cap = (2LL * d.F + 2LL * h->la + d.c + d.h + mb + 1024 + 255) / 256 * 256;  // even: paired ingest
+  d.ring_cap = (2LL * d.F * kRingFrames + 2LL * h->la + d.c + d.h + mb + 1024 + 255) / 256 * 256;  // even: paired ingest
   d.out_cap_bytes = std::max<long long>(1 << 20, 32LL * d.F * 2 * d.bps / 8);
   d.dec_cap = 2LL * d.F + 8192;
   h->n_win_ring = d.F / std::max(d.slip_win, 32) + 8;
@@ -701,10 +727,11 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   RX_AL(d.w_acq, 4 * d.T);
   RX_AL(d.chains, (size_t)d.G * 4 * d.T);
   RX_AL(d.y, 4LL * (kYHist + d.F));
-  RX_AL(d.bl, 2LL * (d.F + 2 * d.W));
-  RX_AL(d.run_int, 2LL * nruns);
-  RX_AL(d.run_m0, 2LL * nruns);
-  RX_AL(d.run_edge, 4LL * nruns);
+  // decision buffers, two sets by decide-pass parity (decide_dev)
+  RX_AL(d.bl, 2 * 2LL * (d.F + 2 * d.W));
+  RX_AL(d.run_int, 2 * 2LL * nruns);
+  RX_AL(d.run_m0, 2 * 2LL * nruns);
+  RX_AL(d.run_edge, 2 * 4LL * nruns);
   RX_AL(d.bps_done, 2);
   RX_AL(d.ber_done, 2);
   RX_AL(d.dec, d.dec_cap);
@@ -778,6 +805,7 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     e = cudaEventCreateWithFlags(&h->ev_mid[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_bpsd[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_bpsp[i], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_front, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_ber, cudaStreamNonBlocking);
