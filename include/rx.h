@@ -62,7 +62,7 @@ typedef struct rx_config {
   double D_ps_nm_km;       /* dispersion parameter D */
   double lambda_m;         /* carrier wavelength (1550e-9) */
   double rrc_rolloff;      /* RRC matched filter roll-off folded into H; < 0: none */
-  int fft_n;               /* OLS FFT size (power of two, 1024..16384); 0: auto */
+  int fft_n;               /* OLS FFT size (power of two, 1024..32768); 0: auto */
   int cd_halo;             /* OLS overlap M-1 in samples (even); 0: 1.1 x CD memory */
   int mimo_taps;           /* T, odd, 3..31 */
   int bps_angles;          /* B: 32 or 64 */
@@ -302,7 +302,7 @@ int rx_decide_block_noalloc(const void* y, int64_t n, int modulation, int bps_an
  * Picks the overlap-save FFT size for cfg on this GPU.  A larger N wastes a
  * smaller halo fraction h / N but costs more per output sample; the paper
  * fixes its block geometry for its own GPU (Sec. II).  Every admissible N
- * (a power of two in [1024, 16384] with N - halo >= 256) runs cfg's whole
+ * (a power of two in [1024, 32768] with N - halo >= 256) runs cfg's whole
  * chain on a zero stream (BER off): two frames untimed (the first, with the
  * acquisition, completes), then `frames` frames (1..64) timed; the fastest goes to *fft_n and its
  * time per 2^20 samples per polarisation to *ms_per_msample (may be NULL).  Creates and frees one

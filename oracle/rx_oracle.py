@@ -123,7 +123,9 @@ def beta2(cfg: RxConfig) -> float:
 def geometry(cfg: RxConfig) -> Geometry:
     """OLS sizes.  CD memory = |D| L (lambda^2 Rs (1+rho) / c) fs samples;
     halo M-1 = ceil(1.1 * memory) rounded up to even; N = smallest power of
-    two >= max(1024, 4 (M-1)), at most 16384, unless given."""
+    two >= max(1024, 4 (M-1)), at most 16384, doubled to 32768 when 16384
+    points would keep less than half of each block (M-1 > 8192), unless
+    given."""
     fs = 2.0 * cfg.baud_hz
     rho = max(cfg.rrc_rolloff, 0.0)
     D = abs(cfg.D_ps_nm_km) * 1e-6
@@ -137,6 +139,8 @@ def geometry(cfg: RxConfig) -> Geometry:
     else:
         N = 1024
         while N < 4 * halo and N < 16384:
+            N *= 2
+        if 2 * halo > N:
             N *= 2
     if N - halo < 2:
         raise ValueError("fft_n too small for the CD halo")

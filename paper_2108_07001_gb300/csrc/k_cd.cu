@@ -23,6 +23,8 @@
 // and the Godard sum ride on the last forward pass, and the last inverse
 // pass writes z and the periodogram input directly, so each transform
 // makes one shared-memory round trip fewer per end.
+#include <cooperative_groups.h>
+
 #include "fft_smem.cuh"
 
 namespace rx {
@@ -230,6 +232,251 @@ __global__ void __launch_bounds__(NT) cd_ols_batch_kernel(BView v, int pass) {
   cd_ols_body<N, NT, STOR>(f.d, pass ? f.fa : f.fe, vb);
 }
 
+// ---- 32768-point overlap-save on a cluster of two CTAs -------------------
+//
+// The 32768-point complex array (256 KB) is larger than one CTA's shared
+// memory, so each OLS block is a cluster of two CTAs holding half of the
+// transform each, joined by distributed shared memory.  Radix-2 splits at
+// both ends make the halves independent 16384-point transforms:
+//   forward (decimation in frequency): CTA 0 transforms u[i] = x[i] +
+//   x[i + N/2], giving the even bins X[2k]; CTA 1 transforms
+//   v[i] = (x[i] - x[i + N/2]) W_N^i, giving the odd bins X[2k + 1] (each
+//   CTA reads both halves of the window from the ring);
+//   filter, Godard sum: bin pairs (k, k + N/2) have equal parity, so each
+//   CTA sums over its own bins;
+//   inverse: CTA 0 holds E = IDFT_{N/2}(even bins), CTA 1 O = IDFT_{N/2}(odd
+//   bins), and z[n] = E[n mod N/2] +- W_N^{-n mod N/2} O[n mod N/2] (+ for
+//   n < N/2): each CTA forms the kept samples of its half, reading the
+//   other half-transform from its peer's shared memory;
+//   periodogram (N/2 = 16384 points): both CTAs place the 4th powers in
+//   both CTAs' buffers, then split once more (CTA 0 even bins, CTA 1 odd
+//   bins of two 8192-point transforms).
+// Every cluster barrier is reached by both CTAs on every path (their
+// branch conditions depend only on the block and the frame).
+constexpr int kCdN2 = 16384;  // half-transform per CTA
+constexpr int kCdNT2 = 1024;
+
+template <int STOR>
+__device__ __forceinline__ void cd_ols2_body(const RxDev& d, const FrameArgs& fa, VBlock vb) {
+  namespace cg = cooperative_groups;
+  constexpr int N2 = kCdN2, NT = kCdNT2;
+  extern __shared__ float2 buf[];
+  __shared__ float scratch[NT / 32];
+  __shared__ float2 tw_s[2 * kTwSplit];  // twiddles of the 16384-point half-transforms
+  __shared__ float2 tn_s[2 * kTwSplit];  // W_32768^m, m < 16384
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  float2* peer = cl.map_shared_rank(buf, rank ^ 1);
+  for (int i = threadIdx.x; i < 2 * kTwSplit; i += NT) {
+    tn_s[i] = d.tw2[i];
+    tw_s[i] = d.tw2[2 * kTwSplit + i];
+  }
+  __syncthreads();
+  const int pol = vb.y;
+  const long long a = fa.s0 + (long long)(vb.x >> 1) * d.L;
+  const long long zlen_f = 2LL * fa.Ff + 2 * d.c;
+  const int keep = (int)min((long long)d.L, fa.s0 + zlen_f - a);
+  const long long lo = a - d.h;
+  const long long rbase = (long long)pol * d.ring_cap;
+  long long r0 = lo % d.ring_cap;
+  if (r0 < 0) r0 += d.ring_cap;
+  auto sample = [&](int i) -> float2 {  // window sample i (zero outside the stream)
+    const long long n = lo + i;
+    long long slot = r0 + i;
+    if (slot >= d.ring_cap) slot -= d.ring_cap;
+    return (n >= 0 && n < fa.n_valid) ? load_sample(d.ring, STOR, rbase + slot) : make_float2(0.f, 0.f);
+  };
+
+  // first forward pass (radix 16) of the half-transform, fused with the
+  // split: butterfly j takes local samples j + r N2/16
+  {
+    const int j = threadIdx.x;
+    float2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int i = j + r * (N2 / 16);
+      const float2 x0 = sample(i), x1 = sample(i + N2);
+      v[r] = rank == 0 ? cadd(x0, x1) : cmul(csub(x0, x1), twiddle(tn_s, i));
+    }
+    dft<16, false>(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[swz(16 * j + r)] = v[r];
+  }
+  __syncthreads();
+  constexpr int NSL = last_ns<N2>();
+  constexpr int RL = N2 / NSL;
+  constexpr int PERL = (NSL + NT - 1) / NT;
+  fft_passes<N2, NT, 16, NSL, false>(buf, tw_s, 1);
+
+  // last forward pass, filter (global bin 2k + rank) and Godard sum over
+  // the local pairs (k, k + N2/2) = global (k, k + N/2)
+  float gr = 0.f, gi = 0.f;
+  {
+    float2 v[PERL][RL];
+#pragma unroll
+    for (int u = 0; u < PERL; ++u) {
+      const int j = threadIdx.x + u * NT;
+      if ((NSL % NT) == 0 || j < NSL) {
+#pragma unroll
+        for (int r = 0; r < RL; ++r) v[u][r] = buf[swz(j + r * NSL)];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PERL; ++u) {
+      const int j = threadIdx.x + u * NT;
+      if ((NSL % NT) == 0 || j < NSL) {
+        pass_butterfly<N2, RL, NSL, false>(v[u], j, tw_s, 1);
+#pragma unroll
+        for (int r = 0; r < RL; ++r) v[u][r] = cmul(v[u][r], __ldg(&d.Hf[2 * (j + r * NSL) + rank]));
+#pragma unroll
+        for (int r = 0; r < RL / 2; ++r) {
+          const float2 p = cmulc(v[u][r], v[u][r + RL / 2]);
+          gr += p.x;
+          gi += p.y;
+        }
+        if (!fa.est_only) {
+#pragma unroll
+          for (int r = 0; r < RL; ++r) buf[swz(j + r * NSL)] = v[u][r];
+        }
+      }
+    }
+  }
+  gr = block_sum<NT>(gr, scratch);
+  gi = block_sum<NT>(gi, scratch);
+  if (threadIdx.x == 0) {
+    const float sg = (lo & 1) ? -1.f : 1.f;
+    FrameAcc* acc = d.acc + fa.acc_slot;
+    atomicAdd(&acc->C[0], (double)(sg * gr));
+    atomicAdd(&acc->C[1], (double)(sg * gi));
+  }
+  if (fa.est_only) return;  // both CTAs: no shared memory of the peer was touched
+  fft_passes<N2, NT, 1, NSL, true>(buf, tw_s, 1);
+  {  // last inverse pass: the half-transform E (rank 0) or O (rank 1) stays in place
+    float2 v[PERL][RL];
+#pragma unroll
+    for (int u = 0; u < PERL; ++u) {
+      const int j = threadIdx.x + u * NT;
+      if ((NSL % NT) == 0 || j < NSL) {
+#pragma unroll
+        for (int r = 0; r < RL; ++r) v[u][r] = buf[swz(j + r * NSL)];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PERL; ++u) {
+      const int j = threadIdx.x + u * NT;
+      if ((NSL % NT) == 0 || j < NSL) {
+        pass_butterfly<N2, RL, NSL, true>(v[u], j, tw_s, 1);
+#pragma unroll
+        for (int r = 0; r < RL; ++r) buf[swz(j + r * NSL)] = v[u][r];
+      }
+    }
+  }
+  cl.sync();  // both half-transforms complete
+
+  // kept samples of this CTA's half: window index n = rank N2 + m
+  float2* zp = d.z + (long long)pol * d.zlen + (a - fa.s0);
+  const long long lo_n = max(a, fa.f0), hi_n = min(a + keep, fa.f1);
+  const long long e0 = lo_n + (lo_n & 1);
+  const int cnt = hi_n > e0 ? (int)((hi_n - e0 + 1) / 2) : 0;
+  const int off = d.h + (int)(e0 - a);  // window index of sample e0
+  constexpr int PM = N2 / NT;
+  float pw = 0.f;
+#pragma unroll 4
+  for (int k = 0; k < PM; ++k) {
+    const int m = threadIdx.x + k * NT;
+    const int o = rank * N2 + m;
+    if (o >= d.h && o < d.h + keep) {
+      const float2 own = buf[swz(m)], oth = peer[swz(m)];
+      const float2 E = rank ? oth : own, O = rank ? own : oth;
+      float2 w = twiddle(tn_s, m);
+      w.y = -w.y;  // W_N^{-m}
+      const float2 t = cmul(w, O);
+      const float2 x = rank ? csub(E, t) : cadd(E, t);
+      zp[o - d.h] = x;
+      const long long n = a + (o - d.h);
+      if (n >= fa.f0 && n < fa.f1) pw += x.x * x.x + x.y * x.y;
+    }
+  }
+  pw = block_sum<NT>(pw, scratch);
+  if (threadIdx.x == 0) atomicAdd(&d.acc[fa.acc_slot].P, (double)pw);
+  cl.sync();  // the peer has read this CTA's half-transform
+  if (cnt == 0) return;  // both CTAs
+
+  // periodogram input in both CTAs' buffers: slots [0, cnt) are written
+  // (each by the CTA that owns the sample, into both buffers), the rest are
+  // zero; the two sets are disjoint, so the zeroing needs no barrier
+  for (int i = cnt + threadIdx.x; i < N2; i += NT) buf[swz(i)] = make_float2(0.f, 0.f);
+  // the 4th powers of the even in-frame samples this thread wrote to z
+  // (read back from its own stores) go to slot (n - e0) / 2
+#pragma unroll 4
+  for (int k = 0; k < PM; ++k) {
+    const int o = rank * N2 + threadIdx.x + k * NT;
+    const int q = o - off;
+    if (o >= d.h && o < d.h + keep && q >= 0 && (q & 1) == 0 && (q >> 1) < cnt) {
+      const float2 x = zp[o - d.h];
+      const float2 x2 = make_float2(x.x * x.x - x.y * x.y, 2.f * x.x * x.y);
+      const float2 x4 = make_float2(x2.x * x2.x - x2.y * x2.y, 2.f * x2.x * x2.y);
+      buf[swz(q >> 1)] = x4;
+      peer[swz(q >> 1)] = x4;
+    }
+  }
+  cl.sync();  // every slot written; no access to the peer's memory after this
+  // split of the 16384-point periodogram transform: rank 0 even bins, rank 1 odd
+  constexpr int NP = N2 / 2;
+#pragma unroll
+  for (int k = 0; k < NP / NT; ++k) {
+    const int s = threadIdx.x + k * NT;
+    const float2 x0 = buf[swz(s)], x1 = buf[swz(s + NP)];
+    buf[swz(s)] = rank == 0 ? cadd(x0, x1) : cmul(csub(x0, x1), twiddle(tw_s, s));
+  }
+  __syncthreads();
+  constexpr int NSP = last_ns<NP>();
+  constexpr int RP = NP / NSP;
+  constexpr int PERP = (NSP + NT - 1) / NT;
+  fft_passes<NP, NT, 1, NSP, false>(buf, tw_s, 2);
+  double* psd = d.psd + (long long)fa.acc_slot * (d.N / 2);
+  {
+    float2 v[PERP][RP];
+#pragma unroll
+    for (int u = 0; u < PERP; ++u) {
+      const int j = threadIdx.x + u * NT;
+      if ((NSP % NT) == 0 || j < NSP) {
+#pragma unroll
+        for (int r = 0; r < RP; ++r) v[u][r] = buf[swz(j + r * NSP)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PERP; ++u) {
+      const int j = threadIdx.x + u * NT;
+      if ((NSP % NT) == 0 || j < NSP) {
+        pass_butterfly<NP, RP, NSP, false>(v[u], j, tw_s, 2);
+#pragma unroll
+        for (int r = 0; r < RP; ++r)
+          atomicAdd(&psd[2 * (j + r * NSP) + rank], (double)(v[u][r].x * v[u][r].x + v[u][r].y * v[u][r].y));
+      }
+    }
+  }
+}
+
+// Grid x = 2 x OLS blocks (a cluster per block), y = polarisation.
+template <int STOR>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kCdNT2) cd_ols2_kernel(RxDev d, FrameArgs fa) {
+  cd_ols2_body<STOR>(d, fa, own_block());
+}
+
+// Batched: the launch list gives every frame an even number of blocks, so
+// the two CTAs of a cluster always fall on the same frame.
+template <int STOR>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kCdNT2) cd_ols2_batch_kernel(BView v, int pass) {
+  int fi;
+  VBlock vb;
+  if (!batch_block(v, fi, vb)) return;  // both CTAs of a cluster (even offsets)
+  const BFrame& f = v.frames[fi];
+  cd_ols2_body<STOR>(f.d, pass ? f.fa : f.fe, vb);
+}
+
 // x reduced to [-pi, pi] in FP64 (x - 2 pi rint(x / 2 pi)).
 __device__ __forceinline__ double wrap_pi(double x) {
   constexpr double kTwoPi = 6.283185307179586477, kInvTwoPi = 0.15915494309189533577;
@@ -415,6 +662,27 @@ static cudaError_t cd_attr_n() {
   return e;
 }
 
+static cudaError_t launch_cd2(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
+  const long long zlen_f = 2LL * fa.Ff + 2 * d.c;
+  const int nblk = (int)((zlen_f + d.L - 1) / d.L);
+  const size_t smem = sizeof(float2) * kCdN2;
+  dim3 grid(2 * nblk, 2);
+  if (d.storage == 2) cd_ols2_kernel<2><<<grid, kCdNT2, smem, s>>>(d, fa);
+  else cd_ols2_kernel<1><<<grid, kCdNT2, smem, s>>>(d, fa);
+  return cudaGetLastError();
+}
+
+static cudaError_t cd2_attr() {
+  const int smem = (int)(sizeof(float2) * kCdN2);
+  cudaError_t e = cudaFuncSetAttribute(cd_ols2_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(cd_ols2_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(cd_ols2_batch_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(cd_ols2_batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
+
 // Opt-in to the dynamic shared memory of every FFT size (once per process).
 cudaError_t cd_set_attributes() {
   cudaError_t e = cd_attr_n<1024, 256>();
@@ -422,6 +690,7 @@ cudaError_t cd_set_attributes() {
   if (e == cudaSuccess) e = cd_attr_n<4096, 256>();
   if (e == cudaSuccess) e = cd_attr_n<8192, 512>();
   if (e == cudaSuccess) e = cd_attr_n<16384, 1024>();
+  if (e == cudaSuccess) e = cd2_attr();
   return e;
 }
 
@@ -432,6 +701,7 @@ cudaError_t launch_cd(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
     case 4096: return launch_cd_n<4096, 256>(d, fa, s);
     case 8192: return launch_cd_n<8192, 512>(d, fa, s);
     case 16384: return launch_cd_n<16384, 1024>(d, fa, s);
+    case 32768: return launch_cd2(d, fa, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -447,7 +717,8 @@ cudaError_t launch_est(const RxDev& d, const FrameArgs& fa, int mode, cudaStream
 
 int cd_grid_x(const RxDev& d, const FrameArgs& fa) {
   const long long zlen_f = 2LL * fa.Ff + 2 * d.c;
-  return (int)((zlen_f + d.L - 1) / d.L);
+  const int nblk = (int)((zlen_f + d.L - 1) / d.L);
+  return d.N == 32768 ? 2 * nblk : nblk;  // a cluster of two CTAs per block at N = 32768
 }
 
 template <int N, int NT>
@@ -467,6 +738,12 @@ cudaError_t launch_cd_batch(const RxDev& d, const BView& v, int blocks, int pass
     case 4096: return launch_cd_batch_n<4096, 256>(d, v, blocks, pass, s);
     case 8192: return launch_cd_batch_n<8192, 512>(d, v, blocks, pass, s);
     case 16384: return launch_cd_batch_n<16384, 1024>(d, v, blocks, pass, s);
+    case 32768: {
+      const size_t smem = sizeof(float2) * kCdN2;
+      if (d.storage == 2) cd_ols2_batch_kernel<2><<<blocks, kCdNT2, smem, s>>>(v, pass);
+      else cd_ols2_batch_kernel<1><<<blocks, kCdNT2, smem, s>>>(v, pass);
+      return cudaGetLastError();
+    }
     default: return cudaErrorInvalidValue;
   }
 }

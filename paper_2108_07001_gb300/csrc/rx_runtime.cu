@@ -646,8 +646,9 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   if (N <= 0) {
     N = 1024;
     while (N < 4 * halo && N < 16384) N *= 2;
+    if (2 * halo > N) N *= 2;  // 16384 points would keep less than half of each block: 32768
   }
-  if (N < 1024 || N > 16384 || (N & (N - 1))) { delete h; return fail(RX_EINVAL, "fft_n must be a power of two in [1024, 16384]"); }
+  if (N < 1024 || N > 32768 || (N & (N - 1))) { delete h; return fail(RX_EINVAL, "fft_n must be a power of two in [1024, 32768]"); }
   if (N - halo < 256) { delete h; return fail(RX_EINVAL, "CD halo too long for the FFT size (need N - halo >= 256)"); }
   {
     int ndev = 0;
@@ -715,7 +716,7 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   RX_AL(d.Hs, N);
   RX_AL(d.Hf, N);
   RX_AL(d.tw, N);
-  RX_AL(d.tw2, 256);
+  RX_AL(d.tw2, 512);  // [N table | N/2 table]: the 32768-point form's half-transforms use the second
   RX_AL(d.z, (long long)kZSlots * 2 * d.zlen);
   RX_AL(d.rot_hi, (long long)kZSlots * (d.zlen / kRotLo + 2));
   RX_AL(d.rot_lo, (long long)kZSlots * kRotLo);
@@ -766,13 +767,16 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
     cudaMemcpy(d.Hs, Hs.data(), N * sizeof(float2), cudaMemcpyHostToDevice);
     cudaMemcpy(d.Hf, Hs.data(), N * sizeof(float2), cudaMemcpyHostToDevice);
     cudaMemcpy(d.tw, tw.data(), N * sizeof(float2), cudaMemcpyHostToDevice);
-    std::vector<float2> tw2(256);
-    for (int i = 0; i < 128; ++i) {
-      const double ah = -2.0 * M_PI * (double)(i * 128) / N, al = -2.0 * M_PI * (double)i / N;
-      tw2[i] = make_float2((float)std::cos(ah), (float)std::sin(ah));
-      tw2[128 + i] = make_float2((float)std::cos(al), (float)std::sin(al));
+    std::vector<float2> tw2(512);
+    for (int t = 0; t < 2; ++t) {
+      const double Nt = (double)N / (1 << t);
+      for (int i = 0; i < 128; ++i) {
+        const double ah = -2.0 * M_PI * (double)(i * 128) / Nt, al = -2.0 * M_PI * (double)i / Nt;
+        tw2[256 * t + i] = make_float2((float)std::cos(ah), (float)std::sin(ah));
+        tw2[256 * t + 128 + i] = make_float2((float)std::cos(al), (float)std::sin(al));
+      }
     }
-    cudaMemcpy(d.tw2, tw2.data(), 256 * sizeof(float2), cudaMemcpyHostToDevice);
+    cudaMemcpy(d.tw2, tw2.data(), 512 * sizeof(float2), cudaMemcpyHostToDevice);
   }
   // PRBS jump matrices A^(2^i): A shifts the window down one bit and sets
   // bit 30 = bit 3 ^ bit 0.

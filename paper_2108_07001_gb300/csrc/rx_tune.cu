@@ -70,7 +70,7 @@ extern "C" int rx_autotune_fft(const rx_config* cfg, int frames, int* fft_n, dou
   }
   const int halo = rx::cd_halo_samples(cfg);
   std::vector<int> cand;
-  for (int N = 1024; N <= 16384; N *= 2)
+  for (int N = 1024; N <= 32768; N *= 2)
     if (N - halo >= 256) cand.push_back(N);
   if (cand.empty()) {
     rx::set_last_error("rx_autotune_fft: CD halo too long for every FFT size");

@@ -167,7 +167,7 @@ def test_autotune_argument_checks_without_device(lib):
     cfg = rx.default_config()
     assert lib.rx_autotune_fft(None, 3, ctypes.byref(n), None) == rx.RX_EINVAL
     assert lib.rx_autotune_fft(ctypes.byref(cfg), 0, ctypes.byref(n), None) == rx.RX_EINVAL
-    far = rx.default_config(fiber_len_m=100000e3)  # halo longer than any FFT size
+    far = rx.default_config(fiber_len_m=200000e3)  # halo (~50k samples) longer than any FFT size
     assert lib.rx_autotune_fft(ctypes.byref(far), 3, ctypes.byref(n), None) == rx.RX_EINVAL
     assert b"halo" in lib.rx_last_error()
 

@@ -34,6 +34,9 @@ def stream_case(kind, seed):
     elif kind == "qpsk3000_fft8192":
         link = dict(baud_hz=32e9, bits_per_sym=2, n_sym=3 * F + 77, fiber_len_m=3000e3, snr_db=11.0)
         cfg = dict(baud_hz=32e9, modulation=2, fiber_len_m=3000e3, fft_n=8192)
+    elif kind == "qpsk64_fft32768":
+        link = dict(baud_hz=64e9, bits_per_sym=2, n_sym=3 * F + 1000, fiber_len_m=4000e3, snr_db=13.0)
+        cfg = dict(baud_hz=64e9, modulation=2, fiber_len_m=4000e3, fft_n=32768)
     elif kind == "qpsk_two_stage_fp16":
         link = dict(baud_hz=28e9, bits_per_sym=2, n_sym=5 * F, fiber_len_m=1500e3, snr_db=12.0)
         cfg = dict(baud_hz=28e9, modulation=2, fiber_len_m=1500e3, bps_coarse_stride=4,
@@ -60,7 +63,7 @@ def stream_case(kind, seed):
     return cfg, blocks, n_sym
 
 
-KINDS = ("qpsk1000", "qpsk3000_fft8192", "qpsk_two_stage_fp16", "qam16")
+KINDS = ("qpsk1000", "qpsk3000_fft8192", "qpsk_two_stage_fp16", "qam16", "qpsk64_fft32768")
 
 
 @pytest.fixture(scope="module")

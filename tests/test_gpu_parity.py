@@ -244,7 +244,7 @@ def test_autotuned_fft_size_is_admissible_and_keeps_parity():
     rx_kw = dict(fiber_len_m=3000e3, frame_syms=1 << 14, prbs_seed=41, cma_syms=8192, acq_syms=12288,
                  ber_skip_syms=4096)
     n, ms = rx.autotune_fft(rx.default_config(**rx_kw), frames=2)
-    assert n in (1024, 2048, 4096, 8192, 16384) and ms > 0
+    assert n in (1024, 2048, 4096, 8192, 16384, 32768) and ms > 0
     sim = rxsim.simulate(link(n_sym=1 << 15, snr_db=12.0, fiber_len_m=3000e3, prbs_seed=41, seed=41))
     kw = dict(rx_kw, fft_n=n)
     gpu, r = run_gpu(sim["rx"], kw)
@@ -335,18 +335,51 @@ def test_headline_stream_parity_two_frames():
     r.close()
 
 
-def test_64gbd_10000km_parity():
-    """64 GBd over 10,000 km: a CD halo of ~12k samples in a 16384-point
-    block, the largest halo fraction the overlap-save kernel meets; two
-    frames of 2^17 symbols pushed in 2^16-symbol blocks."""
+@pytest.mark.parametrize("fft_n", [0, 16384], ids=["default_32768", "fft_16384"])
+def test_64gbd_10000km_parity(fft_n):
+    """64 GBd over 10,000 km, a CD halo of ~13.5k samples: the default rule
+    takes the 32768-point transform (a cluster of two CTAs per block, ~59 %
+    of each block kept); forced to 16384 points, the largest halo fraction
+    the single-CTA kernel meets (~18 % kept).  Two frames of 2^17 symbols
+    pushed in 2^16-symbol blocks."""
+    from oracle import rx_oracle as O
     n_sym = 1 << 18
     sim = rxsim.simulate(link(baud_hz=64e9, n_sym=n_sym, fiber_len_m=10000e3, snr_db=12.0, prbs_seed=64,
                               seed=6400, out_dtype="c64"))
-    rx_kw = dict(baud_hz=64e9, fiber_len_m=10000e3, frame_syms=1 << 17, prbs_seed=64)
+    rx_kw = dict(baud_hz=64e9, fiber_len_m=10000e3, frame_syms=1 << 17, prbs_seed=64, fft_n=fft_n)
+    assert O.geometry(O.RxConfig(**workloads.oracle_kwargs(rx_kw))).N == (fft_n or 32768)
     gpu, r = run_gpu(sim["rx"], rx_kw, pushes=[1 << 17] * (2 * n_sym >> 17))
     ref = run_oracle(sim["rx"], rx_kw)
     rep = compare(gpu, ref, rx_kw)
     st, b = gpu["stats"], ref["ber"]
     assert st["bits"] == b["bits"] and st["cycle_slips"] == b["slips"]
     assert abs(int(st["bit_errors"]) - b["errors"]) <= 2 * rep.get("bit_mismatch_syms", 0)
+    tr = gpu["trace"]
+    assert np.allclose(tr[:, 0], ref["trace"]["tau"], atol=1e-4 / 64e9)
+    assert np.allclose(tr[:, 1], ref["trace"]["dfo"], atol=2e3)
+    assert np.allclose(tr[:, 2], ref["trace"]["gain"], rtol=1e-5)
+    r.close()
+
+
+def test_32768_point_transform_ragged_pushes_fp16():
+    """The two-CTA 32768-point form with irregular pushes, FP16 storage and
+    three frames plus a ragged tail (the last block of each frame partial,
+    the stream edge zero-padded)."""
+    F = 1 << 14
+    n_sym = 3 * F + 3333
+    sim = rxsim.simulate(link(baud_hz=56e9, n_sym=n_sym, fiber_len_m=6000e3, snr_db=13.0, prbs_seed=56, seed=5600,
+                              out_dtype="c16"))
+    rx_kw = dict(baud_hz=56e9, fiber_len_m=6000e3, frame_syms=F, acq_syms=F, cma_syms=8192, prbs_seed=56,
+                 ber_skip_syms=8192, sync_syms=2048, fft_n=32768, storage_dtype=2)
+    n = sim["rx"].shape[1]
+    pushes, left = [], n
+    rng = np.random.default_rng(56)
+    while left:
+        m = int(min(left, rng.integers(1000, 40000)))
+        pushes.append(m)
+        left -= m
+    gpu, r = run_gpu(sim["rx"], rx_kw, pushes=pushes)
+    ref = run_oracle(sim["rx"], rx_kw)
+    compare(gpu, ref, rx_kw)
+    assert gpu["stats"]["bits"] == ref["ber"]["bits"]
     r.close()

@@ -78,6 +78,25 @@ def test_ols_exact_for_filters_inside_the_halo():
     assert np.max(np.abs(out2 - ref2)) < 1e-12
 
 
+def test_default_fft_size_rule():
+    """N = smallest power of two >= max(1024, 4 halo), at most 16384, and
+    32768 when 16384 points would keep less than half of each block: the
+    28 GBd 10,000 km link (halo ~2.5k) takes 16384 points; 64 GBd over
+    10,000 km (halo ~13.5k) takes 32768 and keeps ~59 % of each block
+    (~18 % at 16384 points); 56 GBd over 7,000 km (halo ~7.2k, more than
+    half of 16384 kept) stays at 16384; short links stay at 1024."""
+    g28 = O.geometry(O.RxConfig(baud_hz=28e9, fiber_len_m=10000e3))
+    g64 = O.geometry(O.RxConfig(baud_hz=64e9, fiber_len_m=10000e3))
+    g1 = O.geometry(O.RxConfig(baud_hz=28e9, fiber_len_m=100e3))
+    g48 = O.geometry(O.RxConfig(baud_hz=56e9, fiber_len_m=7000e3))
+    assert g48.N == 16384 and 8192 > g48.halo > 4096
+    assert g28.N == 16384 and 4 * g28.halo > 8192
+    assert g64.N == 32768 and g64.L / g64.N > 0.55 and (16384 - g64.halo) / 16384 < 0.2
+    assert g1.N == 1024
+    for g in (g28, g64, g1, g48):
+        assert g.N >= min(4 * g.halo, 16384) and 2 * g.halo <= g.N and g.halo % 2 == 0 and g.L == g.N - g.halo
+
+
 def test_paper_ols_geometry_golden():
     """Sec. II: a 2^22-sample buffer, 1024-point FFTs, 100 % overlap (512 new
     per block) gives 8192 blocks."""
