@@ -133,11 +133,12 @@ def profiled_traffic(kernel):
     return None
 
 
-def workload(stride=1):
-    """The stream workload; stride > 1 selects the two-stage blind phase
-    search over bps_angles / stride coarse angles."""
+def workload(stride=1, name=None):
+    """The stream workload (default: the 28 GBd 10,000 km stream); stride > 1
+    selects the two-stage blind phase search over bps_angles / stride coarse
+    angles."""
     from paper_2108_07001_gb300 import workloads
-    wl = workloads.DP_QPSK_10000KM_STREAM
+    wl = workloads.STREAMS[name] if name else workloads.DP_QPSK_10000KM_STREAM
     if stride > 1:
         wl = dict(wl, rx=dict(wl["rx"], bps_coarse_stride=stride))
     return wl
@@ -165,7 +166,7 @@ def run_ours(args):
     import torch
     from paper_2108_07001_gb300 import rx
 
-    wl = workload(args.bps_coarse_stride)
+    wl = workload(args.bps_coarse_stride, args.stream)
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
     if args.fft_n:  # an FFT size, or -1: the one rx_autotune_fft picks on this GPU
@@ -358,9 +359,30 @@ def run_ours(args):
                   gpu_launches, clocks, host0, host1, gen_s, e2e)
 
 
+def chain_dram(n_sym, bits_per_sym, ms_step, hbm_peak):
+    """Whole-chain DRAM bytes of a step, from the ncu capture in
+    profiles/traffic.txt ('chain': every kernel of one 2^20-symbol frame,
+    caches not flushed between kernels), scaled to the step's frames,
+    beside the algorithmic bytes (complex64 input read once, decided bits
+    written once); None once the kernel sources changed since the capture."""
+    per_frame = profiled_traffic("chain")
+    alg = 4 * n_sym * 8 + n_sym * 2 * bits_per_sym / 8
+    out = {"algorithmic_bytes_per_step": int(alg), "source": "profiles/ingest_and_chain_traffic_dp-qpsk-10000km.md"}
+    if per_frame is None:
+        out["measured_bytes_per_step"] = None
+        return out
+    meas = per_frame * n_sym / (1 << 20)
+    out["measured_bytes_per_step"] = int(meas)
+    out["measured_over_algorithmic"] = round(meas / alg, 2)
+    out["measured_gbs"] = round(meas / (ms_step * 1e-3) / 1e9, 1)
+    if hbm_peak:
+        out["measured_frac_of_hbm"] = round(meas / (ms_step * 1e-3) / 1e9 / hbm_peak, 4)
+    return out
+
+
 def finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, other_ms,
            gpu_launches, clocks, host0, host1, gen_s, e2e):
-    cpu = cpu_baseline(args.bps_coarse_stride) if args.cpu_baseline else None
+    cpu = cpu_baseline(args.bps_coarse_stride, wl["name"]) if args.cpu_baseline else None
     batched = batched_fp16_summary(measured_peaks().get("hbm_gbs")) if args.batched else None
     line = {
         "metric": "gsamples_per_s", "value": round(value, 3), "unit": "Gsamples/s",
@@ -383,7 +405,7 @@ def finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, o
         "roofline": roof, "stages": stages, "other_stage_ms": other_ms,
         "stage_timing": "per-stage CUDA events on a second, profiled handle over the same timed protocol",
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
-        "batched_fp16": batched,
+        "batched_fp16": batched, "dram": chain_dram(n_sym, cfg.modulation, ms_step, measured_peaks().get("hbm_gbs")),
         "host_launch_s_per_step": round((host1 - host0) / args.steps, 4), "sim_seconds": round(gen_s, 1),
     }
     r.close()
@@ -451,8 +473,8 @@ def oracle_times(n_sym, reps, stride=1):
 CPU_BASELINE_SYMS = 1 << 20  # one full frame, acquisition included (10-30 s of one core)
 
 
-def cpu_baseline(stride=1):
-    t = oracle_times(CPU_BASELINE_SYMS, 1, stride)[0]
+def cpu_baseline(stride=1, name=None):
+    t = oracle_run(CPU_BASELINE_SYMS, 1, name, stride)["times"][0]
     v = 4 * CPU_BASELINE_SYMS / t / 1e9
     return {"value": round(v, 6), "unit": "Gsamples/s", "cores": 1, "host_cores": os.cpu_count(),
             "kind": "oracle",
@@ -1382,6 +1404,9 @@ def main():
                     help="stream workload: overlap-save FFT size (0: the default rule, -1: the autotuner's pick)")
     ap.add_argument("--batched-forms", default="all", choices=["all", "batch"],
                     help="batched workload: all forms, or the batched launch alone")
+    ap.add_argument("--stream", default=None,
+                    help="stream workload by name (default dp-qpsk-28gbd-10000km-stream-2^24sym; "
+                         "dp-qpsk-64gbd-10000km-stream: 64 GBd, the 32768-point transform)")
     ap.add_argument("--bps-coarse-stride", type=int, default=1,
                     help="stream workload: 4 = two-stage BPS over 16 coarse angles (default 1: all 64)")
     ap.add_argument("--workload", default="stream", choices=["stream", "qam16", "serving", "batched", "kk", "kk_batch", "kkrx_batch"],

@@ -1,9 +1,9 @@
 // Parts shared by the blind-phase-search kernels (full search in k_bps.cu,
 // two-stage search in k_bps2.cu): the unwrap increment, the per-run
-// decisions / unwrap sums / EVM sums, and the block epilogue whose last
-// block per polarisation turns the runs' unwrap sums into run start
-// counters (paper Sec. II: the carrier phase is followed across the whole
-// stream, so the pi/2 branch of every symbol depends on all before it).
+// decisions / unwrap sums / EVM sums, the block epilogue, and the unwrap
+// scan that turns the runs' unwrap sums into run start counters (paper
+// Sec. II: the carrier phase is followed across the whole stream, so the
+// pi/2 branch of every symbol depends on all before it).
 #pragma once
 
 #include "rx_internal.cuh"
@@ -56,20 +56,13 @@ __device__ __forceinline__ void bps_finish_run(const RxDev& d, const FrameArgs& 
 }
 
 // Block epilogue (every thread of the NT-thread block calls it, after its
-// warps' bps_finish_run calls): the block's EVM sums go to the statistics;
-// the last block of this polarisation to arrive (an atomic counter after a
-// fence; nothing waits) scans the runs' unwrap sums into each run's starting
-// counter and carries the last angle and counter to the next frame.
+// warps' bps_finish_run calls): the block's EVM sums go to the statistics.
 // evn / evd: the calling warp's sums (read on lane 0).
 template <int NT>
-__device__ __forceinline__ void bps_finish_block(const RxDev& d, int pol, int nruns, float evn, float evd,
-                                                 int nblk) {
+__device__ __forceinline__ void bps_finish_block(const RxDev& d, float evn, float evd) {
   constexpr int NW = NT / 32;
   __shared__ float red_s[NW][2];
-  __shared__ int part[NT];
-  __shared__ int am_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int stride = d.F / kRun + 4;
   if (lane == 0) {
     red_s[warp][0] = evn;
     red_s[warp][1] = evd;
@@ -86,21 +79,28 @@ __device__ __forceinline__ void bps_finish_block(const RxDev& d, int pol, int nr
       atomicAdd(&d.st->evm_den, (double)c);
     }
   }
-  // the lane-0 threads wrote the run sums and edges
-  if (lane == 0) __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) am_last = atomicAdd(&d.bps_done[pol], 1u) == (unsigned)nblk - 1;
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
+}
+
+// Unwrap scan of one polarisation's frame (one NT-thread block, after the
+// BPS of the frame and after the previous frame's scan, in stream order):
+// the runs' unwrap sums become each run's starting counter, and the last
+// angle and counter carry to the next frame.  Kept out of the BPS kernel,
+// so the BPS of consecutive frames depend on nothing of each other.
+template <int NT>
+__device__ __forceinline__ void unwrap_scan_body(const RxDev& d, const FrameArgs& fa, int pol) {
+  __shared__ int part[NT];
+  const long long n_dec = fa.k_b - fa.k_a;
+  const int nruns = (int)((n_dec + kRun - 1) / kRun);
+  if (nruns <= 0) return;
+  const int stride = d.F / kRun + 4;
   const int per = (nruns + NT - 1) / NT;
   const int r0 = threadIdx.x * per, r1 = min(r0 + per, nruns);
   const int b_last_prev = d.st->bhat_last[pol];
   int loc = 0;
   for (int r = r0; r < r1; ++r) {
-    const int bf = __ldcg(&d.run_edge[(pol * stride + r) * 2 + 0]);
-    const int bp = r == 0 ? b_last_prev : __ldcg(&d.run_edge[(pol * stride + r - 1) * 2 + 1]);
-    loc += (bp >= 0 ? unwrap_inc(bp, bf, d.B) : 0) + __ldcg(&d.run_int[pol * stride + r]);
+    const int bf = d.run_edge[(pol * stride + r) * 2 + 0];
+    const int bp = r == 0 ? b_last_prev : d.run_edge[(pol * stride + r - 1) * 2 + 1];
+    loc += (bp >= 0 ? unwrap_inc(bp, bf, d.B) : 0) + d.run_int[pol * stride + r];
   }
   part[threadIdx.x] = loc;
   __syncthreads();
@@ -113,17 +113,16 @@ __device__ __forceinline__ void bps_finish_block(const RxDev& d, int pol, int nr
   const int m_last = d.st->m_last[pol];
   int acc = m_last + (threadIdx.x > 0 ? part[threadIdx.x - 1] : 0);
   for (int r = r0; r < r1; ++r) {
-    const int bf = __ldcg(&d.run_edge[(pol * stride + r) * 2 + 0]);
-    const int bp = r == 0 ? b_last_prev : __ldcg(&d.run_edge[(pol * stride + r - 1) * 2 + 1]);
+    const int bf = d.run_edge[(pol * stride + r) * 2 + 0];
+    const int bp = r == 0 ? b_last_prev : d.run_edge[(pol * stride + r - 1) * 2 + 1];
     const int binc = bp >= 0 ? unwrap_inc(bp, bf, d.B) : 0;
     d.run_m0[pol * stride + r] = acc + binc;
-    acc += binc + __ldcg(&d.run_int[pol * stride + r]);
+    acc += binc + d.run_int[pol * stride + r];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     d.st->m_last[pol] = m_last + part[NT - 1];
-    d.st->bhat_last[pol] = __ldcg(&d.run_edge[(pol * stride + nruns - 1) * 2 + 1]);
-    d.bps_done[pol] = 0;
+    d.st->bhat_last[pol] = d.run_edge[(pol * stride + nruns - 1) * 2 + 1];
   }
 }
 

@@ -17,9 +17,10 @@
 // reduced with an integer min once per super-step of 2W+1 steps (QPSK with
 // 64 angles derives a lane's second angle from the rotation of its first,
 // see bps_kernel).  Runs that touch no
-// stream edge take no per-step predicate.  The last block of each
-// polarisation (found with an atomic counter after a fence; nothing waits)
-// turns the runs' unwrap sums into each run's starting counter.
+// stream edge take no per-step predicate.  A separate one-block-per-
+// polarisation kernel, queued before the demap, turns the runs' unwrap
+// sums into each run's starting counter (so the BPS of the next frame
+// need not wait for this one).
 #include "bps_common.cuh"
 
 namespace rx {
@@ -293,7 +294,7 @@ __device__ __forceinline__ void bps_body(const RxDev& d, const FrameArgs& fa, VB
   float evn, evd;
   bps_finish_run(d, fa, pol, run, nruns, kr, ract, bh_s[warp], cs_s,
                  [&](int ko) { return PAIR ? make_float2(ys4[W + ko].x, ys4[W + ko].y) : ys2[W + ko]; }, evn, evd);
-  bps_finish_block<256>(d, pol, nruns, evn, evd, vb.nx);
+  bps_finish_block<256>(d, evn, evd);
 }
 
 template <int B, int W, bool QAM16>
@@ -416,6 +417,19 @@ __device__ __forceinline__ void demap_body(const RxDev& d, const FrameArgs& fa, 
   (void)n_dec;
 }
 
+__global__ void __launch_bounds__(256) unwrap_scan_kernel(RxDev d, FrameArgs fa) {
+  unwrap_scan_body<256>(d, fa, blockIdx.x);
+}
+
+// Batched: virtual block x = polarisation of the frame.
+__global__ void __launch_bounds__(256) unwrap_scan_batch_kernel(BView v) {
+  int fi;
+  VBlock vb;
+  if (!batch_block(v, fi, vb)) return;
+  const BFrame& f = v.frames[fi];
+  unwrap_scan_body<256>(f.d, f.fa, vb.x);
+}
+
 __global__ void __launch_bounds__(128) demap_kernel(RxDev d, FrameArgs fa) {
   demap_body(d, fa, own_block());
 }
@@ -518,10 +532,18 @@ cudaError_t launch_demap_batch(const BView& v, int blocks, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_scan_batch(const BView& v, int blocks, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  unwrap_scan_batch_kernel<<<blocks, 256, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
+// The unwrap scan (one block per polarisation), then the demap.
 cudaError_t launch_unwrap_demap(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
   if (fa.k_b <= fa.k_a) return cudaSuccess;
   const long long n_dec = fa.k_b - fa.k_a;
   const int nruns = (int)((n_dec + kRun - 1) / kRun);
+  unwrap_scan_kernel<<<2, 256, 0, s>>>(d, fa);
   demap_kernel<<<nruns, 128, 0, s>>>(d, fa);
   return cudaGetLastError();
 }

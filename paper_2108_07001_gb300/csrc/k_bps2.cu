@@ -260,7 +260,7 @@ __device__ __forceinline__ void bps2_body(const RxDev& d, const FrameArgs& fa, V
     evn += en;
     evd += ed;
   }
-  bps_finish_block<128>(d, pol, nruns, evn, evd, vb.nx);
+  bps_finish_block<128>(d, evn, evd);
 }
 
 template <int W, bool QAM16>

@@ -32,7 +32,8 @@ using namespace rxrt;
 
 namespace {
 
-enum BStageId { BS_CD0, BS_EST0, BS_CD, BS_EST1, BS_ACQ, BS_MIMO, BS_BPS, BS_DEMAP, BS_REF0, BS_SYNC, BS_REF1, BS_BER, BS_N };
+enum BStageId { BS_CD0, BS_EST0, BS_CD, BS_EST1, BS_ACQ, BS_MIMO, BS_BPS, BS_SCAN, BS_DEMAP, BS_REF0, BS_SYNC, BS_REF1,
+                BS_BER, BS_N };
 
 // Work of one stream at one ordinal.
 struct BPlan {
@@ -171,6 +172,7 @@ void add_plan(rx_batch* b, char* base, int o, int fi, int c, const BPlan& p) {
   }
   if (fa.k_b > fa.k_a) {
     list_add(b, L(BS_BPS), fi, bps_grid_x(d, fa), 2 * bps_grid_x(d, fa));
+    list_add(b, L(BS_SCAN), fi, 2, 2);  // one block per polarisation
     list_add(b, L(BS_DEMAP), fi, demap_grid_x(fa), demap_grid_x(fa));
   }
   if (p.ber.sync) {
@@ -191,7 +193,7 @@ int join_stream(rx_handle* h, cudaStream_t cs, cudaStream_t batch_end) {
     RX_CK(cudaStreamWaitEvent(cs, h->ev_copy, 0));
   }
   if (h->own_work) {
-    cudaStream_t ss[4] = {h->s_front, h->s_mid, h->s_comp, h->s_ber};
+    cudaStream_t ss[5] = {h->s_front, h->s_mid, h->s_comp, h->s_comp2, h->s_ber};
     cudaEvent_t e = get_event(h);
     for (cudaStream_t x : ss) {
       RX_CK(cudaEventRecord(e, x));
@@ -236,6 +238,7 @@ int launch_ordinal(rx_batch* b, char* dbase, char* hbase, int o, int ps, cudaStr
         case BS_ACQ: e = launch_acquire_batch(d, v, blocks, cs); break;
         case BS_MIMO: e = launch_mimo_batch(d, v, blocks, cs); break;
         case BS_BPS: e = launch_bps_batch(d, v, blocks, cs); break;
+        case BS_SCAN: e = launch_scan_batch(v, blocks, cs); break;
         case BS_DEMAP: e = launch_demap_batch(v, blocks, cs); break;
         case BS_REF0: e = launch_ref_gen_batch(v, blocks, 0, cs); break;
         case BS_SYNC: e = launch_sync_batch(v, blocks, cs); break;

@@ -44,6 +44,7 @@ cudaError_t launch_acquire_batch(const RxDev& d, const BView& v, int blocks, cud
 cudaError_t launch_mimo_batch(const RxDev& d, const BView& v, int blocks, cudaStream_t s);
 cudaError_t launch_bps_batch(const RxDev& d, const BView& v, int blocks, cudaStream_t s);
 cudaError_t launch_demap_batch(const BView& v, int blocks, cudaStream_t s);
+cudaError_t launch_scan_batch(const BView& v, int blocks, cudaStream_t s);
 cudaError_t launch_ref_gen_batch(const BView& v, int blocks, int use_delay, cudaStream_t s);
 cudaError_t launch_sync_batch(const BView& v, int blocks, cudaStream_t s);
 cudaError_t launch_ber_batch(const BView& v, int blocks, cudaStream_t s);
@@ -95,7 +96,8 @@ struct rx_handle {
   cudaStream_t s_copy = nullptr;
   cudaStream_t s_front = nullptr;  // CD + estimator of each frame
   cudaStream_t s_mid = nullptr;    // acquisition and MIMO
-  cudaStream_t s_comp = nullptr;   // BPS ("back")
+  cudaStream_t s_comp = nullptr;   // BPS of even decide passes ("back")
+  cudaStream_t s_comp2 = nullptr;  // BPS of odd decide passes (consecutive frames' BPS overlap)
   cudaEvent_t ev_mid[2] = {};      // MIMO of a frame done (its y buffer written), by frame parity
   cudaEvent_t ev_bpsd[2] = {};     // BPS of a frame done (its y buffer free again), by frame parity
   cudaEvent_t ev_bpsp[2] = {};     // BPS of a decide pass done (its decision buffers written), by pass parity

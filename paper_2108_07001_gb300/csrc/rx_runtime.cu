@@ -142,6 +142,7 @@ void free_all(rx_handle* h) {
   if (h->ev_reset) cudaEventDestroy(h->ev_reset);
   if (h->s_copy) cudaStreamDestroy(h->s_copy);
   if (h->s_comp) cudaStreamDestroy(h->s_comp);
+  if (h->s_comp2) cudaStreamDestroy(h->s_comp2);
   if (h->s_mid) cudaStreamDestroy(h->s_mid);
   for (int i = 0; i < 2; ++i) {
     if (h->ev_mid[i]) cudaEventDestroy(h->ev_mid[i]);
@@ -256,6 +257,7 @@ cudaError_t sync_all(rx_handle* h) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_front);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_mid);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_comp);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_comp2);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_ber);
   return e;
 }
@@ -310,15 +312,21 @@ BerPlan plan_ber(rx_handle* h, const FrameArgs& fa, bool final_) {
 // BPS on the back stream, then unwrap/demap and the BER work on the BER
 // stream, so the next pass's BPS overlaps this pass's demap.  pf.ev_done
 // is recorded after the demap (the bits are out).
-int launch_decide(rx_handle* h, PendingFrame& pf, const FrameArgs& fa, bool final_) {
+int launch_decide(rx_handle* h, PendingFrame& pf, const FrameArgs& fa, bool final_, cudaEvent_t after,
+                  bool start_here) {
   const long long pass = h->n_decide;
   const int par = (int)(pass & 1);
   const RxDev d = decide_dev(h->d, pass);
+  // the BPS of consecutive passes run on two streams (nothing of one is
+  // read by the next: the unwrap scan runs with the demap)
+  cudaStream_t sp = par ? h->s_comp2 : h->s_comp;
+  RX_CK(cudaStreamWaitEvent(sp, after, 0));
+  if (start_here) RX_CK(cudaEventRecord(pf.ev_start, sp));
   // this pass's decision buffers were read by the demap of pass n - 2
-  if (pass >= 2) RX_CK(cudaStreamWaitEvent(h->s_comp, h->ev_dem[par], 0));
-  RX_STAGE(RX_STAGE_BPS, 1, h->s_comp, launch_bps(d, fa, h->s_comp));
-  if (fa.f >= 0) RX_CK(cudaEventRecord(h->ev_bpsd[fa.f & 1], h->s_comp));
-  RX_CK(cudaEventRecord(h->ev_bpsp[par], h->s_comp));
+  if (pass >= 2) RX_CK(cudaStreamWaitEvent(sp, h->ev_dem[par], 0));
+  RX_STAGE(RX_STAGE_BPS, 1, sp, launch_bps(d, fa, sp));
+  if (fa.f >= 0) RX_CK(cudaEventRecord(h->ev_bpsd[fa.f & 1], sp));
+  RX_CK(cudaEventRecord(h->ev_bpsp[par], sp));
   cudaStream_t sb = h->s_ber;
   RX_CK(cudaStreamWaitEvent(sb, h->ev_bpsp[par], 0));
   // (the decision ring slots it writes were read by the BER work of pass
@@ -459,8 +467,7 @@ int launch_frame(rx_handle* h, long long f, bool final_) {
   RX_CK(cudaEventRecord(h->ev_mid[f & 1], sm));
   // back: decisions, after the frame's equaliser (the MIMO of frame f + 1
   // runs meanwhile)
-  RX_CK(cudaStreamWaitEvent(h->s_comp, h->ev_mid[f & 1], 0));
-  int rc = launch_decide(h, pf, fa, final_);
+  int rc = launch_decide(h, pf, fa, final_, h->ev_mid[f & 1], false);
   if (rc != RX_OK) return rc;
   h->decided = fa.k_b;
   pf.dec_after = fa.k_b;
@@ -486,9 +493,7 @@ int launch_tail(rx_handle* h) {
   pf.ev_done = get_event(h);
   RX_CK(mark_copy(h));
   RX_CK(cudaEventRecord(pf.ev_in, h->last_cs));
-  RX_CK(cudaStreamWaitEvent(h->s_comp, h->ev_copy, 0));
-  RX_CK(cudaEventRecord(pf.ev_start, h->s_comp));
-  int rc = launch_decide(h, pf, fa, true);
+  int rc = launch_decide(h, pf, fa, true, h->ev_copy, true);
   if (rc != RX_OK) return rc;
   h->decided = n_sym;
   pf.dec_after = n_sym;
@@ -805,6 +810,7 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_stage_free[i], h->s_copy);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_comp, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_comp2, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_mid, cudaStreamNonBlocking);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     e = cudaEventCreateWithFlags(&h->ev_mid[i], cudaEventDisableTiming);
@@ -1044,6 +1050,7 @@ int rx_destroy(rx_handle* h) {
   if (h->s_front) cudaStreamSynchronize(h->s_front);
   if (h->s_mid) cudaStreamSynchronize(h->s_mid);
   if (h->s_comp) cudaStreamSynchronize(h->s_comp);
+  if (h->s_comp2) cudaStreamSynchronize(h->s_comp2);
   if (h->s_ber) cudaStreamSynchronize(h->s_ber);
   if (h->s_copy) cudaStreamSynchronize(h->s_copy);
   free_all(h);
@@ -1068,6 +1075,8 @@ int rx_reset(rx_handle* h) {
   RX_CK(cudaStreamWaitEvent(s, h->ev_berd[0], 0));
   RX_CK(cudaEventRecord(h->ev_mid[0], h->s_mid));
   RX_CK(cudaStreamWaitEvent(s, h->ev_mid[0], 0));
+  RX_CK(cudaEventRecord(h->ev_bpsp[1], h->s_comp2));
+  RX_CK(cudaStreamWaitEvent(s, h->ev_bpsp[1], 0));
   RX_CK(cudaMemcpyAsync(d.st, &h->st_init, sizeof(StreamState), cudaMemcpyHostToDevice, s));
   RX_CK(cudaMemcpyAsync(d.Hf, d.Hs, d.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
   RX_CK(cudaMemsetAsync(d.acc, 0, 3 * sizeof(FrameAcc), s));
@@ -1082,6 +1091,7 @@ int rx_reset(rx_handle* h) {
   }
   RX_CK(cudaEventRecord(h->ev_reset, s));
   RX_CK(cudaStreamWaitEvent(h->s_front, h->ev_reset, 0));
+  RX_CK(cudaStreamWaitEvent(h->s_comp2, h->ev_reset, 0));
   RX_CK(cudaStreamWaitEvent(h->s_ber, h->ev_reset, 0));
   RX_CK(cudaStreamWaitEvent(h->s_mid, h->ev_reset, 0));
   h->n_decide = 0;
@@ -1103,19 +1113,13 @@ int rx_reset(rx_handle* h) {
 int rx_join(rx_handle* h, void* cuda_stream) {
   if (!h) return fail(RX_EINVAL, "null handle");
   RX_CK(cudaSetDevice(h->cfg.device));
-  cudaEvent_t e = get_event(h), e2 = get_event(h), e3 = get_event(h), e4 = get_event(h);
-  RX_CK(cudaEventRecord(e, h->s_comp));
-  RX_CK(cudaEventRecord(e2, h->s_front));
-  RX_CK(cudaEventRecord(e3, h->s_ber));
-  RX_CK(cudaEventRecord(e4, h->s_mid));
-  RX_CK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, e, 0));
-  RX_CK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, e2, 0));
-  RX_CK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, e3, 0));
-  RX_CK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, e4, 0));
-  h->ev_pool.push_back(e);
-  h->ev_pool.push_back(e2);
-  h->ev_pool.push_back(e3);
-  h->ev_pool.push_back(e4);
+  cudaStream_t ss[5] = {h->s_comp, h->s_comp2, h->s_front, h->s_ber, h->s_mid};
+  for (cudaStream_t x : ss) {
+    cudaEvent_t e = get_event(h);
+    RX_CK(cudaEventRecord(e, x));
+    RX_CK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, e, 0));
+    h->ev_pool.push_back(e);
+  }
   return RX_OK;
 }
 

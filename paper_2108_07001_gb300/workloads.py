@@ -27,6 +27,17 @@ DP_QPSK_10000KM_STREAM = dict(
     push_syms=1 << 16,
 )
 
+DP_QPSK_64GBD_10000KM_STREAM = dict(
+    name="dp-qpsk-64gbd-10000km-stream",
+    link=dict(baud_hz=64e9, bits_per_sym=2, n_sym=1 << 22, fiber_len_m=10000e3, D_ps_nm_km=17.0,
+              snr_db=12.0, fo_hz=100e6, linewidth_hz=100e3, rotate=True, prbs_seed=1005, seed=1005,
+              out_dtype="c64"),
+    rx=dict(baud_hz=64e9, modulation=2, fiber_len_m=10000e3, mimo_taps=15, bps_angles=64,
+            bps_half_window=16, frame_syms=1 << 20, seg_syms=512, prbs_seed=1005,
+            max_block_samples=1 << 17),
+    push_syms=1 << 16,
+)
+
 DP_16QAM_5000KM = dict(
     name="dp-16qam-32gbd-5000km-2^22sym",
     link=dict(baud_hz=32e9, bits_per_sym=4, n_sym=1 << 22, fiber_len_m=5000e3, D_ps_nm_km=17.0,
@@ -36,7 +47,8 @@ DP_16QAM_5000KM = dict(
             bps_half_window=32, frame_syms=1 << 20, prbs_seed=1002, mu_dd=2e-3),
 )
 
-ALL = [DP_QPSK_1000KM, DP_QPSK_10000KM_STREAM, DP_16QAM_5000KM]
+ALL = [DP_QPSK_1000KM, DP_QPSK_10000KM_STREAM, DP_16QAM_5000KM, DP_QPSK_64GBD_10000KM_STREAM]
+STREAMS = {w["name"]: w for w in (DP_QPSK_10000KM_STREAM, DP_QPSK_64GBD_10000KM_STREAM)}
 
 
 def oracle_kwargs(rx: dict) -> dict:
