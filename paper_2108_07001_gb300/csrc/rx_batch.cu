@@ -193,7 +193,7 @@ int join_stream(rx_handle* h, cudaStream_t cs, cudaStream_t batch_end) {
     RX_CK(cudaStreamWaitEvent(cs, h->ev_copy, 0));
   }
   if (h->own_work) {
-    cudaStream_t ss[5] = {h->s_front, h->s_mid, h->s_comp, h->s_comp2, h->s_ber};
+    cudaStream_t ss[6] = {h->s_front, h->s_mid, h->s_comp, h->s_comp2, h->s_dem, h->s_ber};
     cudaEvent_t e = get_event(h);
     for (cudaStream_t x : ss) {
       RX_CK(cudaEventRecord(e, x));

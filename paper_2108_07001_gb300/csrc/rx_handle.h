@@ -103,7 +103,8 @@ struct rx_handle {
   cudaEvent_t ev_bpsp[2] = {};     // BPS of a decide pass done (its decision buffers written), by pass parity
   cudaEvent_t ev_front[rxrt::kZSlots] = {};  // front work of the frame in slot done
   cudaEvent_t ev_mimo[rxrt::kZSlots] = {};   // MIMO of the frame in slot done (slot reusable)
-  cudaStream_t s_ber = nullptr;        // unwrap/demap and BER counting, after the BPS
+  cudaStream_t s_dem = nullptr;        // unwrap scan and demap, after the BPS
+  cudaStream_t s_ber = nullptr;        // BER counting (metrics), after the demap
   cudaEvent_t ev_dem[2] = {};          // demap of a decide pass done (its decision buffers free), by pass parity
   cudaEvent_t ev_berd[2] = {};         // BER work of a frame done (its ring slots reusable)
   long long n_decide = 0;              // decision passes launched in this stream

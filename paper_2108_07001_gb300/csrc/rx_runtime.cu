@@ -143,6 +143,7 @@ void free_all(rx_handle* h) {
   if (h->s_copy) cudaStreamDestroy(h->s_copy);
   if (h->s_comp) cudaStreamDestroy(h->s_comp);
   if (h->s_comp2) cudaStreamDestroy(h->s_comp2);
+  if (h->s_dem) cudaStreamDestroy(h->s_dem);
   if (h->s_mid) cudaStreamDestroy(h->s_mid);
   for (int i = 0; i < 2; ++i) {
     if (h->ev_mid[i]) cudaEventDestroy(h->ev_mid[i]);
@@ -258,6 +259,7 @@ cudaError_t sync_all(rx_handle* h) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_mid);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_comp);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_comp2);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_dem);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_ber);
   return e;
 }
@@ -327,17 +329,19 @@ int launch_decide(rx_handle* h, PendingFrame& pf, const FrameArgs& fa, bool fina
   RX_STAGE(RX_STAGE_BPS, 1, sp, launch_bps(d, fa, sp));
   if (fa.f >= 0) RX_CK(cudaEventRecord(h->ev_bpsd[fa.f & 1], sp));
   RX_CK(cudaEventRecord(h->ev_bpsp[par], sp));
-  cudaStream_t sb = h->s_ber;
-  RX_CK(cudaStreamWaitEvent(sb, h->ev_bpsp[par], 0));
-  // (the decision ring slots it writes were read by the BER work of pass
-  // n - 2, earlier on the same stream)
-  RX_STAGE(RX_STAGE_DEMAP, 1, sb, launch_unwrap_demap(d, fa, sb));
-  RX_CK(cudaEventRecord(h->ev_dem[par], sb));
+  // unwrap scan + demap on their own stream, after the pass's BPS and after
+  // the BER work of pass n - 2 has read the decision ring slots they write
+  cudaStream_t sd = h->s_dem, sb = h->s_ber;
+  RX_CK(cudaStreamWaitEvent(sd, h->ev_bpsp[par], 0));
+  if (d.ber_on && pass >= 2) RX_CK(cudaStreamWaitEvent(sd, h->ev_berd[par], 0));
+  RX_STAGE(RX_STAGE_DEMAP, 1, sd, launch_unwrap_demap(d, fa, sd));
+  RX_CK(cudaEventRecord(h->ev_dem[par], sd));
   // the bits are out; with per-stage timing, the pass ends after its BER
   // work too, so every stage event of the pass is complete at ev_done
-  if (!h->cfg.profile) RX_CK(cudaEventRecord(pf.ev_done, sb));
+  if (!h->cfg.profile) RX_CK(cudaEventRecord(pf.ev_done, sd));
   h->n_decide++;
   if (d.ber_on) {
+    RX_CK(cudaStreamWaitEvent(sb, h->ev_dem[par], 0));
     int rcb = staged(h, pf, RX_STAGE_BER, sb, [&]() -> int {
       const BerPlan p = plan_ber(h, fa, final_);
       if (p.sync) {
@@ -352,7 +356,10 @@ int launch_decide(rx_handle* h, PendingFrame& pf, const FrameArgs& fa, bool fina
     if (rcb != RX_OK) return rcb;
     RX_CK(cudaEventRecord(h->ev_berd[par], sb));
   }
-  if (h->cfg.profile) RX_CK(cudaEventRecord(pf.ev_done, sb));
+  if (h->cfg.profile) {
+    RX_CK(cudaStreamWaitEvent(sd, h->ev_berd[par], 0));
+    RX_CK(cudaEventRecord(pf.ev_done, sd));
+  }
   return RX_OK;
 }
 
@@ -811,6 +818,7 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_comp, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_comp2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_dem, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_mid, cudaStreamNonBlocking);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     e = cudaEventCreateWithFlags(&h->ev_mid[i], cudaEventDisableTiming);
@@ -1051,6 +1059,7 @@ int rx_destroy(rx_handle* h) {
   if (h->s_mid) cudaStreamSynchronize(h->s_mid);
   if (h->s_comp) cudaStreamSynchronize(h->s_comp);
   if (h->s_comp2) cudaStreamSynchronize(h->s_comp2);
+  if (h->s_dem) cudaStreamSynchronize(h->s_dem);
   if (h->s_ber) cudaStreamSynchronize(h->s_ber);
   if (h->s_copy) cudaStreamSynchronize(h->s_copy);
   free_all(h);
@@ -1077,6 +1086,8 @@ int rx_reset(rx_handle* h) {
   RX_CK(cudaStreamWaitEvent(s, h->ev_mid[0], 0));
   RX_CK(cudaEventRecord(h->ev_bpsp[1], h->s_comp2));
   RX_CK(cudaStreamWaitEvent(s, h->ev_bpsp[1], 0));
+  RX_CK(cudaEventRecord(h->ev_dem[1], h->s_dem));
+  RX_CK(cudaStreamWaitEvent(s, h->ev_dem[1], 0));
   RX_CK(cudaMemcpyAsync(d.st, &h->st_init, sizeof(StreamState), cudaMemcpyHostToDevice, s));
   RX_CK(cudaMemcpyAsync(d.Hf, d.Hs, d.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
   RX_CK(cudaMemsetAsync(d.acc, 0, 3 * sizeof(FrameAcc), s));
@@ -1092,6 +1103,7 @@ int rx_reset(rx_handle* h) {
   RX_CK(cudaEventRecord(h->ev_reset, s));
   RX_CK(cudaStreamWaitEvent(h->s_front, h->ev_reset, 0));
   RX_CK(cudaStreamWaitEvent(h->s_comp2, h->ev_reset, 0));
+  RX_CK(cudaStreamWaitEvent(h->s_dem, h->ev_reset, 0));
   RX_CK(cudaStreamWaitEvent(h->s_ber, h->ev_reset, 0));
   RX_CK(cudaStreamWaitEvent(h->s_mid, h->ev_reset, 0));
   h->n_decide = 0;
@@ -1113,7 +1125,7 @@ int rx_reset(rx_handle* h) {
 int rx_join(rx_handle* h, void* cuda_stream) {
   if (!h) return fail(RX_EINVAL, "null handle");
   RX_CK(cudaSetDevice(h->cfg.device));
-  cudaStream_t ss[5] = {h->s_comp, h->s_comp2, h->s_front, h->s_ber, h->s_mid};
+  cudaStream_t ss[6] = {h->s_comp, h->s_comp2, h->s_dem, h->s_front, h->s_ber, h->s_mid};
   for (cudaStream_t x : ss) {
     cudaEvent_t e = get_event(h);
     RX_CK(cudaEventRecord(e, x));
