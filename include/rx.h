@@ -2,7 +2,7 @@
  * rx.h -- C ABI of the GB300 dual-polarisation coherent receiver.
  *
  * One handle = one receiver stream.  The handle owns device memory on one
- * CUDA device and two CUDA streams of its own; every step of the chain runs
+ * CUDA device and CUDA streams of its own; every step of the chain runs
  * in hand-written CUDA kernels (sm_103a) behind these calls.
  *
  * The chain (per stream, both polarisations jointly), with the passage of
@@ -91,6 +91,10 @@ typedef struct rx_config {
                               the device for inspection; 0: off */
   int profile;             /* 1: time every stage with CUDA events */
   int device;              /* CUDA device ordinal */
+  /* Launch tiles (results do not depend on them; rx_autotune_tiles picks
+   * them on the GPU at hand): */
+  int mimo_block_warps;    /* equaliser segment chains (one warp each) per block: 1, 2, 4 or 8; 0: 4 */
+  int bps_block_runs;      /* full-search BPS runs of 256 symbols (one warp each) per block: 4 or 8; 0: 8 */
 } rx_config;
 
 /* Stages reported by rx_stage_times, in this order. */
@@ -309,6 +313,20 @@ int rx_decide_block_noalloc(const void* y, int64_t n, int modulation, int bps_an
  * receiver per candidate; errors as rx_create, RX_EINVAL on bad arguments
  * or when no N is admissible. */
 int rx_autotune_fft(const rx_config* cfg, int frames, int* fft_n, double* ms_per_msample);
+
+/* Picks the FFT size and the launch tiles for cfg on this GPU: first the
+ * FFT size as rx_autotune_fft (tiles 4 and 8), then the equaliser's
+ * segment chains per block (1, 2, 4, 8), then the full blind phase
+ * search's runs per block (4, 8; not for the two-stage search), each timed
+ * with the others at their best so far and kept only if more than 1 %
+ * faster.  The tiles change no result (rx_config.mimo_block_warps,
+ * bps_block_runs); the paper picks its buffer and block sizes for its GPU
+ * (Sec. II), this picks them for the GPU at hand.  Results in *fft_n,
+ * *mimo_block_warps, *bps_block_runs and the time per 2^20 samples per
+ * polarisation in *ms_per_msample (may be NULL).  Errors as
+ * rx_autotune_fft. */
+int rx_autotune_tiles(const rx_config* cfg, int frames, int* fft_n, int* mimo_block_warps, int* bps_block_runs,
+                      double* ms_per_msample);
 
 /* FP32 arithmetic peak of device, measured (the denominator of the ALU
  * rooflines): every SM filled with 2048 threads running eight independent

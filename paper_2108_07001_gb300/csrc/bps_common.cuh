@@ -55,13 +55,13 @@ __device__ __forceinline__ void bps_finish_run(const RxDev& d, const FrameArgs& 
   }
 }
 
-// Block epilogue (every thread of the NT-thread block calls it, after its
-// warps' bps_finish_run calls): the block's EVM sums go to the statistics.
-// evn / evd: the calling warp's sums (read on lane 0).
+// Block epilogue (every thread of the block, at most NT threads, calls it
+// after its warps' bps_finish_run calls): the block's EVM sums go to the
+// statistics.  evn / evd: the calling warp's sums (read on lane 0).
 template <int NT>
 __device__ __forceinline__ void bps_finish_block(const RxDev& d, float evn, float evd) {
-  constexpr int NW = NT / 32;
-  __shared__ float red_s[NW][2];
+  __shared__ float red_s[NT / 32][2];
+  const int NW = (int)(blockDim.x >> 5);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
     red_s[warp][0] = evn;

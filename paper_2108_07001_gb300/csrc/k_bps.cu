@@ -53,9 +53,11 @@ struct BpsSmem {
   static constexpr int NSUP = (YS + WIN - 1) / WIN;      // super-steps per run
   static constexpr int ROWS = WIN - 1 + NSUP;            // key rows per warp
   static constexpr int YSP = (NSUP * WIN + 7) / 8 * 8;     // staged entries (whole super-steps)
-  static constexpr size_t KEY_BYTES = sizeof(uint32_t) * 8 * ROWS * ROW;
-  static constexpr size_t Y_BYTES = (size_t)8 * YSP * (PAIR ? 24 : 8);
-  static constexpr size_t BYTES = KEY_BYTES + Y_BYTES;
+  static constexpr size_t KEY_WARP = sizeof(uint32_t) * ROWS * ROW;  // key rows of one warp
+  static constexpr size_t Y_WARP = (size_t)YSP * (PAIR ? 24 : 8);    // staged symbols of one warp
+  // a block of nw warps (runs): every warp's key rows, then every warp's symbols
+  static constexpr size_t bytes(int nw) { return (size_t)nw * (KEY_WARP + Y_WARP); }
+  static constexpr size_t BYTES = bytes(8);  // the largest block (8 runs)
 };
 
 // One warp = one run of kRun symbols of one polarisation; lane l holds the
@@ -90,7 +92,8 @@ __device__ __forceinline__ void bps_body(const RxDev& d, const FrameArgs& fa, VB
   const int pol = vb.y;
   const long long n_dec = fa.k_b - fa.k_a;
   const int nruns = (int)((n_dec + kRun - 1) / kRun);
-  const int run = vb.x * 8 + warp;
+  const int nw = (int)(blockDim.x >> 5);  // runs per block (d.bps_nw)
+  const int run = vb.x * nw + warp;
   const long long kr = fa.k_a + (long long)run * kRun;
   const int ract = run < nruns ? (int)min((long long)kRun, fa.k_b - kr) : 0;
 
@@ -117,9 +120,9 @@ __device__ __forceinline__ void bps_body(const RxDev& d, const FrameArgs& fa, VB
   const int sv_lo = (int)max(0LL, (long long)W - kr);
   const int sv_hi = (int)min((long long)total, ylim - (kr - W));
   uint32_t* kw = keys_smem + warp * SM::ROWS * ROW;
-  unsigned char* ybase = reinterpret_cast<unsigned char*>(keys_smem) + SM::KEY_BYTES;
+  unsigned char* ybase = reinterpret_cast<unsigned char*>(keys_smem) + nw * SM::KEY_WARP;
   float4* ys4 = reinterpret_cast<float4*>(ybase) + warp * SM::YSP;            // paired: {x, y, y, x}
-  float2* hs2 = reinterpret_cast<float2*>(ybase + (size_t)8 * SM::YSP * 16) + warp * SM::YSP;  // paired: {h, h}
+  float2* hs2 = reinterpret_cast<float2*>(ybase + (size_t)nw * SM::YSP * 16) + warp * SM::YSP;  // paired: {h, h}
   float2* ys2 = reinterpret_cast<float2*>(ybase) + warp * SM::YSP;
   // the paired form stages whole super-steps (zeros past the run) and so
   // runs every super-step, the partial last one included, without predicates
@@ -451,8 +454,9 @@ template <int B, int W, bool Q>
 static void launch_bps_t(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
   const long long n_dec = fa.k_b - fa.k_a;
   const int nruns = (int)((n_dec + kRun - 1) / kRun);
-  dim3 grid((nruns + 7) / 8, 2);
-  bps_kernel<B, W, Q><<<grid, 256, BpsSmem<B, W, Q>::BYTES, s>>>(d, fa);
+  const int nw = d.bps_nw;
+  dim3 grid((nruns + nw - 1) / nw, 2);
+  bps_kernel<B, W, Q><<<grid, 32 * nw, BpsSmem<B, W, Q>::bytes(nw), s>>>(d, fa);
 }
 
 template <int B, int W>
@@ -505,7 +509,7 @@ int launch_bps2_batch(const RxDev& d, const BView& v, int blocks, cudaStream_t s
 int bps_grid_x(const RxDev& d, const FrameArgs& fa) {
   const long long n_dec = fa.k_b - fa.k_a;
   const int nruns = (int)((n_dec + kRun - 1) / kRun);
-  return d.bps_stride > 1 ? (nruns + 15) / 16 : (nruns + 7) / 8;
+  return d.bps_stride > 1 ? (nruns + 15) / 16 : (nruns + d.bps_nw - 1) / d.bps_nw;
 }
 
 int demap_grid_x(const FrameArgs& fa) { return (int)((fa.k_b - fa.k_a + kRun - 1) / kRun); }
@@ -516,8 +520,8 @@ cudaError_t launch_bps_batch(const RxDev& d, const BView& v, int blocks, cudaStr
   const bool q16 = d.bps == 4;
 #define RX_BW(b, w)                                                                                 \
   if (d.B == b && d.W == w) {                                                                       \
-    if (q16) bps_batch_kernel<b, w, true><<<blocks, 256, BpsSmem<b, w, true>::BYTES, s>>>(v);       \
-    else bps_batch_kernel<b, w, false><<<blocks, 256, BpsSmem<b, w, false>::BYTES, s>>>(v);         \
+    if (q16) bps_batch_kernel<b, w, true><<<blocks, 32 * d.bps_nw, BpsSmem<b, w, true>::bytes(d.bps_nw), s>>>(v); \
+    else bps_batch_kernel<b, w, false><<<blocks, 32 * d.bps_nw, BpsSmem<b, w, false>::bytes(d.bps_nw), s>>>(v);   \
     return cudaGetLastError();                                                                      \
   }
   RX_BW(64, 16) RX_BW(32, 16) RX_BW(64, 32) RX_BW(32, 32) RX_BW(64, 8) RX_BW(32, 8)

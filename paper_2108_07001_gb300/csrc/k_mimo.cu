@@ -385,12 +385,14 @@ __global__ void __launch_bounds__(256) acq_batch_kernel(BView v) {
   acq_body<T>(f.d, f.fa);
 }
 
-// All segments of one frame, one warp per segment.
+// All segments of one frame, one warp per segment, d.mimo_nw warps per
+// block (the block's dynamic shared memory holds one ChainSmem per warp).
 template <int T>
 __device__ __forceinline__ void mimo_body(const RxDev& d, const FrameArgs& fa, long long hist_base, VBlock vb) {
-  __shared__ ChainSmem<T> sms[4];
+  extern __shared__ float4 mimo_smem4[];
+  ChainSmem<T>* sms = reinterpret_cast<ChainSmem<T>*>(mimo_smem4);
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = vb.x * 4 + wib;
+  const int j = vb.x * (int)(blockDim.x >> 5) + wib;
   const int nseg = (fa.Ff + d.S - 1) / d.S;
   if (j >= nseg) return;
   ChainSmem<T>& sm = sms[wib];
@@ -468,12 +470,12 @@ __device__ __forceinline__ void mimo_body(const RxDev& d, const FrameArgs& fa, l
 }
 
 template <int T>
-__global__ void __launch_bounds__(128) mimo_kernel(RxDev d, FrameArgs fa, long long hist_base) {
+__global__ void __launch_bounds__(256) mimo_kernel(RxDev d, FrameArgs fa, long long hist_base) {
   mimo_body<T>(d, fa, hist_base, own_block());
 }
 
 template <int T>
-__global__ void __launch_bounds__(128) mimo_batch_kernel(BView v) {
+__global__ void __launch_bounds__(256) mimo_batch_kernel(BView v) {
   int fi;
   VBlock vb;
   if (!batch_block(v, fi, vb)) return;
@@ -492,7 +494,8 @@ static cudaError_t launch_acq_t(const RxDev& d, const FrameArgs& fa, cudaStream_
 template <int T>
 static cudaError_t launch_mimo_t(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
   const int nseg = (fa.Ff + d.S - 1) / d.S;
-  mimo_kernel<T><<<(nseg + 3) / 4, 128, 0, s>>>(d, fa, fa.f * (long long)d.F);
+  const int nw = d.mimo_nw;
+  mimo_kernel<T><<<(nseg + nw - 1) / nw, 32 * nw, nw * sizeof(ChainSmem<T>), s>>>(d, fa, fa.f * (long long)d.F);
   return cudaGetLastError();
 }
 
@@ -520,7 +523,7 @@ cudaError_t launch_mimo(const RxDev& d, const FrameArgs& fa, cudaStream_t s) {
 
 int mimo_grid_x(const RxDev& d, const FrameArgs& fa) {
   const int nseg = (fa.Ff + d.S - 1) / d.S;
-  return (nseg + 3) / 4;
+  return (nseg + d.mimo_nw - 1) / d.mimo_nw;
 }
 
 cudaError_t launch_acquire_batch(const RxDev& d, const BView& v, int blocks, cudaStream_t s) {
@@ -537,7 +540,7 @@ cudaError_t launch_acquire_batch(const RxDev& d, const BView& v, int blocks, cud
 cudaError_t launch_mimo_batch(const RxDev& d, const BView& v, int blocks, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
   switch (d.T) {
-#define RX_T(t) case t: mimo_batch_kernel<t><<<blocks, 128, 0, s>>>(v); break;
+#define RX_T(t) case t: mimo_batch_kernel<t><<<blocks, 32 * d.mimo_nw, d.mimo_nw * sizeof(ChainSmem<t>), s>>>(v); break;
     RX_TAPS(RX_T)
 #undef RX_T
     default: return cudaErrorInvalidValue;

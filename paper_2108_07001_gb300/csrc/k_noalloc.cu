@@ -133,6 +133,7 @@ extern "C" int rx_decide_block_noalloc(const void* y, int64_t n, int modulation,
   d.F = (int)kF;
   d.B = bps_angles;
   d.bps_stride = 1;
+  d.bps_nw = 8;
   d.W = W;
   d.bps = modulation;
   d.nl = modulation == RX_QPSK ? 2 : 4;

@@ -333,8 +333,9 @@ int rx_batch_create(rx_handle* const* streams, int n_streams, rx_batch** out) {
   auto key = [](const RxDev& d, int st) -> long long {
     switch (st) {
       case BS_CD0: case BS_CD: return (long long)d.N * 4 + d.storage;
-      case BS_ACQ: case BS_MIMO: return d.T;
-      case BS_BPS: return (((long long)d.B * 64 + d.W) * 8 + d.bps) * 64 + d.bps_stride;
+      case BS_ACQ: return d.T;
+      case BS_MIMO: return (long long)d.T * 16 + d.mimo_nw;  // the launch's block size is the group's
+      case BS_BPS: return ((((long long)d.B * 64 + d.W) * 8 + d.bps) * 64 + d.bps_stride) * 16 + d.bps_nw;
       default: return 0;
     }
   };

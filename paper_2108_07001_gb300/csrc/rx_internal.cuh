@@ -66,6 +66,8 @@ struct RxDev {
   int N, halo, h, L, c, T, K, S, F, G, B, W, bps;
   int nl;                      // levels per dimension (2 or 4)
   int bps_stride;              // BPS coarse stride S: 1 full search, > 1 two-stage over B/S angles
+  int bps_nw;                  // full-search BPS: runs (warps) per block, 4 or 8
+  int mimo_nw;                 // MIMO: segment chains (warps) per block, 1..8
   int zlen;                    // 2F + 2c
   int storage;                 // RX_C64 / RX_C16
   long long ring_cap;          // samples per polarisation

@@ -519,6 +519,11 @@ int validate(const rx_config* c, std::string& why) {
   if (W != 8 && W != 12 && W != 16 && W != 24 && W != 32) return why = "bps_half_window must be one of 8, 12, 16, 24, 32", RX_EINVAL;
   if (c->bps_coarse_stride != 1 && c->bps_coarse_stride * (c->modulation == RX_QAM16 ? 8 : 16) != c->bps_angles)
     return why = "bps_coarse_stride must be 1 or bps_angles/16 (QPSK), bps_angles/8 (16QAM)", RX_EINVAL;
+  if (c->mimo_block_warps != 0 && c->mimo_block_warps != 1 && c->mimo_block_warps != 2 && c->mimo_block_warps != 4 &&
+      c->mimo_block_warps != 8)
+    return why = "mimo_block_warps must be 0, 1, 2, 4 or 8", RX_EINVAL;
+  if (c->bps_block_runs != 0 && c->bps_block_runs != 4 && c->bps_block_runs != 8)
+    return why = "bps_block_runs must be 0, 4 or 8", RX_EINVAL;
   if (c->sub_block_syms != 64) return why = "sub_block_syms must be 64", RX_EINVAL;
   if (c->seg_syms < 64 || c->seg_syms % 64) return why = "seg_syms must be a positive multiple of 64", RX_EINVAL;
   if (c->frame_syms < c->seg_syms || c->frame_syms % c->seg_syms || c->frame_syms % kRun)
@@ -685,6 +690,8 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   d.B = cfg->bps_angles;
   d.W = cfg->bps_half_window;
   d.bps_stride = cfg->bps_coarse_stride;
+  d.bps_nw = cfg->bps_block_runs ? cfg->bps_block_runs : 8;
+  d.mimo_nw = cfg->mimo_block_warps ? cfg->mimo_block_warps : 4;
   d.bps = cfg->modulation;
   d.nl = d.bps == 2 ? 2 : 4;
   d.zlen = 2 * d.F + 2 * d.c;

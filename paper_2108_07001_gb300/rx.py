@@ -35,7 +35,7 @@ EXPORTS = ["rx_config_default", "rx_create", "rx_push_block", "rx_pull_bits", "r
            "rx_server_config_default", "rx_server_create", "rx_server_open", "rx_server_submit",
            "rx_server_end", "rx_server_sync", "rx_server_pull_bits", "rx_server_stream_stats",
            "rx_server_handle", "rx_server_close", "rx_server_stats", "rx_server_destroy",
-           "rx_autotune_fft", "rx_fp32_peak",
+           "rx_autotune_fft", "rx_autotune_tiles", "rx_fp32_peak",
            "rx_kk_config_default", "rx_kk_create", "rx_kk_push", "rx_kk_end", "rx_kk_reset",
            "rx_kk_position", "rx_kk_destroy", "rx_kk_batch_create", "rx_kk_batch_push", "rx_kk_batch_destroy",
            "rx_kkrx_config_default", "rx_kkrx_create", "rx_kkrx_push", "rx_kkrx_end", "rx_kkrx_equalised",
@@ -75,6 +75,8 @@ class RxConfig(ctypes.Structure):
         ("history_syms", ctypes.c_int64),
         ("profile", ctypes.c_int),
         ("device", ctypes.c_int),
+        ("mimo_block_warps", ctypes.c_int),
+        ("bps_block_runs", ctypes.c_int),
     ]
 
 
@@ -219,6 +221,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rx_server_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
     lib.rx_server_destroy.argtypes = [P]
     lib.rx_autotune_fft.argtypes = [ctypes.POINTER(RxConfig), I, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double)]
+    lib.rx_autotune_tiles.argtypes = [ctypes.POINTER(RxConfig), I, ctypes.POINTER(I), ctypes.POINTER(I),
+                                      ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double)]
     lib.rx_kk_config_default.argtypes = [ctypes.POINTER(KKConfig)]
     lib.rx_kk_config_default.restype = None
     lib.rx_kk_create.argtypes = [ctypes.POINTER(KKConfig), ctypes.POINTER(P)]
@@ -592,6 +596,16 @@ def autotune_fft(cfg: RxConfig | None = None, frames: int = 3, **overrides) -> t
     ms = ctypes.c_double()
     _check(load().rx_autotune_fft(ctypes.byref(cfg), frames, ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
+
+
+def autotune_tiles(cfg: RxConfig | None = None, frames: int = 3, **overrides) -> dict:
+    """FFT size and launch tiles for cfg on this GPU (rx_autotune_tiles)."""
+    cfg = cfg if cfg is not None else default_config(**overrides)
+    n, mw, br = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(load().rx_autotune_tiles(ctypes.byref(cfg), frames, ctypes.byref(n), ctypes.byref(mw), ctypes.byref(br),
+                                    ctypes.byref(ms)))
+    return {"fft_n": n.value, "mimo_block_warps": mw.value, "bps_block_runs": br.value, "ms_per_msample": ms.value}
 
 
 def default_kk_config(**overrides) -> KKConfig:

@@ -56,6 +56,8 @@ def oracle_kwargs(rx: dict) -> dict:
     m = dict(rx)
     m.pop("max_block_samples", None)
     m.pop("storage_dtype", None)
+    m.pop("mimo_block_warps", None)  # launch tiles: no effect on any result
+    m.pop("bps_block_runs", None)
     if "modulation" in m:
         m["bits_per_sym"] = m.pop("modulation")
     return m

@@ -74,6 +74,8 @@ def test_defaults(lib):
     ("baud_hz", 0.0, "baud_hz"),
     ("fft_n", 3000, "fft_n"),
     ("fft_n", 1024, "halo"),
+    ("mimo_block_warps", 3, "mimo_block_warps"),
+    ("bps_block_runs", 2, "bps_block_runs"),
 ])
 def test_invalid_config_is_rejected(lib, field, value, msg):
     from paper_2108_07001_gb300 import rx
@@ -170,6 +172,12 @@ def test_autotune_argument_checks_without_device(lib):
     far = rx.default_config(fiber_len_m=200000e3)  # halo (~50k samples) longer than any FFT size
     assert lib.rx_autotune_fft(ctypes.byref(far), 3, ctypes.byref(n), None) == rx.RX_EINVAL
     assert b"halo" in lib.rx_last_error()
+    mw, br = ctypes.c_int(), ctypes.c_int()
+    assert lib.rx_autotune_tiles(ctypes.byref(cfg), 3, ctypes.byref(n), None, ctypes.byref(br), None) == rx.RX_EINVAL
+    assert lib.rx_autotune_tiles(ctypes.byref(cfg), 65, ctypes.byref(n), ctypes.byref(mw), ctypes.byref(br),
+                                 None) == rx.RX_EINVAL
+    assert lib.rx_autotune_tiles(ctypes.byref(far), 3, ctypes.byref(n), ctypes.byref(mw), ctypes.byref(br),
+                                 None) == rx.RX_EINVAL
 
 
 def test_kk_struct_layout_matches_c(tmp_path, lib):

@@ -26,14 +26,14 @@ F = 1 << 13
 
 def stream_case(kind, seed):
     """A short stream and its receiver configuration; the kinds differ in
-    FFT size, tap count, BPS form, modulation and storage type, so the
-    batch runs several launch groups per stage."""
+    FFT size, tap count, BPS form, modulation, storage type and launch
+    tiles, so the batch runs several launch groups per stage."""
     if kind == "qpsk1000":
         link = dict(baud_hz=28e9, bits_per_sym=2, n_sym=4 * F + 999, fiber_len_m=1000e3, snr_db=12.0)
         cfg = dict(baud_hz=28e9, modulation=2, fiber_len_m=1000e3)
     elif kind == "qpsk3000_fft8192":
         link = dict(baud_hz=32e9, bits_per_sym=2, n_sym=3 * F + 77, fiber_len_m=3000e3, snr_db=11.0)
-        cfg = dict(baud_hz=32e9, modulation=2, fiber_len_m=3000e3, fft_n=8192)
+        cfg = dict(baud_hz=32e9, modulation=2, fiber_len_m=3000e3, fft_n=8192, mimo_block_warps=2, bps_block_runs=4)
     elif kind == "qpsk64_fft32768":
         link = dict(baud_hz=64e9, bits_per_sym=2, n_sym=3 * F + 1000, fiber_len_m=4000e3, snr_db=13.0)
         cfg = dict(baud_hz=64e9, modulation=2, fiber_len_m=4000e3, fft_n=32768)
@@ -44,7 +44,7 @@ def stream_case(kind, seed):
     else:
         link = dict(baud_hz=32e9, bits_per_sym=4, n_sym=3 * F + 500, fiber_len_m=500e3, snr_db=18.0)
         cfg = dict(baud_hz=32e9, modulation=4, fiber_len_m=500e3, mimo_taps=25, bps_angles=32, bps_half_window=32,
-                   mu_dd=2e-3)
+                   mu_dd=2e-3, mimo_block_warps=8)
     sim = rxsim.simulate(rxsim.LinkConfig(**link, prbs_seed=seed, seed=seed, out_dtype="c64"))
     n_sym = link["n_sym"]
     cfg.update(frame_syms=F, acq_syms=F, cma_syms=4096, prbs_seed=seed, ber_skip_syms=2048, sync_syms=2048,

@@ -383,3 +383,29 @@ def test_32768_point_transform_ragged_pushes_fp16():
     compare(gpu, ref, rx_kw)
     assert gpu["stats"]["bits"] == ref["ber"]["bits"]
     r.close()
+
+
+def test_launch_tiles_do_not_change_results():
+    """Every equaliser tile (1, 2, 4, 8 segment chains per block) and BPS
+    tile (4, 8 runs per block) gives bit for bit the same bits, equalised
+    symbols and counters; the tile autotuner returns admissible tiles."""
+    from paper_2108_07001_gb300 import rx
+    F = 1 << 14
+    sim = rxsim.simulate(link(n_sym=3 * F + 700, snr_db=12.0, fiber_len_m=1500e3, prbs_seed=15, seed=1515,
+                              out_dtype="c64"))
+    base = dict(fiber_len_m=1500e3, frame_syms=F, acq_syms=8192, cma_syms=4096, prbs_seed=15, ber_skip_syms=4096)
+    ref = None
+    for mw, br in ((4, 8), (1, 8), (2, 4), (8, 4)):
+        gpu, r = run_gpu(sim["rx"], dict(base, mimo_block_warps=mw, bps_block_runs=br), pushes=[20000] * 4 + [
+            sim["rx"].shape[1] - 80000])
+        st = gpu["stats"]
+        got = (gpu["bits"], gpu["y"], st["bit_errors"], st["bits"], st["cycle_slips"])
+        r.close()
+        if ref is None:
+            ref = got
+            continue
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), (mw, br)
+        assert got[2:] == ref[2:], (mw, br)
+    t = rx.autotune_tiles(rx.default_config(**base), frames=2)
+    assert t["fft_n"] in (1024, 2048, 4096, 8192, 16384, 32768)
+    assert t["mimo_block_warps"] in (1, 2, 4, 8) and t["bps_block_runs"] in (4, 8) and t["ms_per_msample"] > 0

@@ -41,3 +41,14 @@ def test_error_in_one_frame_fails():
     g[:, 3 * F:4 * F] *= 1.0 + 2e-4
     with pytest.raises(AssertionError):
         check_equalised(g, y, F, 1 << 14)
+
+
+def test_oracle_settings_drop_launch_only_fields():
+    """Launch tiles, storage type and block sizes are not method settings:
+    the oracle's configuration is built without them."""
+    from oracle import rx_oracle as O
+    from paper_2108_07001_gb300.workloads import oracle_kwargs
+    kw = oracle_kwargs(dict(fiber_len_m=1000e3, modulation=4, mimo_block_warps=2, bps_block_runs=4,
+                            storage_dtype=1, max_block_samples=1 << 15))
+    cfg = O.RxConfig(**kw)
+    assert cfg.bits_per_sym == 4 and cfg.fiber_len_m == 1000e3
