@@ -1217,10 +1217,11 @@ def plain_pass(streams, data):
     return wall, per
 
 
-def batch_pass(streams, data, fft, storage, barrier=None):
+def batch_pass(streams, data, fft, storage, barrier=None, graph=False):
     """All streams through one rx_batch: round j pushes every stream's j-th
-    block in one call (one launch per stage and frame ordinal), the last
-    call ends every stream."""
+    block in one call (one launch per stage and frame ordinal, or with
+    graph one replay of the batch's captured graph), the last call ends
+    every stream."""
     import torch
     from paper_2108_07001_gb300 import rx
     cur = torch.cuda.current_stream()
@@ -1228,7 +1229,7 @@ def batch_pass(streams, data, fft, storage, barrier=None):
     recs = [rx.Receiver(**dict(rxc, fft_n=fft[i], storage_dtype=storage)) for i, (_, rxc, _) in enumerate(streams)]
     dummy = torch.zeros(16, dtype=torch.complex64, device=dev)
     n_rounds = max(len(b) for b in data)
-    with rx.Batch(recs) as batch:
+    with rx.Batch(recs, graph=graph) as batch:
         torch.cuda.synchronize()
         if barrier:
             barrier()
@@ -1243,7 +1244,7 @@ def batch_pass(streams, data, fft, storage, barrier=None):
         wall = time.perf_counter() - t_start
         if barrier:
             barrier()
-        info = batch.info()
+        info = dict(batch.info(), **{"graph_" + k: v for k, v in batch.graph_info().items()})
     per = [r.stats() for r in recs]
     for r in recs:
         r.close()
@@ -1260,11 +1261,12 @@ def run_batched(args, rank=0, world=1, barrier=None):
     submitted at once: through the serving layer with per-stream pushes
     (FFT size of the default rule (N >= 4 halo), the size the autotuner picks
     per stream, and the latter with FP16 sample storage), through the
-    serving layer in batched rounds (FP32 and FP16 storage), and through one
-    rx_batch (round j pushes every stream's j-th block in one call: one
-    launch per stage and frame ordinal, pipelined over the batch's four
-    streams); beside them the plain per-stream chain (one stream at a time).
-    The value is the fastest form."""
+    serving layer in batched rounds (FP32 and FP16 storage; FP16 also with
+    graph replay), and through one rx_batch (round j pushes every stream's
+    j-th block in one call: one launch per stage and frame ordinal,
+    pipelined over the batch's four streams, or one replay of the batch's
+    captured graph); beside them the plain per-stream chain (one stream at a
+    time).  The value is the fastest form."""
     import torch
     from paper_2108_07001_gb300 import rx
     dev = torch.device("cuda:0")
@@ -1303,7 +1305,8 @@ def run_batched(args, rank=0, world=1, barrier=None):
     for form, fft, storage, batch in (("default_fft", deflt, rx.RX_C64, 0), ("autotuned_fft", tuned, rx.RX_C64, 0),
                                       ("autotuned_fft_fp16_storage", tuned, rx.RX_C16, 0),
                                       ("served_batched_default_fft", deflt, rx.RX_C64, 1),
-                                      ("served_batched_default_fft_fp16_storage", deflt, rx.RX_C16, 1)):
+                                      ("served_batched_default_fft_fp16_storage", deflt, rx.RX_C16, 1),
+                                      ("served_batched_graph_default_fft_fp16_storage", deflt, rx.RX_C16, 2)):
         serve_pass(streams, data, fft, storage, batch)
         wall, st, per = serve_pass(streams, data, fft, storage, batch)
         forms[form] = dict({"gsamples_s": round(total_samples / wall / 1e9, 3), "wall_ms": round(wall * 1e3, 1),
@@ -1311,11 +1314,13 @@ def run_batched(args, rank=0, world=1, barrier=None):
                             "latency_p99_ms": round(st["latency_p99_ms"], 3),
                             "mem_gib": round(st["mem_in_use_bytes"] / 2 ** 30, 2) if st["mem_in_use_bytes"] else None,
                             "batch_calls": st["batch_calls"]}, **stream_summary(per))
-    for form, fft, storage in (("batch_default_fft", deflt, rx.RX_C64),
-                               ("batch_default_fft_fp16_storage", deflt, rx.RX_C16),
-                               ("batch_autotuned_fft_fp16_storage", tuned, rx.RX_C16)):
-        batch_pass(streams, data, fft, storage)
-        wall, host, info, per = batch_pass(streams, data, fft, storage)
+    for form, fft, storage, graph in (("batch_default_fft", deflt, rx.RX_C64, False),
+                                      ("batch_default_fft_fp16_storage", deflt, rx.RX_C16, False),
+                                      ("batch_autotuned_fft_fp16_storage", tuned, rx.RX_C16, False),
+                                      ("batch_graph_default_fft", deflt, rx.RX_C64, True),
+                                      ("batch_graph_default_fft_fp16_storage", deflt, rx.RX_C16, True)):
+        batch_pass(streams, data, fft, storage, graph=graph)
+        wall, host, info, per = batch_pass(streams, data, fft, storage, graph=graph)
         # block latency of a call (its start on the stream to its bits), the
         # same for every stream the call carried
         forms[form] = dict({"gsamples_s": round(total_samples / wall / 1e9, 3), "wall_ms": round(wall * 1e3, 1),
@@ -1323,6 +1328,7 @@ def run_batched(args, rank=0, world=1, barrier=None):
                             "latency_p99_ms": round(max(p["latency_p99_ms"] for p in per), 3),
                             "host_ms": round(host * 1e3, 1), "host_wait_ms": round(info["wait_ms"], 1),
                             "calls": info["calls"], "launches": info["launches"],
+                            "graph_replays": info["graph_replays"], "graph_nodes": info["graph_nodes"],
                             "fft_groups": len(set(fft)) if fft[0] else None}, **stream_summary(per))
     base = forms["plain_per_stream"]["gsamples_s"]
     strong = forms["default_fft"]["gsamples_s"]

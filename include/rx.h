@@ -215,7 +215,25 @@ int rx_stats(rx_handle* h, rx_stats_t* out);
  * the host time its calls spent waiting for a table (ms; NULL pointers
  * skipped).
  * rx_batch_destroy: waits for the batch's streams, frees the batch (not
- * the streams). */
+ * the streams).
+ * rx_batch_set_graph: on = 1, before the batch's first push, switches it to
+ * graph replay.  One CUDA graph is built here, node by node (no stream
+ * capture, so other threads' CUDA calls are unaffected): every stage
+ * launch of up to the batch's largest ordinal count per call, one kernel
+ * node per ordinal and launch group, with the same stage-to-stage and
+ * buffer-reuse edges as the stream mode.  Every later call replays it with one launch
+ * on the batch's last stage stream after the call's ingest; on the host a
+ * call only sets the grid of each node whose block count changed and
+ * disables the nodes with no work (ordinals beyond the call's, groups with
+ * no frame at an ordinal).  The graph reads the call's per-ordinal tables
+ * from one fixed device table, so a call's table copy waits (on the
+ * device) for the previous call's graph: consecutive calls do not overlap
+ * their stages as in the stream mode.  Results equal the stream mode's.
+ * on = 0 before the first push returns to the stream mode.  RX_EINVAL
+ * (null batch), RX_ESTATE (the batch has pushed), RX_EDEVICE (building or
+ * instantiating the graph failed; the batch stays in the stream mode).
+ * rx_batch_graph_info: replays of the graph so far and kernel nodes in it
+ * (both 0 in the stream mode); NULL pointers skipped. */
 #define RX_BATCH_MAX 256
 typedef struct rx_batch rx_batch;
 int rx_batch_create(rx_handle* const* streams, int n_streams, rx_batch** out);
@@ -223,6 +241,8 @@ int rx_batch_push(rx_batch* b, const void* const* samples, const size_t* n_per_p
                   void* cuda_stream);
 int rx_batch_info(const rx_batch* b, int64_t* calls, int64_t* launches, int64_t* frames, double* wait_ms);
 void rx_batch_destroy(rx_batch* b);
+int rx_batch_set_graph(rx_batch* b, int on);
+int rx_batch_graph_info(const rx_batch* b, int64_t* replays, int64_t* nodes);
 
 /* Waits for queued work and frees everything the handle owns. */
 int rx_destroy(rx_handle* h);
@@ -356,7 +376,7 @@ int rx_fp32_peak(int device, double* tflops_fma, double* tflops_fma2);
  * completed the frame's input (its look-ahead included) to the frame's
  * bits being ready, host clock, queueing inside the server included.
  *
- * Batched rounds (batch = 1; max_streams <= RX_BATCH_MAX, one worker): the
+ * Batched rounds (batch = 1 or 2; max_streams <= RX_BATCH_MAX, one worker): the
  * worker keeps one rx_batch over the open streams and, each round, takes
  * the first queued block of every stream and pushes the device blocks of
  * one input type (dtype and on_device of the first such block) and the
@@ -366,9 +386,11 @@ int rx_fp32_peak(int device, double* tflops_fma, double* tflops_fma2);
  * stream's output ring is full) go through their stream's rx_push_block.
  * A stream's results are the same alone and in any mix, and equal to the
  * same blocks pushed through an rx_batch of its own.  When streams open
- * or close, the worker replaces the batch at its next round, waiting for
- * the old batch's work (rx_server_close returns once the stream is out of
- * the batch and freed).
+ * or close, the worker builds the new batch at its next round and frees
+ * the old one once its work is complete, without waiting for it
+ * (rx_server_close returns once the stream is out of the batch and the
+ * batch is freed).  batch = 2 switches each batch to graph replay
+ * (rx_batch_set_graph) when it is built.
  *
  * Each receiver runs four CUDA streams; set CUDA_DEVICE_MAX_CONNECTIONS=32
  * in the environment before the process creates its CUDA context, or the
@@ -384,7 +406,8 @@ typedef struct rx_server_config {
   int64_t bits_cap_bytes;   /* per-stream host buffer of decided bits not yet pulled (>= 4096);
                                when full the stream's blocks wait (backpressure) */
   int workers;              /* worker threads, 1..64; worker k serves the streams with id % workers == k */
-  int batch;                /* 0: every block through its stream's rx_push_block; 1: batched rounds (below) */
+  int batch;                /* 0: every block through its stream's rx_push_block; 1: batched rounds (below);
+                               2: batched rounds replaying one CUDA graph per round (rx_batch_set_graph) */
 } rx_server_config;
 
 typedef struct rx_server_stats_t {

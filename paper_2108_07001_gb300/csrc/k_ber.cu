@@ -587,20 +587,17 @@ bool ingest_pairs_ok(const RxDev& d, const void* src, int dtype, long long n, lo
 
 cudaError_t launch_ref_gen_batch(const BView& v, int blocks, int use_delay, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
-  ref_gen_batch_kernel<<<blocks, 128, 0, s>>>(v, use_delay);
-  return cudaGetLastError();
+  return launch_k(ref_gen_batch_kernel, blocks, 128, 0, s, v, use_delay);
 }
 
 cudaError_t launch_sync_batch(const BView& v, int blocks, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
-  sync_batch_kernel<<<blocks, 256, 0, s>>>(v);
-  return cudaGetLastError();
+  return launch_k(sync_batch_kernel, blocks, 256, 0, s, v);
 }
 
 cudaError_t launch_ber_batch(const BView& v, int blocks, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
-  ber_count_batch_kernel<<<blocks, 256, kSlipChunk * 8 * sizeof(unsigned), s>>>(v);
-  return cudaGetLastError();
+  return launch_k(ber_count_batch_kernel, blocks, 256, kSlipChunk * 8 * sizeof(unsigned), s, v);
 }
 
 cudaError_t launch_ingest_batch(const BIngest* ing, const BView& v, int blocks, cudaStream_t s) {

@@ -520,9 +520,9 @@ cudaError_t launch_bps_batch(const RxDev& d, const BView& v, int blocks, cudaStr
   const bool q16 = d.bps == 4;
 #define RX_BW(b, w)                                                                                 \
   if (d.B == b && d.W == w) {                                                                       \
-    if (q16) bps_batch_kernel<b, w, true><<<blocks, 32 * d.bps_nw, BpsSmem<b, w, true>::bytes(d.bps_nw), s>>>(v); \
-    else bps_batch_kernel<b, w, false><<<blocks, 32 * d.bps_nw, BpsSmem<b, w, false>::bytes(d.bps_nw), s>>>(v);   \
-    return cudaGetLastError();                                                                      \
+    if (q16)                                                                                        \
+      return launch_k(bps_batch_kernel<b, w, true>, blocks, 32 * d.bps_nw, BpsSmem<b, w, true>::bytes(d.bps_nw), s, v); \
+    return launch_k(bps_batch_kernel<b, w, false>, blocks, 32 * d.bps_nw, BpsSmem<b, w, false>::bytes(d.bps_nw), s, v); \
   }
   RX_BW(64, 16) RX_BW(32, 16) RX_BW(64, 32) RX_BW(32, 32) RX_BW(64, 8) RX_BW(32, 8)
   RX_BW(64, 12) RX_BW(32, 12) RX_BW(64, 24) RX_BW(32, 24)
@@ -532,14 +532,12 @@ cudaError_t launch_bps_batch(const RxDev& d, const BView& v, int blocks, cudaStr
 
 cudaError_t launch_demap_batch(const BView& v, int blocks, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
-  demap_batch_kernel<<<blocks, 128, 0, s>>>(v);
-  return cudaGetLastError();
+  return launch_k(demap_batch_kernel, blocks, 128, 0, s, v);
 }
 
 cudaError_t launch_scan_batch(const BView& v, int blocks, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
-  unwrap_scan_batch_kernel<<<blocks, 256, 0, s>>>(v);
-  return cudaGetLastError();
+  return launch_k(unwrap_scan_batch_kernel, blocks, 256, 0, s, v);
 }
 
 // The unwrap scan (one block per polarisation), then the demap.

@@ -333,9 +333,8 @@ int launch_bps2_batch(const RxDev& d, const BView& v, int blocks, cudaStream_t s
   if (d.bps_stride * (q16 ? 8 : 16) != d.B) return cudaErrorInvalidValue;
 #define RX_W(w)                                                                                 \
   if (d.W == w) {                                                                               \
-    if (q16) bps2_batch_kernel<w, true><<<blocks, 128, Bps2Smem<w, true>::BYTES, s>>>(v);       \
-    else bps2_batch_kernel<w, false><<<blocks, 128, Bps2Smem<w, false>::BYTES, s>>>(v);         \
-    return cudaGetLastError();                                                                  \
+    if (q16) return launch_k(bps2_batch_kernel<w, true>, blocks, 128, Bps2Smem<w, true>::BYTES, s, v); \
+    return launch_k(bps2_batch_kernel<w, false>, blocks, 128, Bps2Smem<w, false>::BYTES, s, v);        \
   }
   RX_W(16) RX_W(32) RX_W(8) RX_W(12) RX_W(24)
 #undef RX_W

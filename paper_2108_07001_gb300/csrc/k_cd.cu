@@ -724,9 +724,8 @@ int cd_grid_x(const RxDev& d, const FrameArgs& fa) {
 template <int N, int NT>
 static cudaError_t launch_cd_batch_n(const RxDev& d, const BView& v, int blocks, int pass, cudaStream_t s) {
   const size_t smem = sizeof(float2) * N;
-  if (d.storage == 2) cd_ols_batch_kernel<N, NT, 2><<<blocks, NT, smem, s>>>(v, pass);
-  else cd_ols_batch_kernel<N, NT, 1><<<blocks, NT, smem, s>>>(v, pass);
-  return cudaGetLastError();
+  if (d.storage == 2) return launch_k(cd_ols_batch_kernel<N, NT, 2>, blocks, NT, smem, s, v, pass);
+  return launch_k(cd_ols_batch_kernel<N, NT, 1>, blocks, NT, smem, s, v, pass);
 }
 
 // Every frame of v has d's FFT size and storage type.
@@ -740,9 +739,8 @@ cudaError_t launch_cd_batch(const RxDev& d, const BView& v, int blocks, int pass
     case 16384: return launch_cd_batch_n<16384, 1024>(d, v, blocks, pass, s);
     case 32768: {
       const size_t smem = sizeof(float2) * kCdN2;
-      if (d.storage == 2) cd_ols2_batch_kernel<2><<<blocks, kCdNT2, smem, s>>>(v, pass);
-      else cd_ols2_batch_kernel<1><<<blocks, kCdNT2, smem, s>>>(v, pass);
-      return cudaGetLastError();
+      if (d.storage == 2) return launch_k(cd_ols2_batch_kernel<2>, blocks, kCdNT2, smem, s, v, pass);
+      return launch_k(cd_ols2_batch_kernel<1>, blocks, kCdNT2, smem, s, v, pass);
     }
     default: return cudaErrorInvalidValue;
   }
@@ -750,8 +748,7 @@ cudaError_t launch_cd_batch(const RxDev& d, const BView& v, int blocks, int pass
 
 cudaError_t launch_est_batch(const BView& v, int blocks, int mode, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
-  est_batch_kernel<<<blocks, 1024, 0, s>>>(v, mode);
-  return cudaGetLastError();
+  return launch_k(est_batch_kernel, blocks, 1024, 0, s, v, mode);
 }
 
 }  // namespace rx

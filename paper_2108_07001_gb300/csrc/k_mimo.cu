@@ -529,23 +529,22 @@ int mimo_grid_x(const RxDev& d, const FrameArgs& fa) {
 cudaError_t launch_acquire_batch(const RxDev& d, const BView& v, int blocks, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
   switch (d.T) {
-#define RX_T(t) case t: acq_batch_kernel<t><<<blocks, 256, 0, s>>>(v); break;
+#define RX_T(t) case t: return launch_k(acq_batch_kernel<t>, blocks, 256, 0, s, v);
     RX_TAPS(RX_T)
 #undef RX_T
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_mimo_batch(const RxDev& d, const BView& v, int blocks, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
   switch (d.T) {
-#define RX_T(t) case t: mimo_batch_kernel<t><<<blocks, 32 * d.mimo_nw, d.mimo_nw * sizeof(ChainSmem<t>), s>>>(v); break;
+#define RX_T(t) \
+  case t: return launch_k(mimo_batch_kernel<t>, blocks, 32 * d.mimo_nw, d.mimo_nw * sizeof(ChainSmem<t>), s, v);
     RX_TAPS(RX_T)
 #undef RX_T
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace rx

@@ -12,6 +12,10 @@
 using namespace rx;
 using namespace rxrt;
 
+namespace rx {
+thread_local GraphRecorder* t_graph_rec = nullptr;
+}
+
 // ---- batched pushes of many streams (rx_batch_*) ---------------------------
 //
 // One call ingests every stream's block with one launch on the caller's
@@ -75,6 +79,21 @@ struct rx_batch {
   long long calls = 0, launches = 0, frames = 0;
   long long calls_done = 0;          // calls seen complete (batch_calls_done)
   double wait_s = 0.0;                // host time spent waiting for table slots
+  // graph replay (rx_batch_set_graph): one graph of every stage launch of
+  // max_ord ordinals, a kernel node per (ordinal, launch list)
+  struct GNode {
+    cudaGraphNode_t node = nullptr;
+    cudaKernelNodeParams p = {};      // as captured (argument values held by the graph)
+    int o = 0, list = 0;              // ordinal and launch-list slot
+    int grid = 0;                     // grid now set in the executable graph
+    bool on = true;                   // enabled in the executable graph
+  };
+  bool graph = false;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t gx = nullptr;
+  std::vector<GNode> gnodes;
+  void* gdev = nullptr;               // the graph's device table (table layout, ordinal part used)
+  long long replays = 0;
 };
 
 namespace {
@@ -217,18 +236,25 @@ int stage_of(int st) {
 }
 
 // The launches of one ordinal's lists that belong to pipeline stage ps.
-int launch_ordinal(rx_batch* b, char* dbase, char* hbase, int o, int ps, cudaStream_t cs) {
+// capture (a graph recorder set on this thread): every list gets a kernel
+// node (the smallest grid: the lists are empty until a call fills them),
+// kept for graph replay.
+int launch_ordinal(rx_batch* b, char* dbase, char* hbase, int o, int ps, cudaStream_t cs, bool capture = false) {
   BView v;
   v.frames = blob_frames(b, dbase, o);
   v.nmax = b->nh;
   for (int st = 0; st < BS_N; ++st) {
     if (stage_of(st) != ps) continue;
     for (int g = 0; g < b->slot0[st + 1] - b->slot0[st]; ++g) {
-      const int* L = blob_list(b, hbase, o, b->slot0[st] + g);
-      const int blocks = list_blocks(b, L);
-      if (blocks <= 0) continue;
-      v.list = blob_list(b, dbase, o, b->slot0[st] + g);
       const RxDev& d = b->h[b->rep[st][g]]->d;
+      int blocks;
+      if (capture) {
+        blocks = (st == BS_CD0 || st == BS_CD) && d.N == 32768 ? 2 : 1;  // 32768: clusters of two CTAs
+      } else {
+        blocks = list_blocks(b, blob_list(b, hbase, o, b->slot0[st] + g));
+        if (blocks <= 0) continue;
+      }
+      v.list = blob_list(b, dbase, o, b->slot0[st] + g);
       cudaError_t e = cudaSuccess;
       switch (st) {
         case BS_CD0: e = launch_cd_batch(d, v, blocks, 0, cs); break;
@@ -246,8 +272,103 @@ int launch_ordinal(rx_batch* b, char* dbase, char* hbase, int o, int ps, cudaStr
         case BS_BER: e = launch_ber_batch(v, blocks, cs); break;
       }
       if (e != cudaSuccess) return cuda_fail(e, "rx_batch_push: launch");
-      b->launches++;
+      if (!capture) {
+        b->launches++;
+        continue;
+      }
+      rx_batch::GNode n;
+      n.node = t_graph_rec->last;  // the node launch_k just added
+      n.o = o;
+      n.list = b->slot0[st] + g;
+      n.grid = blocks;
+      b->gnodes.push_back(n);
     }
+  }
+  return RX_OK;
+}
+
+void graph_free(rx_batch* b) {
+  if (b->gx) cudaGraphExecDestroy(b->gx);
+  if (b->g) cudaGraphDestroy(b->g);
+  b->gx = nullptr;
+  b->g = nullptr;
+  b->gnodes.clear();
+}
+
+// Builds the graph of every stage launch of max_ord ordinals, node by node
+// (no stream capture).  Each pipeline stage is a chain of nodes in launch
+// order, and the first node of stage ps at ordinal o also depends on the
+// stream mode's in-call waits: front on the MIMO kZSlots ordinals back,
+// every later stage on the ordinal's previous stage, mid and back on the
+// next stage two ordinals back.  The waits across calls are not needed:
+// replays run one after another on one stream.
+int graph_build(rx_batch* b) {
+  b->gnodes.clear();
+  cudaGraph_t g = nullptr;
+  RX_CK(cudaGraphCreate(&g, 0));
+  const int M = b->max_ord;
+  std::vector<cudaGraphNode_t> done(4 * (size_t)M, nullptr);  // last node of stage ps at ordinal o
+  cudaGraphNode_t tail[4] = {};
+  GraphRecorder rec;
+  rec.g = g;
+  char* gd = static_cast<char*>(b->gdev);
+  int rc = RX_OK;
+  t_graph_rec = &rec;
+  for (int o = 0; o < M && rc == RX_OK; ++o)
+    for (int ps = 0; ps < 4 && rc == RX_OK; ++ps) {
+      rec.ndeps = 0;
+      auto dep = [&](cudaGraphNode_t n) {
+        if (n) rec.deps[rec.ndeps++] = n;
+      };
+      dep(tail[ps]);
+      if (ps == 0) {
+        if (o >= kZSlots) dep(done[1 * (size_t)M + o - kZSlots]);
+      } else {
+        dep(done[(ps - 1) * (size_t)M + o]);
+        if (ps < 3 && o >= 2) dep(done[(ps + 1) * (size_t)M + o - 2]);
+      }
+      rec.last = nullptr;
+      rc = launch_ordinal(b, gd, nullptr, o, ps, nullptr, true);
+      if (rc == RX_OK && !rec.last) {  // a stage without launches keeps its place in the chain
+        const cudaError_t e = cudaGraphAddEmptyNode(&rec.last, g, rec.deps, (size_t)rec.ndeps);
+        if (e != cudaSuccess) rc = cuda_fail(e, "rx_batch_set_graph: empty node");
+      }
+      tail[ps] = done[ps * (size_t)M + o] = rec.last;
+    }
+  t_graph_rec = nullptr;
+  b->g = g;
+  if (rc == RX_OK) {
+    const cudaError_t e = cudaGraphInstantiate(&b->gx, g, 0);
+    if (e != cudaSuccess) rc = cuda_fail(e, "rx_batch_set_graph: instantiate");
+  }
+  for (size_t i = 0; i < b->gnodes.size() && rc == RX_OK; ++i) {
+    const cudaError_t e = cudaGraphKernelNodeGetParams(b->gnodes[i].node, &b->gnodes[i].p);
+    if (e != cudaSuccess) rc = cuda_fail(e, "rx_batch_set_graph: node parameters");
+  }
+  if (rc != RX_OK) {
+    cudaGetLastError();
+    graph_free(b);
+  }
+  return rc;
+}
+
+// Per call: grids of the nodes whose block count changed, and the nodes
+// without work (no frame in the list, ordinal beyond the call's) disabled.
+int graph_update(rx_batch* b, char* hb, int n_ord) {
+  for (rx_batch::GNode& n : b->gnodes) {
+    const int blocks = n.o < n_ord ? list_blocks(b, blob_list(b, hb, n.o, n.list)) : 0;
+    const bool on = blocks > 0;
+    if (on && blocks != n.grid) {
+      cudaKernelNodeParams p = n.p;
+      p.gridDim = dim3((unsigned)blocks, 1, 1);
+      RX_CK(cudaGraphExecKernelNodeSetParams(b->gx, n.node, &p));
+      n.grid = blocks;
+    }
+    if (on != n.on) {
+      RX_CK(cudaGraphNodeSetEnabled(b->gx, n.node, on ? 1u : 0u));
+      n.on = on;
+    }
+    if (on) b->launches++;
   }
   return RX_OK;
 }
@@ -265,6 +386,8 @@ void batch_free(rx_batch* b) {
   }
   if (b->ev_ing) cudaEventDestroy(b->ev_ing);
   for (cudaEvent_t e : b->ev_ring) cudaEventDestroy(e);
+  graph_free(b);
+  if (b->gdev) cudaFree(b->gdev);
 }
 
 }  // namespace
@@ -524,7 +647,14 @@ int rx_batch_push(rx_batch* b, const void* const* samples, const size_t* n_per_p
   cudaEvent_t ev_a = b->ev_ring[b->ev_i++ % b->ev_ring.size()];
   cudaEvent_t ev_b = b->ev_ring[b->ev_i++ % b->ev_ring.size()];
   RX_CK(cudaEventRecord(ev_a, cs));
-  RX_CK(cudaMemcpyAsync(db, hb, used, cudaMemcpyHostToDevice, cs));
+  if (b->graph) {  // the ordinal part to the graph's table (the previous replay is done with it)
+    RX_CK(cudaMemcpyAsync(db, hb, b->ing_bytes, cudaMemcpyHostToDevice, cs));
+    if (n_ord > 0)
+      RX_CK(cudaMemcpyAsync(static_cast<char*>(b->gdev) + b->ing_bytes, hb + b->ing_bytes,
+                            (size_t)n_ord * b->ord_bytes, cudaMemcpyHostToDevice, cs));
+  } else {
+    RX_CK(cudaMemcpyAsync(db, hb, used, cudaMemcpyHostToDevice, cs));
+  }
   {
     BView v;
     v.frames = nullptr;
@@ -537,8 +667,16 @@ int rx_batch_push(rx_batch* b, const void* const* samples, const size_t* n_per_p
     }
   }
   RX_CK(cudaEventRecord(b->ev_ing, cs));
+  cudaStream_t se = b->s_stage[3];
+  if (b->graph && n_ord > 0) {
+    int rc = graph_update(b, hb, n_ord);
+    if (rc != RX_OK) return rc;
+    RX_CK(cudaStreamWaitEvent(se, b->ev_ing, 0));
+    RX_CK(cudaGraphLaunch(b->gx, se));
+    b->replays++;
+  }
   constexpr int kQ = rx_batch::kQ;
-  for (int o = 0; o < n_ord; ++o) {
+  for (int o = 0; o < n_ord && !b->graph; ++o) {
     const long long q = b->q++;
     for (int ps = 0; ps < 4; ++ps) {
       cudaStream_t sp = b->s_stage[ps];
@@ -556,10 +694,10 @@ int rx_batch_push(rx_batch* b, const void* const* samples, const size_t* n_per_p
     b->ev_front_last = b->ev_stage[0][q % kQ];
   }
   // the call's end on the BER stream (after its last ordinal, or the ingest alone)
-  cudaStream_t se = b->s_stage[3];
   RX_CK(cudaStreamWaitEvent(se, b->ev_ing, 0));
   RX_CK(cudaEventRecord(ev_b, se));
   RX_CK(cudaEventRecord(b->ev_slot[sl], se));
+  if (b->graph) b->ev_front_last = ev_b;  // the next call's ingest and table copy wait for the whole replay
   b->calls++;
   for (int c = 0; c < nh; ++c) {
     rx_handle* h = b->h[c];
@@ -591,6 +729,32 @@ int rx_batch_info(const rx_batch* b, int64_t* calls, int64_t* launches, int64_t*
   if (launches) *launches = b->launches;
   if (frames) *frames = b->frames;
   if (wait_ms) *wait_ms = 1e3 * b->wait_s;
+  return RX_OK;
+}
+
+int rx_batch_set_graph(rx_batch* b, int on) {
+  if (!b) return fail(RX_EINVAL, "null batch");
+  if (b->calls > 0) return fail(RX_ESTATE, "rx_batch_set_graph: the batch has pushed");
+  RX_CK(cudaSetDevice(b->device));
+  if (!on) {
+    graph_free(b);
+    b->graph = false;
+    return RX_OK;
+  }
+  if (b->graph) return RX_OK;
+  cudaError_t e = cudaSuccess;
+  if (!b->gdev) e = cudaMalloc(&b->gdev, b->blob_bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "rx_batch_set_graph");
+  const int rc = graph_build(b);
+  if (rc != RX_OK) return rc;
+  b->graph = true;
+  return RX_OK;
+}
+
+int rx_batch_graph_info(const rx_batch* b, int64_t* replays, int64_t* nodes) {
+  if (!b) return fail(RX_EINVAL, "null batch");
+  if (replays) *replays = b->replays;
+  if (nodes) *nodes = b->graph ? (int64_t)b->gnodes.size() : 0;
   return RX_OK;
 }
 

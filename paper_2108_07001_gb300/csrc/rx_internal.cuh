@@ -13,6 +13,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <tuple>
+
 namespace rx {
 
 constexpr int kMaxTaps = 31;
@@ -266,6 +268,45 @@ __device__ __forceinline__ bool batch_block(const BView& v, int& frame, VBlock& 
   vb.y = r / vb.nx;
   frame = idx[lo];
   return true;
+}
+
+// Batched launches go through launch_k: a kernel launch on s, or, while a
+// graph recorder is set on the calling thread, a kernel node added to the
+// recorder's graph after the recorder's dependencies (the node becomes the
+// only dependency of the next one).  Building a graph this way involves
+// no stream capture, so other threads' device-wide calls are unaffected.
+struct GraphRecorder {
+  cudaGraph_t g = nullptr;
+  cudaGraphNode_t deps[4] = {};
+  int ndeps = 0;
+  cudaGraphNode_t last = nullptr;  // the node added last
+};
+extern thread_local GraphRecorder* t_graph_rec;
+
+template <typename... P, typename... A>
+cudaError_t launch_k(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, const A&... a) {
+  // the arguments converted to the kernel's parameter types, and their addresses
+  std::tuple<P...> vals(a...);
+  void* ptrs[sizeof...(P) > 0 ? sizeof...(P) : 1];
+  std::apply([&](auto&... v) {
+    int i = 0;
+    ((ptrs[i++] = static_cast<void*>(&v)), ...);
+  }, vals);
+  GraphRecorder* r = t_graph_rec;
+  if (!r) return cudaLaunchKernel(reinterpret_cast<const void*>(kern), grid, block, ptrs, smem, s);
+  cudaKernelNodeParams p = {};
+  p.func = reinterpret_cast<void*>(kern);
+  p.gridDim = grid;
+  p.blockDim = block;
+  p.sharedMemBytes = (unsigned)smem;
+  p.kernelParams = ptrs;
+  cudaGraphNode_t n = nullptr;
+  const cudaError_t e = cudaGraphAddKernelNode(&n, r->g, r->deps, (size_t)r->ndeps, &p);
+  if (e != cudaSuccess) return e;
+  r->deps[0] = n;
+  r->ndeps = 1;
+  r->last = n;
+  return cudaSuccess;
 }
 
 }  // namespace rx

@@ -360,8 +360,13 @@ int refresh_batch(rx_server* s) {
   if (!want.empty()) {
     std::vector<rx_handle*> hs;
     for (Stream* st : want) hs.push_back(st->h);
-    const int rc = rx_batch_create(hs.data(), (int)hs.size(), &nb);
+    int rc = rx_batch_create(hs.data(), (int)hs.size(), &nb);
     if (rc != RX_OK) return rc;
+    if (s->cfg.batch == 2) rc = rx_batch_set_graph(nb, 1);
+    if (rc != RX_OK) {
+      rx_batch_destroy(nb);
+      return rc;
+    }
   }
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -607,8 +612,8 @@ int rx_server_create(const rx_server_config* cfg, rx_server** out) {
   if (cfg->max_streams < 1 || cfg->max_streams > 1024) return err(RX_EINVAL, "max_streams must be in 1..1024");
   if (cfg->bits_cap_bytes < 4096) return err(RX_EINVAL, "bits_cap_bytes must be >= 4096");
   if (cfg->workers < 1 || cfg->workers > 64) return err(RX_EINVAL, "workers must be in 1..64");
-  if (cfg->batch != 0 && cfg->batch != 1) return err(RX_EINVAL, "batch must be 0 or 1");
-  if (cfg->batch && cfg->max_streams > RX_BATCH_MAX) return err(RX_EINVAL, "batch = 1 takes at most RX_BATCH_MAX streams");
+  if (cfg->batch < 0 || cfg->batch > 2) return err(RX_EINVAL, "batch must be 0, 1 or 2");
+  if (cfg->batch && cfg->max_streams > RX_BATCH_MAX) return err(RX_EINVAL, "batched rounds take at most RX_BATCH_MAX streams");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
     cudaGetLastError();

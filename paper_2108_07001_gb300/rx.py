@@ -32,6 +32,7 @@ EXPORTS = ["rx_config_default", "rx_create", "rx_push_block", "rx_pull_bits", "r
            "rx_destroy", "rx_reset", "rx_join", "rx_stage_times", "rx_last_error",
            "rx_frame_trace", "rx_get_taps", "rx_get_equalised", "rx_get_phase",
            "rx_decide_block_noalloc", "rx_batch_create", "rx_batch_push", "rx_batch_info", "rx_batch_destroy",
+           "rx_batch_set_graph", "rx_batch_graph_info",
            "rx_server_config_default", "rx_server_create", "rx_server_open", "rx_server_submit",
            "rx_server_end", "rx_server_sync", "rx_server_pull_bits", "rx_server_stream_stats",
            "rx_server_handle", "rx_server_close", "rx_server_stats", "rx_server_destroy",
@@ -258,6 +259,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                   ctypes.POINTER(ctypes.c_double)]
     lib.rx_batch_destroy.argtypes = [P]
     lib.rx_batch_destroy.restype = None
+    lib.rx_batch_set_graph.argtypes = [P, I]
+    lib.rx_batch_graph_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
     for name in ["rx_create", "rx_push_block", "rx_pull_bits", "rx_stats", "rx_destroy", "rx_reset",
                  "rx_join", "rx_stage_times", "rx_frame_trace", "rx_get_taps", "rx_get_equalised",
                  "rx_get_phase", "rx_decide_block_noalloc", "rx_server_create", "rx_server_open",
@@ -267,7 +270,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                  "rx_kk_batch_create", "rx_kk_batch_push",
                  "rx_kkrx_create", "rx_kkrx_push", "rx_kkrx_end", "rx_kkrx_equalised", "rx_kkrx_reset",
                  "rx_kkrx_batch_create", "rx_kkrx_batch_push", "rx_batch_create", "rx_batch_push",
-                 "rx_batch_info", "rx_fp32_peak"]:
+                 "rx_batch_info", "rx_batch_set_graph", "rx_batch_graph_info", "rx_fp32_peak", "rx_autotune_tiles"]:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -452,9 +455,10 @@ class _Borrowed(Receiver):
 
 class Batch:
     """Several receiver streams pushed together (rx_batch_*): one launch per
-    stage and frame ordinal over every stream's frames."""
+    stage and frame ordinal over every stream's frames; graph=True replays
+    one captured CUDA graph per call instead (rx_batch_set_graph)."""
 
-    def __init__(self, receivers: list):
+    def __init__(self, receivers: list, graph: bool = False):
         self.lib = load()
         self.receivers = list(receivers)
         n = len(self.receivers)
@@ -462,6 +466,12 @@ class Batch:
         b = ctypes.c_void_p()
         _check(self.lib.rx_batch_create(arr, n, ctypes.byref(b)))
         self.b = b
+        if graph:
+            try:
+                _check(self.lib.rx_batch_set_graph(self.b, 1))
+            except Exception:
+                self.close()
+                raise
         self._ptr = (ctypes.c_void_p * n)()
         self._n = (ctypes.c_size_t * n)()
 
@@ -482,6 +492,11 @@ class Batch:
         c, l, f, w = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
         _check(self.lib.rx_batch_info(self.b, ctypes.byref(c), ctypes.byref(l), ctypes.byref(f), ctypes.byref(w)))
         return {"calls": c.value, "launches": l.value, "frames": f.value, "wait_ms": w.value}
+
+    def graph_info(self) -> dict:
+        r, n = ctypes.c_int64(), ctypes.c_int64()
+        _check(self.lib.rx_batch_graph_info(self.b, ctypes.byref(r), ctypes.byref(n)))
+        return {"replays": r.value, "nodes": n.value}
 
     def close(self) -> None:
         if getattr(self, "b", None):

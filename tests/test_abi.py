@@ -154,6 +154,12 @@ def test_server_config_checks_without_device(lib):
     assert lib.rx_server_create(ctypes.byref(bad), ctypes.byref(s)) == rx.RX_EINVAL
     bad = rx.default_server_config(workers=0)
     assert lib.rx_server_create(ctypes.byref(bad), ctypes.byref(s)) == rx.RX_EINVAL
+    for b in (-1, 3):
+        bad = rx.default_server_config(batch=b)
+        assert lib.rx_server_create(ctypes.byref(bad), ctypes.byref(s)) == rx.RX_EINVAL
+        assert b"batch" in lib.rx_last_error()
+    bad = rx.default_server_config(batch=2, max_streams=257)
+    assert lib.rx_server_create(ctypes.byref(bad), ctypes.byref(s)) == rx.RX_EINVAL
     # no GPU in this container: a valid config stops at the device check
     rc = lib.rx_server_create(ctypes.byref(rx.default_server_config()), ctypes.byref(s))
     assert rc in (rx.RX_OK, rx.RX_EDEVICE)
@@ -302,6 +308,8 @@ def test_batch_argument_checks_without_device(lib):
     assert lib.rx_batch_create(arr, 257, ctypes.byref(b)) == rx.RX_EINVAL
     assert lib.rx_batch_push(None, None, None, rx.RX_C64, 1, None) == rx.RX_EINVAL
     assert lib.rx_batch_info(None, None, None, None, None) == rx.RX_EINVAL
+    assert lib.rx_batch_set_graph(None, 1) == rx.RX_EINVAL
+    assert lib.rx_batch_graph_info(None, None, None) == rx.RX_EINVAL
     lib.rx_batch_destroy(None)  # no-op
 
 

@@ -104,11 +104,14 @@ def plain(cases):
     return out
 
 
-def test_batch_equals_plain_pushes(cases):
+@pytest.mark.parametrize("graph", [False, True], ids=["streams", "graph_replay"])
+def test_batch_equals_plain_pushes(cases, graph):
     """Uneven rounds (some streams idle in a round), one stream's block of
     round 2 pushed through its own call in the middle of the batch's
     rounds, one stream ended through its own call, the others by the
-    batch: bits, equalised symbols and counters equal the plain pushes'."""
+    batch: bits, equalised symbols and counters equal the plain pushes',
+    with the stages launched on the batch's streams or replayed as one
+    captured graph per call."""
     import torch
     want = plain(cases)
     s = torch.cuda.current_stream().cuda_stream
@@ -116,7 +119,7 @@ def test_batch_equals_plain_pushes(cases):
     dev = [[torch.from_numpy(b).cuda() for b in blocks] for _, blocks, _ in cases]
     dummy = torch.zeros(16, dtype=torch.complex64, device="cuda")  # a non-null pointer for "nothing"
     n_rounds = max(len(b) for b in dev)
-    with rx.Batch(recs) as batch:
+    with rx.Batch(recs, graph=graph) as batch:
         for j in range(n_rounds):
             ptrs, ns = [], []
             for c, blocks in enumerate(dev):
@@ -136,6 +139,7 @@ def test_batch_equals_plain_pushes(cases):
         ptrs = [dummy.data_ptr()] + [None] * (len(recs) - 1)
         batch.push(ptrs, [0] * len(recs), rx.RX_C64, s)
         info = batch.info()
+        ginfo = batch.graph_info()
     got = [results(r, n_sym) for r, (_, _, n_sym) in zip(recs, cases)]
     for r in recs:
         r.close()
@@ -165,6 +169,31 @@ def test_batch_equals_plain_pushes(cases):
     assert 0 < info["frames"] <= frames
     assert info["calls"] == n_rounds + 1
     assert info["launches"] > 0
+    if graph:
+        assert ginfo["nodes"] > 0 and 0 < ginfo["replays"] <= info["calls"]
+    else:
+        assert ginfo == {"replays": 0, "nodes": 0}
+
+
+def test_graph_mode_is_set_before_the_first_push(cases):
+    """rx_batch_set_graph is refused once the batch has pushed, and a graph
+    batch can be switched back to the stream mode before it pushes."""
+    import torch
+    cfg, blocks, _ = cases[0]
+    r = rx.Receiver(**cfg)
+    lib = rx.load()
+    with rx.Batch([r], graph=True) as batch:
+        assert batch.graph_info()["nodes"] > 0
+        assert lib.rx_batch_set_graph(batch.b, 0) == rx.RX_OK
+        assert batch.graph_info()["nodes"] == 0
+        assert lib.rx_batch_set_graph(batch.b, 1) == rx.RX_OK
+        t = torch.from_numpy(blocks[0]).cuda() if blocks[0].shape[1] else torch.zeros((2, 1), dtype=torch.complex64,
+                                                                                      device="cuda")
+        batch.push([t.data_ptr()], [t.shape[1]], rx.RX_C64, torch.cuda.current_stream().cuda_stream)
+        assert lib.rx_batch_set_graph(batch.b, 0) == rx.RX_ESTATE
+        assert lib.rx_batch_set_graph(batch.b, 1) == rx.RX_ESTATE
+        torch.cuda.synchronize()
+    r.close()
 
 
 def test_refused_batch_push_changes_nothing(cases):

@@ -94,7 +94,8 @@ def cases():
     return {k: stream_case(k, 700 + i) for i, k in enumerate(CASES)}
 
 
-MODES = {"per_stream": dict(batch=0, device=False), "batched": dict(batch=1, device=True)}
+MODES = {"per_stream": dict(batch=0, device=False), "batched": dict(batch=1, device=True),
+         "batched_graph": dict(batch=2, device=True)}
 
 
 @pytest.fixture(scope="module", params=list(MODES))
@@ -110,7 +111,8 @@ def mixed(cases, mode):
 def test_each_stream_alone_equals_the_mix(cases, mixed, mode):
     """Bit for bit: decided bits, equalised symbols and counters of each
     stream served alone and served in the mix (per-stream pushes, and
-    batched rounds where the mix shares every launch)."""
+    batched rounds where the mix shares every launch, launched on streams
+    or replayed as a graph)."""
     mix, _ = mixed
     for k in CASES:
         alone, _ = serve({k: cases[k]}, **MODES[mode])
@@ -149,7 +151,7 @@ def test_served_stream_equals_a_plain_receiver(cases, mixed, mode):
 def test_batched_rounds_equal_a_batch_of_the_stream_alone(cases, mixed, mode):
     """A stream served in batched rounds gives bit for bit what its blocks
     pushed through an rx_batch of its own give (the same batched kernels)."""
-    if mode != "batched":
+    if not mode.startswith("batched"):
         pytest.skip("per-stream pushes: compared with a plain receiver above")
     import torch
     mix, sst = mixed
@@ -159,7 +161,7 @@ def test_batched_rounds_equal_a_batch_of_the_stream_alone(cases, mixed, mode):
     r = rx.Receiver(**cfg)
     s = torch.cuda.current_stream().cuda_stream
     dev = [torch.from_numpy(b).cuda() for b in blocks]
-    with rx.Batch([r]) as batch:
+    with rx.Batch([r], graph=mode == "batched_graph") as batch:
         for t in dev:
             batch.push([t.data_ptr()], [t.shape[1]], rx.RX_C64, s)
         batch.end(s)
@@ -189,7 +191,7 @@ def test_served_streams_match_the_oracle(cases, mixed):
 
 def test_server_statistics(cases, mixed, mode):
     mix, sst = mixed
-    assert (sst["batch_calls"] > 0) == (mode == "batched")
+    assert (sst["batch_calls"] > 0) == mode.startswith("batched")
     n_blocks = sum(len(cases[k][1]) for k in CASES)
     assert sst["blocks_submitted"] == sst["blocks_pushed"] == n_blocks
     assert sst["blocks_queued"] == 0 and sst["worker_error"] == 0
@@ -220,15 +222,17 @@ def test_streams_are_admitted_by_device_memory(cases):
         assert srv.stats()["mem_in_use_bytes"] == 2 * one
 
 
-def test_batched_server_admits_and_retires_streams_continuously(cases):
+@pytest.mark.parametrize("batch", [1, 2], ids=["streams", "graph_replay"])
+def test_batched_server_admits_and_retires_streams_continuously(cases, batch):
     """Batched rounds with streams opening and closing while others are on
     the GPU: a stream opened after the others have been running, and a
     stream closed (and its receiver freed) in the middle, each give what
-    they give served alone."""
+    they give served alone (every change of membership builds a new batch,
+    in graph replay a new graph)."""
     import torch
     keep = []
     got = {}
-    with rx.Server(max_streams=16, batch=1) as srv:
+    with rx.Server(max_streams=16, batch=batch) as srv:
         a = srv.open(**cases["qpsk1000"][0])
         b = srv.open(**cases["qam16"][0])
         qa, qb = list(cases["qpsk1000"][1]), list(cases["qam16"][1])
@@ -256,7 +260,7 @@ def test_batched_server_admits_and_retires_streams_continuously(cases):
             got[k] = srv.pull_bytes(sid)
         assert srv.stats()["batch_calls"] > 0
     for k in ("qpsk1000", "qam16", "qpsk2000"):
-        alone, _ = serve({k: cases[k]}, batch=1, device=True)
+        alone, _ = serve({k: cases[k]}, batch=batch, device=True)
         bits, nb = got[k]
         assert nb == alone[k][1] > 0, k
         assert np.array_equal(bits, alone[k][0]), k
