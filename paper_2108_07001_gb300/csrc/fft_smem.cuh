@@ -120,6 +120,17 @@ __device__ __forceinline__ float2 twiddle(const float2* tw_s, int m) {
   return cmul(tw_s[m / kTwSplit], tw_s[kTwSplit + (m % kTwSplit)]);
 }
 
+// Direct twiddle table of the radix-16 passes with sub-transform length 16
+// and 256 (the table option TP): a radix-16 pass at length NS multiplies
+// input r of butterfly j by exp(-+2 pi i r (j mod NS) / (16 NS)), which
+// does not depend on the transform size, so one table of 15 x 16 + 15 x
+// 256 entries, entry (r - 1) NS + (j mod NS) at offset 0 (NS = 16) or 240
+// (NS = 256), serves every size; each entry is one correctly rounded value
+// instead of a product of table values (kTwPass entries, rx_internal.cuh).
+
+template <int R, int NS>
+constexpr bool pass_table() { return R == 16 && (NS == 16 || NS == 256); }
+
 // Sub-transform length of the last pass (passes use radix 16 while at
 // least 16 remain) and its radix.
 template <int N>
@@ -132,9 +143,18 @@ constexpr int last_ns() {
 // Twiddles and R-point DFT of butterfly j of the pass with sub-transform
 // length NS: inputs v[r] = element j + r N/R, outputs v[r] = element
 // (j / NS) NS R + (j mod NS) + r NS.  Inverse passes conjugate the twiddles.
-template <int N, int R, int NS, bool INV>
-__device__ __forceinline__ void pass_butterfly(float2 (&v)[R], int j, const float2* __restrict__ tw, int tws) {
-  if (NS > 1) {
+template <int N, int R, int NS, bool INV, bool TP = false>
+__device__ __forceinline__ void pass_butterfly(float2 (&v)[R], int j, const float2* __restrict__ tw, int tws,
+                                               const float2* __restrict__ tp = nullptr) {
+  if constexpr (TP && pass_table<R, NS>()) {
+    const float2* t = tp + (NS == 16 ? 0 : 240) + (j & (NS - 1));
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      float2 w = t[(r - 1) * NS];
+      if (INV) w.y = -w.y;
+      v[r] = cmul(v[r], w);
+    }
+  } else if (NS > 1) {
     // w^r for r < R from the table entries w, w^2, w^4, w^8 (each power is
     // a product of at most four correctly rounded table values)
     constexpr int STEP = N / (NS * R);
@@ -161,8 +181,9 @@ __device__ __forceinline__ void pass_butterfly(float2 (&v)[R], int j, const floa
 }
 
 // One Stockham pass through shared memory.
-template <int N, int NT, int R, int NS, bool INV>
-__device__ __forceinline__ void fft_pass(float2* buf, const float2* __restrict__ tw, int tws) {
+template <int N, int NT, int R, int NS, bool INV, bool TP = false>
+__device__ __forceinline__ void fft_pass(float2* buf, const float2* __restrict__ tw, int tws,
+                                         const float2* __restrict__ tp = nullptr) {
   constexpr int NB = N / R;
   constexpr int PER = (NB + NT - 1) / NT;
   float2 v[PER][R];
@@ -179,7 +200,7 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* __restrict__
   for (int u = 0; u < PER; ++u) {
     const int j = threadIdx.x + u * NT;
     if ((NB % NT) == 0 || j < NB) {
-      pass_butterfly<N, R, NS, INV>(v[u], j, tw, tws);
+      pass_butterfly<N, R, NS, INV, TP>(v[u], j, tw, tws, tp);
       const int idxD = (j / NS) * NS * R + (j & (NS - 1));
 #pragma unroll
       for (int r = 0; r < R; ++r) buf[swz(idxD + r * NS)] = v[u][r];
@@ -189,13 +210,14 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* __restrict__
 }
 
 // The passes with sub-transform lengths NS, 16 NS, ... below NS_END.
-template <int N, int NT, int NS, int NS_END, bool INV>
-__device__ __forceinline__ void fft_passes(float2* buf, const float2* __restrict__ tw, int tws) {
+template <int N, int NT, int NS, int NS_END, bool INV, bool TP = false>
+__device__ __forceinline__ void fft_passes(float2* buf, const float2* __restrict__ tw, int tws,
+                                           const float2* __restrict__ tp = nullptr) {
   if constexpr (NS < NS_END) {
     constexpr int REM = N / NS;
     constexpr int R = REM >= 16 ? 16 : REM;
-    fft_pass<N, NT, R, NS, INV>(buf, tw, tws);
-    fft_passes<N, NT, NS * R, NS_END, INV>(buf, tw, tws);
+    fft_pass<N, NT, R, NS, INV, TP>(buf, tw, tws, tp);
+    fft_passes<N, NT, NS * R, NS_END, INV, TP>(buf, tw, tws, tp);
   }
 }
 

@@ -49,7 +49,11 @@ __device__ __forceinline__ void cd_ols_body(const RxDev& d, const FrameArgs& fa,
   extern __shared__ float2 buf[];
   __shared__ float scratch[NT / 32];
   __shared__ float2 tw_s[2 * kTwSplit];  // [hi | lo] two-level twiddle table
+  constexpr bool TP = N >= 8192;          // the direct pass table repays its copy from 8192 points on
+  __shared__ float2 tp_s[TP ? kTwPass : 1];
   for (int i = threadIdx.x; i < 2 * kTwSplit; i += NT) tw_s[i] = d.tw2[i];
+  if (TP)
+    for (int i = threadIdx.x; i < kTwPass; i += NT) tp_s[i] = d.tw2[4 * kTwSplit + i];
   const int pol = vb.y;
   const long long a = fa.s0 + (long long)vb.x * d.L;
   const long long zlen_f = 2LL * fa.Ff + 2 * d.c;
@@ -89,7 +93,7 @@ __device__ __forceinline__ void cd_ols_body(const RxDev& d, const FrameArgs& fa,
   constexpr int NSL = last_ns<N>();  // sub-transform length of the last pass
   constexpr int RL = N / NSL;        // its radix; its butterfly j (< NSL) outputs bins j + r NSL
   constexpr int PERL = (NSL + NT - 1) / NT;
-  fft_passes<N, NT, 16, NSL, false>(buf, tw_s, 1);
+  fft_passes<N, NT, 16, NSL, false, TP>(buf, tw_s, 1, tp_s);
 
   // last forward pass, filter and Godard sum over bin pairs (k, k + N/2) =
   // outputs (r, r + RL/2) of one butterfly
@@ -109,7 +113,7 @@ __device__ __forceinline__ void cd_ols_body(const RxDev& d, const FrameArgs& fa,
     for (int u = 0; u < PERL; ++u) {
       const int j = threadIdx.x + u * NT;
       if ((NSL % NT) == 0 || j < NSL) {
-        pass_butterfly<N, RL, NSL, false>(v[u], j, tw_s, 1);
+        pass_butterfly<N, RL, NSL, false, TP>(v[u], j, tw_s, 1, tp_s);
 #pragma unroll
         for (int r = 0; r < RL; ++r) v[u][r] = cmul(v[u][r], __ldg(&d.Hf[j + r * NSL]));
 #pragma unroll
@@ -134,7 +138,7 @@ __device__ __forceinline__ void cd_ols_body(const RxDev& d, const FrameArgs& fa,
     atomicAdd(&acc->C[1], (double)(sg * gi));
   }
   if (fa.est_only) return;
-  fft_passes<N, NT, 1, NSL, true>(buf, tw_s, 1);  // block_sum ended with a barrier
+  fft_passes<N, NT, 1, NSL, true, TP>(buf, tw_s, 1, tp_s);  // block_sum ended with a barrier
 
   // last inverse pass: output o = j + r NSL is window sample o; the kept
   // ones (h <= o < h + keep) go to z, their in-frame power is summed, and
@@ -161,7 +165,7 @@ __device__ __forceinline__ void cd_ols_body(const RxDev& d, const FrameArgs& fa,
     for (int u = 0; u < PERL; ++u) {
       const int j = threadIdx.x + u * NT;
       if ((NSL % NT) == 0 || j < NSL) {
-        pass_butterfly<N, RL, NSL, true>(v[u], j, tw_s, 1);
+        pass_butterfly<N, RL, NSL, true, TP>(v[u], j, tw_s, 1, tp_s);
 #pragma unroll
         for (int r = 0; r < RL; ++r) {
           const int o = j + r * NSL;
@@ -192,7 +196,7 @@ __device__ __forceinline__ void cd_ols_body(const RxDev& d, const FrameArgs& fa,
   constexpr int NSL2 = last_ns<N2>();
   constexpr int RL2 = N2 / NSL2;
   constexpr int PERL2 = (NSL2 + NT - 1) / NT;
-  fft_passes<N2, NT, 1, NSL2, false>(buf, tw_s, 2);
+  fft_passes<N2, NT, 1, NSL2, false, TP>(buf, tw_s, 2, tp_s);
   double* psd = d.psd + (long long)fa.acc_slot * N2;
   {
     float2 v[PERL2][RL2];
@@ -208,7 +212,7 @@ __device__ __forceinline__ void cd_ols_body(const RxDev& d, const FrameArgs& fa,
     for (int u = 0; u < PERL2; ++u) {
       const int j = threadIdx.x + u * NT;
       if ((NSL2 % NT) == 0 || j < NSL2) {
-        pass_butterfly<N2, RL2, NSL2, false>(v[u], j, tw_s, 2);
+        pass_butterfly<N2, RL2, NSL2, false, TP>(v[u], j, tw_s, 2, tp_s);
 #pragma unroll
         for (int r = 0; r < RL2; ++r)
           atomicAdd(&psd[j + r * NSL2], (double)(v[u][r].x * v[u][r].x + v[u][r].y * v[u][r].y));
@@ -264,6 +268,7 @@ __device__ __forceinline__ void cd_ols2_body(const RxDev& d, const FrameArgs& fa
   __shared__ float scratch[NT / 32];
   __shared__ float2 tw_s[2 * kTwSplit];  // twiddles of the 16384-point half-transforms
   __shared__ float2 tn_s[2 * kTwSplit];  // W_32768^m, m < 16384
+  __shared__ float2 tp_s[kTwPass];       // direct pass table
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   float2* peer = cl.map_shared_rank(buf, rank ^ 1);
@@ -271,6 +276,7 @@ __device__ __forceinline__ void cd_ols2_body(const RxDev& d, const FrameArgs& fa
     tn_s[i] = d.tw2[i];
     tw_s[i] = d.tw2[2 * kTwSplit + i];
   }
+  for (int i = threadIdx.x; i < kTwPass; i += NT) tp_s[i] = d.tw2[4 * kTwSplit + i];
   __syncthreads();
   const int pol = vb.y;
   const long long a = fa.s0 + (long long)(vb.x >> 1) * d.L;
@@ -306,7 +312,7 @@ __device__ __forceinline__ void cd_ols2_body(const RxDev& d, const FrameArgs& fa
   constexpr int NSL = last_ns<N2>();
   constexpr int RL = N2 / NSL;
   constexpr int PERL = (NSL + NT - 1) / NT;
-  fft_passes<N2, NT, 16, NSL, false>(buf, tw_s, 1);
+  fft_passes<N2, NT, 16, NSL, false, true>(buf, tw_s, 1, tp_s);
 
   // last forward pass, filter (global bin 2k + rank) and Godard sum over
   // the local pairs (k, k + N2/2) = global (k, k + N/2)
@@ -326,7 +332,7 @@ __device__ __forceinline__ void cd_ols2_body(const RxDev& d, const FrameArgs& fa
     for (int u = 0; u < PERL; ++u) {
       const int j = threadIdx.x + u * NT;
       if ((NSL % NT) == 0 || j < NSL) {
-        pass_butterfly<N2, RL, NSL, false>(v[u], j, tw_s, 1);
+        pass_butterfly<N2, RL, NSL, false, true>(v[u], j, tw_s, 1, tp_s);
 #pragma unroll
         for (int r = 0; r < RL; ++r) v[u][r] = cmul(v[u][r], __ldg(&d.Hf[2 * (j + r * NSL) + rank]));
 #pragma unroll
@@ -351,7 +357,7 @@ __device__ __forceinline__ void cd_ols2_body(const RxDev& d, const FrameArgs& fa
     atomicAdd(&acc->C[1], (double)(sg * gi));
   }
   if (fa.est_only) return;  // both CTAs: no shared memory of the peer was touched
-  fft_passes<N2, NT, 1, NSL, true>(buf, tw_s, 1);
+  fft_passes<N2, NT, 1, NSL, true, true>(buf, tw_s, 1, tp_s);
   {  // last inverse pass: the half-transform E (rank 0) or O (rank 1) stays in place
     float2 v[PERL][RL];
 #pragma unroll
@@ -367,7 +373,7 @@ __device__ __forceinline__ void cd_ols2_body(const RxDev& d, const FrameArgs& fa
     for (int u = 0; u < PERL; ++u) {
       const int j = threadIdx.x + u * NT;
       if ((NSL % NT) == 0 || j < NSL) {
-        pass_butterfly<N2, RL, NSL, true>(v[u], j, tw_s, 1);
+        pass_butterfly<N2, RL, NSL, true, true>(v[u], j, tw_s, 1, tp_s);
 #pragma unroll
         for (int r = 0; r < RL; ++r) buf[swz(j + r * NSL)] = v[u][r];
       }
@@ -435,7 +441,7 @@ __device__ __forceinline__ void cd_ols2_body(const RxDev& d, const FrameArgs& fa
   constexpr int NSP = last_ns<NP>();
   constexpr int RP = NP / NSP;
   constexpr int PERP = (NSP + NT - 1) / NT;
-  fft_passes<NP, NT, 1, NSP, false>(buf, tw_s, 2);
+  fft_passes<NP, NT, 1, NSP, false, true>(buf, tw_s, 2, tp_s);
   double* psd = d.psd + (long long)fa.acc_slot * (d.N / 2);
   {
     float2 v[PERP][RP];
@@ -451,7 +457,7 @@ __device__ __forceinline__ void cd_ols2_body(const RxDev& d, const FrameArgs& fa
     for (int u = 0; u < PERP; ++u) {
       const int j = threadIdx.x + u * NT;
       if ((NSP % NT) == 0 || j < NSP) {
-        pass_butterfly<NP, RP, NSP, false>(v[u], j, tw_s, 2);
+        pass_butterfly<NP, RP, NSP, false, true>(v[u], j, tw_s, 2, tp_s);
 #pragma unroll
         for (int r = 0; r < RP; ++r)
           atomicAdd(&psd[2 * (j + r * NSP) + rank], (double)(v[u][r].x * v[u][r].x + v[u][r].y * v[u][r].y));

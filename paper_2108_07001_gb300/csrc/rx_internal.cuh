@@ -23,6 +23,7 @@ constexpr int kRun = 256;             // BPS run / demap tile length (symbols)
 constexpr int kMaxTrace = 4096;       // per-frame estimate records kept
 constexpr int kYHist = 64;            // equalised-symbol history kept before each frame (>= 2W)
 constexpr int kFoeMinSyms = 4096;     // shorter frames reuse the previous FO estimate
+constexpr int kTwPass = 15 * 16 + 15 * 256;  // direct twiddles of the radix-16 passes (fft_smem.cuh)
 
 // Per-frame estimates written by the estimator kernel (also the trace).
 struct FrameRec {
@@ -86,7 +87,8 @@ struct RxDev {
   float2* Hs;                  // static CD x RRC response, 1/N folded in
   float2* Hf;                  // Hs x timing phase of the coming pass
   float2* tw;                  // tw[k] = exp(-2 pi i k / N)
-  float2* tw2;                 // [256]: exp(-2 pi i 128 h / N) for h < 128, then exp(-2 pi i l / N), l < 128
+  float2* tw2;                 // [512 + kTwPass]: two-level tables of N and N/2 (each exp(-2 pi i 128 h / Nt),
+                               // h < 128, then exp(-2 pi i l / Nt), l < 128), then the direct pass table
   float2* z;
   float2* rot_hi;              // [ceil(zlen/1024)]  gain * exp(-j(theta + w (hi*1024 - c)))
   float2* rot_lo;              // [1024]             exp(-j w lo)

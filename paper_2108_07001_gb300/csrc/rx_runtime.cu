@@ -735,7 +735,7 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
   RX_AL(d.Hs, N);
   RX_AL(d.Hf, N);
   RX_AL(d.tw, N);
-  RX_AL(d.tw2, 512);  // [N table | N/2 table]: the 32768-point form's half-transforms use the second
+  RX_AL(d.tw2, 512 + kTwPass);  // [N table | N/2 table | pass table]: the 32768-point form's halves use the second
   RX_AL(d.z, (long long)kZSlots * 2 * d.zlen);
   RX_AL(d.rot_hi, (long long)kZSlots * (d.zlen / kRotLo + 2));
   RX_AL(d.rot_lo, (long long)kZSlots * kRotLo);
@@ -786,7 +786,7 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
     cudaMemcpy(d.Hs, Hs.data(), N * sizeof(float2), cudaMemcpyHostToDevice);
     cudaMemcpy(d.Hf, Hs.data(), N * sizeof(float2), cudaMemcpyHostToDevice);
     cudaMemcpy(d.tw, tw.data(), N * sizeof(float2), cudaMemcpyHostToDevice);
-    std::vector<float2> tw2(512);
+    std::vector<float2> tw2(512 + kTwPass);
     for (int t = 0; t < 2; ++t) {
       const double Nt = (double)N / (1 << t);
       for (int i = 0; i < 128; ++i) {
@@ -795,7 +795,17 @@ int rx_create(const rx_config* cfg, rx_handle** out) {
         tw2[256 * t + 128 + i] = make_float2((float)std::cos(al), (float)std::sin(al));
       }
     }
-    cudaMemcpy(d.tw2, tw2.data(), 512 * sizeof(float2), cudaMemcpyHostToDevice);
+    // the radix-16 passes at sub-transform length ns = 16, 256: entry
+    // (r - 1) ns + m = exp(-2 pi i r m / (16 ns)), r = 1..15, m < ns
+    for (int ns : {16, 256}) {
+      float2* t = tw2.data() + 512 + (ns == 16 ? 0 : 15 * 16);
+      for (int r = 1; r < 16; ++r)
+        for (int m = 0; m < ns; ++m) {
+          const double a = -2.0 * M_PI * (double)(r * m) / (16.0 * ns);
+          t[(r - 1) * ns + m] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+    }
+    cudaMemcpy(d.tw2, tw2.data(), tw2.size() * sizeof(float2), cudaMemcpyHostToDevice);
   }
   // PRBS jump matrices A^(2^i): A shifts the window down one bit and sets
   // bit 30 = bit 3 ^ bit 0.
