@@ -63,7 +63,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -384,6 +384,8 @@ def finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, o
            gpu_launches, clocks, host0, host1, gen_s, e2e):
     cpu = cpu_baseline(args.bps_coarse_stride, wl["name"]) if args.cpu_baseline else None
     batched = batched_fp16_summary(measured_peaks().get("hbm_gbs")) if args.batched else None
+    qam16 = qam16_summary() if args.batched else None
+    serving = serving_summary() if args.batched else None
     line = {
         "metric": "gsamples_per_s", "value": round(value, 3), "unit": "Gsamples/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
@@ -405,7 +407,7 @@ def finish(args, wl, cfg, r, value, ms_step, n_sym, gbps, stats, roof, stages, o
         "roofline": roof, "stages": stages, "other_stage_ms": other_ms,
         "stage_timing": "per-stage CUDA events on a second, profiled handle over the same timed protocol",
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
-        "batched_fp16": batched, "dram": chain_dram(n_sym, cfg.modulation, ms_step, measured_peaks().get("hbm_gbs")),
+        "batched_fp16": batched, "qam16_fp16": qam16, "serving": serving, "dram": chain_dram(n_sym, cfg.modulation, ms_step, measured_peaks().get("hbm_gbs")),
         "host_launch_s_per_step": round((host1 - host0) / args.steps, 4), "sim_seconds": round(gen_s, 1),
     }
     r.close()
@@ -487,7 +489,9 @@ REFERENCE_STEP_SYMS = 1 << 18
 
 def run_reference(args):
     wl = workload()
-    n_sym = REFERENCE_STEP_SYMS
+    # ~1.6 s of one core per 2^18-symbol step: smaller samples for long runs,
+    # so that the whole run stays within a few minutes
+    n_sym = REFERENCE_STEP_SYMS if args.steps + args.warmup <= 40 else REFERENCE_STEP_SYMS // 4
     times = oracle_times(n_sym, args.warmup + args.steps)[args.warmup:]
     t = sum(times) / len(times)
     v = 4 * n_sym / t / 1e9
@@ -1393,15 +1397,48 @@ def batched_fp16_summary(hbm_peak):
     return out
 
 
+def qam16_summary():
+    """The DP-16QAM workload (32 GBd, 5,000 km, 18 dB, 2^22 symbols, 25 taps,
+    32 angles) in the default line: FP16 and FP32 sample storage (FP32
+    arithmetic), throughput, BER and the EVM penalty of each over the FP64
+    oracle on the same samples (run_qam16, fewer timed steps)."""
+    r = run_qam16(argparse.Namespace(symbols=0, steps=5, warmup=2))
+    f16, f32, o = r["forms"]["fp16_storage"], r["forms"]["fp32_storage"], r["oracle"]
+    return {"workload": r["config"]["workload"], "symbols_per_pol": r["config"]["symbols_per_pol"],
+            "fp16_storage_gsamples_s": f16["value"], "fp32_storage_gsamples_s": f32["value"],
+            "ber_fp16_storage": f16["ber"], "ber_fp32_storage": f32["ber"], "ber_oracle": o["ber"],
+            "evm_penalty_db_fp16_storage": f16["evm_penalty_db"], "evm_penalty_db_fp32_storage": f32["evm_penalty_db"],
+            "cycle_slips": f16["cycle_slips"] + f32["cycle_slips"], "oracle_cores": o["cores"],
+            "oracle_seconds": o["seconds"]}
+
+
+def serving_summary():
+    """The serving workload (16 mixed QPSK/16QAM streams, 28-64 GBd, 10,000
+    km, blocks of 2^16-2^20 symbols) in the default line: capacity, then
+    Poisson arrivals at 80 % of it, per-stream pushes with FP32 and FP16
+    storage and batched rounds with FP16 storage (run_serving)."""
+    r = run_serving(argparse.Namespace(symbols=0))
+    out = {"streams": r["config"]["streams"], "symbols_per_pol_per_stream": r["config"]["symbols_per_pol_per_stream"],
+           "arrivals": r["config"]["arrivals"]}
+    for form in ("fp32_storage", "fp16_storage", "batched_fp16_storage"):
+        f = r["forms"][form]
+        out[form] = {k: f[k] for k in ("capacity_gsamples_s", "sustained_gsamples_s", "sustained_decoded_gbps",
+                                       "latency_p50_ms", "latency_p99_ms", "ber_max", "synced_streams",
+                                       "cycle_slips")}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)  # ~0.74 s timed on the stream workload
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
-                    help="stream workload: leave out the batched_fp16 sub-record (64 streams, batched serving)")
+                    help="stream workload: leave out the sub-records of the other workloads (batched_fp16: 64 "
+                         "streams, batched serving; qam16_fp16: DP-16QAM storage forms against the oracle; "
+                         "serving: 16 streams under Poisson arrivals)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--symbols", type=int, default=0, help="stream length per pol (default: the workload's 2^24)")
     ap.add_argument("--oracle-child", nargs=4, help=argparse.SUPPRESS)
