@@ -67,6 +67,7 @@ __device__ __forceinline__ void cd_ols_body(const RxDev& d, const FrameArgs& fa,
 
   // first forward pass (radix 16, no twiddles) straight from the ring:
   // butterfly j takes window samples j + r N/16
+  const bool interior = lo >= 0 && lo + N <= fa.n_valid && r0 + N <= d.ring_cap;
   {
     constexpr int NB = N / 16;
     constexpr int PER = (NB + NT - 1) / NT;
@@ -75,13 +76,19 @@ __device__ __forceinline__ void cd_ols_body(const RxDev& d, const FrameArgs& fa,
       const int j = threadIdx.x + u * NT;
       if ((NB % NT) == 0 || j < NB) {
         float2 v[16];
+        if (interior) {  // the window lies inside the stream and does not wrap the ring
+          const long long b0 = rbase + r0 + j;
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
-          const int i = j + r * NB;
-          const long long n = lo + i;
-          long long slot = r0 + i;
-          if (slot >= d.ring_cap) slot -= d.ring_cap;
-          v[r] = (n >= 0 && n < fa.n_valid) ? load_sample(d.ring, STOR, rbase + slot) : make_float2(0.f, 0.f);
+          for (int r = 0; r < 16; ++r) v[r] = load_sample(d.ring, STOR, b0 + r * NB);
+        } else {
+#pragma unroll
+          for (int r = 0; r < 16; ++r) {
+            const int i = j + r * NB;
+            const long long n = lo + i;
+            long long slot = r0 + i;
+            if (slot >= d.ring_cap) slot -= d.ring_cap;
+            v[r] = (n >= 0 && n < fa.n_valid) ? load_sample(d.ring, STOR, rbase + slot) : make_float2(0.f, 0.f);
+          }
         }
         dft<16, false>(v);
 #pragma unroll
@@ -286,7 +293,10 @@ __device__ __forceinline__ void cd_ols2_body(const RxDev& d, const FrameArgs& fa
   const long long rbase = (long long)pol * d.ring_cap;
   long long r0 = lo % d.ring_cap;
   if (r0 < 0) r0 += d.ring_cap;
+  // the window lies inside the stream and does not wrap the ring: plain loads
+  const bool interior = lo >= 0 && lo + 2 * N2 <= fa.n_valid && r0 + 2 * N2 <= d.ring_cap;
   auto sample = [&](int i) -> float2 {  // window sample i (zero outside the stream)
+    if (interior) return load_sample(d.ring, STOR, rbase + r0 + i);
     const long long n = lo + i;
     long long slot = r0 + i;
     if (slot >= d.ring_cap) slot -= d.ring_cap;
