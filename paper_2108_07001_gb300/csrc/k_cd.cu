@@ -156,6 +156,7 @@ __device__ __forceinline__ void cd_ols_body(const RxDev& d, const FrameArgs& fa,
   const long long e0 = lo_n + (lo_n & 1);
   const int cnt = hi_n > e0 ? (int)((hi_n - e0 + 1) / 2) : 0;
   const int off = d.h + (int)(e0 - a);  // window index of sample e0
+  const bool inframe = a >= fa.f0 && a + keep <= fa.f1;  // every kept sample is in the frame
   float pw = 0.f;
   {
     float2 v[PERL][RL];
@@ -179,8 +180,13 @@ __device__ __forceinline__ void cd_ols_body(const RxDev& d, const FrameArgs& fa,
           const float2 x = v[u][r];
           if (o >= d.h && o < d.h + keep) {
             zp[o - d.h] = x;
-            const long long n = a + (o - d.h);
-            if (n >= fa.f0 && n < fa.f1) pw += x.x * x.x + x.y * x.y;
+            const float p2 = fmaf(x.x, x.x, x.y * x.y);  // the same rounding on both paths
+            if (inframe) {
+              pw += p2;
+            } else {
+              const long long n = a + (o - d.h);
+              if (n >= fa.f0 && n < fa.f1) pw += p2;
+            }
             const int q = o - off;
             if (q >= 0 && (q & 1) == 0 && (q >> 1) < cnt) {
               const float2 x2 = make_float2(x.x * x.x - x.y * x.y, 2.f * x.x * x.y);
